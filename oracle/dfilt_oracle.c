@@ -1,0 +1,199 @@
+/*
+ * FP64 CPU oracle for batched direct-form IIR filters and their closed-form
+ * gradients.  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library; the product path
+ * (the CUDA library and its Python binding) never does, and shares no code,
+ * header, table or constant with it.
+ *
+ * Notation (paper, Eq. rtf and Sec. 2): per channel
+ *     H(z) = (b_0 + b_1 z^-1 + ... + b_N z^-N) / (1 + a_1 z^-1 + ... + a_M z^-M)
+ * with b zero-padded to order M (the paper pads the shorter polynomial, Sec. 2).
+ * The coefficient array `a` holds a_1..a_M (a_0 = 1 is implicit), so a[k-1] is a_k.
+ *
+ * Initial state zi[0..M) follows the transposed direct form II (TDF-II, the form
+ * the paper names for SciPy/MATLAB in Sec. 2): zi is the TDF-II state vector at
+ * n = 0.  Equivalently zi[k] is added to the all-pole input at time k (k < M).
+ *
+ * Every function here is the plain definition, looped in the paper's order, in
+ * double precision.  Nothing is blocked, fused or reordered.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* b_k with the zero padding of Sec. 2 (k > N gives 0). */
+static double bcoef(const double *b, int N, int k) { return k <= N ? b[k] : 0.0; }
+
+/*
+ * Forward, TDF-II state recursion (Sec. 2: state-space form with A replaced by
+ * its transpose and B, C swapped, i.e. Eqs. ss_recursion/ss_output for TDF):
+ *     y[n]   = b_0 x[n] + s_0
+ *     s_k   <- s_{k+1} + b_{k+1} x[n] - a_{k+1} y[n]     (k = 0..M-1, s_M = 0)
+ * starting from s = zi.
+ */
+static void fwd_tdf2(const double *x, const double *b, const double *a, const double *zi,
+                     double *y, int64_t T, int N, int M, double *s)
+{
+    for (int k = 0; k < M; ++k) s[k] = zi ? zi[k] : 0.0;
+    for (int64_t n = 0; n < T; ++n) {
+        const double xn = x[n];
+        const double yn = b[0] * xn + s[0];
+        for (int k = 0; k < M; ++k) {
+            const double nxt = (k + 1 < M) ? s[k + 1] : 0.0;
+            s[k] = nxt + bcoef(b, N, k + 1) * xn - a[k] * yn;
+        }
+        y[n] = yn;
+    }
+}
+
+/*
+ * Forward, the same filter written as the difference equation of Eq. rtf with
+ * the initial state injected into the recursion input:
+ *     w[n] = sum_{k=0..N} b_k x[n-k] + zi[n] [n < M]
+ *     y[n] = w[n] - sum_{k=1..M} a_k y[n-k]
+ * (x, y are zero at negative times).  A second formulation used to cross-check
+ * the state recursion above.
+ */
+static void fwd_injection(const double *x, const double *b, const double *a, const double *zi,
+                          double *y, int64_t T, int N, int M)
+{
+    for (int64_t n = 0; n < T; ++n) {
+        double w = 0.0;
+        for (int k = 0; k <= N; ++k)
+            if (n - k >= 0) w += b[k] * x[n - k];
+        if (zi && n < M) w += zi[n];
+        double acc = w;
+        for (int k = 1; k <= M; ++k)
+            if (n - k >= 0) acc -= a[k - 1] * y[n - k];
+        y[n] = acc;
+    }
+}
+
+/*
+ * Backward: the reverse-time adjoint recursion (Eqs. dLdz, dLdx, dLdvBA and the
+ * boundary condition of App. A, dL/dz(N-1) = 0), in scalar difference form:
+ *     u[n]       = g[n] - sum_{k=1..M} a_k u[n+k],        u[n >= T] = 0
+ *     grad_x[n]  = sum_{k=0..N} b_k u[n+k]
+ *     grad_b[k]  = sum_{n=k..T-1} u[n] x[n-k]             (k = 0..N)
+ *     grad_a[k]  = -sum_{n=k..T-1} u[n] y[n-k]            (k = 1..M)
+ *     grad_zi[k] = u[k]                                   (k = 0..M-1; 0 if k >= T)
+ * u is the gradient with respect to the all-pole input; grad_zi is the gradient
+ * with respect to the initial state (App. A, dL/dv(0)).
+ * Any output pointer may be NULL (not requested).  u is caller scratch [T].
+ */
+static void bwd_channel(const double *g, const double *x, const double *y,
+                        const double *b, const double *a,
+                        double *gx, double *gb, double *ga, double *gzi,
+                        int64_t T, int N, int M, double *u)
+{
+    for (int64_t n = T - 1; n >= 0; --n) {
+        double acc = g[n];
+        for (int k = 1; k <= M; ++k)
+            if (n + k < T) acc -= a[k - 1] * u[n + k];
+        u[n] = acc;
+    }
+    if (gx)
+        for (int64_t n = 0; n < T; ++n) {
+            double acc = 0.0;
+            for (int k = 0; k <= N; ++k)
+                if (n + k < T) acc += b[k] * u[n + k];
+            gx[n] = acc;
+        }
+    if (gb)
+        for (int k = 0; k <= N; ++k) {
+            double acc = 0.0;
+            for (int64_t n = k; n < T; ++n) acc += u[n] * x[n - k];
+            gb[k] = acc;
+        }
+    if (ga)
+        for (int k = 1; k <= M; ++k) {
+            double acc = 0.0;
+            for (int64_t n = k; n < T; ++n) acc += u[n] * y[n - k];
+            ga[k - 1] = -acc;
+        }
+    if (gzi)
+        for (int k = 0; k < M; ++k) gzi[k] = (k < T) ? u[k] : 0.0;
+}
+
+static int pick_threads(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/*
+ * Ragged batch drivers.  Channel i owns samples [offs[i], offs[i+1]) of the packed
+ * signal arrays, has orders Ms[i], Ns[i] (1 <= Ms[i] <= Mmax, 0 <= Ns[i] <= Ms[i]) and
+ * coefficient rows b + i*(Nmax+1), a + i*Mmax, zi + i*Mmax (zi may be NULL).
+ * `form` selects the forward formulation: 0 = TDF-II state, 1 = injection.
+ * Returns 0, or -1 on an allocation failure.
+ */
+int oracle_forward_ragged(const double *x, const int64_t *offs, const int *Ms, const int *Ns,
+                          const double *b, const double *a, const double *zi, double *y,
+                          int64_t B, int Nmax, int Mmax, int form, int nthreads)
+{
+    int fail = 0;
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        double *s = (double *)malloc(sizeof(double) * (size_t)(Mmax > 0 ? Mmax : 1));
+        if (!s) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < B; ++i) {
+            if (!s) continue;
+            const int64_t o = offs[i], T = offs[i + 1] - offs[i];
+            const double *zii = zi ? zi + i * Mmax : NULL;
+            if (form == 0)
+                fwd_tdf2(x + o, b + i * (Nmax + 1), a + i * Mmax, zii, y + o, T, Ns[i], Ms[i], s);
+            else
+                fwd_injection(x + o, b + i * (Nmax + 1), a + i * Mmax, zii, y + o, T, Ns[i], Ms[i]);
+        }
+        free(s);
+    }
+    return fail ? -1 : 0;
+}
+
+int oracle_backward_ragged(const double *g, const double *x, const double *y,
+                           const int64_t *offs, const int *Ms, const int *Ns,
+                           const double *b, const double *a,
+                           double *gx, double *gb, double *ga, double *gzi,
+                           int64_t B, int Nmax, int Mmax, int nthreads)
+{
+    int fail = 0;
+    int64_t Tmax = 0;
+    for (int64_t i = 0; i < B; ++i)
+        if (offs[i + 1] - offs[i] > Tmax) Tmax = offs[i + 1] - offs[i];
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        double *u = (double *)malloc(sizeof(double) * (size_t)(Tmax > 0 ? Tmax : 1));
+        if (!u) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < B; ++i) {
+            if (!u) continue;
+            const int64_t o = offs[i], T = offs[i + 1] - offs[i];
+            bwd_channel(g + o, x + o, y + o, b + i * (Nmax + 1), a + i * Mmax,
+                        gx ? gx + o : NULL, gb ? gb + i * (Nmax + 1) : NULL,
+                        ga ? ga + i * Mmax : NULL, gzi ? gzi + i * Mmax : NULL,
+                        T, Ns[i], Ms[i], u);
+        }
+        free(u);
+    }
+    return fail ? -1 : 0;
+}
+
+/* Threads an OpenMP region actually gets (for reporting the CPU baseline). */
+int oracle_max_threads(void) { return pick_threads(0); }

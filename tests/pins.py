@@ -1,0 +1,260 @@
+"""Pins for the FP64 oracle: checks against things the paper and the mathematics
+fix, independent of the oracle's own code.  Each function raises AssertionError
+on failure and takes an optional ``lib`` (a loaded oracle variant), so the same
+pins can be run against a copy of the oracle with a planted mistake.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from oracle import pyref
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if not (np.iscomplexobj(a) or np.iscomplexobj(b)):
+        a = a.astype(np.float64)
+        b = b.astype(np.float64)
+    den = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / den)
+
+
+# --------------------------------------------------------------------------
+# forward pins
+# --------------------------------------------------------------------------
+
+def pin_single_pole(lib=None):
+    """a = [-p], b = [c]: impulse response c p^n (geometric series)."""
+    for p, c in [(0.9, 1.0), (-0.75, 2.5), (0.5, -1.0)]:
+        T = 200
+        x = np.zeros((1, T)); x[0, 0] = 1.0
+        y = oracle.forward(x, [[c]], [[-p]], lib=lib)
+        ref = c * p ** np.arange(T)
+        assert _rel(y[0], ref) < 1e-13, ("single pole", p)
+
+
+def pin_biquad_allpole(lib=None):
+    """Poles r e^{+-i th}: a = [-2 r cos th, r^2], h[n] = r^n sin((n+1) th) / sin th."""
+    for r, th in [(0.95, 0.3), (0.6, 2.0), (0.99, 1.1)]:
+        T = 500
+        x = np.zeros((1, T)); x[0, 0] = 1.0
+        y = oracle.forward(x, [[1.0]], [[-2 * r * np.cos(th), r * r]], lib=lib)
+        n = np.arange(T)
+        ref = r ** n * np.sin((n + 1) * th) / np.sin(th)
+        assert _rel(y[0], ref) < 1e-12, ("biquad", r, th)
+
+
+def _random_filter(rng, M, N, rmax=0.9):
+    poles = []
+    for _ in range(M // 2):
+        r, th = rng.uniform(0.3, rmax), rng.uniform(0, np.pi)
+        poles += [r * np.exp(1j * th), r * np.exp(-1j * th)]
+    if M % 2:
+        poles.append(rng.uniform(-rmax, rmax))
+    a = np.real(np.poly(poles))[1:]
+    b = rng.standard_normal(N + 1)
+    return b, a
+
+
+def pin_transfer_function(lib=None):
+    """The DFT of a long impulse response equals B(e^{jw}) / A(e^{jw}) at w = 2 pi k / K
+    (Eq. rtf), up to the truncation r^K."""
+    rng = np.random.default_rng(11)
+    for M, N in [(1, 0), (2, 2), (5, 3), (8, 8)]:
+        b, a = _random_filter(rng, M, N, rmax=0.9)
+        K = 4096
+        x = np.zeros((1, K)); x[0, 0] = 1.0
+        h = oracle.forward(x, b[None], a[None], lib=lib)[0]
+        Hfft = np.fft.fft(h)
+        zinv = np.exp(-2j * np.pi * np.arange(K) / K)
+        num = np.polyval(b[::-1], zinv)
+        den = np.polyval(np.concatenate([[1.0], a])[::-1], zinv)
+        assert _rel(Hfft, num / den) < 1e-10, ("transfer function", M, N)
+
+
+def pin_lfilter(lib=None):
+    """Library cross-check: SciPy lfilter (TDF-II with zi), called, never copied."""
+    import scipy.signal as ss
+    rng = np.random.default_rng(12)
+    for M, N, T in [(1, 0, 50), (2, 2, 300), (3, 1, 257), (6, 6, 400), (9, 4, 130)]:
+        b, a = _random_filter(rng, M, N, rmax=0.95)
+        x = rng.standard_normal(T)
+        zi = rng.standard_normal(M)
+        y = oracle.forward(x[None], b[None], a[None], zi[None], lib=lib)[0]
+        bp = np.zeros(M + 1); bp[: N + 1] = b
+        ref, _ = ss.lfilter(bp, np.concatenate([[1.0], a]), x, zi=zi)
+        assert _rel(y, ref) < 1e-12, ("lfilter", M, N)
+
+
+def pin_injection_form(lib=None):
+    """TDF-II initial state == injecting zi into the all-pole input at times 0..M-1."""
+    rng = np.random.default_rng(13)
+    for M, N, T in [(1, 1, 20), (4, 2, 100), (7, 7, 3), (3, 0, 64)]:
+        b, a = _random_filter(rng, M, N)
+        x = rng.standard_normal((2, T))
+        zi = rng.standard_normal((2, M))
+        B2 = np.stack([b, b]); A2 = np.stack([a, a])
+        y1 = oracle.forward(x, B2, A2, zi, form="tdf2", lib=lib)
+        y2 = oracle.forward(x, B2, A2, zi, form="injection", lib=lib)
+        assert _rel(y1, y2) < 1e-12, ("injection", M, N, T)
+
+
+def pin_linearity_shift(lib=None):
+    """y(x, zi) = y(x, 0) + y(0, zi); zero-state response is shift invariant."""
+    rng = np.random.default_rng(14)
+    M, N, T = 4, 3, 120
+    b, a = _random_filter(rng, M, N)
+    x = rng.standard_normal((1, T)); zi = rng.standard_normal((1, M))
+    f = lambda xx, zz: oracle.forward(xx, b[None], a[None], zz, lib=lib)
+    assert _rel(f(x, zi), f(x, None) + f(np.zeros_like(x), zi)) < 1e-12
+    s = 17
+    xs = np.zeros_like(x); xs[0, s:] = x[0, : T - s]
+    assert _rel(f(xs, None)[0, s:], f(x, None)[0, : T - s]) < 1e-12
+
+
+def _exact_forward(x, b, a, zi):
+    return pyref.forward(x, b, a, zi)
+
+
+def pin_exact_forward(lib=None):
+    """Exact rational arithmetic (Fractions) through the difference equation."""
+    b = [Fraction(1), Fraction(1, 2)]
+    a = [Fraction(-1, 2)]
+    x = [Fraction(1), Fraction(2), Fraction(0), Fraction(0)]
+    zi = [Fraction(1, 4)]
+    y = _exact_forward(x, b, a, zi)
+    # by hand: y0 = 1 + 1/4; y1 = 2 + 1/2*1 + 1/2*y0; y2 = 1/2*2 + 1/2*y1; y3 = 1/2*y2
+    assert y == [Fraction(5, 4), Fraction(25, 8), Fraction(41, 16), Fraction(41, 32)]
+    yo = oracle.forward(np.array([[1.0, 2, 0, 0]]), [[1.0, 0.5]], [[-0.5]], [[0.25]], lib=lib)
+    assert np.array_equal(yo[0], np.array([float(v) for v in y]))
+
+
+# --------------------------------------------------------------------------
+# backward pins
+# --------------------------------------------------------------------------
+
+def _rat_filter(rng, M, N):
+    """Small random stable rational coefficients."""
+    b = [Fraction(int(rng.integers(-8, 9)), 8) for _ in range(N + 1)]
+    a = [Fraction(int(rng.integers(-3, 4)), 16) for _ in range(M)]
+    return b, a
+
+
+def pin_exact_gradients(lib=None):
+    """Brute force in exact rationals.
+
+    The filter is linear in (x, zi): column j of the Jacobian is the response to a
+    unit impulse, so grad_x = J_x^T g and grad_zi = J_zi^T g exactly.  It is
+    nonlinear in (a, b): there the exact directional derivatives come from
+    forward-mode tangents of the difference equation,
+        dy/db_k = (1/A) [x delayed by k],
+        dy/da_k = (1/A) [-(y delayed by k)],
+    (differentiate y[n] + sum a_k y[n-k] = sum b_k x[n-k] + zi-injection), and
+    grad_theta = <g, dy/dtheta>.  The oracle's FP64 adjoint must agree to rounding.
+    """
+    rng = np.random.default_rng(21)
+    for M, N, T in [(1, 0, 5), (2, 2, 7), (3, 1, 9), (4, 4, 6), (3, 3, 2)]:
+        b, a = _rat_filter(rng, M, N)
+        x = [Fraction(int(rng.integers(-9, 10)), 4) for _ in range(T)]
+        zi = [Fraction(int(rng.integers(-9, 10)), 4) for _ in range(M)]
+        g = [Fraction(int(rng.integers(-9, 10)), 4) for _ in range(T)]
+        zero = [Fraction(0)] * T
+        y = pyref.forward(x, b, a, zi)
+        gx = []
+        for j in range(T):
+            e = [Fraction(0)] * T; e[j] = Fraction(1)
+            col = pyref.forward(e, b, a, None)
+            gx.append(sum(gi * ci for gi, ci in zip(g, col)))
+        gzi = []
+        for k in range(M):
+            e = [Fraction(0)] * M; e[k] = Fraction(1)
+            col = pyref.forward(zero, b, a, e)
+            gzi.append(sum(gi * ci for gi, ci in zip(g, col)))
+        allpole = lambda s: pyref.forward(s, [Fraction(1)], a, None)
+        gb = []
+        for k in range(N + 1):
+            xd = [x[n - k] if n - k >= 0 else Fraction(0) for n in range(T)]
+            gb.append(sum(gi * ti for gi, ti in zip(g, allpole(xd))))
+        ga = []
+        for k in range(1, M + 1):
+            yd = [-y[n - k] if n - k >= 0 else Fraction(0) for n in range(T)]
+            ga.append(sum(gi * ti for gi, ti in zip(g, allpole(yd))))
+        f = lambda v: np.array([float(t) for t in v])[None]
+        ox, ob, oa, oz = oracle.backward(f(g), f(x), f(y), f(b), f(a), lib=lib)
+        for got, ref, nm in [(ox, gx, "x"), (ob, gb, "b"), (oa, ga, "a"), (oz, gzi, "zi")]:
+            ref = np.array([float(t) for t in ref])
+            assert _rel(got[0], ref) < 1e-12 or np.abs(got[0] - ref).max() < 1e-13, \
+                ("exact gradient", nm, M, N, T)
+
+
+def pin_finite_differences(lib=None):
+    """FP64 central differences of L = <g, y> with respect to a, b, zi, x."""
+    rng = np.random.default_rng(22)
+    for M, N, T in [(2, 2, 64), (5, 3, 48), (1, 0, 30)]:
+        b, a = _random_filter(rng, M, N, rmax=0.8)
+        x = rng.standard_normal(T); zi = rng.standard_normal(M); g = rng.standard_normal(T)
+        L = lambda bb, aa, zz, xx: float(g @ oracle.forward(xx[None], bb[None], aa[None],
+                                                            zz[None], lib=lib)[0])
+        y = oracle.forward(x[None], b[None], a[None], zi[None], lib=lib)
+        gx, gb, ga, gz = oracle.backward(g[None], x[None], y, b[None], a[None], lib=lib)
+        h = 1e-6
+        def fd(vec, which):
+            out = np.zeros_like(vec)
+            for i in range(vec.size):
+                vp, vm = vec.copy(), vec.copy(); vp[i] += h; vm[i] -= h
+                args_p = dict(bb=b, aa=a, zz=zi, xx=x); args_m = dict(bb=b, aa=a, zz=zi, xx=x)
+                args_p[which] = vp; args_m[which] = vm
+                out[i] = (L(**args_p) - L(**args_m)) / (2 * h)
+            return out
+        assert _rel(gb[0], fd(b, "bb")) < 1e-7, ("fd b", M, N)
+        assert _rel(ga[0], fd(a, "aa")) < 1e-7, ("fd a", M, N)
+        assert _rel(gz[0], fd(zi, "zz")) < 1e-7, ("fd zi", M, N)
+        assert _rel(gx[0][:8], fd(x, "xx")[:8]) < 1e-7, ("fd x", M, N)
+
+
+def pin_duality(lib=None):
+    """grad_x is the same (b, a) filter run time-reversed on g with zero state
+    (Sec. 3.1: the adjoint of the form is a filter running backwards in time)."""
+    rng = np.random.default_rng(23)
+    for M, N, T in [(2, 2, 300), (6, 4, 77)]:
+        b, a = _random_filter(rng, M, N)
+        x = rng.standard_normal((1, T)); g = rng.standard_normal((1, T))
+        y = oracle.forward(x, b[None], a[None], lib=lib)
+        gx = oracle.backward(g, x, y, b[None], a[None], lib=lib)[0]
+        rev = oracle.forward(g[:, ::-1], b[None], a[None], lib=lib)[:, ::-1]
+        assert _rel(gx, rev) < 1e-12, ("duality", M, N)
+
+
+def pin_statespace(lib=None):
+    """App. B operator under the Sec. 2 mapping gives the same output and gradients."""
+    from oracle import statespace
+    rng = np.random.default_rng(24)
+    for M, N, T in [(1, 1, 40), (2, 2, 100), (5, 2, 64), (4, 0, 33)]:
+        b, a = _random_filter(rng, M, N)
+        x = rng.standard_normal(T); zi = rng.standard_normal(M); g = rng.standard_normal(T)
+        y_ss, gx_ss, gb_ss, ga_ss, gz_ss = statespace.tdf_filter_and_grads(x, b, a, zi, g)
+        y = oracle.forward(x[None], b[None], a[None], zi[None], lib=lib)
+        gx, gb, ga, gz = oracle.backward(g[None], x[None], y, b[None], a[None], lib=lib)
+        for got, ref, nm in [(y[0], y_ss, "y"), (gx[0], gx_ss, "gx"), (gb[0], gb_ss, "gb"),
+                             (ga[0], ga_ss, "ga"), (gz[0], gz_ss, "gzi")]:
+            assert _rel(got, ref) < 1e-11, ("state space", nm, M, N)
+
+
+ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfilter,
+            pin_injection_form, pin_linearity_shift, pin_exact_forward,
+            pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace]
+
+
+def run_all(lib=None):
+    """Run every pin; returns the list of (name, error message) that failed."""
+    failed = []
+    for pin in ALL_PINS:
+        try:
+            pin(lib=lib)
+        except Exception as e:  # noqa: BLE001 -- a planted mistake may raise anything
+            failed.append((pin.__name__, repr(e)))
+    return failed
