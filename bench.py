@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: forward + backward throughput (Gsamples/s) of batched direct-form IIR
+filters on GB300, chunked tensor-core path vs the sequential kernel, at a stated
+relative error against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = coefficient setup + forward + backward (all gradients) over one batch of
+the workload (default: 1024 biquad channels x 48000 samples).  Under torchrun every
+rank filters its own copy of the batch (channels are independent problems, no
+collective on the data path): weak scaling.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Gsamples/s, chunked TC vs sequential kernel at stated rel err vs FP64"
+UNIT = "Gsamples/s"
+FALLBACK_HBM = 6800.0
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="biquad_1024x48000")
+    p.add_argument("--algo", default="chunked", choices=["chunked", "sequential"])
+    p.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel leg")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(torch.cuda.current_device())
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on the host cores
+# ----------------------------------------------------------------------------
+
+def cpu_oracle_rate(w, budget_s=3.0):
+    import oracle
+    total, t0, reps = 0, time.perf_counter(), 0
+    while True:
+        y = oracle.forward(w.x, w.b, w.a, w.zi)
+        oracle.backward(w.gy, w.x, y, w.b, w.a)
+        total += w.x.size
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": total / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"the whole workload ({w.B} x {w.x.shape[1]}), FP64 forward + backward "
+                      f"(all gradients), repeated {reps}x over {dt:.1f} s"}
+
+
+def run_reference(a, world, rank):
+    from paper_2511_14390_gb300 import inputs
+    import oracle
+    if rank != 0:
+        return
+    w = inputs.make(a.workload)
+    step = lambda: oracle.backward(w.gy, w.x, oracle.forward(w.x, w.b, w.a, w.zi), w.b, w.a)
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = (time.perf_counter() - t0) / a.steps
+    v = w.x.size / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, a.workload, "oracle"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"whole workload per step ({w.B} x {w.x.shape[1]})"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, name, algo):
+    return {"workload": name, "B": int(w.B), "T": int(w.x.shape[1]), "M": int(w.M),
+            "N": int(w.N), "algo": algo,
+            "l2": "inputs larger than L2: x and gy are %.0f MB each, 129 MB L2" % (w.x.nbytes / 1e6)}
+
+
+# ----------------------------------------------------------------------------
+# GPU legs
+# ----------------------------------------------------------------------------
+
+def main():
+    a = args_()
+    world, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2511_14390_gb300 import dfilt, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = inputs.make(a.workload)
+    B, T = w.x.shape
+    N, M = w.N, w.M
+    dev = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+    x, b, av, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    L = dfilt.lib()
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def setup(algo):
+        o = dfilt.make_opts(algo=algo, precision="tf32x3")
+        fws, sv, bws = dfilt.dfilt_workspace_size(B, T, N, M, o)
+        buf = lambda n: torch.empty(max(n, 16), dtype=torch.uint8, device="cuda")
+        st = {"o": o, "fws": fws, "bws": bws, "y": torch.empty_like(x),
+              "saved": buf(sv) if sv else None, "wf": buf(fws), "wb": buf(bws),
+              "gx": torch.empty_like(x), "gb": torch.empty_like(b), "ga": torch.empty_like(av),
+              "gz": torch.empty_like(zi)}
+        return st
+
+    P = dfilt._ptr
+
+    def fwd(st):
+        dfilt._check(L.dfilt_forward(P(x), P(b), P(av), P(zi), P(st["y"]), P(st["saved"]),
+                                     P(st["wf"]), st["fws"], B, T, N, M, ctypes.byref(st["o"]),
+                                     sptr), "dfilt_forward")
+
+    def bwd(st):
+        yarg = None if st["saved"] is not None else st["y"]
+        dfilt._check(L.dfilt_backward(P(gy), P(x), P(yarg), P(b), P(av), P(zi), P(st["saved"]),
+                                      P(st["gx"]), P(st["gb"]), P(st["ga"]), P(st["gz"]),
+                                      P(st["wb"]), st["bws"], B, T, N, M, ctypes.byref(st["o"]),
+                                      sptr), "dfilt_backward")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(st, steps, warmup):
+        for _ in range(warmup):
+            fwd(st)
+            bwd(st)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            fwd(st)
+            ev[k][1].record(stream)
+            bwd(st)
+            ev[k][2].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        tot = e0.elapsed_time(e1)
+        tf = [e[0].elapsed_time(e[1]) for e in ev]
+        tb = [e[1].elapsed_time(e[2]) for e in ev]
+        return tot / steps, statistics.mean(tf), statistics.mean(tb)
+
+    def maxrank(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    algo = a.algo
+    st = setup(algo)
+    clk = Clocks(gpu_uuid(torch))
+    ms, ms_f, ms_b = timed(st, a.steps, a.warmup)
+    clocks = clk.stop()
+    ms = maxrank(ms)
+    samples_all = B * T * world
+    value = samples_all / (ms / 1e3) / 1e9
+    status = dfilt.dfilt_sync_status()
+    if status != 0:
+        raise RuntimeError(f"device status {dfilt.STATUS[status]}")
+
+    # accuracy of this run's outputs against the FP64 oracle on sampled channels
+    rel_err = None
+    if rank == 0:
+        import oracle
+        idx = np.linspace(0, B - 1, 8).astype(int)
+        sub = inputs.Workload(x=w.x[idx], b=w.b[idx], a=w.a[idx], zi=w.zi[idx], gy=w.gy[idx],
+                              M=M, N=N, radius=w.radius[idx])
+        yr = oracle.forward(sub.x, sub.b, sub.a, sub.zi)
+        gr = oracle.backward(sub.gy, sub.x, yr, sub.b, sub.a)
+        rel = lambda g, r: float((np.abs(g.cpu().numpy()[idx].astype(np.float64) - r).max(-1)
+                                  / np.abs(r).max(-1)).max())
+        rel_err = {"y": rel(st["y"], yr), "grad_x": rel(st["gx"], gr[0]),
+                   "grad_b": rel(st["gb"], gr[1]), "grad_a": rel(st["ga"], gr[2]),
+                   "grad_zi": rel(st["gz"], gr[3]), "channels_checked": len(idx),
+                   "metric": "per-channel max|err| / max|ref|, max over checked channels"}
+
+    # sequential-kernel leg (the baseline the chunked form is compared with)
+    seq = None
+    if not a.no_seq and algo == "chunked":
+        sst = setup("sequential")
+        sms, sf, sb = timed(sst, max(3, a.steps // 4), 2)
+        sms = maxrank(sms)
+        seq = {"value": samples_all / (sms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": sms,
+               "ms_fwd": sf, "ms_bwd": sb}
+        del sst
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        hx = torch.from_numpy(w.x).pin_memory()
+        hgy = torch.from_numpy(w.gy).pin_memory()
+        hb, ha, hz = (torch.from_numpy(t).pin_memory() for t in (w.b, w.a, w.zi))
+        oy = torch.empty_like(hx).pin_memory()
+        ogx = torch.empty_like(hx).pin_memory()
+        ogb, oga, ogz = (torch.empty_like(t).pin_memory() for t in (hb, ha, hz))
+        h2d = sum(t.numel() * 4 for t in (hx, hgy, hb, ha, hz))
+        d2h = sum(t.numel() * 4 for t in (oy, ogx, ogb, oga, ogz))
+
+        def e2e_step():
+            for d_, h_ in ((x, hx), (gy, hgy), (b, hb), (av, ha), (zi, hz)):
+                d_.copy_(h_, non_blocking=True)
+            fwd(st)
+            bwd(st)
+            for h_, d_ in ((oy, st["y"]), (ogx, st["gx"]), (ogb, st["gb"]), (oga, st["ga"]),
+                           (ogz, st["gz"])):
+                h_.copy_(d_, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        k = max(3, a.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = maxrank(e0.elapsed_time(e1) / k)
+        e2e = {"value": samples_all / (ems / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_oracle_rate(w)
+
+    if rank == 0:
+        hbm, src = peaks()
+        # algorithmic bytes per sample: forward reads x, writes y; backward reads gy and
+        # x, writes grad_x (y is recomputed from M floats of chunk state per 64 samples)
+        bytes_f = (8.0 + (4.0 * M / 64.0)) * B * T
+        bytes_b = (12.0 + (4.0 * M / 64.0)) * B * T
+        dom_b, dom_ms, dom = ((bytes_b, ms_b, "backward") if ms_b >= ms_f
+                              else (bytes_f, ms_f, "forward"))
+        achieved = dom_b / (dom_ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "precision": "tf32x3" if algo == "chunked" else "fp32",
+            "data": "synthetic", "config": workload_config(w, a.workload, algo),
+            "ms_fwd": ms_f, "ms_bwd": ms_b, "rel_err_vs_fp64": rel_err, "sequential": seq,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": f"chunked {dom} (setup + main kernel, one C-ABI call)",
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                         else "fallback"},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 4 * a.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

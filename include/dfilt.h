@@ -1,0 +1,186 @@
+/*
+ * dfilt.h -- C ABI of libdfilt.so: batched direct-form IIR filters and their
+ * closed-form gradients on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (paper: "Accelerating Automatic Differentiation of Direct Form
+ * Digital Filters", Eq. rtf, Sec. 2): for every channel i of a batch,
+ *
+ *     y[n] = sum_{k=0..N} b_k x[n-k] - sum_{k=1..M} a_k y[n-k]
+ *
+ * with a_0 = 1 implicit, b zero-padded to order M (Sec. 2 pads the shorter
+ * polynomial) and an initial state zi[0..M) in the transposed direct form II
+ * convention (the form Sec. 2 names for SciPy/MATLAB): zi is the TDF-II state at
+ * n = 0, equivalently zi[k] is added to the all-pole input at time k.
+ *
+ * The backward (Sec. 3.1, Eqs. dLdz, dLdx, dLdvBA; boundary condition App. A) is
+ * the same recursion run in reversed time.  With u the reverse-time adjoint
+ *     u[n] = gy[n] - sum_{k=1..M} a_k u[n+k],  u[n >= T] = 0,
+ * the library returns
+ *     grad_x[n]  = sum_{k=0..N} b_k u[n+k]
+ *     grad_b[k]  = sum_n u[n] x[n-k]       (k = 0..N)
+ *     grad_a[k]  = -sum_n u[n] y[n-k]      (k = 1..M)
+ *     grad_zi[k] = u[k]                    (k = 0..M-1)
+ *
+ * Conventions shared by every entry point:
+ *   - All array pointers are DEVICE pointers into caller-owned, contiguous,
+ *     row-major fp32 memory (the ragged metadata arrays are int64/int32, also on
+ *     the device).  The library never allocates or frees memory: outputs, the
+ *     `saved` buffer and the workspace `ws` are sized with dfilt_workspace_size*
+ *     and allocated by the caller.
+ *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Argument errors are detected on the
+ *     host and returned synchronously, before anything is launched.  A wait that
+ *     ran out inside a kernel is recorded in a device status word that
+ *     dfilt_sync_status() returns (and clears).
+ *   - Shapes: 1 <= M <= 64, 0 <= N <= M, B >= 0, T >= 0.  Larger M returns
+ *     DFILT_ERR_UNSUPPORTED; N > M returns DFILT_ERR_INVALID_ARG.
+ *   - The library is not thread-safe with respect to concurrent calls that share
+ *     a workspace or saved buffer.
+ */
+#ifndef DFILT_H
+#define DFILT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DFILT_OK = 0,
+    DFILT_ERR_INVALID_ARG = 1,   /* bad shape, NULL where required, misaligned buffer */
+    DFILT_ERR_UNSUPPORTED = 2,   /* M > 64, unsupported option or device */
+    DFILT_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, copy) */
+    DFILT_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    DFILT_ERR_NUMERIC = 5,       /* optional non-finite output check failed */
+    DFILT_ERR_WORKSPACE = 6      /* ws_bytes smaller than dfilt_workspace_size asks */
+} dfilt_status;
+
+typedef enum {
+    DFILT_ALGO_AUTO = 0,         /* library choice (chunked where supported) */
+    DFILT_ALGO_SEQUENTIAL = 1,   /* one thread per channel, serial recursion */
+    DFILT_ALGO_CHUNKED = 2       /* chunked scan: Toeplitz products on the tensor cores */
+} dfilt_algo;
+
+typedef enum {
+    DFILT_PREC_FP32 = 0,         /* sequential kernel arithmetic (CUDA cores) */
+    DFILT_PREC_TF32 = 1,         /* chunked: one TF32 product per Toeplitz tile */
+    DFILT_PREC_TF32X3 = 3        /* chunked: split TF32 (hi*hi + hi*lo + lo*hi), FP32-class */
+} dfilt_precision;
+
+typedef struct {
+    int algo;        /* dfilt_algo */
+    int precision;   /* dfilt_precision; ignored by the sequential algorithm */
+    int chunk_len;   /* chunk length L of the chunked algorithm; 0 = default (64) */
+    int fp64_scan;   /* chunk-state scan in FP64: -1 auto, 0 off, 1 on */
+} dfilt_opts;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int dfilt_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *dfilt_status_string(dfilt_status s);
+
+/*
+ * Fill *opts with the defaults: AUTO algorithm, TF32X3, default chunk length,
+ * automatic FP64 scan.  opts must not be NULL.
+ */
+dfilt_status dfilt_default_opts(dfilt_opts *opts);
+
+/*
+ * Byte sizes the caller must provide for a fixed-shape batch x[B,T]:
+ *   fwd_ws     -- workspace of dfilt_forward
+ *   saved      -- buffer dfilt_forward fills for dfilt_backward (chunk-boundary
+ *                 states; 0 for the sequential algorithm, which re-reads y)
+ *   bwd_ws     -- workspace of dfilt_backward
+ * opts may be NULL (defaults).  Output pointers may be NULL (not wanted).
+ */
+dfilt_status dfilt_workspace_size(int64_t B, int64_t T, int N, int M, const dfilt_opts *opts,
+                                  size_t *fwd_ws, size_t *saved, size_t *bwd_ws);
+
+/*
+ * Forward filter of a fixed-shape batch (Eq. rtf, TDF-II initial state).
+ *   x   [B,T]      input signal
+ *   b   [B,N+1]    numerator b_0..b_N per channel
+ *   a   [B,M]      denominator a_1..a_M per channel (a_0 = 1 implicit)
+ *   zi  [B,M]      initial TDF-II state; NULL = zero
+ *   y   [B,T]      output (must not alias any input)
+ *   saved          NULL, or at least `saved` bytes from dfilt_workspace_size: filled
+ *                  with what dfilt_backward needs to recompute y per chunk
+ *   ws, ws_bytes   workspace of at least `fwd_ws` bytes (may be NULL when 0)
+ * Returns DFILT_OK once all work is enqueued on `stream`.
+ */
+dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const float *zi,
+                           float *y, void *saved, void *ws, size_t ws_bytes,
+                           int64_t B, int64_t T, int N, int M, const dfilt_opts *opts,
+                           void *stream);
+
+/*
+ * Backward (closed-form adjoint of Sec. 3.1) of a fixed-shape batch.
+ *   gy  [B,T]      upstream gradient dL/dy
+ *   x   [B,T]      the forward's input
+ *   y   [B,T]      the forward's output; may be NULL only for the chunked algorithm
+ *                  when `saved` holds the forward's chunk states (y is then
+ *                  recomputed per chunk)
+ *   b, a, zi       the forward's coefficients and initial state
+ *   saved          the forward's saved buffer, or NULL when y is given
+ *   gx  [B,T], gb [B,N+1], ga [B,M], gzi [B,M]   gradients; each may be NULL (not
+ *                  wanted)
+ *   ws, ws_bytes   workspace of at least `bwd_ws` bytes
+ * opts must select the same algorithm and chunk length as the forward that
+ * filled `saved`.
+ */
+dfilt_status dfilt_backward(const float *gy, const float *x, const float *y,
+                            const float *b, const float *a, const float *zi, const void *saved,
+                            float *gx, float *gb, float *ga, float *gzi,
+                            void *ws, size_t ws_bytes,
+                            int64_t B, int64_t T, int N, int M, const dfilt_opts *opts,
+                            void *stream);
+
+/*
+ * Ragged batch: channel i owns samples [offsets[i], offsets[i+1]) of the packed
+ * signals (x, y, gy, gx of `total` floats), has orders Ms[i] (1..Mmax) and
+ * Ns[i] (0..Ms[i]), and coefficient rows b[i*(Nmax+1) ..], a[i*Mmax ..],
+ * zi[i*Mmax ..], zero-padded past its own order.  offsets (int64[B+1]), Ms, Ns
+ * (int32[B]) are device arrays; offsets must be non-decreasing with offsets[0] = 0
+ * and offsets[B] = total (checked on the device; a violation is reported through
+ * dfilt_sync_status as DFILT_ERR_INVALID_ARG).
+ * Workspace sizes depend only on (B, total, Nmax, Mmax).
+ */
+dfilt_status dfilt_workspace_size_ragged(int64_t B, int64_t total, int Nmax, int Mmax,
+                                         const dfilt_opts *opts, size_t *fwd_ws, size_t *saved,
+                                         size_t *bwd_ws);
+
+dfilt_status dfilt_forward_ragged(const float *x, const int64_t *offsets, const int *Ms,
+                                  const int *Ns, const float *b, const float *a, const float *zi,
+                                  float *y, void *saved, void *ws, size_t ws_bytes,
+                                  int64_t B, int64_t total, int Nmax, int Mmax,
+                                  const dfilt_opts *opts, void *stream);
+
+dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float *y,
+                                   const int64_t *offsets, const int *Ms, const int *Ns,
+                                   const float *b, const float *a, const float *zi,
+                                   const void *saved, float *gx, float *gb, float *ga, float *gzi,
+                                   void *ws, size_t ws_bytes, int64_t B, int64_t total,
+                                   int Nmax, int Mmax, const dfilt_opts *opts, void *stream);
+
+/*
+ * Synchronise `stream` and return (then clear) the device status word: DFILT_OK,
+ * DFILT_ERR_TIMEOUT (a bounded wait ran out; outputs of that call are undefined),
+ * DFILT_ERR_INVALID_ARG (ragged metadata failed its device-side check), or
+ * DFILT_ERR_CUDA if the synchronisation itself failed.
+ */
+dfilt_status dfilt_sync_status(void *stream);
+
+/*
+ * Test hook: cap every bounded device-side wait at `iters` polls (0 restores the
+ * default cap).  Lets tests drive the timeout path without hanging a GPU.
+ */
+dfilt_status dfilt_set_wait_limit(int64_t iters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFILT_H */

@@ -1,0 +1,292 @@
+// C ABI of libdfilt.so (declared in include/dfilt.h): argument checks on the host,
+// workspace sizing, algorithm choice and kernel dispatch.  No entry point allocates
+// or frees device memory.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.h"
+
+using namespace dfilt;
+
+// Device status word: first nonzero dfilt_status a kernel records wins.
+__device__ int g_dfilt_status;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int *g_status_addr[kMaxDevices] = {};
+int g_num_sms[kMaxDevices] = {};
+long long g_wait_limit = kDefaultWaitLimit;
+
+struct DevInfo {
+    int *status;
+    int num_sms;
+};
+
+bool dev_info(DevInfo *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dfilt_status) != cudaSuccess) return false;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return false;
+        g_status_addr[dev] = static_cast<int *>(p);
+        g_num_sms[dev] = sms;
+    }
+    out->status = g_status_addr[dev];
+    out->num_sms = g_num_sms[dev];
+    return true;
+}
+
+struct Resolved {
+    int algo;
+    int precision;
+    bool fp64_scan;
+};
+
+dfilt_status resolve(const dfilt_opts *o, int Mmax, Resolved *r) {
+    dfilt_opts d;
+    dfilt_default_opts(&d);
+    if (!o) o = &d;
+    if (o->algo < DFILT_ALGO_AUTO || o->algo > DFILT_ALGO_CHUNKED) return DFILT_ERR_INVALID_ARG;
+    if (o->chunk_len != 0 && o->chunk_len != kL) return DFILT_ERR_UNSUPPORTED;
+    if (o->fp64_scan < -1 || o->fp64_scan > 1) return DFILT_ERR_INVALID_ARG;
+    r->algo = o->algo == DFILT_ALGO_AUTO ? DFILT_ALGO_CHUNKED : o->algo;
+    r->precision = o->precision;
+    if (r->algo == DFILT_ALGO_CHUNKED) {
+        if (o->precision != DFILT_PREC_TF32 && o->precision != DFILT_PREC_TF32X3)
+            return DFILT_ERR_UNSUPPORTED;
+    } else if (o->precision != DFILT_PREC_FP32 && o->precision != DFILT_PREC_TF32 &&
+               o->precision != DFILT_PREC_TF32X3) {
+        return DFILT_ERR_INVALID_ARG;
+    }
+    r->fp64_scan = chunk_layout(Mmax, o->fp64_scan).fp64_scan;
+    return DFILT_OK;
+}
+
+dfilt_status check_orders(int N, int M) {
+    if (M > 64) return DFILT_ERR_UNSUPPORTED;
+    if (M < 1 || N < 0 || N > M) return DFILT_ERR_INVALID_ARG;
+    return DFILT_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+dfilt_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DFILT_OK;
+    if (e == cudaErrorNotSupported) return DFILT_ERR_UNSUPPORTED;
+    return DFILT_ERR_CUDA;
+}
+
+void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, size_t *fwd, size_t *saved,
+           size_t *bwd) {
+    size_t f = 0, s = 0, w = 0;
+    if (r.algo == DFILT_ALGO_CHUNKED) {
+        f = chunk_fwd_ws_bytes(B, Mmax, r.fp64_scan);
+        s = chunk_saved_bytes(B, total, Mmax);
+        w = chunk_bwd_ws_bytes(B, Mmax, r.fp64_scan);
+    }
+    if (fwd) *fwd = f;
+    if (saved) *saved = s;
+    if (bwd) *bwd = w;
+}
+
+Batch make_batch(const DevInfo &di, const int64_t *offsets, const int *Ms, const int *Ns,
+                 int64_t B, int64_t T, int64_t total, int N, int M, int Nmax, int Mmax) {
+    Batch bt;
+    bt.offsets = offsets;
+    bt.Ms = Ms;
+    bt.Ns = Ns;
+    bt.B = B;
+    bt.T = T;
+    bt.total = total;
+    bt.M = M;
+    bt.N = N;
+    bt.Mstride = Mmax;
+    bt.Nstride = Nmax + 1;
+    bt.status = di.status;
+    bt.wait_limit = g_wait_limit;
+    return bt;
+}
+
+dfilt_status do_forward(const float *x, const float *b, const float *a, const float *zi, float *y,
+                        void *saved, void *ws, size_t ws_bytes, const Batch &bt, int Mmax,
+                        const Resolved &r, const DevInfo &di, cudaStream_t st) {
+    if (bt.B == 0 || bt.total == 0) return DFILT_OK;
+    if (r.algo == DFILT_ALGO_SEQUENTIAL)
+        return cuda_status(launch_seq_fwd(x, b, a, zi, y, bt, Mmax, st));
+    size_t need = chunk_fwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
+    if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
+    if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
+    return cuda_status(launch_chunk_fwd(x, b, a, zi, y, static_cast<float *>(saved), ws, bt, Mmax,
+                                        r.fp64_scan, r.precision, di.num_sms, st));
+}
+
+dfilt_status do_backward(const float *gy, const float *x, const float *y, const float *b,
+                         const float *a, const void *saved, float *gx, float *gb, float *ga,
+                         float *gzi, void *ws, size_t ws_bytes, const Batch &bt, int Mmax,
+                         const Resolved &r, const DevInfo &di, cudaStream_t st) {
+    if (bt.B == 0) return DFILT_OK;
+    if (r.algo == DFILT_ALGO_SEQUENTIAL) {
+        if (!y) return DFILT_ERR_INVALID_ARG;
+        return cuda_status(launch_seq_bwd(gy, x, y, b, a, gx, gb, ga, gzi, bt, Mmax, st));
+    }
+    if (!y && !saved) return DFILT_ERR_INVALID_ARG;
+    size_t need = chunk_bwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
+    if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
+    if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
+    return cuda_status(launch_chunk_bwd(gy, x, y, b, a, static_cast<const float *>(saved), gx, gb,
+                                        ga, gzi, ws, bt, Mmax, r.fp64_scan, r.precision,
+                                        di.num_sms, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfilt_version(void) { return 100; }
+
+const char *dfilt_status_string(dfilt_status s) {
+    switch (s) {
+        case DFILT_OK: return "DFILT_OK";
+        case DFILT_ERR_INVALID_ARG: return "DFILT_ERR_INVALID_ARG";
+        case DFILT_ERR_UNSUPPORTED: return "DFILT_ERR_UNSUPPORTED";
+        case DFILT_ERR_CUDA: return "DFILT_ERR_CUDA";
+        case DFILT_ERR_TIMEOUT: return "DFILT_ERR_TIMEOUT";
+        case DFILT_ERR_NUMERIC: return "DFILT_ERR_NUMERIC";
+        case DFILT_ERR_WORKSPACE: return "DFILT_ERR_WORKSPACE";
+    }
+    return "DFILT_ERR_UNKNOWN";
+}
+
+dfilt_status dfilt_default_opts(dfilt_opts *o) {
+    if (!o) return DFILT_ERR_INVALID_ARG;
+    o->algo = DFILT_ALGO_AUTO;
+    o->precision = DFILT_PREC_TF32X3;
+    o->chunk_len = 0;
+    o->fp64_scan = -1;
+    return DFILT_OK;
+}
+
+dfilt_status dfilt_workspace_size(int64_t B, int64_t T, int N, int M, const dfilt_opts *opts,
+                                  size_t *fwd_ws, size_t *saved, size_t *bwd_ws) {
+    if (B < 0 || T < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(N, M);
+    if (s) return s;
+    Resolved r;
+    if ((s = resolve(opts, M, &r))) return s;
+    sizes(r, B, B * T, M, fwd_ws, saved, bwd_ws);
+    return DFILT_OK;
+}
+
+dfilt_status dfilt_workspace_size_ragged(int64_t B, int64_t total, int Nmax, int Mmax,
+                                         const dfilt_opts *opts, size_t *fwd_ws, size_t *saved,
+                                         size_t *bwd_ws) {
+    if (B < 0 || total < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(Nmax, Mmax);
+    if (s) return s;
+    Resolved r;
+    if ((s = resolve(opts, Mmax, &r))) return s;
+    sizes(r, B, total, Mmax, fwd_ws, saved, bwd_ws);
+    return DFILT_OK;
+}
+
+dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const float *zi,
+                           float *y, void *saved, void *ws, size_t ws_bytes, int64_t B, int64_t T,
+                           int N, int M, const dfilt_opts *opts, void *stream) {
+    if (B < 0 || T < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(N, M);
+    if (s) return s;
+    if (B > 0 && T > 0 && (!x || !b || !a || !y)) return DFILT_ERR_INVALID_ARG;
+    Resolved r;
+    if ((s = resolve(opts, M, &r))) return s;
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    Batch bt = make_batch(di, nullptr, nullptr, nullptr, B, T, B * T, N, M, N, M);
+    return do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, M, r, di,
+                      static_cast<cudaStream_t>(stream));
+}
+
+dfilt_status dfilt_backward(const float *gy, const float *x, const float *y, const float *b,
+                            const float *a, const float *zi, const void *saved, float *gx,
+                            float *gb, float *ga, float *gzi, void *ws, size_t ws_bytes, int64_t B,
+                            int64_t T, int N, int M, const dfilt_opts *opts, void *stream) {
+    (void)zi;   // carried inside `saved` (chunk 0's entry state) when y is recomputed
+    if (B < 0 || T < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(N, M);
+    if (s) return s;
+    if (B > 0 && (!gy || !x || !b || !a)) return DFILT_ERR_INVALID_ARG;
+    Resolved r;
+    if ((s = resolve(opts, M, &r))) return s;
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    Batch bt = make_batch(di, nullptr, nullptr, nullptr, B, T, B * T, N, M, N, M);
+    return do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, M, r, di,
+                       static_cast<cudaStream_t>(stream));
+}
+
+dfilt_status dfilt_forward_ragged(const float *x, const int64_t *offsets, const int *Ms,
+                                  const int *Ns, const float *b, const float *a, const float *zi,
+                                  float *y, void *saved, void *ws, size_t ws_bytes, int64_t B,
+                                  int64_t total, int Nmax, int Mmax, const dfilt_opts *opts,
+                                  void *stream) {
+    if (B < 0 || total < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(Nmax, Mmax);
+    if (s) return s;
+    if (B > 0 && (!offsets || !Ms || !Ns || !b || !a || (total > 0 && (!x || !y))))
+        return DFILT_ERR_INVALID_ARG;
+    Resolved r;
+    if ((s = resolve(opts, Mmax, &r))) return s;
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    Batch bt = make_batch(di, offsets, Ms, Ns, B, 0, total, Nmax, Mmax, Nmax, Mmax);
+    return do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, Mmax, r, di,
+                      static_cast<cudaStream_t>(stream));
+}
+
+dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float *y,
+                                   const int64_t *offsets, const int *Ms, const int *Ns,
+                                   const float *b, const float *a, const float *zi,
+                                   const void *saved, float *gx, float *gb, float *ga, float *gzi,
+                                   void *ws, size_t ws_bytes, int64_t B, int64_t total, int Nmax,
+                                   int Mmax, const dfilt_opts *opts, void *stream) {
+    (void)zi;
+    if (B < 0 || total < 0) return DFILT_ERR_INVALID_ARG;
+    dfilt_status s = check_orders(Nmax, Mmax);
+    if (s) return s;
+    if (B > 0 && (!offsets || !Ms || !Ns || !b || !a || (total > 0 && (!gy || !x))))
+        return DFILT_ERR_INVALID_ARG;
+    Resolved r;
+    if ((s = resolve(opts, Mmax, &r))) return s;
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    Batch bt = make_batch(di, offsets, Ms, Ns, B, 0, total, Nmax, Mmax, Nmax, Mmax);
+    return do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, Mmax, r, di,
+                       static_cast<cudaStream_t>(stream));
+}
+
+dfilt_status dfilt_sync_status(void *stream) {
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return DFILT_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, di.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DFILT_ERR_CUDA;
+    if (v != 0 && cudaMemset(di.status, 0, sizeof(int)) != cudaSuccess) return DFILT_ERR_CUDA;
+    return static_cast<dfilt_status>(v);
+}
+
+dfilt_status dfilt_set_wait_limit(int64_t iters) {
+    if (iters < 0) return DFILT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_wait_limit = iters == 0 ? kDefaultWaitLimit : (long long)iters;
+    return DFILT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,552 @@
+// Chunked backward (closed-form adjoint of Sec. 3.1) on the tensor cores (sm_103a).
+//
+// The adjoint u[n] = gy[n] - sum_k a_k u[n+k] (u = 0 past the end, App. A) and
+// grad_x = B applied anti-causally to u are the forward machinery run backwards in
+// time.  A CTA owns whole channels and walks their tiles from the last to the first.
+// Per tile:
+//   1. cp.async gy (swizzled K-major A operand, split into TF32 hi/lo) and x (and y
+//      when it is given) into shared memory;
+//   2. tcgen05.mma: D[128 x 128] = G [T_g^a | T_h^a]^T -- columns 0..63 of row c are
+//      chunk c's zero-state grad_x, columns 64..127 its zero-state adjoint u;
+//   3. reverse chunk scan of the adjoint state S'_c = u[(c+1)L .. (c+1)L+MB)
+//      (S'_{c-1} = Abar' S'_c + u_zs,c[0:MB]), FP32 Hillis-Steele or serial FP64;
+//   4. fused epilogue per chunk: u = u_zs + O^u S', grad_x = gx_zs + O^gx S' (stored),
+//      y recomputed from the forward's saved chunk state (or read), and the lag
+//      correlations grad_b[k] += sum u[n+k] x[n], grad_a[k] -= sum u[n+1+k] y[n]
+//      reduced warp-wise into per-CTA FP64 accumulators; grad_zi = u[0:M].
+#include "chunk.cuh"
+
+#ifndef DFILT_MB
+#error "compile once per state bucket with -DDFILT_MB=<2|4|8|16|32|64>"
+#endif
+
+namespace dfilt {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr uint32_t kTileBytes = kChunks * kL * 4;   // 32 KB
+constexpr uint32_t kKBlock = kChunks * 128;
+
+template <int MB, bool F64, bool READ_Y>
+struct BwdSmem {
+    using Tab = ChunkTab<MB>;
+    static constexpr int NM = Tab::NBWD;
+    // For MB == L with the FP64 scan, O^u is read from the FP64 transition (Abar' = O^u).
+    static constexpr bool OU_FROM_AT = F64 && MB == kL;
+    static constexpr uint32_t AHI = 0;
+    static constexpr uint32_t ALO = AHI + kTileBytes;
+    static constexpr uint32_t BHI = ALO + kTileBytes;
+    static constexpr uint32_t BLO = BHI + NM * 256;
+    static constexpr uint32_t XS = BLO + NM * 256;
+    static constexpr uint32_t YS = XS + kTileBytes;
+    static constexpr uint32_t OU = YS + (READ_Y ? kTileBytes : 0);
+    static constexpr uint32_t OGX = OU + (OU_FROM_AT ? 0 : kL * MB * 4);
+    static constexpr uint32_t SCAN = OGX + kL * MB * 4;
+    static constexpr uint32_t COEF = (SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
+    static constexpr uint32_t ACC = (COEF + 2 * (MB + 1) * 4 + 15) / 16 * 16;   // 4 x (2MB+1) doubles
+    static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
+    static constexpr uint32_t BYTES = MISC + 32;
+    static constexpr uint32_t ALLOC = BYTES + 1024;
+};
+
+__device__ __forceinline__ void load_tile_sw(uint32_t dst, const float *src, int64_t start, int n,
+                                             bool al16) {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+        const int id = threadIdx.x + kThreads * q;
+        const int r = id >> 4, j16 = id & 15;
+        const uint32_t d = dst + (j16 >> 3) * kKBlock + r * 128 + ((((j16 & 7) ^ (r & 7))) << 4);
+        const int s = r * kL + j16 * 4;
+        const int nv = min(max(n - s, 0), 4);
+        const float *g = src + start + s;
+        if (al16) {
+            cp_async16(d, nv ? (const void *)g : (const void *)src, nv * 4);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                cp_async4(d + 4 * e, e < nv ? (const void *)(g + e) : (const void *)src, e < nv ? 4 : 0);
+        }
+    }
+}
+
+// Row-staged tile: row c = chunk c (256 bytes), 16-byte piece j at ((j ^ (c & 15)) << 4).
+__device__ __forceinline__ void load_tile_rows(uint32_t dst, const float *src, int64_t start, int n,
+                                               bool al16) {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+        const int id = threadIdx.x + kThreads * q;
+        const int r = id >> 4, j = id & 15;
+        const uint32_t d = dst + r * 256 + ((j ^ (r & 15)) << 4);
+        const int s = r * kL + j * 4;
+        const int nv = min(max(n - s, 0), 4);
+        const float *g = src + start + s;
+        if (al16) {
+            cp_async16(d, nv ? (const void *)g : (const void *)src, nv * 4);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                cp_async4(d + 4 * e, e < nv ? (const void *)(g + e) : (const void *)src, e < nv ? 4 : 0);
+        }
+    }
+}
+
+__device__ __forceinline__ void split_tile(char *smem, uint32_t a_off, uint32_t lo_off, bool three) {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+        const int id = threadIdx.x + kThreads * q;
+        const int r = id >> 4, j16 = id & 15;
+        const uint32_t o = a_off + (j16 >> 3) * kKBlock + r * 128 + ((((j16 & 7) ^ (r & 7))) << 4);
+        float4 v = *reinterpret_cast<float4 *>(smem + o);
+        float4 h, l;
+        split_tf32(v.x, h.x, l.x);
+        split_tf32(v.y, h.y, l.y);
+        split_tf32(v.z, h.z, l.z);
+        split_tf32(v.w, h.w, l.w);
+        *reinterpret_cast<float4 *>(smem + o) = h;
+        if (three) *reinterpret_cast<float4 *>(smem + o + lo_off) = l;
+    }
+}
+
+__device__ __forceinline__ void store_tile(float *dst, int64_t start, int n, const char *stag,
+                                           bool al16) {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+        const int id = threadIdx.x + kThreads * q;
+        const int r = id >> 4, j = id & 15;
+        const float4 v = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ (r & 15)) << 4));
+        const int s = r * kL + j * 4;
+        const int nv = min(max(n - s, 0), 4);
+        float *g = dst + start + s;
+        if (nv == 4 && al16) {
+            *reinterpret_cast<float4 *>(g) = v;
+        } else {
+            if (nv > 0) g[0] = v.x;
+            if (nv > 1) g[1] = v.y;
+            if (nv > 2) g[2] = v.z;
+            if (nv > 3) g[3] = v.w;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 row_piece(const char *buf, int r, int j) {
+    return *reinterpret_cast<const float4 *>(buf + r * 256 + ((j ^ (r & 15)) << 4));
+}
+
+template <int MB>
+__device__ __forceinline__ void matvec_f32(const float *P, const float (&v)[MB], float (&out)[MB]) {
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < MB; ++j) acc = fmaf(P[i * MB + j], v[j], acc);
+        out[i] = acc;
+    }
+}
+
+template <int MB, bool F64, bool READ_Y>
+__global__ void __launch_bounds__(kThreads, 1)
+    chunk_bwd_kernel(const float *__restrict__ gy, const float *__restrict__ x,
+                     const float *__restrict__ y, const float *__restrict__ b,
+                     const float *__restrict__ a, const float *__restrict__ saved,
+                     float *__restrict__ gx, float *__restrict__ gb, float *__restrict__ ga,
+                     float *__restrict__ gzi, const char *__restrict__ ws,
+                     unsigned long long *__restrict__ counter, Batch bt, int three, int al_mask) {
+    using Tab = ChunkTab<MB>;
+    using SM = BwdSmem<MB, F64, READ_Y>;
+    constexpr int NM = SM::NM;
+    constexpr int NACC = 2 * MB + 1;
+    extern __shared__ char smem_raw[];
+    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + SM::MISC);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::MISC + 8);
+    int64_t *ch_slot = reinterpret_cast<int64_t *>(smem + SM::MISC + 16);
+    int *flag_slot = reinterpret_cast<int *>(smem + SM::MISC + 24);
+    float *sOU = reinterpret_cast<float *>(smem + SM::OU);
+    float *sOGX = reinterpret_cast<float *>(smem + SM::OGX);
+    const float *sP = reinterpret_cast<const float *>(smem + SM::SCAN);
+    const double *sAt = reinterpret_cast<const double *>(smem + SM::SCAN);
+    float *sa = reinterpret_cast<float *>(smem + SM::COEF);
+    float *sb = sa + (MB + 1);
+    double *sacc = reinterpret_cast<double *>(smem + SM::ACC);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, 128);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool alive = true;
+    const size_t rec = Tab::bwd_rec(F64);
+    constexpr uint32_t idesc = idesc_tf32_m128(NM);
+    const bool gy_al = al_mask & 1, x_al = al_mask & 2, y_al = al_mask & 4, gx_al = al_mask & 8;
+
+    while (alive) {
+        if (tid == 0) *ch_slot = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t ch = *ch_slot;
+        if (ch >= bt.B) break;
+        const Channel c = channel_of(bt, ch);
+        const char *R = ws + kWsHeader + (size_t)ch * rec;
+        {
+            const float *g = reinterpret_cast<const float *>(R + Tab::B_G);
+            const float *h = reinterpret_cast<const float *>(R + Tab::B_H);
+            for (int idx = tid; idx < NM * kL; idx += kThreads) {
+                const int i = idx / kL, k = idx % kL;
+                // row i < L: grad_x output i, T_g^a[i][k] = g[k-i]; row L+i: u output i
+                const int ii = i < kL ? i : i - kL;
+                const float *imp = i < kL ? g : h;
+                const float v = k >= ii ? imp[k - ii] : 0.f;
+                float hv, lv;
+                split_tf32(v, hv, lv);
+                const uint32_t o = (k >> 5) * (NM * 128) + sw128_off(i, k & 31);
+                *reinterpret_cast<float *>(smem + SM::BHI + o) = hv;
+                *reinterpret_cast<float *>(smem + SM::BLO + o) = lv;
+            }
+            if constexpr (!SM::OU_FROM_AT) {
+                const float *Ou = reinterpret_cast<const float *>(R + Tab::B_OU);
+                for (int idx = tid; idx < kL * MB; idx += kThreads) sOU[idx] = Ou[idx];
+            }
+            const float *Ogx = reinterpret_cast<const float *>(R + Tab::B_OGX);
+            for (int idx = tid; idx < kL * MB; idx += kThreads) sOGX[idx] = Ogx[idx];
+            const float4 *src = reinterpret_cast<const float4 *>(R + Tab::B_SCAN);
+            float4 *dst = reinterpret_cast<float4 *>(smem + SM::SCAN);
+            for (int idx = tid; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kThreads) dst[idx] = src[idx];
+            if (tid < MB) sa[tid] = tid < c.M ? a[ch * bt.Mstride + tid] : 0.f;
+            if (tid <= MB) sb[tid] = tid <= c.N ? b[ch * bt.Nstride + tid] : 0.f;
+            for (int idx = tid; idx < 4 * NACC; idx += kThreads) sacc[idx] = 0.0;
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        float Sin[MB];   // adjoint state entering the current tile from the right
+        double S64a = 0.0, S64b = 0.0;
+#pragma unroll
+        for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
+        const int64_t ntiles = (c.len + kTileSamples - 1) / kTileSamples;
+        const int64_t chunk_base = c.off / kL + ch;
+
+        for (int64_t t = ntiles - 1; t >= 0; --t) {
+            const int64_t tstart = c.off + t * kTileSamples;
+            const int tlen = (int)(c.len - t * kTileSamples < kTileSamples ? c.len - t * kTileSamples : kTileSamples);
+            const int nch = (tlen + kL - 1) / kL;
+            const bool a4 = (tstart & 3) == 0;
+            load_tile_sw(sbase + SM::AHI, gy, tstart, tlen, gy_al && a4);
+            load_tile_rows(sbase + SM::XS, x, tstart, tlen, x_al && a4);
+            if constexpr (READ_Y) load_tile_rows(sbase + SM::YS, y, tstart, tlen, y_al && a4);
+            cp_async_commit();
+            cp_async_wait_all();
+            split_tile(smem, SM::AHI, SM::ALO - SM::AHI, three != 0);
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int s = 0; s < kL / 8; ++s) {
+                    const uint32_t ka = (s >> 2) * kKBlock + (s & 3) * 32;
+                    const uint32_t kb = (s >> 2) * (NM * 128) + (s & 3) * 32;
+                    const uint64_t ahi = sdesc_sw128(sbase + SM::AHI + ka);
+                    const uint64_t bhi = sdesc_sw128(sbase + SM::BHI + kb);
+                    mma_tf32(tmem, ahi, bhi, idesc, s > 0 ? 1u : 0u);
+                    if (three) {
+                        const uint64_t alo = sdesc_sw128(sbase + SM::ALO + ka);
+                        const uint64_t blo = sdesc_sw128(sbase + SM::BLO + kb);
+                        mma_tf32(tmem, ahi, blo, idesc, 1u);
+                        mma_tf32(tmem, alo, bhi, idesc, 1u);
+                    }
+                }
+                mma_commit(mbar);
+                bool ok = mbar_wait_bounded(mbar, phase, bt.wait_limit);
+                if (!ok) {
+                    set_status(bt.status, DFILT_ERR_TIMEOUT);
+                    mbar_wait_bounded(mbar, phase, kDefaultWaitLimit);
+                }
+                *flag_slot = ok ? 1 : 0;
+            }
+            phase ^= 1u;
+            __syncthreads();
+            tc_fence_after();
+            if (!*flag_slot) {
+                alive = false;
+                break;
+            }
+
+            // ---- E'_c = u_zs[0:MB] (TMEM columns L .. L+MB) ----
+            float E[MB];
+#pragma unroll
+            for (int cb = 0; cb < (MB + 15) / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + kL + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (cb * 16 + i < MB) E[cb * 16 + i] = v[i];
+            }
+            float S[MB];   // S'_c: adjoint values u[(c+1)L + m]
+            float *xbuf = reinterpret_cast<float *>(smem + SM::ALO);
+            if constexpr (!F64) {
+                // inclusive reverse Hillis-Steele: I'_c = sum_{j >= c} Abar'^(j-c) E'_j
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    const int d = 1 << k;
+                    float nxt[MB];
+                    bool valid;
+                    if (d < 32) {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) nxt[m] = __shfl_down_sync(0xffffffffu, E[m], d);
+                        valid = lane + d < 32;
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
+                        __syncthreads();
+                        valid = tid + d < kChunks;
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) nxt[m] = valid ? xbuf[(tid + d) * MB + m] : 0.f;
+                        __syncthreads();
+                    }
+                    if (valid) {
+                        float add[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, nxt, add);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) E[m] += add[m];
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
+                __syncthreads();
+                // S'_c = I'_{c+1} + Abar'^(127-c) S'_in
+                float v[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) v[m] = Sin[m];
+                const int e = kChunks - 1 - tid;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    if ((e >> k) & 1) {
+                        float w[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, v, w);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) v[m] = w[m];
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) S[m] = (tid + 1 < kChunks ? xbuf[(tid + 1) * MB + m] : 0.f) + v[m];
+                // state leaving the tile to the left: I'_0 + Abar'^128 S'_in
+                float w[MB];
+                matvec_f32<MB>(sP + 7 * MB * MB, Sin, w);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = xbuf[m] + w[m];
+                __syncthreads();
+            } else {
+                float *sbuf = reinterpret_cast<float *>(smem + SM::AHI);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
+                __syncthreads();
+                if (warp == 0) {
+                    for (int cc = nch - 1; cc >= 0; --cc) {
+                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
+                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
+                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
+#pragma unroll 8
+                        for (int j = 0; j < MB; ++j) {
+                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
+                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
+                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
+                        }
+                        S64a = acc_a;
+                        S64b = acc_b;
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < MB; ++m) S[m] = tid < nch ? sbuf[tid * MB + m] : 0.f;
+                __syncthreads();
+            }
+
+            // ---- y for this chunk: read, or recomputed from the forward's chunk state ----
+            float yv[kL];
+            if constexpr (READ_Y) {
+#pragma unroll
+                for (int j = 0; j < kL / 4; ++j) {
+                    const float4 p = row_piece(smem + SM::YS, tid, j);
+                    yv[4 * j] = p.x; yv[4 * j + 1] = p.y; yv[4 * j + 2] = p.z; yv[4 * j + 3] = p.w;
+                }
+            } else {
+                float s[MB];
+                const bool vch = tid < nch;
+                const float *src = saved + (size_t)(chunk_base + t * kChunks + tid) * bt.Mstride;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) s[m] = (vch && m < c.M) ? src[m] : 0.f;
+#pragma unroll
+                for (int j = 0; j < kL / 4; ++j) {
+                    const float4 p = row_piece(smem + SM::XS, tid, j);
+                    const float xs4[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float xn = xs4[e];
+                        const float yn = fmaf(sb[0], xn, s[0]);
+#pragma unroll
+                        for (int k = 0; k < MB; ++k)
+                            s[k] = fmaf(-sa[k], yn, fmaf(sb[k + 1], xn, k + 1 < MB ? s[k + 1] : 0.f));
+                        yv[4 * j + e] = yn;
+                    }
+                }
+            }
+
+            // ---- u and grad_x for this chunk; correlations ----
+            float u[kL];
+            char *stag = smem + SM::AHI;   // gy tile is no longer needed
+            float pb[MB + 1], pa[MB];
+#pragma unroll
+            for (int k = 0; k <= MB; ++k) pb[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < MB; ++k) pa[k] = 0.f;
+#pragma unroll
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float vu[16], vg[16];
+                tmem_ld16(taddr + kL + cb * 16, vu);
+                tmem_ld16(taddr + cb * 16, vg);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int n = cb * 16 + i;
+                    float au = vu[i], ag = vg[i];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) {
+                        const float ou = SM::OU_FROM_AT ? (float)sAt[m * MB + n] : sOU[n * MB + m];
+                        au = fmaf(ou, S[m], au);
+                        ag = fmaf(sOGX[n * MB + m], S[m], ag);
+                    }
+                    u[n] = au;
+                    vg[i] = ag;
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int j = cb * 4 + p;
+                    *reinterpret_cast<float4 *>(stag + tid * 256 + ((j ^ (tid & 15)) << 4)) =
+                        make_float4(vg[4 * p], vg[4 * p + 1], vg[4 * p + 2], vg[4 * p + 3]);
+                }
+            }
+            // ext[n] = u[n] for n < L, S'[n - L] above
+#define DFILT_EXT(n) ((n) < kL ? u[(n)] : S[(n) - kL])
+#pragma unroll
+            for (int j = 0; j < kL / 4; ++j) {
+                const float4 p = row_piece(smem + SM::XS, tid, j);
+                const float xs4[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n = 4 * j + e;
+#pragma unroll
+                    for (int k = 0; k <= MB; ++k) pb[k] = fmaf(DFILT_EXT(n + k), xs4[e], pb[k]);
+#pragma unroll
+                    for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(n + 1 + k), yv[n], pa[k]);
+                }
+            }
+#undef DFILT_EXT
+            if (gzi && t == 0 && tid == 0) {
+#pragma unroll
+                for (int m = 0; m < MB; ++m)
+                    if (m < c.M) gzi[ch * bt.Mstride + m] = (m < c.len) ? u[m] : 0.f;
+            }
+            // warp reduction of the correlations, then into the CTA's FP64 accumulators
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                float v = k <= MB ? pb[k] : pa[k - MB - 1];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) sacc[warp * NACC + k] += (double)v;
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (gx) store_tile(gx, tstart, tlen, stag, gx_al && a4);
+            __syncthreads();
+        }
+        if (!alive) break;
+        // ---- channel done: coefficient gradients ----
+        for (int k = tid; k < NACC; k += kThreads) {
+            const double v = sacc[k] + sacc[NACC + k] + sacc[2 * NACC + k] + sacc[3 * NACC + k];
+            if (k <= MB) {
+                if (gb && k <= c.N) gb[ch * bt.Nstride + k] = (float)v;
+            } else {
+                const int m = k - MB - 1;
+                if (ga && m < c.M) ga[ch * bt.Mstride + m] = (float)(-v);
+            }
+        }
+        if (gzi && c.len == 0 && tid < c.M) gzi[ch * bt.Mstride + tid] = 0.f;
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 128);
+    }
+}
+
+template <int MB, bool F64, bool READ_Y>
+cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const float *b,
+                         const float *a, const float *saved, float *gx, float *gb, float *ga,
+                         float *gzi, const char *ws, const Batch &bt, int three, int num_sms,
+                         cudaStream_t st) {
+    using SM = BwdSmem<MB, F64, READ_Y>;
+    static_assert(SM::ALLOC <= 232448, "shared memory budget");
+    auto kern = chunk_bwd_kernel<MB, F64, READ_Y>;
+    static int occ[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        occ[dev] = o < 1 ? 1 : (o > 2 ? 2 : o);
+    }
+    const int64_t slots = (int64_t)num_sms * occ[dev];
+    const int64_t grid = bt.B < slots ? bt.B : slots;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int mask = (al(gy) ? 1 : 0) | (al(x) ? 2 : 0) | ((y && al(y)) ? 4 : 0) | ((gx && al(gx)) ? 8 : 0);
+    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
+    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws,
+                                                      counter, bt, three, mask);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <int MB>
+cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const float *b,
+                         const float *a, const float *saved, float *gx, float *gb, float *ga,
+                         float *gzi, const char *ws, const Batch &bt, bool fp64_scan, bool read_y,
+                         int three, int num_sms, cudaStream_t st) {
+#define ARGS gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st
+    if (read_y) {
+        if constexpr (MB <= 32) {
+            if (fp64_scan) return launch_bwd_t<MB, true, true>(ARGS);
+            if constexpr (MB <= kMaxF32ScanBucket) return launch_bwd_t<MB, false, true>(ARGS);
+        }
+        return cudaErrorNotSupported;
+    }
+    if (fp64_scan) return launch_bwd_t<MB, true, false>(ARGS);
+    if constexpr (MB <= kMaxF32ScanBucket) return launch_bwd_t<MB, false, false>(ARGS);
+    return cudaErrorNotSupported;
+#undef ARGS
+}
+
+template cudaError_t chunk_bwd_mb<DFILT_MB>(const float *, const float *, const float *,
+                                            const float *, const float *, const float *, float *,
+                                            float *, float *, float *, const char *, const Batch &,
+                                            bool, bool, int, int, cudaStream_t);
+
+}  // namespace dfilt

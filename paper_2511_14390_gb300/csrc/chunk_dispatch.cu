@@ -1,0 +1,95 @@
+// Host-side dispatch of the chunked algorithm: state-dimension bucket, scan precision,
+// workspace sizes, and the setup + main kernel launches per bucket.
+#include "chunk.cuh"
+
+namespace dfilt {
+
+#define DFILT_EXTERN(V)                                                                          \
+    extern template cudaError_t chunk_fwd_mb<V>(const float *, const float *, float *, float *, \
+                                                const char *, const Batch &, bool, int, int,    \
+                                                cudaStream_t);                                   \
+    extern template cudaError_t chunk_bwd_mb<V>(                                                 \
+        const float *, const float *, const float *, const float *, const float *,              \
+        const float *, float *, float *, float *, float *, const char *, const Batch &, bool,    \
+        bool, int, int, cudaStream_t);
+DFILT_CHUNK_BUCKETS(DFILT_EXTERN)
+#undef DFILT_EXTERN
+
+int chunk_bucket(int M) {
+    for (int mb : {2, 4, 8, 16, 32, 64})
+        if (M <= mb) return mb;
+    return -1;
+}
+
+ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt) {
+    ChunkLayout l;
+    l.MB = chunk_bucket(Mmax);
+    // FP32 powers of the chunk transition stay stable for low orders; above order 4 the
+    // transient growth of companion-matrix powers makes an FP32 scan diverge on some
+    // filters, so the automatic choice is the FP64 scan there (and it is the only one
+    // above the FP32 table bucket limit).
+    l.fp64_scan = fp64_scan_opt < 0 ? (Mmax > 4) : (fp64_scan_opt != 0);
+    if (l.MB > kMaxF32ScanBucket) l.fp64_scan = true;
+    size_t f = 0, b = 0;
+    switch (l.MB) {
+#define X(V)                                   \
+    case V:                                    \
+        f = ChunkTab<V>::fwd_rec(l.fp64_scan); \
+        b = ChunkTab<V>::bwd_rec(l.fp64_scan); \
+        break;
+        DFILT_CHUNK_BUCKETS(X)
+#undef X
+    }
+    l.fwd_tab = f;
+    l.bwd_tab = b;
+    return l;
+}
+
+size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan) {
+    return kWsHeader + (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).fwd_tab;
+}
+
+size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan) {
+    return kWsHeader + (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).bwd_tab;
+}
+
+cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
+                             float *y, float *saved, void *ws, const Batch &bt, int Mmax,
+                             bool fp64_scan, int precision, int num_sms, cudaStream_t st) {
+    const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
+    cudaError_t e = launch_chunk_setup(b, a, ws, bt, l.MB, l.fp64_scan, false, st);
+    if (e != cudaSuccess) return e;
+    const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
+    const char *w = static_cast<const char *>(ws);
+    switch (l.MB) {
+#define X(V) \
+    case V: return chunk_fwd_mb<V>(x, zi, y, saved, w, bt, l.fp64_scan, three, num_sms, st);
+        DFILT_CHUNK_BUCKETS(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
+                             const float *a, const float *saved, float *gx, float *gb, float *ga,
+                             float *gzi, void *ws, const Batch &bt, int Mmax, bool fp64_scan,
+                             int precision, int num_sms, cudaStream_t st) {
+    const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
+    const bool read_y = saved == nullptr;   // y is recomputed whenever the chunk states exist
+    if (read_y && (!y || l.MB > 32)) return cudaErrorNotSupported;
+    cudaError_t e = launch_chunk_setup(b, a, ws, bt, l.MB, l.fp64_scan, true, st);
+    if (e != cudaSuccess) return e;
+    const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
+    const char *w = static_cast<const char *>(ws);
+    switch (l.MB) {
+#define X(V)                                                                                   \
+    case V:                                                                                    \
+        return chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, bt, l.fp64_scan,     \
+                               read_y, three, num_sms, st);
+        DFILT_CHUNK_BUCKETS(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dfilt

@@ -1,0 +1,67 @@
+// Internal launchers shared between the kernel translation units and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dfilt {
+
+// ---- sequential algorithm (seq.cu) ----
+int seq_bucket(int M);
+cudaError_t launch_seq_fwd(const float *x, const float *b, const float *a, const float *zi,
+                           float *y, const Batch &bt, int Mmax, cudaStream_t st);
+cudaError_t launch_seq_bwd(const float *gy, const float *x, const float *y, const float *b,
+                           const float *a, float *gx, float *gb, float *ga, float *gzi,
+                           const Batch &bt, int Mmax, cudaStream_t st);
+
+// ---- chunked algorithm (chunk_*.cu) ----
+// Chunk length L and chunks per tensor-core tile are fixed: 64 samples x 128 chunks.
+constexpr int kL = 64;
+constexpr int kChunks = 128;
+constexpr int kTileSamples = kL * kChunks;
+
+// State-dimension bucket of the chunked kernels (M padded with zero coefficients).
+int chunk_bucket(int M);
+
+// Per-channel table sizes (floats / doubles) written by the setup kernels.
+struct ChunkLayout {
+    int MB;             // state bucket
+    bool fp64_scan;     // chunk-state scan precision
+    size_t fwd_tab;     // bytes of forward tables per channel
+    size_t bwd_tab;     // bytes of backward tables per channel
+};
+ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt);
+
+// Chunk-state buffer (`saved`): channel i's chunks start at chunk index
+// offsets[i] / L + i; each chunk stores Mstride floats.
+inline size_t chunk_saved_bytes(int64_t B, int64_t total, int Mstride) {
+    return (size_t)(total / kL + B + 1) * (size_t)Mstride * sizeof(float);
+}
+
+// Per-bucket launchers (one translation unit per bucket, compiled with -DDFILT_MB=<MB>).
+template <int MB>
+cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *ws,
+                         const Batch &bt, bool fp64_scan, int three, int num_sms, cudaStream_t st);
+template <int MB>
+cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const float *b,
+                         const float *a, const float *saved, float *gx, float *gb, float *ga,
+                         float *gzi, const char *ws, const Batch &bt, bool fp64_scan, bool read_y,
+                         int three, int num_sms, cudaStream_t st);
+#define DFILT_CHUNK_BUCKETS(X) X(2) X(4) X(8) X(16) X(32) X(64)
+// Largest bucket whose FP32 Hillis-Steele scan tables fit (and are used at all).
+constexpr int kMaxF32ScanBucket = 16;
+
+cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
+                             float *y, float *saved, void *ws, const Batch &bt, int Mmax,
+                             bool fp64_scan, int precision, int num_sms, cudaStream_t st);
+cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
+                             const float *a, const float *saved, float *gx, float *gb,
+                             float *ga, float *gzi, void *ws, const Batch &bt, int Mmax,
+                             bool fp64_scan, int precision, int num_sms, cudaStream_t st);
+size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
+size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
+
+}  // namespace dfilt

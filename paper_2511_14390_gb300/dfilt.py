@@ -1,0 +1,264 @@
+"""Thin Python binding of libdfilt.so (include/dfilt.h) plus a torch.autograd.Function.
+
+Argument marshalling only: every step of the filter and its gradients runs in the
+library's CUDA kernels.  PyTorch provides device memory and the current stream.
+There is no fallback: if the library is missing or a call fails, this module raises.
+
+Names follow the C ABI (``dfilt_forward``, ``dfilt_backward``, ...).  The operation
+(paper: Eq. rtf; gradients Sec. 3.1) is, per channel,
+    y[n] = sum_{k=0..N} b_k x[n-k] - sum_{k=1..M} a_k y[n-k]
+with the initial state zi in the transposed-direct-form-II convention.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfilt.so")
+
+ALGOS = {"auto": 0, "sequential": 1, "chunked": 2}
+PRECISIONS = {"fp32": 0, "tf32": 1, "tf32x3": 3}
+STATUS = {0: "DFILT_OK", 1: "DFILT_ERR_INVALID_ARG", 2: "DFILT_ERR_UNSUPPORTED",
+          3: "DFILT_ERR_CUDA", 4: "DFILT_ERR_TIMEOUT", 5: "DFILT_ERR_NUMERIC",
+          6: "DFILT_ERR_WORKSPACE"}
+EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_workspace_size",
+           "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
+           "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
+           "dfilt_set_wait_limit"]
+
+
+class DfiltError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int),
+                ("chunk_len", ctypes.c_int), ("fp64_scan", ctypes.c_int)]
+
+
+def make_opts(algo="auto", precision="tf32x3", fp64_scan=-1, chunk_len=0) -> Opts:
+    if isinstance(algo, str):
+        algo = ALGOS[algo]
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    if algo == ALGOS["sequential"]:
+        precision = PRECISIONS["fp32"]
+    return Opts(int(algo), int(precision), int(chunk_len), int(fp64_scan))
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libdfilt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2511_14390_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+            PO = ctypes.POINTER(Opts)
+            Psz = ctypes.POINTER(sz)
+            L.dfilt_version.restype = i32
+            L.dfilt_status_string.argtypes = [i32]
+            L.dfilt_status_string.restype = ctypes.c_char_p
+            L.dfilt_default_opts.argtypes = [PO]
+            L.dfilt_workspace_size.argtypes = [i64, i64, i32, i32, PO, Psz, Psz, Psz]
+            L.dfilt_workspace_size_ragged.argtypes = [i64, i64, i32, i32, PO, Psz, Psz, Psz]
+            L.dfilt_forward.argtypes = [P, P, P, P, P, P, P, sz, i64, i64, i32, i32, PO, P]
+            L.dfilt_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32,
+                                         i32, PO, P]
+            L.dfilt_forward_ragged.argtypes = [P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32,
+                                               i32, PO, P]
+            L.dfilt_backward_ragged.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, sz,
+                                                i64, i64, i32, i32, PO, P]
+            L.dfilt_sync_status.argtypes = [P]
+            L.dfilt_set_wait_limit.argtypes = [i64]
+            for name in EXPORTS:
+                getattr(L, name).restype = getattr(L, name).restype or i32
+            L.dfilt_status_string.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise DfiltError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    return t.contiguous()
+
+
+# ---------------------------------------------------------------------------
+# C-ABI wrappers (same names as include/dfilt.h)
+# ---------------------------------------------------------------------------
+
+def dfilt_workspace_size(B, T, N, M, opts: Opts | None = None):
+    o = opts or make_opts()
+    f, s, w = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().dfilt_workspace_size(B, T, N, M, ctypes.byref(o), ctypes.byref(f),
+                                      ctypes.byref(s), ctypes.byref(w)), "dfilt_workspace_size")
+    return f.value, s.value, w.value
+
+
+def dfilt_workspace_size_ragged(B, total, Nmax, Mmax, opts: Opts | None = None):
+    o = opts or make_opts()
+    f, s, w = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().dfilt_workspace_size_ragged(B, total, Nmax, Mmax, ctypes.byref(o),
+                                             ctypes.byref(f), ctypes.byref(s), ctypes.byref(w)),
+           "dfilt_workspace_size_ragged")
+    return f.value, s.value, w.value
+
+
+def _buf(nbytes, device):
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def dfilt_forward(x, b, a, zi=None, *, opts: Opts | None = None, y=None, saved=None, ws=None,
+                  want_saved=True, stream=None):
+    """y[B,T] (and the `saved` chunk-state buffer) for a fixed-shape batch."""
+    x, b, a, zi = _f32(x, "x"), _f32(b, "b"), _f32(a, "a"), _f32(zi, "zi")
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    o = opts or make_opts()
+    fws, sv, _ = dfilt_workspace_size(B, T, N, M, o)
+    y = torch.empty_like(x) if y is None else y
+    if want_saved and sv and saved is None:
+        saved = _buf(sv, x.device)
+    ws = _buf(fws, x.device) if ws is None else ws
+    _check(lib().dfilt_forward(_ptr(x), _ptr(b), _ptr(a), _ptr(zi), _ptr(y),
+                               _ptr(saved) if want_saved else None, _ptr(ws), ws.numel(),
+                               B, T, N, M, ctypes.byref(o), _stream(stream)), "dfilt_forward")
+    return y, (saved if want_saved and sv else None)
+
+
+def dfilt_backward(gy, x, y, b, a, zi=None, saved=None, *, opts: Opts | None = None,
+                   needs=(True, True, True, True), ws=None, stream=None):
+    """(grad_x, grad_b, grad_a, grad_zi); entries not in `needs` are None."""
+    gy, x, y = _f32(gy, "gy"), _f32(x, "x"), _f32(y, "y")
+    b, a = _f32(b, "b"), _f32(a, "a")
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    o = opts or make_opts()
+    _, _, bws = dfilt_workspace_size(B, T, N, M, o)
+    gx = torch.empty_like(x) if needs[0] else None
+    gb = torch.empty_like(b) if needs[1] else None
+    ga = torch.empty_like(a) if needs[2] else None
+    gzi = torch.empty((B, M), dtype=torch.float32, device=x.device) if needs[3] else None
+    ws = _buf(bws, x.device) if ws is None else ws
+    _check(lib().dfilt_backward(_ptr(gy), _ptr(x), _ptr(y), _ptr(b), _ptr(a), _ptr(zi),
+                                _ptr(saved), _ptr(gx), _ptr(gb), _ptr(ga), _ptr(gzi), _ptr(ws),
+                                ws.numel(), B, T, N, M, ctypes.byref(o), _stream(stream)),
+           "dfilt_backward")
+    return gx, gb, ga, gzi
+
+
+def dfilt_forward_ragged(x, offsets, Ms, Ns, b, a, zi=None, *, opts: Opts | None = None,
+                         y=None, saved=None, ws=None, want_saved=True, stream=None):
+    x, b, a, zi = _f32(x, "x"), _f32(b, "b"), _f32(a, "a"), _f32(zi, "zi")
+    B = Ms.shape[0]
+    total = x.shape[0]
+    Nmax, Mmax = b.shape[1] - 1, a.shape[1]
+    o = opts or make_opts()
+    fws, sv, _ = dfilt_workspace_size_ragged(B, total, Nmax, Mmax, o)
+    y = torch.empty_like(x) if y is None else y
+    if want_saved and sv and saved is None:
+        saved = _buf(sv, x.device)
+    ws = _buf(fws, x.device) if ws is None else ws
+    _check(lib().dfilt_forward_ragged(_ptr(x), _ptr(offsets), _ptr(Ms), _ptr(Ns), _ptr(b),
+                                      _ptr(a), _ptr(zi), _ptr(y),
+                                      _ptr(saved) if want_saved else None, _ptr(ws), ws.numel(),
+                                      B, total, Nmax, Mmax, ctypes.byref(o), _stream(stream)),
+           "dfilt_forward_ragged")
+    return y, (saved if want_saved and sv else None)
+
+
+def dfilt_backward_ragged(gy, x, y, offsets, Ms, Ns, b, a, zi=None, saved=None, *,
+                          opts: Opts | None = None, needs=(True, True, True, True), ws=None,
+                          stream=None):
+    gy, x, y = _f32(gy, "gy"), _f32(x, "x"), _f32(y, "y")
+    b, a = _f32(b, "b"), _f32(a, "a")
+    B = Ms.shape[0]
+    total = x.shape[0]
+    Nmax, Mmax = b.shape[1] - 1, a.shape[1]
+    o = opts or make_opts()
+    _, _, bws = dfilt_workspace_size_ragged(B, total, Nmax, Mmax, o)
+    gx = torch.empty_like(x) if needs[0] else None
+    gb = torch.zeros_like(b) if needs[1] else None
+    ga = torch.zeros_like(a) if needs[2] else None
+    gzi = torch.zeros((B, Mmax), dtype=torch.float32, device=x.device) if needs[3] else None
+    ws = _buf(bws, x.device) if ws is None else ws
+    _check(lib().dfilt_backward_ragged(_ptr(gy), _ptr(x), _ptr(y), _ptr(offsets), _ptr(Ms),
+                                       _ptr(Ns), _ptr(b), _ptr(a), _ptr(zi), _ptr(saved),
+                                       _ptr(gx), _ptr(gb), _ptr(ga), _ptr(gzi), _ptr(ws),
+                                       ws.numel(), B, total, Nmax, Mmax, ctypes.byref(o),
+                                       _stream(stream)), "dfilt_backward_ragged")
+    return gx, gb, ga, gzi
+
+
+def dfilt_sync_status(stream=None) -> int:
+    """Synchronise the stream; return (and clear) the device status word."""
+    return int(lib().dfilt_sync_status(_stream(stream)))
+
+
+def dfilt_set_wait_limit(iters: int):
+    _check(lib().dfilt_set_wait_limit(int(iters)), "dfilt_set_wait_limit")
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+class DFilt(torch.autograd.Function):
+    """y = DFilt.apply(x, b, a, zi, opts): batched direct-form filter whose backward
+    is the library's closed-form adjoint (Sec. 3.1).  zi may be None."""
+
+    @staticmethod
+    def forward(ctx, x, b, a, zi=None, opts: Opts | None = None):
+        opts = opts or make_opts()
+        y, saved = dfilt_forward(x, b, a, zi, opts=opts)
+        keep_y = saved is None   # without chunk states the backward re-reads y
+        ctx.opts = opts
+        ctx.has_zi = zi is not None
+        ctx.save_for_backward(x, b, a, zi if zi is not None else x.new_empty(0),
+                              saved if saved is not None else x.new_empty(0),
+                              y if keep_y else x.new_empty(0))
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, b, a, zi, saved, y = ctx.saved_tensors
+        needs = tuple(bool(v) for v in ctx.needs_input_grad[:4])
+        gx, gb, ga, gzi = dfilt_backward(gy.contiguous(), x, y if y.numel() else None, b, a,
+                                         zi if ctx.has_zi else None,
+                                         saved if saved.numel() else None, opts=ctx.opts,
+                                         needs=needs)
+        return gx, gb, ga, (gzi if ctx.has_zi else None), None
+
+
+def filt(x, b, a, zi=None, **opt_kwargs):
+    """Differentiable batched direct-form filter (see DFilt)."""
+    return DFilt.apply(x, b, a, zi, make_opts(**opt_kwargs) if opt_kwargs else None)

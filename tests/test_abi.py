@@ -1,0 +1,72 @@
+"""The C-ABI library: builds for sm_103a, loads, exports every symbol include/dfilt.h
+declares, and validates arguments on the host (no compute call without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2511_14390_gb300 import build as pkg_build
+from paper_2511_14390_gb300 import dfilt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    pkg_build.build()
+    return dfilt.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dfilt.h")).read()
+    return sorted(set(re.findall(r"\b(dfilt_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 11
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) == set(dfilt.EXPORTS)
+
+
+def test_host_only_calls(L):
+    assert L.dfilt_version() == 100
+    assert L.dfilt_status_string(4) == b"DFILT_ERR_TIMEOUT"
+    o = dfilt.Opts()
+    assert L.dfilt_default_opts(ctypes.byref(o)) == 0
+    assert (o.algo, o.precision, o.chunk_len, o.fp64_scan) == (0, 3, 0, -1)
+
+
+def test_workspace_sizes(L):
+    f, s, w = dfilt.dfilt_workspace_size(1024, 48000, 2, 2)
+    assert f > 0 and w > 0 and s >= 1024 * 48000 // 64 * 2 * 4
+    f, s, w = dfilt.dfilt_workspace_size(1024, 48000, 2, 2, dfilt.make_opts("sequential"))
+    assert (f, s, w) == (0, 0, 0)
+    f, s, w = dfilt.dfilt_workspace_size_ragged(4096, 10 ** 6, 32, 32)
+    assert f > 0 and s > 0 and w > 0
+
+
+@pytest.mark.parametrize("B,T,N,M,code", [(4, 10, 0, 65, 2), (4, 10, 3, 2, 1), (4, 10, 0, 0, 1),
+                                          (-1, 10, 0, 2, 1), (4, -5, 0, 2, 1)])
+def test_argument_errors(L, B, T, N, M, code):
+    o = dfilt.make_opts()
+    sz = ctypes.c_size_t()
+    assert L.dfilt_workspace_size(B, T, N, M, ctypes.byref(o), ctypes.byref(sz), None, None) == code
+    assert L.dfilt_forward(None, None, None, None, None, None, None, 0, B, T, N, M,
+                           ctypes.byref(o), None) == code
+
+
+def test_bad_options(L):
+    o = dfilt.make_opts(chunk_len=32)
+    sz = ctypes.c_size_t()
+    assert L.dfilt_workspace_size(4, 10, 0, 2, ctypes.byref(o), ctypes.byref(sz), None, None) == 2
+    o = dfilt.Opts(7, 3, 0, -1)
+    assert L.dfilt_workspace_size(4, 10, 0, 2, ctypes.byref(o), ctypes.byref(sz), None, None) == 1
+
+
+def test_missing_pointers_rejected(L):
+    o = dfilt.make_opts()
+    assert L.dfilt_forward(None, None, None, None, None, None, None, 0, 4, 10, 0, 2,
+                           ctypes.byref(o), None) == 1

@@ -1,0 +1,241 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Sizes span several kernel tiles (sequential: 32-sample tiles; chunked: 8192-sample
+tiles of 128 chunks x 64) with ragged tails; full-size cases compare sampled channels
+(each channel is independent, so the oracle recomputes only those)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_14390_gb300 import dfilt, inputs
+
+from tol import log_errors, rel_rows
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+OPTS = {
+    "seq": dict(algo="sequential"),
+    "chunk3": dict(algo="chunked", precision="tf32x3"),
+    "chunk1": dict(algo="chunked", precision="tf32"),
+}
+TOL = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": 5e-3}
+GTOL = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": 5e-3}
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run_fixed(w, mode, needs=(True, True, True, True)):
+    o = dfilt.make_opts(**OPTS[mode])
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o)
+    grads = dfilt.dfilt_backward(gy, x, None if saved is not None else y, b, a, zi, saved,
+                                 opts=o, needs=needs)
+    st = dfilt.dfilt_sync_status()
+    assert st == 0, dfilt.STATUS[st]
+    host = lambda t: None if t is None else t.cpu().numpy()
+    return host(y), [host(g) for g in grads]
+
+
+def oracle_fixed(w):
+    y = oracle.forward(w.x, w.b, w.a, w.zi)
+    return y, oracle.backward(w.gy, w.x, y, w.b, w.a)
+
+
+def check(name, mode, w, needs=(True, True, True, True), tol=None, gtol=None):
+    tol = TOL[mode] if tol is None else tol
+    gtol = GTOL[mode] if gtol is None else gtol
+    y, grads = run_fixed(w, mode, needs)
+    yr, gref = oracle_fixed(w)
+    errs = {"y": rel_rows(y, yr)}
+    for nm, g, r, nd in zip(["gx", "gb", "ga", "gzi"], grads, gref, needs):
+        if nd:
+            errs[nm] = rel_rows(g, r)
+    log_errors(f"{name}/{mode}", **errs)
+    assert errs["y"].max() < tol, (name, mode, "y", errs["y"].max())
+    for nm in ["gx", "gb", "ga", "gzi"]:
+        if nm in errs:
+            assert errs[nm].max() < gtol, (name, mode, nm, errs[nm].max())
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3", "chunk1"])
+def test_allpole2(mode):
+    w = inputs.make("allpole2_4x4096", B=8, T=3 * 8192 + 501)
+    check("allpole2", mode, w, needs=(True, False, True, False))
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3", "chunk1"])
+def test_biquad(mode):
+    w = inputs.make("biquad_1024x48000", B=40, T=2 * 8192 + 4321)
+    check("biquad", mode, w)
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+@pytest.mark.parametrize("M", [1, 3, 4, 5, 8, 13, 16, 17, 32, 40, 64])
+def test_orders_well_conditioned(mode, M):
+    """Every state bucket, at pole radii where the direct form is well conditioned."""
+    w = inputs.make("biquad_1024x48000", B=3, T=8192 + 333, M=M, N=M, seed=M)
+    rng = np.random.default_rng(100 + M)
+    for i in range(w.B):   # rescale to radius <= 0.7 (stable, modest conditioning)
+        a, _, _ = inputs.draw_denominator(rng, M, 0.3, 0.7)
+        w.a[i] = a
+        w.b[i] = inputs.draw_numerator(rng, M, True)
+    check(f"orders_M{M}", mode, w, tol=1e-4, gtol=1e-4)
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+def test_ragged(mode):
+    w = inputs.make_ragged(B=37, T_range=(1, 20000), M_range=(1, 6), seed=9)
+    # plant two empty channels
+    lens = np.diff(w.offsets)
+    lens[[3, 20]] = 0
+    offs = np.zeros_like(w.offsets)
+    offs[1:] = np.cumsum(lens)
+    x = np.concatenate([w.x[w.offsets[i]:w.offsets[i] + lens[i]] for i in range(w.B)])
+    gy = np.concatenate([w.gy[w.offsets[i]:w.offsets[i] + lens[i]] for i in range(w.B)])
+    o = dfilt.make_opts(**OPTS[mode])
+    dx, dgy = dev(x), dev(gy)
+    doffs, dMs, dNs = dev(offs), dev(w.Ms), dev(w.Ns)
+    db, da, dzi = dev(w.b), dev(w.a), dev(w.zi)
+    y, saved = dfilt.dfilt_forward_ragged(dx, doffs, dMs, dNs, db, da, dzi, opts=o)
+    g = dfilt.dfilt_backward_ragged(dgy, dx, None if saved is not None else y, doffs, dMs, dNs,
+                                    db, da, dzi, saved, opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    yr = oracle.forward_ragged(x, offs, w.Ms, w.Ns, w.b, w.a, w.zi)
+    gr = oracle.backward_ragged(gy, x, yr, offs, w.Ms, w.Ns, w.b, w.a)
+    y = y.cpu().numpy()
+    gx, gb, ga, gz = [t.cpu().numpy() for t in g]
+    for i in range(w.B):
+        s, e = offs[i], offs[i + 1]
+        M, N = int(w.Ms[i]), int(w.Ns[i])
+        if e > s:
+            assert rel_rows(y[s:e], yr[s:e])[0] < 1e-5, (mode, i)
+            assert rel_rows(gx[s:e], gr[0][s:e])[0] < 1e-5, (mode, i)
+            assert rel_rows(gb[i, :N + 1], gr[1][i, :N + 1])[0] < 1e-5, (mode, i)
+            assert rel_rows(ga[i, :M], gr[2][i, :M])[0] < 1e-5, (mode, i)
+            assert rel_rows(gz[i, :M], gr[3][i, :M])[0] < 1e-5, (mode, i)
+        else:
+            assert not gb[i].any() and not ga[i].any() and not gz[i].any()
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+@pytest.mark.parametrize("T,M,N", [(1, 2, 2), (3, 4, 1), (64, 2, 2), (65, 3, 3), (8192, 2, 0),
+                                   (8193, 2, 2)])
+def test_edge_lengths(mode, T, M, N):
+    w = inputs.make("biquad_1024x48000", B=5, T=T, M=M, N=N, seed=T)
+    check(f"edge_T{T}_M{M}", mode, w, tol=1e-5, gtol=2e-5)
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+def test_unaligned_buffers(mode):
+    """Channel starts that are not 16-byte aligned (T odd, base offset by one float)."""
+    w = inputs.make("biquad_1024x48000", B=5, T=9001)
+    o = dfilt.make_opts(**OPTS[mode])
+    big = torch.zeros(w.x.size + 1, device=DEV)
+    x = big[1:].view(w.B, 9001)
+    x.copy_(dev(w.x))
+    y, saved = dfilt.dfilt_forward(x, dev(w.b), dev(w.a), dev(w.zi), opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    yr = oracle.forward(w.x, w.b, w.a, w.zi)
+    assert rel_rows(y.cpu().numpy(), yr).max() < 1e-5
+
+
+def test_zero_sizes():
+    o = dfilt.make_opts()
+    e = torch.empty(0, 5, device=DEV)
+    y, _ = dfilt.dfilt_forward(e, torch.ones(0, 3, device=DEV), torch.zeros(0, 2, device=DEV), opts=o)
+    assert y.shape == (0, 5)
+    e = torch.empty(3, 0, device=DEV)
+    y, _ = dfilt.dfilt_forward(e, torch.ones(3, 3, device=DEV), torch.zeros(3, 2, device=DEV), opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+
+
+def test_full_size_biquad_sampled():
+    """The benchmark's workload (1024 x 48000 biquads) in the benchmark's launch
+    configuration; 12 sampled channels recomputed by the oracle."""
+    w = inputs.make("biquad_1024x48000")
+    y, grads = run_fixed(w, "chunk3")
+    idx = np.array([0, 1, 77, 255, 256, 511, 600, 767, 800, 1000, 1022, 1023])
+    sub = inputs.Workload(x=w.x[idx], b=w.b[idx], a=w.a[idx], zi=w.zi[idx], gy=w.gy[idx],
+                          M=w.M, N=w.N, radius=w.radius[idx])
+    yr, gr = oracle_fixed(sub)
+    errs = {"y": rel_rows(y[idx], yr)}
+    for nm, g, r in zip(["gx", "gb", "ga", "gzi"], grads, gr):
+        errs[nm] = rel_rows(g[idx], r)
+    log_errors("biquad_full_sampled/chunk3", **errs)
+    for nm, e in errs.items():
+        assert e.max() < 1e-5, (nm, e.max())
+
+
+def test_timeout_path_reports_status():
+    """A bounded device wait that runs out is reported, and the context stays usable."""
+    w = inputs.make("biquad_1024x48000", B=4, T=20000)
+    x, b, a, zi = dev(w.x), dev(w.b), dev(w.a), dev(w.zi)
+    o = dfilt.make_opts(algo="chunked")
+    try:
+        dfilt.dfilt_set_wait_limit(1)
+        dfilt.dfilt_forward(x, b, a, zi, opts=o)
+        assert dfilt.dfilt_sync_status() == 4
+    finally:
+        dfilt.dfilt_set_wait_limit(0)
+    y, _ = dfilt.dfilt_forward(x, b, a, zi, opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    assert rel_rows(y.cpu().numpy(), oracle.forward(w.x, w.b, w.a, w.zi)).max() < 1e-5
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+def test_autograd(mode):
+    w = inputs.make("biquad_1024x48000", B=6, T=10000)
+    x, b, a, zi = [dev(t).requires_grad_() for t in (w.x, w.b, w.a, w.zi)]
+    y = dfilt.filt(x, b, a, zi, **OPTS[mode])
+    (y * dev(w.gy)).sum().backward()
+    yr, (gx, gb, ga, gz) = oracle_fixed(w)
+    assert rel_rows(y.detach().cpu().numpy(), yr).max() < 1e-5
+    for t, r in [(x, gx), (b, gb), (a, ga), (zi, gz)]:
+        assert rel_rows(t.grad.cpu().numpy(), r).max() < 1e-5
+
+
+def test_cuda_graph_capture():
+    """Forward + backward captured once in a CUDA graph and replayed."""
+    w = inputs.make("biquad_1024x48000", B=16, T=20000)
+    o = dfilt.make_opts(algo="chunked")
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    B, T = w.x.shape
+    fws, sv, bws = dfilt.dfilt_workspace_size(B, T, w.N, w.M, o)
+    y = torch.empty_like(x)
+    saved = torch.empty(sv, dtype=torch.uint8, device=DEV)
+    ws1 = torch.empty(fws, dtype=torch.uint8, device=DEV)
+    ws2 = torch.empty(bws, dtype=torch.uint8, device=DEV)
+    gx, gb, ga, gz = (torch.empty_like(x), torch.empty_like(b), torch.empty_like(a),
+                      torch.empty_like(zi))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+
+    def step():
+        L = dfilt.lib()
+        st = dfilt._stream(s)
+        dfilt._check(L.dfilt_forward(dfilt._ptr(x), dfilt._ptr(b), dfilt._ptr(a), dfilt._ptr(zi),
+                                     dfilt._ptr(y), dfilt._ptr(saved), dfilt._ptr(ws1), fws, B, T,
+                                     w.N, w.M, dfilt.ctypes.byref(o), st), "fwd")
+        dfilt._check(L.dfilt_backward(dfilt._ptr(gy), dfilt._ptr(x), None, dfilt._ptr(b),
+                                      dfilt._ptr(a), dfilt._ptr(zi), dfilt._ptr(saved),
+                                      dfilt._ptr(gx), dfilt._ptr(gb), dfilt._ptr(ga),
+                                      dfilt._ptr(gz), dfilt._ptr(ws2), bws, B, T, w.N, w.M,
+                                      dfilt.ctypes.byref(o), st), "bwd")
+
+    with torch.cuda.stream(s):
+        step()                      # warm-up outside capture (kernel attributes)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        step()
+    y.zero_(); gx.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert dfilt.dfilt_sync_status() == 0
+    yr, (rx, rb, ra, rz) = oracle_fixed(w)
+    assert rel_rows(y.cpu().numpy(), yr).max() < 1e-5
+    assert rel_rows(gx.cpu().numpy(), rx).max() < 1e-5
+    assert rel_rows(gb.cpu().numpy(), rb).max() < 1e-5
