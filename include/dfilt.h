@@ -174,8 +174,14 @@ dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float 
 dfilt_status dfilt_sync_status(void *stream);
 
 /*
- * Test hook: cap every bounded device-side wait at `iters` polls (0 restores the
- * default cap).  Lets tests drive the timeout path without hanging a GPU.
+ * Test hook for the bounded device-side waits (no waits are unbounded).
+ *   iters > 0   cap every wait at `iters` polls
+ *   iters == 0  restore the default cap
+ *   iters < 0   timeout drill: cap at -iters polls and make each tensor-core kernel
+ *               additionally wait on a barrier that nothing ever signals, so the
+ *               timeout path (status word, drain of in-flight work, tensor-memory
+ *               release) runs deterministically without faulting or hanging the GPU.
+ * Applies to calls made after it on any thread of the process.
  */
 dfilt_status dfilt_set_wait_limit(int64_t iters);
 

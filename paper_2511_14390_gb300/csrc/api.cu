@@ -19,6 +19,7 @@ std::mutex g_mu;
 int *g_status_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 long long g_wait_limit = kDefaultWaitLimit;
+int g_stall_drill = 0;
 
 struct DevInfo {
     int *status;
@@ -110,7 +111,11 @@ Batch make_batch(const DevInfo &di, const int64_t *offsets, const int *Ms, const
     bt.Mstride = Mmax;
     bt.Nstride = Nmax + 1;
     bt.status = di.status;
-    bt.wait_limit = g_wait_limit;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        bt.wait_limit = g_wait_limit;
+        bt.stall_drill = g_stall_drill;
+    }
     return bt;
 }
 
@@ -283,9 +288,9 @@ dfilt_status dfilt_sync_status(void *stream) {
 }
 
 dfilt_status dfilt_set_wait_limit(int64_t iters) {
-    if (iters < 0) return DFILT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    g_wait_limit = iters == 0 ? kDefaultWaitLimit : (long long)iters;
+    g_stall_drill = iters < 0 ? 1 : 0;
+    g_wait_limit = iters == 0 ? kDefaultWaitLimit : (long long)(iters < 0 ? -iters : iters);
     return DFILT_OK;
 }
 

@@ -21,7 +21,7 @@ struct ChunkTab {
     static constexpr int MPAD = MB <= 16 ? 16 : (MB <= 32 ? 32 : 64);
     static constexpr int NFWD = kL + MPAD;          // forward MMA N: [T_g rows | R_L rows]
     static constexpr int NBWD = 2 * kL;             // backward MMA N: [T_g^a rows | T_h^a rows]
-    static constexpr int NPOW = 8;                  // Abar^(2^k), k < 8 (Hillis-Steele scan)
+    static constexpr int NPOW = 6;                  // Abar^(2^k), k < 6 (warp scan + carries)
 
     // forward record (bytes): g[L] f32 | RL[MB][L] f32 | OL[L][MB] f32 | scan block
     static constexpr size_t F_G = 0;

@@ -46,7 +46,7 @@ struct BwdSmem {
     static constexpr uint32_t COEF = (SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
     static constexpr uint32_t ACC = (COEF + 2 * (MB + 1) * 4 + 15) / 16 * 16;   // 4 x (2MB+1) doubles
     static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
-    static constexpr uint32_t BYTES = MISC + 32;
+    static constexpr uint32_t BYTES = MISC + 48;
     static constexpr uint32_t ALLOC = BYTES + 1024;
 };
 
@@ -176,8 +176,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_alloc(tmem_slot, 128);
         tmem_relinquish();
     }
+    uint64_t *mbar_dead = reinterpret_cast<uint64_t *>(smem + SM::MISC + 32);   // never signalled (timeout drill)
     if (tid == 0) {
         mbar_init(mbar, 1);
+        mbar_init(mbar_dead, 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -267,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 mma_commit(mbar);
                 bool ok = mbar_wait_bounded(mbar, phase, bt.wait_limit);
+                if (ok && bt.stall_drill) ok = mbar_wait_bounded(mbar_dead, 0, bt.wait_limit);
                 if (!ok) {
                     set_status(bt.status, DFILT_ERR_TIMEOUT);
                     mbar_wait_bounded(mbar, phase, kDefaultWaitLimit);
@@ -295,56 +298,61 @@ __global__ void __launch_bounds__(kThreads, 1)
             float S[MB];   // S'_c: adjoint values u[(c+1)L + m]
             float *xbuf = reinterpret_cast<float *>(smem + SM::ALO);
             if constexpr (!F64) {
-                // inclusive reverse Hillis-Steele: I'_c = sum_{j >= c} Abar'^(j-c) E'_j
+                // Two-level reverse scan.  (1) warp-local: W'_c = sum_{j=c..32w+31} Abar'^(j-c) E'_j
 #pragma unroll
-                for (int k = 0; k < 7; ++k) {
+                for (int k = 0; k < 5; ++k) {
                     const int d = 1 << k;
                     float nxt[MB];
-                    bool valid;
-                    if (d < 32) {
 #pragma unroll
-                        for (int m = 0; m < MB; ++m) nxt[m] = __shfl_down_sync(0xffffffffu, E[m], d);
-                        valid = lane + d < 32;
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
-                        __syncthreads();
-                        valid = tid + d < kChunks;
-#pragma unroll
-                        for (int m = 0; m < MB; ++m) nxt[m] = valid ? xbuf[(tid + d) * MB + m] : 0.f;
-                        __syncthreads();
-                    }
-                    if (valid) {
+                    for (int m = 0; m < MB; ++m) nxt[m] = __shfl_down_sync(0xffffffffu, E[m], d);
+                    if (lane + d < 32) {
                         float add[MB];
                         matvec_f32<MB>(sP + k * MB * MB, nxt, add);
 #pragma unroll
                         for (int m = 0; m < MB; ++m) E[m] += add[m];
                     }
                 }
+                // (2) carries from the right: C'_3 = S'_in, C'_{w-1} = Abar'^32 C'_w + W'_{32w}
+                // (state entering chunk 32w+31 from the right); the last one leaves the tile
+                if (lane == 0) {
 #pragma unroll
-                for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
+                    for (int m = 0; m < MB; ++m) xbuf[warp * MB + m] = E[m];
+                }
                 __syncthreads();
-                // S'_c = I'_{c+1} + Abar'^(127-c) S'_in
+                float C[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) C[m] = Sin[m];
+                for (int ww = kChunks / 32 - 1; ww >= 0; --ww) {
+                    if (ww == warp) {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) S[m] = C[m];
+                    }
+                    float w2[MB];
+                    matvec_f32<MB>(sP + 5 * MB * MB, C, w2);
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) C[m] = w2[m] + xbuf[ww * MB + m];
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = C[m];
+                // (3) state entering chunk c = 32w + l from the right: Abar'^(31-l) C'_w + W'_{c+1}
                 float v[MB];
 #pragma unroll
-                for (int m = 0; m < MB; ++m) v[m] = Sin[m];
-                const int e = kChunks - 1 - tid;
+                for (int m = 0; m < MB; ++m) v[m] = S[m];
+                const int e = 31 - lane;
 #pragma unroll
-                for (int k = 0; k < 7; ++k) {
+                for (int k = 0; k < 5; ++k) {
                     if ((e >> k) & 1) {
-                        float w[MB];
-                        matvec_f32<MB>(sP + k * MB * MB, v, w);
+                        float w2[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, v, w2);
 #pragma unroll
-                        for (int m = 0; m < MB; ++m) v[m] = w[m];
+                        for (int m = 0; m < MB; ++m) v[m] = w2[m];
                     }
                 }
 #pragma unroll
-                for (int m = 0; m < MB; ++m) S[m] = (tid + 1 < kChunks ? xbuf[(tid + 1) * MB + m] : 0.f) + v[m];
-                // state leaving the tile to the left: I'_0 + Abar'^128 S'_in
-                float w[MB];
-                matvec_f32<MB>(sP + 7 * MB * MB, Sin, w);
-#pragma unroll
-                for (int m = 0; m < MB; ++m) Sin[m] = xbuf[m] + w[m];
+                for (int m = 0; m < MB; ++m) {
+                    const float wnext = __shfl_down_sync(0xffffffffu, E[m], 1);
+                    S[m] = v[m] + (lane < 31 ? wnext : 0.f);
+                }
                 __syncthreads();
             } else {
                 float *sbuf = reinterpret_cast<float *>(smem + SM::AHI);

@@ -41,8 +41,8 @@ struct FwdSmem {
     static constexpr uint32_t OL = BLO + NM * 256;
     static constexpr uint32_t SCAN = OL + kL * MB * 4;
     static constexpr uint32_t MISC = (SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
-    // misc block: mbarrier (8) | tmem base (4) | channel (4) | flags (4) | pad | S_in (MB doubles)
-    static constexpr uint32_t BYTES = MISC + 32 + MB * 8;
+    // misc block: mbarrier (8) | tmem base (4) | channel (8) | flag (4) | drill mbarrier (8) | S_in (MB doubles)
+    static constexpr uint32_t BYTES = MISC + 48 + MB * 8;
     static constexpr uint32_t ALLOC = BYTES + 1024;   // slack for 1024-byte alignment
 };
 
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::MISC + 8);
     int64_t *ch_slot = reinterpret_cast<int64_t *>(smem + SM::MISC + 16);
     int *flag_slot = reinterpret_cast<int *>(smem + SM::MISC + 24);
-    double *sin_buf = reinterpret_cast<double *>(smem + SM::MISC + 32);
+    double *sin_buf = reinterpret_cast<double *>(smem + SM::MISC + 48);
     float *sOL = reinterpret_cast<float *>(smem + SM::OL);
     const float *sP = reinterpret_cast<const float *>(smem + SM::SCAN);
     const double *sAt = reinterpret_cast<const double *>(smem + SM::SCAN);
@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_alloc(tmem_slot, 128);
         tmem_relinquish();
     }
+    uint64_t *mbar_dead = reinterpret_cast<uint64_t *>(smem + SM::MISC + 32);   // never signalled (timeout drill)
     if (tid == 0) {
         mbar_init(mbar, 1);
+        mbar_init(mbar_dead, 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 mma_commit(mbar);
                 bool ok = mbar_wait_bounded(mbar, phase, bt.wait_limit);
+                if (ok && bt.stall_drill) ok = mbar_wait_bounded(mbar_dead, 0, bt.wait_limit);
                 if (!ok) {
                     set_status(bt.status, DFILT_ERR_TIMEOUT);
                     // drain: the MMAs still own tensor memory; wait for them before leaving
@@ -264,55 +267,61 @@ __global__ void __launch_bounds__(kThreads, 1)
             float S[MB];   // state entering this thread's chunk
             float *xbuf = reinterpret_cast<float *>(smem + SM::ALO);   // A tile is free now
             if constexpr (!F64) {
-                // inclusive Hillis-Steele scan over the 128 chunks (zero entry state)
+                // Two-level scan.  (1) warp-local inclusive Hillis-Steele over the warp's 32
+                // chunks: W_c = sum_{j=32w..c} Abar^(c-j) E_j;
 #pragma unroll
-                for (int k = 0; k < 7; ++k) {
+                for (int k = 0; k < 5; ++k) {
                     const int d = 1 << k;
                     float prev[MB];
-                    bool valid;
-                    if (d < 32) {
 #pragma unroll
-                        for (int m = 0; m < MB; ++m) prev[m] = __shfl_up_sync(0xffffffffu, E[m], d);
-                        valid = lane >= d;
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
-                        __syncthreads();
-                        valid = tid >= d;
-#pragma unroll
-                        for (int m = 0; m < MB; ++m) prev[m] = valid ? xbuf[(tid - d) * MB + m] : 0.f;
-                        __syncthreads();
-                    }
-                    if (valid) {
+                    for (int m = 0; m < MB; ++m) prev[m] = __shfl_up_sync(0xffffffffu, E[m], d);
+                    if (lane >= d) {
                         float add[MB];
                         matvec_f32<MB>(sP + k * MB * MB, prev, add);
 #pragma unroll
                         for (int m = 0; m < MB; ++m) E[m] += add[m];
                     }
                 }
-                // exclusive: I_{c-1}; plus the free evolution Abar^c S_in
+                // (2) carries: C_0 = S_in, C_{w+1} = Abar^32 C_w + W_{32w+31} (state entering
+                // chunk 32w); C_4 leaves the tile;
+                if (lane == 31) {
 #pragma unroll
-                for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
+                    for (int m = 0; m < MB; ++m) xbuf[warp * MB + m] = E[m];
+                }
                 __syncthreads();
+                float C[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) C[m] = Sin[m];
+                for (int ww = 0; ww < kChunks / 32; ++ww) {
+                    if (ww == warp) {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) S[m] = C[m];
+                    }
+                    float w2[MB];
+                    matvec_f32<MB>(sP + 5 * MB * MB, C, w2);
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) C[m] = w2[m] + xbuf[ww * MB + m];
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = C[m];
+                // (3) entry state of chunk c = 32w + l: Abar^l C_w + W_{c-1}
                 float v[MB];
 #pragma unroll
-                for (int m = 0; m < MB; ++m) v[m] = Sin[m];
+                for (int m = 0; m < MB; ++m) v[m] = S[m];
 #pragma unroll
-                for (int k = 0; k < 7; ++k) {
-                    if ((tid >> k) & 1) {
-                        float w[MB];
-                        matvec_f32<MB>(sP + k * MB * MB, v, w);
+                for (int k = 0; k < 5; ++k) {
+                    if ((lane >> k) & 1) {
+                        float w2[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, v, w2);
 #pragma unroll
-                        for (int m = 0; m < MB; ++m) v[m] = w[m];
+                        for (int m = 0; m < MB; ++m) v[m] = w2[m];
                     }
                 }
 #pragma unroll
-                for (int m = 0; m < MB; ++m) S[m] = (tid > 0 ? xbuf[(tid - 1) * MB + m] : 0.f) + v[m];
-                // tile exit state: I_127 + Abar^128 S_in (all threads compute it redundantly)
-                float w[MB];
-                matvec_f32<MB>(sP + 7 * MB * MB, Sin, w);
-#pragma unroll
-                for (int m = 0; m < MB; ++m) Sin[m] = xbuf[127 * MB + m] + w[m];
+                for (int m = 0; m < MB; ++m) {
+                    const float wprev = __shfl_up_sync(0xffffffffu, E[m], 1);
+                    S[m] = v[m] + (lane > 0 ? wprev : 0.f);
+                }
                 __syncthreads();
             } else {
                 // serial FP64 scan by warp 0: S_{c+1} = Abar S_c + E_c, state carried in FP64

@@ -36,6 +36,7 @@ struct Batch {
     int Mstride, Nstride;     // row strides of a/zi and b (Mmax, Nmax+1)
     int *status;              // device status word
     long long wait_limit;     // cap on polls of any bounded wait
+    int stall_drill;          // test mode: also wait on a barrier nothing signals
 };
 
 struct Channel {
