@@ -185,6 +185,28 @@ dfilt_status dfilt_sync_status(void *stream);
  */
 dfilt_status dfilt_set_wait_limit(int64_t iters);
 
+/*
+ * Forward filter that allocates nothing and takes no workspace (the paper has no
+ * counterpart; this is a deployment convenience).  For callers that must not
+ * allocate device memory while they run -- a real-time audio callback, where
+ * cudaMalloc/cudaFree can synchronise the device and stall for an unbounded time, or
+ * a host program without a device allocator to obtain a workspace from.
+ *   Arguments as dfilt_forward without `saved`, `ws` and `ws_bytes`; computes the
+ *   same y with the chunked algorithm (opts->algo must be AUTO or CHUNKED).
+ *   Scratch: a fixed 4 MiB device array inside this library (per GPU that loads it,
+ *   held until the process exits) instead of a caller workspace.  A batch whose
+ *   per-channel tables need more (dfilt_workspace_size's fwd_ws > 4 MiB, e.g. more
+ *   than 2730 channels at M <= 2, 63 channels at M = 64) is rejected with
+ *   DFILT_ERR_WORKSPACE before anything is launched.
+ *   The first call on each device looks up the array's address (one-time set-up);
+ *   make that first call before any stream capture.  All calls share the array:
+ *   calls whose work overlaps on the GPU (other streams or threads) race and must be
+ *   serialised by the caller.  Nothing needs clearing between calls.
+ */
+dfilt_status dfilt_forward_noalloc(const float *x, const float *b, const float *a,
+                                   const float *zi, float *y, int64_t B, int64_t T, int N, int M,
+                                   const dfilt_opts *opts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -152,6 +152,21 @@ dfilt_status do_backward(const float *gy, const float *x, const float *y, const 
 
 }  // namespace
 
+namespace dfilt {
+// Status word, SM count and wait settings of the current device, for entry points
+// defined in other translation units.
+bool api_launch_context(int **status, int *num_sms, long long *wait_limit, int *stall_drill) {
+    DevInfo di;
+    if (!dev_info(&di)) return false;
+    *status = di.status;
+    *num_sms = di.num_sms;
+    std::lock_guard<std::mutex> lk(g_mu);
+    *wait_limit = g_wait_limit;
+    *stall_drill = g_stall_drill;
+    return true;
+}
+}  // namespace dfilt
+
 extern "C" {
 
 int dfilt_version(void) { return 100; }

@@ -28,7 +28,7 @@ STATUS = {0: "DFILT_OK", 1: "DFILT_ERR_INVALID_ARG", 2: "DFILT_ERR_UNSUPPORTED",
 EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_workspace_size",
            "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
-           "dfilt_set_wait_limit"]
+           "dfilt_set_wait_limit", "dfilt_forward_noalloc"]
 
 
 class DfiltError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
                                                 i64, i64, i32, i32, PO, P]
             L.dfilt_sync_status.argtypes = [P]
             L.dfilt_set_wait_limit.argtypes = [i64]
+            L.dfilt_forward_noalloc.argtypes = [P, P, P, P, P, i64, i64, i32, i32, PO, P]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i32
             L.dfilt_status_string.restype = ctypes.c_char_p
@@ -217,6 +218,18 @@ def dfilt_backward_ragged(gy, x, y, offsets, Ms, Ns, b, a, zi=None, saved=None, 
                                        ws.numel(), B, total, Nmax, Mmax, ctypes.byref(o),
                                        _stream(stream)), "dfilt_backward_ragged")
     return gx, gb, ga, gzi
+
+
+def dfilt_forward_noalloc(x, b, a, zi=None, *, y, opts: Opts | None = None, stream=None):
+    """Forward into the caller's `y` with the library's fixed internal scratch: no
+    workspace and no device allocation by the library (see include/dfilt.h)."""
+    x, b, a, zi = _f32(x, "x"), _f32(b, "b"), _f32(a, "a"), _f32(zi, "zi")
+    B, T = x.shape
+    o = opts or make_opts()
+    _check(lib().dfilt_forward_noalloc(_ptr(x), _ptr(b), _ptr(a), _ptr(zi), _ptr(y), B, T,
+                                       b.shape[1] - 1, a.shape[1], ctypes.byref(o),
+                                       _stream(stream)), "dfilt_forward_noalloc")
+    return y
 
 
 def dfilt_sync_status(stream=None) -> int:
