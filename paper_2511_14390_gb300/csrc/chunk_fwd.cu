@@ -407,9 +407,19 @@ cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved
     if (!occ[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::ALLOC);
         if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, SM::ALLOC);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
+        int smem_sm = 0, smem_blk = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_blk, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        // CTAs per SM that the shared-memory budget allows (tensor memory allows 4 x 128
+        // columns; the register budget is checked by the occupancy query)
+        int o = smem_sm / (int)(SM::ALLOC + smem_blk);
+        int oq = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oq, kern, kThreads, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        if (oq > 0 && oq < o) o = oq;
         occ[dev] = o < 1 ? 1 : (o > 2 ? 2 : o);   // tensor memory: 128 columns per CTA
     }
     const int64_t slots = (int64_t)num_sms * occ[dev];
