@@ -22,7 +22,7 @@ UNITS = ([("api", "api.cu", []), ("seq", "seq.cu", []), ("chunk_setup", "chunk_s
           ("chunk_dispatch", "chunk_dispatch.cu", []), ("noalloc", "noalloc.cu", [])]
          + [(f"chunk_fwd_{m}", "chunk_fwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS]
          + [(f"chunk_bwd_{m}", "chunk_bwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS])
-HEADERS = ["common.cuh", "kernels.h", "chunk.cuh", "dword.cuh"]
+HEADERS = ["common.cuh", "kernels.h", "chunk.cuh", "chunk_pipe.cuh", "dword.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=true",
               "-I", os.path.join(ROOT, "include")]

@@ -14,7 +14,9 @@
 //      y recomputed from the forward's saved chunk state (or read), and the lag
 //      correlations grad_b[k] += sum u[n+k] x[n], grad_a[k] -= sum u[n+1+k] y[n]
 //      reduced warp-wise into per-CTA FP64 accumulators; grad_zi = u[0:M].
-#include "chunk.cuh"
+#include <cstring>
+
+#include "chunk_pipe.cuh"
 
 #ifndef DFILT_MB
 #error "compile once per state bucket with -DDFILT_MB=<2|4|8|16|32|64>"
@@ -541,6 +543,560 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
     return cudaGetLastError();
 }
 
+
+// ===========================================================================
+// Warp-specialised backward (state buckets whose layout fits), the forward's
+// pipeline structure run on reversed tiles:
+//   warps 0-2  converters: work (tiles of a channel from last to first), tables
+//              (B = T_h^a, O^u, scan block, coefficients; double-buffered by channel
+//              parity), gy tile -> stage s (TMA or cp.async) -> TF32 hi/lo -> full[s];
+//              L2 prefetch of the x tile the epilogue will read
+//   warp 3     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk)
+//   warps 4-7  epilogue: reverse chunk scan of S'_c = u[(c+1)L ..], u = D + O^u S',
+//              grad_x = sum_k b_k u[n+k] (FIR on the adjoint), y recomputed from the
+//              forward's saved chunk state, lag correlations reduced into per-warp FP64
+//              accumulators; grad_x leaves through per-warp staging, coalesced
+// A stage is free as soon as its MMA completed (the epilogue only reads TMEM).
+// ===========================================================================
+
+template <int MB, bool F64>
+struct BwSmem {
+    using Tab = ChunkTab<MB>;
+    static constexpr int NM = kL;                                    // MMA N: T_h^a rows
+    static constexpr uint32_t STAGE = 2 * pipe::kTileBytes;          // hi | lo
+    static constexpr uint32_t TAB0 = 2 * STAGE;
+    static constexpr uint32_t T_BHI = 0;
+    static constexpr uint32_t T_BLO = NM * 256;
+    static constexpr uint32_t T_OU = 2 * NM * 256;
+    static constexpr uint32_t T_SCAN = T_OU + kL * MB * 4;
+    static constexpr uint32_t T_COEF = (T_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
+    static constexpr uint32_t TSLOT = (T_COEF + (2 * MB + 1) * 4 + 1023) / 1024 * 1024;
+    static constexpr uint32_t STG = TAB0 + 2 * TSLOT;                // 4 x 2 KB warp staging
+    // FP64 reverse scan scratch (E' and S' per chunk); the stages may be refilled meanwhile
+    static constexpr uint32_t SCR = STG + 4 * 2048;
+    static constexpr uint32_t ACC = SCR + (F64 ? 2 * kChunks * MB * 4 : 0);   // 4 x (2MB+1) doubles
+    static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
+    static constexpr uint32_t M_BAR = MISC;                          // 14 barriers
+    static constexpr uint32_t M_TMEM = MISC + 112;
+    static constexpr uint32_t M_ABORT = MISC + 116;
+    static constexpr uint32_t M_OK = MISC + 120;
+    static constexpr uint32_t M_WT = MISC + 128;
+    static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
+    static constexpr uint32_t BYTES = M_RING + 8 * 48;
+    static constexpr uint32_t ALLOC = BYTES + 1024;
+};
+
+template <int MB, bool F64>
+__global__ void __launch_bounds__(pipe::kPipeThreads, 1)
+    chunk_bwd_ws_kernel(const float *__restrict__ gy, const float *__restrict__ x,
+                        const float *__restrict__ bco, const float *__restrict__ aco,
+                        const float *__restrict__ saved,
+                        float *__restrict__ gx, float *__restrict__ gb, float *__restrict__ ga,
+                        float *__restrict__ gzi, const char *__restrict__ ws,
+                        unsigned long long *__restrict__ counter, Batch bt, int three, int al_mask,
+                        int use_tma, const __grid_constant__ CUtensorMap tmg) {
+    using namespace pipe;
+    using Tab = ChunkTab<MB>;
+    using SM = BwSmem<MB, F64>;
+    constexpr int NM = SM::NM;
+    constexpr int NACC = 2 * MB + 1;
+    extern __shared__ char smem_raw[];
+    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
+    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *tab_free = bars + 8,
+             *load_bar = bars + 10, *dead = bars + 12, *drain = bars + 13;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
+    volatile int *conv_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK);
+    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 4);
+    float *wt = reinterpret_cast<float *>(smem + SM::M_WT);
+    double *acc_s = reinterpret_cast<double *>(smem + SM::ACC);
+    TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool gy_al = al_mask & 1, x_al = al_mask & 2, gx_al = al_mask & 8;
+
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, 256);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 14; ++i) mbar_init(&bars[i], (i == 2 || i == 3) ? 2 : 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    for (int i = tid; i < 4 * NACC; i += kPipeThreads) acc_s[i] = 0.0;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const size_t rec = Tab::bwd_rec(F64);
+    constexpr uint32_t idesc = idesc_tf32_m128(NM);
+    auto stage_hi = [&](int s) { return (uint32_t)(s * SM::STAGE); };
+    auto stage_lo = [&](int s) { return (uint32_t)(s * SM::STAGE + kTileBytes); };
+    auto tslot = [&](int p) { return (uint32_t)(SM::TAB0 + p * SM::TSLOT); };
+    auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
+        return wait_or_abort(bar, parity, bt.wait_limit, abort_flag, bt.status);
+    };
+
+    if (warp < kMmaWarp) {
+        // ============================ converters ============================
+        const int ct = tid;
+        int64_t cur_ch = -1, cur_t = 0, cur_nt = 0, cur_off = 0, cur_len = 0;
+        int cur_M = 1, ch_seq = -1;
+        // thread 0: describe the next tile into `d` (published to the ring by the caller)
+        auto next_desc = [&](TileDesc &d) {
+            while (cur_ch < 0 || cur_t >= cur_nt) {
+                const int64_t c = (int64_t)atomicAdd(counter, 1ull);
+                if (c >= bt.B) {
+                    d.ch = -1;
+                    return;
+                }
+                const Channel cc = channel_of(bt, c);
+                cur_ch = c;
+                cur_t = 0;
+                cur_off = cc.off;
+                cur_len = cc.len;
+                cur_M = cc.M;
+                cur_nt = (cc.len + kTileSamples - 1) / kTileSamples;
+                if (cur_nt == 0) {
+                    // an empty channel still owes zero coefficient gradients
+                    const Channel z = cc;
+                    for (int k = 0; k <= z.N; ++k)
+                        if (gb) gb[c * bt.Nstride + k] = 0.f;
+                    for (int k = 0; k < z.M; ++k) {
+                        if (ga) ga[c * bt.Mstride + k] = 0.f;
+                        if (gzi) gzi[c * bt.Mstride + k] = 0.f;
+                    }
+                    continue;
+                }
+                ++ch_seq;
+            }
+            const int64_t t = cur_nt - 1 - cur_t;   // reversed time
+            d.ch = cur_ch;
+            d.tstart = cur_off + t * kTileSamples;
+            d.tlen = (int)(cur_len - t * kTileSamples < kTileSamples ? cur_len - t * kTileSamples
+                                                                     : kTileSamples);
+            d.chunk0 = cur_off / kL + cur_ch + t * kChunks;
+            d.tab = ch_seq & 1;
+            d.first = cur_t == 0;
+            d.M = cur_M;
+            ++cur_t;
+            d.last = cur_t == cur_nt;
+        };
+        auto build_tables = [&](const TileDesc &d) {
+            const char *R = ws + kWsHeader + (size_t)d.ch * rec;
+            const float *__restrict__ h = reinterpret_cast<const float *>(R + Tab::B_H);
+            char *T = smem + tslot(d.tab);
+            // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, half of the rows)
+            for (int item = ct; item < 128; item += kConvThreads) {
+                const int k = item & 63, hh = item >> 6;
+                float hv[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int r = 32 * hh + q;
+                    hv[q] = k >= r ? __ldg(h + (k - r)) : 0.f;
+                }
+                const uint32_t kb = (k >> 5) * (NM * 128);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int r = 32 * hh + q;
+                    float hi, lo;
+                    split_tf32(hv[q], hi, lo);
+                    const uint32_t o = kb + sw128_off(r, k & 31);
+                    *reinterpret_cast<float *>(T + SM::T_BHI + o) = hi;
+                    *reinterpret_cast<float *>(T + SM::T_BLO + o) = lo;
+                }
+            }
+            const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
+            float4 *sOu = reinterpret_cast<float4 *>(T + SM::T_OU);
+            for (int idx = ct; idx < kL * MB / 4; idx += kConvThreads) sOu[idx] = __ldg(Ou + idx);
+            const float4 *src = reinterpret_cast<const float4 *>(R + Tab::B_SCAN);
+            float4 *dst = reinterpret_cast<float4 *>(T + SM::T_SCAN);
+            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kConvThreads) dst[idx] = __ldg(src + idx);
+            float *coef = reinterpret_cast<float *>(T + SM::T_COEF);   // a[0..MB) | b[0..MB]
+            const Channel c = channel_of(bt, d.ch);
+            if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
+            if (ct <= MB) coef[MB + ct] = ct <= c.N ? bco[d.ch * bt.Nstride + ct] : 0.f;
+        };
+        auto issue_load = [&](const TileDesc &d, int s) {
+            if (use_tma) {
+                if (ct == 0) {
+                    mbar_arrive_expect_tx(&load_bar[s], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + stage_hi(s), &tmg, 0, 0, row, &load_bar[s]);
+                    tma_load_3d(sbase + stage_hi(s) + kKBlock, &tmg, 0, 1, row, &load_bar[s]);
+                }
+            } else {
+                load_tile_async<kConvThreads>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
+                                              gy_al && ((d.tstart & 3) == 0), ct);
+            }
+            // warm L2 with the x tile the epilogue reads (full aligned tiles only)
+            if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(x + d.tstart),
+                             "r"((uint32_t)kTileBytes)
+                             : "memory");
+        };
+
+        if (ct == 0) {
+            TileDesc d0;
+            next_desc(d0);
+            ring[0] = d0;
+        }
+        named_sync(kNamedConv, kConvThreads);
+        {
+            const TileDesc d0 = ring[0];
+            if (d0.ch >= 0) {
+                build_tables(d0);
+                issue_load(d0, 0);
+            } else if (ct == 0) {
+                mbar_arrive(&full[0]);
+            }
+        }
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const TileDesc d = ring[i & 7];
+            if (d.ch < 0) break;
+            if (ct == 0) {
+                bool ok = true;
+                if (use_tma) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
+                *conv_ok = ok ? 1 : 0;
+            }
+            if (!use_tma) cp_async_wait_all();
+            named_sync(kNamedConv, kConvThreads);
+            if (!*conv_ok) break;
+            split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen, three != 0, ct);
+            fence_proxy_async_smem();
+            named_sync(kNamedConv, kConvThreads);
+            if (ct == 0) mbar_arrive(&full[s]);
+            if (ct == 0) {
+                TileDesc nd;
+                next_desc(nd);
+                bool ok = true;
+                if (nd.ch >= 0 && nd.first && ch_seq >= 2)
+                    ok = wait1(&tab_free[nd.tab], (uint32_t)(((ch_seq >> 1) - 1) & 1));
+                // MMA(i-1) complete: stage s^1 is free, and (through its wait on the TMEM
+                // buffer) the epilogue has finished tile i-3, whose ring slot is reused
+                if (ok && i >= 1) ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
+                ring[(i + 1) & 7] = nd;
+                *conv_ok = ok ? 1 : 0;
+            }
+            named_sync(kNamedConv, kConvThreads);
+            if (!*conv_ok) break;
+            const TileDesc dn = ring[(i + 1) & 7];
+            if (dn.ch < 0) {
+                if (ct == 0) mbar_arrive(&full[s ^ 1]);
+                break;
+            }
+            if (dn.first) build_tables(dn);
+            issue_load(dn, s ^ 1);
+        }
+    } else if (warp == kMmaWarp) {
+        // ============================ MMA issuer ============================
+        bool issued = false;
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            int ok = 1;
+            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            const TileDesc d = ring[i & 7];
+            // TMEM buffer s free (epilogue done with tile i-2); the end marker waits too,
+            // or its arrivals could complete a second phase of mma_done[s] before the
+            // epilogue has observed tile i-2's (a parity wait cannot tell them apart)
+            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[s], par ^ 1u) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            if (d.ch < 0) {
+                if (lane == 0) {
+                    mbar_arrive(&mma_done[s]);
+                    mbar_arrive(&mma_done[s]);
+                }
+                break;
+            }
+            if (lane == 0) {
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
+                const uint32_t tb = tslot(d.tab);
+#pragma unroll
+                for (int kk = 0; kk < kL / 8; ++kk) {
+                    const uint32_t ka = (kk >> 2) * kKBlock + (kk & 3) * 32;
+                    const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
+                    const uint64_t ahi = sdesc_sw128(sbase + stage_hi(s) + ka);
+                    const uint64_t bhi = sdesc_sw128(sbase + tb + SM::T_BHI + kb);
+                    mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    if (three) {
+                        const uint64_t alo = sdesc_sw128(sbase + stage_lo(s) + ka);
+                        const uint64_t blo = sdesc_sw128(sbase + tb + SM::T_BLO + kb);
+                        mma_tf32(d_tmem, ahi, blo, idesc, 1u);
+                        mma_tf32(d_tmem, alo, bhi, idesc, 1u);
+                    }
+                }
+                mma_commit(&mma_done[s]);
+                mbar_arrive(&mma_done[s]);
+            }
+            issued = true;
+            if (bt.stall_drill) {
+                if (lane == 0) wait1(dead, 0);
+                __syncwarp();
+                break;
+            }
+        }
+        if (lane == 0 && issued) {
+            mma_commit(drain);
+            mbar_wait_bounded(drain, 0, kDefaultWaitLimit);
+        }
+        __syncwarp();
+    } else {
+        // ============================ epilogue ==============================
+        const int et = tid - kEpiWarp0 * 32;
+        const int ew = warp - kEpiWarp0;
+        const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+        char *stag = smem + SM::STG + ew * 2048;
+        float Sin[MB];   // state entering the tile from the right
+        double S64a = 0.0, S64b = 0.0;
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            if (et == 0) *epi_ok = wait1(&mma_done[s], par) ? 1 : 0;
+            named_sync(kNamedEpi, 128);
+            if (!*epi_ok) break;
+            tc_fence_after();
+            const TileDesc pv = ring[i & 7];
+            if (pv.ch < 0) break;
+            const char *T = smem + tslot(pv.tab);
+            const float *sOu = reinterpret_cast<const float *>(T + SM::T_OU);
+            const float *sP = reinterpret_cast<const float *>(T + SM::T_SCAN);
+            const double *sAt = reinterpret_cast<const double *>(T + SM::T_SCAN);
+            const float *coef = reinterpret_cast<const float *>(T + SM::T_COEF);
+            const int nch = (pv.tlen + kL - 1) / kL;
+            const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
+            if (pv.first) {   // the channel's last tile in time: nothing to its right
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
+                S64a = S64b = 0.0;
+            }
+            float E[MB];
+            {
+                float v[16];
+                tmem_ld16(taddr, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int m = 0; m < MB; ++m) E[m] = v[m];
+            }
+            float S[MB];   // S'_c = u[(c+1)L + m]
+            if constexpr (!F64) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int dd = 1 << k;
+                    float nx[MB];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) nx[m] = __shfl_down_sync(0xffffffffu, E[m], dd);
+                    if (lane + dd < 32) {
+                        float add[MB];
+                        matvec<MB>(sP + k * MB * MB, nx, add);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) E[m] += add[m];
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) wt[ew * MB + m] = E[m];
+                }
+                named_sync(kNamedEpi, 128);
+                float C[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) C[m] = Sin[m];
+#pragma unroll
+                for (int ww = 3; ww >= 0; --ww) {
+                    if (ww == ew) {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) S[m] = C[m];
+                    }
+                    float w2[MB];
+                    matvec<MB>(sP + 5 * MB * MB, C, w2);
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) C[m] = w2[m] + wt[ww * MB + m];
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = C[m];
+                float v[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) v[m] = S[m];
+                const int e = 31 - lane;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if ((e >> k) & 1) {
+                        float w2[MB];
+                        matvec<MB>(sP + k * MB * MB, v, w2);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) v[m] = w2[m];
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    const float wn = __shfl_down_sync(0xffffffffu, E[m], 1);
+                    S[m] = v[m] + (lane < 31 ? wn : 0.f);
+                }
+                named_sync(kNamedEpi, 128);
+            } else {
+                // serial FP64 reverse scan by the first epilogue warp
+                float *xbuf = reinterpret_cast<float *>(smem + SM::SCR);
+                float *sbuf = xbuf + kChunks * MB;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
+                named_sync(kNamedEpi, 128);
+                if (ew == 0) {
+                    for (int cc = nch - 1; cc >= 0; --cc) {
+                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
+                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
+                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
+#pragma unroll 8
+                        for (int j = 0; j < MB; ++j) {
+                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
+                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
+                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
+                        }
+                        S64a = acc_a;
+                        S64b = acc_b;
+                    }
+                }
+                named_sync(kNamedEpi, 128);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) S[m] = et < nch ? sbuf[et * MB + m] : 0.f;
+                named_sync(kNamedEpi, 128);
+            }
+            // adjoint u for this chunk (TMEM zero-state part + free response)
+            float u[kL];
+#pragma unroll
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int n = cb * 16 + q;
+                    float a = v[q];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) a = fmaf(sOu[n * MB + m], S[m], a);
+                    u[n] = a;
+                }
+            }
+            tc_fence_before();
+            named_sync(kNamedEpi, 128);
+            if (et == 0) mbar_arrive(&tmem_free[s]);
+            if (gzi && pv.last && et == 0) {
+#pragma unroll
+                for (int m = 0; m < MB; ++m)
+                    if (m < pv.M) gzi[pv.ch * bt.Mstride + m] = u[m];
+            }
+#define DFILT_EXT(n) ((n) < kL ? u[(n)] : S[(n) - kL])
+            // grad_x = sum_k b_k u[n+k]
+            float w[kL];
+#pragma unroll
+            for (int n = 0; n < kL; ++n) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k <= MB; ++k) a = fmaf(coef[MB + k], DFILT_EXT(n + k), a);
+                w[n] = a;
+            }
+            if (gx)
+                warp_store_rows(w, stag, gx, pv.tstart, ew * 32, pv.tlen, gx_al && ((pv.tstart & 3) == 0), lane);
+            // x rows, then y recomputed from the forward's chunk state, fused with the
+            // lag correlations grad_b[k] += u[n+k] x[n], grad_a[k] -= u[n+1+k] y[n]
+            warp_load_rows(w, stag, x, pv.tstart, ew * 32, pv.tlen, x_al && ((pv.tstart & 3) == 0), lane);
+            float st[MB];
+            {
+                const bool vch = et < nch;
+                const float *src = saved + (size_t)(pv.chunk0 + et) * bt.Mstride;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) st[m] = (vch && m < pv.M) ? src[m] : 0.f;
+            }
+            float pb[MB + 1], pa[MB];
+#pragma unroll
+            for (int k = 0; k <= MB; ++k) pb[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < MB; ++k) pa[k] = 0.f;
+#pragma unroll
+            for (int n = 0; n < kL; ++n) {
+                const float xn = w[n];
+                const float yn = fmaf(coef[MB], xn, st[0]);
+#pragma unroll
+                for (int k = 0; k < MB; ++k)
+                    st[k] = fmaf(-coef[k], yn, fmaf(coef[MB + 1 + k], xn, k + 1 < MB ? st[k + 1] : 0.f));
+#pragma unroll
+                for (int k = 0; k <= MB; ++k) pb[k] = fmaf(DFILT_EXT(n + k), xn, pb[k]);
+#pragma unroll
+                for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(n + 1 + k), yn, pa[k]);
+            }
+#undef DFILT_EXT
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                float v = k <= MB ? pb[k] : pa[k - MB - 1];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) acc_s[ew * NACC + k] += (double)v;
+            }
+            if (pv.last) {
+                named_sync(kNamedEpi, 128);
+                const Channel c = channel_of(bt, pv.ch);
+                for (int k = et; k < NACC; k += 128) {
+                    const double v = acc_s[k] + acc_s[NACC + k] + acc_s[2 * NACC + k] + acc_s[3 * NACC + k];
+                    if (k <= MB) {
+                        if (gb && k <= c.N) gb[pv.ch * bt.Nstride + k] = (float)v;
+                    } else {
+                        const int m = k - MB - 1;
+                        if (ga && m < c.M) ga[pv.ch * bt.Mstride + m] = (float)(-v);
+                    }
+                }
+                named_sync(kNamedEpi, 128);
+                for (int k = et; k < 4 * NACC; k += 128) acc_s[k] = 0.0;
+                named_sync(kNamedEpi, 128);
+                if (et == 0) mbar_arrive(&tab_free[pv.tab]);
+            }
+        }
+    }
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+template <int MB, bool F64>
+cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
+                          const float *a, const float *saved, float *gx, float *gb, float *ga,
+                          float *gzi, const char *ws, const Batch &bt, int three, int num_sms,
+                          cudaStream_t st) {
+    using SM = BwSmem<MB, F64>;
+    static_assert(SM::ALLOC <= pipe::kSmemMax, "shared memory budget");
+    auto kern = chunk_bwd_ws_kernel<MB, F64>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t grid = bt.B < num_sms ? bt.B : num_sms;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int mask = (al(gy) ? 1 : 0) | (al(x) ? 2 : 0) | ((gx && al(gx)) ? 8 : 0);
+    CUtensorMap tmg;
+    std::memset(&tmg, 0, sizeof(tmg));
+    int use_tma = 0;
+    if (!bt.offsets && bt.T % kL == 0 && make_chunk_tmap(&tmg, gy, bt.total)) use_tma = 1;
+    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
+    kern<<<(unsigned)grid, pipe::kPipeThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, counter,
+                                                       bt, three, mask, use_tma, tmg);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <int MB>
@@ -549,6 +1105,13 @@ cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const 
                          float *gzi, const char *ws, const Batch &bt, bool fp64_scan, bool read_y,
                          int three, int num_sms, cudaStream_t st) {
 #define ARGS gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st
+    if constexpr (MB <= 8) {
+        // warp-specialised kernel (recomputes y from the saved chunk states)
+        if (!read_y) {
+            if (fp64_scan) return launch_bwd_ws<MB, true>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st);
+            return launch_bwd_ws<MB, false>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st);
+        }
+    }
     if (read_y) {
         if constexpr (MB <= 32) {
             if (fp64_scan) return launch_bwd_t<MB, true, true>(ARGS);

@@ -1,5 +1,8 @@
 // Host-side dispatch of the chunked algorithm: state-dimension bucket, scan precision,
 // workspace sizes, and the setup + main kernel launches per bucket.
+#include <cudaTypedefs.h>
+#include <mutex>
+
 #include "chunk.cuh"
 
 namespace dfilt {
@@ -14,6 +17,32 @@ namespace dfilt {
         bool, int, int, cudaStream_t);
 DFILT_CHUNK_BUCKETS(DFILT_EXTERN)
 #undef DFILT_EXTERN
+
+bool make_chunk_tmap(CUtensorMap *map, const float *base, int64_t total) {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode || !base || total <= 0 || total % kL != 0) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t rows = (cuuint64_t)(total / kL);
+    if (rows > 0xFFFFFFFFull) return false;
+    const cuuint64_t dims[3] = {32, 2, rows};
+    const cuuint64_t strides[2] = {128, kL * 4};
+    const cuuint32_t box[3] = {32, 1, (cuuint32_t)kChunks};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base),
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 int chunk_bucket(int M) {
     for (int mb : {2, 4, 8, 16, 32, 64})

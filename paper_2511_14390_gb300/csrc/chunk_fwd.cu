@@ -16,7 +16,9 @@
 //      where FP32 powers lose stability (high-order filters);
 //   4. epilogue: y = D + O_L S_c, staged through shared memory and stored coalesced;
 //      the chunk entry states go to `saved` for the backward's recomputation of y.
-#include "chunk.cuh"
+#include <cstring>
+
+#include "chunk_pipe.cuh"
 
 #ifndef DFILT_MB
 #error "compile once per state bucket with -DDFILT_MB=<2|4|8|16|32|64>"
@@ -27,6 +29,7 @@ namespace dfilt {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr uint32_t kSmemMax = 232448;               // opt-in shared memory per block
 constexpr uint32_t kTileBytes = kChunks * kL * 4;   // 32 KB
 constexpr uint32_t kKBlock = kChunks * 128;         // one 32-wide K block of the A operand
 
@@ -47,12 +50,13 @@ struct FwdSmem {
 };
 
 // Load samples [start, start+n) of src into the swizzled A tile at `dst` (2 K blocks),
-// zero-filling past n.  Thread t handles the 16-byte pieces t, t+128, ...
+// zero-filling past n.  Thread t of NT handles the 16-byte pieces t, t+NT, ...
+template <int NT = kThreads>
 __device__ __forceinline__ void load_tile(uint32_t dst, const float *src, int64_t start, int n,
                                           bool al16) {
 #pragma unroll 4
-    for (int q = 0; q < 16; ++q) {
-        const int id = threadIdx.x + kThreads * q;
+    for (int q = 0; q < 2048 / NT; ++q) {
+        const int id = threadIdx.x + NT * q;
         const int r = id >> 4, j16 = id & 15;
         const uint32_t d = dst + (j16 >> 3) * kKBlock + r * 128 + ((((j16 & 7) ^ (r & 7))) << 4);
         const int s = r * kL + j16 * 4;
@@ -70,10 +74,11 @@ __device__ __forceinline__ void load_tile(uint32_t dst, const float *src, int64_
 }
 
 // Split this thread's pieces of the A tile into TF32 hi (in place) and lo (at +lo_off).
+template <int NT = kThreads>
 __device__ __forceinline__ void split_tile(char *smem, uint32_t a_off, uint32_t lo_off, bool three) {
 #pragma unroll 4
-    for (int q = 0; q < 16; ++q) {
-        const int id = threadIdx.x + kThreads * q;
+    for (int q = 0; q < 2048 / NT; ++q) {
+        const int id = threadIdx.x + NT * q;
         const int r = id >> 4, j16 = id & 15;
         const uint32_t o = a_off + (j16 >> 3) * kKBlock + r * 128 + ((((j16 & 7) ^ (r & 7))) << 4);
         float4 v = *reinterpret_cast<float4 *>(smem + o);
@@ -89,11 +94,12 @@ __device__ __forceinline__ void split_tile(char *smem, uint32_t a_off, uint32_t 
 
 // Store n samples of the staged tile (row c = chunk c, 256-byte rows, 16-byte pieces
 // XOR-swizzled by row) to dst[start ..].
+template <int NT = kThreads>
 __device__ __forceinline__ void store_tile(float *dst, int64_t start, int n, const char *stag,
                                            bool al16) {
 #pragma unroll 4
-    for (int q = 0; q < 16; ++q) {
-        const int id = threadIdx.x + kThreads * q;
+    for (int q = 0; q < 2048 / NT; ++q) {
+        const int id = threadIdx.x + NT * q;
         const int r = id >> 4, j = id & 15;
         const float4 v = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ (r & 15)) << 4));
         const int s = r * kL + j * 4;
@@ -431,11 +437,604 @@ cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved
     return cudaGetLastError();
 }
 
+
+// ===========================================================================
+// Shared-memory layout of the pipelined forward: two stages (signal tile hi | lo)
+// and two per-channel table slots (B operand hi | lo, O_L, scan block, S_in).
+// ===========================================================================
+
+template <int MB, bool F64>
+struct PipeSmem {
+    using Tab = ChunkTab<MB>;
+    static constexpr int NM = Tab::NFWD;
+    static constexpr uint32_t STAGE = 2 * kTileBytes;              // hi | lo
+    static constexpr uint32_t ST0 = 0;                              // stages at 0, STAGE
+    static constexpr uint32_t TAB0 = 2 * STAGE;
+    // per table slot: B hi | B lo | O_L | scan block | S_in (doubles)
+    static constexpr uint32_t T_BHI = 0;
+    static constexpr uint32_t T_BLO = T_BHI + NM * 256;
+    static constexpr uint32_t T_OL = T_BLO + NM * 256;
+    static constexpr uint32_t T_SCAN = T_OL + kL * MB * 4;
+    static constexpr uint32_t T_SIN = (T_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
+    static constexpr uint32_t TSLOT = (T_SIN + MB * 8 + 1023) / 1024 * 1024;
+    static constexpr uint32_t MISC = TAB0 + 2 * TSLOT;
+};
+
+struct TileDesc {
+    int64_t ch;        // channel (-1: none)
+    int64_t tstart;    // first sample (packed index)
+    int64_t chunk0;    // first chunk's index in `saved`
+    int32_t tlen;      // valid samples in the tile
+    int32_t tab;       // table slot
+    int32_t first;     // first tile of its channel
+    int32_t M;         // channel order (for saved states)
+    int32_t last;      // last tile of its channel
+};
+
+// ===========================================================================
+// Warp-specialised forward (state buckets whose double-buffered layout fits).
+//
+// Roles (256 threads), decoupled by mbarriers, two pipeline stages s = i & 1:
+//   warps 0-2  converters: fetch work; build per-channel tables (double-buffered by
+//              channel parity); the signal tile arrives in stage s's hi slot (TMA
+//              tensor load into the 128-byte-swizzled operand layout, or cp.async when
+//              the layout has no chunk-aligned rows); split it into TF32 hi/lo
+//                                                   -> full[s]
+//              then prefetch tile i+1 into the other stage once MMA(i-1) released it
+//   warp 3     MMA issuer: full[s], tmem_free[s] -> tcgen05.mma into TMEM buffer s
+//                                                   -> mma_done[s] (tcgen05.commit)
+//   warps 4-7  epilogue: mma_done[s] -> chunk-state scan, y = D + O_L S, saved
+//              states; y staged in stage s's lo slot in the operand layout and
+//              written by a TMA tensor store (full tiles) or plain stores
+//                                                   -> tmem_free[s], stage_free[s]
+// ===========================================================================
+using pipe::kConvThreads;
+using pipe::kEpiWarp0;
+using pipe::kMmaWarp;
+using pipe::kNamedConv;
+using pipe::kNamedEpi;
+using pipe::kPipeThreads;
+using pipe::named_sync;
+
+template <int MB, bool F64>
+struct WsSmem {
+    using P = PipeSmem<MB, F64>;
+    static constexpr uint32_t MISC = P::MISC;
+    // barriers: full[2] mma[2] tfree[2] sfree[2] tabfree[2] load[2] dead drain (14 x 8)
+    static constexpr uint32_t M_BAR = MISC;
+    static constexpr uint32_t M_TMEM = MISC + 112;
+    static constexpr uint32_t M_ABORT = MISC + 116;
+    static constexpr uint32_t M_OK = MISC + 120;     // converter / epilogue broadcast words
+    static constexpr uint32_t M_WT = MISC + 128;
+    static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
+    static constexpr uint32_t BYTES = M_RING + 4 * 48;
+    static constexpr uint32_t ALLOC = BYTES + 1024;
+};
+
+using pipe::op_piece;
+
+template <int MB, bool F64>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    chunk_fwd_ws_kernel(const float *__restrict__ x, const float *__restrict__ zi,
+                        float *__restrict__ y, float *__restrict__ saved,
+                        const char *__restrict__ ws, unsigned long long *__restrict__ counter,
+                        Batch bt, int three, int x_al, int y_al, int use_tma,
+                        const __grid_constant__ CUtensorMap tmx,
+                        const __grid_constant__ CUtensorMap tmy) {
+    using Tab = ChunkTab<MB>;
+    using PS = PipeSmem<MB, F64>;
+    using SM = WsSmem<MB, F64>;
+    constexpr int NM = PS::NM;
+    extern __shared__ char smem_raw[];
+    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
+    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *stage_free = bars + 6,
+             *tab_free = bars + 8, *load_bar = bars + 10, *dead = bars + 12, *drain = bars + 13;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
+    volatile int *conv_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK);
+    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 4);
+    float *wt = reinterpret_cast<float *>(smem + SM::M_WT);
+    TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, 256);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 14; ++i) mbar_init(&bars[i], (i == 2 || i == 3) ? 2 : 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const size_t rec = Tab::fwd_rec(F64);
+    constexpr uint32_t idesc = idesc_tf32_m128(NM);
+    auto stage_hi = [&](int s) { return (uint32_t)(PS::ST0 + s * PS::STAGE); };
+    auto stage_lo = [&](int s) { return (uint32_t)(PS::ST0 + s * PS::STAGE + kTileBytes); };
+    auto tslot = [&](int p) { return (uint32_t)(PS::TAB0 + p * PS::TSLOT); };
+    // bounded wait by one thread; on timeout (or a peer's abort) raise the abort flag
+    auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
+        for (long long it = 0; it < bt.wait_limit; ++it) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if ((it & 63) == 63) {
+                if (*abort_flag) return false;
+                __nanosleep(32);
+            }
+        }
+        set_status(bt.status, DFILT_ERR_TIMEOUT);
+        *abort_flag = 1;
+        return false;
+    };
+
+    if (warp < kMmaWarp) {
+        // ============================ converters ============================
+        const int ct = tid;   // 0..kConvThreads-1
+        int64_t cur_ch = -1, cur_t = 0, cur_nt = 0, cur_off = 0, cur_len = 0;
+        int cur_M = 1, ch_seq = -1;
+        // thread 0: describe tile i in ring[i & 3]; returns false when the work is done
+        auto next_desc = [&](int64_t i) {
+            TileDesc &d = ring[i & 3];
+            while (cur_ch < 0 || cur_t >= cur_nt) {
+                const int64_t c = (int64_t)atomicAdd(counter, 1ull);
+                if (c >= bt.B) {
+                    d.ch = -1;
+                    return;
+                }
+                const Channel cc = channel_of(bt, c);
+                cur_ch = c;
+                cur_t = 0;
+                cur_off = cc.off;
+                cur_len = cc.len;
+                cur_M = cc.M;
+                cur_nt = (cc.len + kTileSamples - 1) / kTileSamples;
+                if (cur_nt == 0) continue;
+                ++ch_seq;
+            }
+            d.ch = cur_ch;
+            d.tstart = cur_off + cur_t * kTileSamples;
+            d.tlen = (int)(cur_len - cur_t * kTileSamples < kTileSamples ? cur_len - cur_t * kTileSamples
+                                                                         : kTileSamples);
+            d.chunk0 = cur_off / kL + cur_ch + cur_t * kChunks;
+            d.tab = ch_seq & 1;
+            d.first = cur_t == 0;
+            d.M = cur_M;
+            ++cur_t;
+            d.last = cur_t == cur_nt;
+        };
+        // all converters: per-channel tables into slot d.tab (column-parallel expansion
+        // of the Toeplitz block: thread handles column k, half h of the rows)
+        auto build_tables = [&](const TileDesc &d) {
+            const char *R = ws + kWsHeader + (size_t)d.ch * rec;
+            const float *__restrict__ g = reinterpret_cast<const float *>(R + Tab::F_G);
+            const float *__restrict__ RL = reinterpret_cast<const float *>(R + Tab::F_RL);
+            char *T = smem + tslot(d.tab);
+            // work item = (column k, half of the Toeplitz rows; the second half also
+            // writes the end-state rows R_L and the zero padding)
+            for (int item = ct; item < 128; item += kConvThreads) {
+                const int k = item & 63, h = item >> 6;
+                float gv[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int r = 32 * h + q;
+                    gv[q] = r >= k ? __ldg(g + (r - k)) : 0.f;
+                }
+                float rv[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) rv[m] = h ? __ldg(RL + m * kL + k) : 0.f;
+                const uint32_t kb = (k >> 5) * (NM * 128);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int r = 32 * h + q;
+                    float hv, lv;
+                    split_tf32(gv[q], hv, lv);
+                    const uint32_t o = kb + sw128_off(r, k & 31);
+                    *reinterpret_cast<float *>(T + PS::T_BHI + o) = hv;
+                    *reinterpret_cast<float *>(T + PS::T_BLO + o) = lv;
+                }
+                if (h) {
+#pragma unroll
+                    for (int r = kL; r < NM; ++r) {
+                        const float v = r < kL + MB ? rv[r - kL] : 0.f;
+                        float hv, lv;
+                        split_tf32(v, hv, lv);
+                        const uint32_t o = kb + sw128_off(r, k & 31);
+                        *reinterpret_cast<float *>(T + PS::T_BHI + o) = hv;
+                        *reinterpret_cast<float *>(T + PS::T_BLO + o) = lv;
+                    }
+                }
+            }
+            const float4 *OL = reinterpret_cast<const float4 *>(R + Tab::F_OL);
+            float4 *sOL = reinterpret_cast<float4 *>(T + PS::T_OL);
+            for (int idx = ct; idx < kL * MB / 4; idx += kConvThreads) sOL[idx] = __ldg(OL + idx);
+            const float4 *src = reinterpret_cast<const float4 *>(R + Tab::F_SCAN);
+            float4 *dst = reinterpret_cast<float4 *>(T + PS::T_SCAN);
+            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kConvThreads) dst[idx] = __ldg(src + idx);
+            double *sin = reinterpret_cast<double *>(T + PS::T_SIN);
+            if (ct < MB) sin[ct] = (zi && ct < d.M) ? (double)zi[d.ch * bt.Mstride + ct] : 0.0;
+        };
+        // tile i's signal into stage s's hi slot (TMA by thread 0, or cp.async by all)
+        auto issue_load = [&](const TileDesc &d, int s) {
+            if (use_tma) {
+                if (ct == 0) {
+                    mbar_arrive_expect_tx(&load_bar[s], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + stage_hi(s), &tmx, 0, 0, row, &load_bar[s]);
+                    tma_load_3d(sbase + stage_hi(s) + kKBlock, &tmx, 0, 1, row, &load_bar[s]);
+                }
+            } else {
+                pipe::load_tile_async<kConvThreads>(sbase + stage_hi(s), x, d.tstart, d.tlen,
+                                                    x_al && ((d.tstart & 3) == 0), ct);
+            }
+        };
+
+        // prologue: tile 0
+        if (ct == 0) next_desc(0);
+        named_sync(kNamedConv, kConvThreads);
+        {
+            const TileDesc d0 = ring[0];
+            if (d0.ch >= 0) {
+                build_tables(d0);
+                issue_load(d0, 0);
+            } else if (ct == 0) {
+                mbar_arrive(&full[0]);   // no work: end marker
+            }
+        }
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const TileDesc d = ring[i & 3];
+            if (d.ch < 0) break;
+            // (1) tile i landed; lo slot free (tile i-2's y staging consumed)
+            if (ct == 0) {
+                bool ok = true;
+                if (i >= 2) ok = wait1(&stage_free[s], (uint32_t)(((i >> 1) - 1) & 1));
+                if (ok && use_tma) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
+                *conv_ok = ok ? 1 : 0;
+            }
+            if (!use_tma) cp_async_wait_all();
+            named_sync(kNamedConv, kConvThreads);
+            if (!*conv_ok) break;
+            // (2) split into TF32 hi/lo, zero past the tile's valid samples
+            pipe::split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen,
+                                                three != 0, ct);
+            fence_proxy_async_smem();
+            named_sync(kNamedConv, kConvThreads);
+            if (ct == 0) mbar_arrive(&full[s]);
+            // (3) next tile: descriptor, tables of a new channel, prefetch into stage s^1
+            //     once MMA(i-1) has finished reading it
+            if (ct == 0) {
+                next_desc(i + 1);
+                const TileDesc &dn = ring[(i + 1) & 3];
+                bool ok = true;
+                if (dn.ch >= 0 && dn.first) {
+                    // slot dn.tab was last used two channels ago
+                    const int seq = ch_seq;
+                    if (seq >= 2) ok = wait1(&tab_free[dn.tab], (uint32_t)(((seq >> 1) - 1) & 1));
+                }
+                if (ok && dn.ch >= 0 && i >= 1)
+                    ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
+                *conv_ok = ok ? 1 : 0;
+            }
+            named_sync(kNamedConv, kConvThreads);
+            if (!*conv_ok) break;
+            const TileDesc dn = ring[(i + 1) & 3];
+            if (dn.ch < 0) {
+                if (ct == 0) mbar_arrive(&full[s ^ 1]);   // end marker for the MMA warp
+                break;
+            }
+            if (dn.first) build_tables(dn);
+            issue_load(dn, s ^ 1);
+        }
+    } else if (warp == kMmaWarp) {
+        // ============================ MMA issuer ============================
+        bool issued = false;
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            int ok = 1;
+            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            const TileDesc d = ring[i & 3];
+            // TMEM buffer s free (epilogue done with tile i-2); the end marker waits too,
+            // or its arrivals could complete a second phase of mma_done[s] before the
+            // epilogue has observed tile i-2's (a parity wait cannot tell them apart)
+            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[s], par ^ 1u) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            if (d.ch < 0) {
+                if (lane == 0) {
+                    mbar_arrive(&mma_done[s]);   // end marker for the epilogue (2 arrivals)
+                    mbar_arrive(&mma_done[s]);
+                }
+                break;
+            }
+            if (lane == 0) {
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
+                const uint32_t tb = tslot(d.tab);
+#pragma unroll
+                for (int kk = 0; kk < kL / 8; ++kk) {
+                    const uint32_t ka = (kk >> 2) * kKBlock + (kk & 3) * 32;
+                    const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
+                    const uint64_t ahi = sdesc_sw128(sbase + stage_hi(s) + ka);
+                    const uint64_t bhi = sdesc_sw128(sbase + tb + PS::T_BHI + kb);
+                    mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    if (three) {
+                        const uint64_t alo = sdesc_sw128(sbase + stage_lo(s) + ka);
+                        const uint64_t blo = sdesc_sw128(sbase + tb + PS::T_BLO + kb);
+                        mma_tf32(d_tmem, ahi, blo, idesc, 1u);
+                        mma_tf32(d_tmem, alo, bhi, idesc, 1u);
+                    }
+                }
+                mma_commit(&mma_done[s]);
+                mbar_arrive(&mma_done[s]);   // orders the descriptor reads before the epilogue's
+            }
+            issued = true;
+            if (bt.stall_drill) {
+                if (lane == 0) wait1(dead, 0);   // timeout drill: a barrier nothing signals
+                __syncwarp();
+                break;
+            }
+        }
+        // drain: every tensor-core operation this warp issued completes before exit
+        if (lane == 0 && issued) {
+            mma_commit(drain);
+            mbar_wait_bounded(drain, 0, kDefaultWaitLimit);
+        }
+        __syncwarp();
+    } else {
+        // ============================ epilogue ==============================
+        const int et = tid - kEpiWarp0 * 32;   // 0..127 = chunk = TMEM lane
+        const int ew = warp - kEpiWarp0;       // lane quarter
+        const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+        float Sin[MB];
+        double S64a = 0.0, S64b = 0.0;
+#pragma unroll
+        for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
+        for (int64_t i = 0;; ++i) {
+            const int s = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            if (et == 0) *epi_ok = wait1(&mma_done[s], par) ? 1 : 0;
+            named_sync(kNamedEpi, 128);
+            if (!*epi_ok) break;
+            tc_fence_after();
+            const TileDesc pv = ring[i & 3];
+            if (pv.ch < 0) break;
+            const char *T = smem + tslot(pv.tab);
+            const float *sOL = reinterpret_cast<const float *>(T + PS::T_OL);
+            const float *sP = reinterpret_cast<const float *>(T + PS::T_SCAN);
+            const double *sAt = reinterpret_cast<const double *>(T + PS::T_SCAN);
+            const double *sin = reinterpret_cast<const double *>(T + PS::T_SIN);
+            const int nch = (pv.tlen + kL - 1) / kL;
+            const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
+            if (pv.first) {
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = (float)sin[m];
+                if (F64 && ew == 0) {
+                    S64a = lane < MB ? sin[lane] : 0.0;
+                    S64b = lane + 32 < MB ? sin[lane + 32] : 0.0;
+                }
+            }
+            float E[MB];
+#pragma unroll
+            for (int cb = 0; cb < Tab::MPAD / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + kL + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (cb * 16 + q < MB) E[cb * 16 + q] = v[q];
+            }
+            float S[MB];
+            char *lo = smem + stage_lo(s);   // consumed by MMA(i): scan scratch, then y staging
+            if constexpr (!F64) {
+                // two-level scan: warp-local Hillis-Steele, then carries across the 4 warps
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int dd = 1 << k;
+                    float prev[MB];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) prev[m] = __shfl_up_sync(0xffffffffu, E[m], dd);
+                    if (lane >= dd) {
+                        float add[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, prev, add);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) E[m] += add[m];
+                    }
+                }
+                if (lane == 31) {
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) wt[ew * MB + m] = E[m];
+                }
+                named_sync(kNamedEpi, 128);
+                float C[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) C[m] = Sin[m];
+#pragma unroll
+                for (int ww = 0; ww < 4; ++ww) {
+                    if (ww == ew) {
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) S[m] = C[m];
+                    }
+                    float w2[MB];
+                    matvec_f32<MB>(sP + 5 * MB * MB, C, w2);
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) C[m] = w2[m] + wt[ww * MB + m];
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = C[m];
+                float v[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) v[m] = S[m];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if ((lane >> k) & 1) {
+                        float w2[MB];
+                        matvec_f32<MB>(sP + k * MB * MB, v, w2);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) v[m] = w2[m];
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    const float wprev = __shfl_up_sync(0xffffffffu, E[m], 1);
+                    S[m] = v[m] + (lane > 0 ? wprev : 0.f);
+                }
+                named_sync(kNamedEpi, 128);   // wt reusable
+            } else {
+                float *xbuf = reinterpret_cast<float *>(lo);
+                float *sbuf = reinterpret_cast<float *>(lo + 16384);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
+                named_sync(kNamedEpi, 128);
+                if (ew == 0) {
+                    for (int cc = 0; cc < nch; ++cc) {
+                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
+                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
+                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
+#pragma unroll 8
+                        for (int j = 0; j < MB; ++j) {
+                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
+                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
+                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
+                        }
+                        S64a = acc_a;
+                        S64b = acc_b;
+                    }
+                }
+                named_sync(kNamedEpi, 128);
+#pragma unroll
+                for (int m = 0; m < MB; ++m) S[m] = et < nch ? sbuf[et * MB + m] : 0.f;
+                named_sync(kNamedEpi, 128);
+            }
+            if (saved && et < nch) {
+                float *dst = saved + (size_t)(pv.chunk0 + et) * bt.Mstride;
+#pragma unroll
+                for (int m = 0; m < MB; ++m)
+                    if (m < pv.M) dst[m] = S[m];
+            }
+            // y = D + O_L S, staged in the operand layout (row = chunk, two K blocks)
+#pragma unroll 1
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float *ol = sOL + (cb * 16 + q) * MB;
+                    float acc = v[q];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) acc = fmaf(ol[m], S[m], acc);
+                    v[q] = acc;
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int j16 = cb * 4 + p;
+                    *reinterpret_cast<float4 *>(lo + op_piece(et, j16)) =
+                        make_float4(v[4 * p], v[4 * p + 1], v[4 * p + 2], v[4 * p + 3]);
+                }
+            }
+            tc_fence_before();
+            fence_proxy_async_smem();
+            named_sync(kNamedEpi, 128);
+            const bool tma_store = use_tma && pv.tlen == kTileSamples;
+            if (et == 0) {
+                mbar_arrive(&tmem_free[s]);
+                if (tma_store) {
+                    // the converters need this lo slot for tile i+2: release it as soon as
+                    // the bulk store has read it (the write to global continues async)
+                    const int row = (int)(pv.tstart / kL);
+                    tma_store_3d(&tmy, 0, 0, row, sbase + stage_lo(s));
+                    tma_store_3d(&tmy, 0, 1, row, sbase + stage_lo(s) + kKBlock);
+                    bulk_commit();
+                    bulk_wait_read0();
+                    mbar_arrive(&stage_free[s]);
+                }
+                if (pv.last) mbar_arrive(&tab_free[pv.tab]);
+            }
+            if (!tma_store) {
+                const bool al = y_al && ((pv.tstart & 3) == 0);
+#pragma unroll 4
+                for (int q = 0; q < 16; ++q) {
+                    const int id = et + 128 * q;
+                    const int r = id >> 4, j16 = id & 15;
+                    const float4 v = *reinterpret_cast<const float4 *>(lo + op_piece(r, j16));
+                    const int sidx = r * kL + j16 * 4;
+                    const int nv = min(max(pv.tlen - sidx, 0), 4);
+                    float *gp = y + pv.tstart + sidx;
+                    if (nv == 4 && al) {
+                        *reinterpret_cast<float4 *>(gp) = v;
+                    } else {
+                        if (nv > 0) gp[0] = v.x;
+                        if (nv > 1) gp[1] = v.y;
+                        if (nv > 2) gp[2] = v.z;
+                        if (nv > 3) gp[3] = v.w;
+                    }
+                }
+                named_sync(kNamedEpi, 128);
+                if (et == 0) mbar_arrive(&stage_free[s]);
+            }
+        }
+        if (et == 0) bulk_wait0();   // every TMA store complete before the CTA exits
+    }
+    // ---- exit (the MMA warp drained its tensor-core work above) ----
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+template <int MB, bool F64>
+cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *saved, const char *ws,
+                          const Batch &bt, int three, int num_sms, cudaStream_t st) {
+    using SM = WsSmem<MB, F64>;
+    static_assert(SM::ALLOC <= kSmemMax, "shared memory budget");
+    auto kern = chunk_fwd_ws_kernel<MB, F64>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t grid = bt.B < num_sms ? bt.B : num_sms;
+    const int x_al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    const int y_al = (reinterpret_cast<uintptr_t>(y) & 15) == 0;
+    // TMA needs chunk-aligned channel starts (fixed shape, T a multiple of L)
+    CUtensorMap tmx, tmy;
+    std::memset(&tmx, 0, sizeof(tmx));
+    std::memset(&tmy, 0, sizeof(tmy));
+    int use_tma = 0;
+    if (!bt.offsets && bt.T % kL == 0 && make_chunk_tmap(&tmx, x, bt.total) &&
+        make_chunk_tmap(&tmy, y, bt.total))
+        use_tma = 1;
+    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
+    kern<<<(unsigned)grid, kPipeThreads, SM::ALLOC, st>>>(x, zi, y, saved, ws, counter, bt, three, x_al,
+                                                       y_al, use_tma, tmx, tmy);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <int MB>
 cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *ws,
                          const Batch &bt, bool fp64_scan, int three, int num_sms, cudaStream_t st) {
+    // pipelined kernel wherever its double-buffered layout fits the shared memory
+    if constexpr (WsSmem<MB, true>::ALLOC <= kSmemMax)
+        if (fp64_scan) return launch_fwd_ws<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
+    if constexpr (MB <= kMaxF32ScanBucket && WsSmem<MB, false>::ALLOC <= kSmemMax)
+        if (!fp64_scan) return launch_fwd_ws<MB, false>(x, zi, y, saved, ws, bt, three, num_sms, st);
     if (fp64_scan) return launch_fwd_t<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
     if constexpr (MB <= kMaxF32ScanBucket)
         return launch_fwd_t<MB, false>(x, zi, y, saved, ws, bt, three, num_sms, st);

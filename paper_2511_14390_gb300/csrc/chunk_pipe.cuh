@@ -1,0 +1,202 @@
+// Device helpers shared by the warp-specialised chunked kernels (forward and
+// backward): tile descriptors, operand-tile addressing, named barriers, async tile
+// loads, the TF32 split, small mat-vecs, and per-warp staging of row-major chunks.
+#pragma once
+
+#include "chunk.cuh"
+
+namespace dfilt {
+namespace pipe {
+
+constexpr uint32_t kTileBytes = kChunks * kL * 4;   // 32 KB: one signal tile
+constexpr uint32_t kKBlock = kChunks * 128;         // one 32-wide K block of an operand tile
+constexpr uint32_t kSmemMax = 232448;               // opt-in shared memory per block
+constexpr int kNamedConv = 1, kNamedEpi = 2;
+// Warp roles of the warp-specialised kernels: 8 warps, so the register file allows up
+// to 255 registers per thread (a ninth warp would cap it at 168).
+constexpr int kConvThreads = 96;   // warps 0-2: converters
+constexpr int kMmaWarp = 3;        // warp 3: tensor-core issuer
+constexpr int kEpiWarp0 = 4;       // warps 4-7: epilogue (one per TMEM lane quarter)
+constexpr int kPipeThreads = 256;
+
+struct TileDesc {
+    int64_t ch;        // channel (-1: no more work)
+    int64_t tstart;    // first sample (packed index)
+    int64_t chunk0;    // first chunk's index in `saved`
+    int32_t tlen;      // valid samples in the tile
+    int32_t tab;       // table slot
+    int32_t first;     // first tile of its channel (in processing order)
+    int32_t M;         // channel order
+    int32_t last;      // last tile of its channel (in processing order)
+};
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+
+// Offset of logical 16-byte piece (row r, piece j16 of 16) in a two-K-block
+// 128-byte-swizzled operand tile (row = chunk, K = sample within the chunk).
+__device__ __forceinline__ uint32_t op_piece(int r, int j16) {
+    return (uint32_t)((j16 >> 3) * kKBlock + r * 128 + ((((j16 & 7) ^ (r & 7))) << 4));
+}
+
+// cp.async samples [start, start+n) of src into an operand tile at `dst` (zero past n).
+// Thread `t` of NT handles pieces t, t+NT, ...
+template <int NT>
+__device__ __forceinline__ void load_tile_async(uint32_t dst, const float *src, int64_t start,
+                                                int n, bool al16, int t) {
+#pragma unroll 4
+    for (int q = 0; q < (2048 + NT - 1) / NT; ++q) {
+        const int id = t + NT * q;
+        if (id >= 2048) break;
+        const int r = id >> 4, j16 = id & 15;
+        const uint32_t d = dst + op_piece(r, j16);
+        const int s = r * kL + j16 * 4;
+        const int nv = min(max(n - s, 0), 4);
+        const float *g = src + start + s;
+        if (al16) {
+            cp_async16(d, nv ? (const void *)g : (const void *)src, nv * 4);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                cp_async4(d + 4 * e, e < nv ? (const void *)(g + e) : (const void *)src, e < nv ? 4 : 0);
+        }
+    }
+    cp_async_commit();
+}
+
+// Split an operand tile in place into TF32 hi and (at lo_off) lo, zeroing samples past
+// `n`.  Thread `t` of NT handles pieces t, t+NT, ...
+template <int NT>
+__device__ __forceinline__ void split_tile_tf32(char *hi, char *lo, int n, bool three, int t) {
+#pragma unroll 4
+    for (int q = 0; q < (2048 + NT - 1) / NT; ++q) {
+        const int id = t + NT * q;
+        if (id >= 2048) break;
+        const int r = id >> 4, j16 = id & 15;
+        const uint32_t o = op_piece(r, j16);
+        float4 v = *reinterpret_cast<float4 *>(hi + o);
+        const int sidx = r * kL + j16 * 4;
+        if (sidx + 4 > n) {
+            if (sidx + 0 >= n) v.x = 0.f;
+            if (sidx + 1 >= n) v.y = 0.f;
+            if (sidx + 2 >= n) v.z = 0.f;
+            if (sidx + 3 >= n) v.w = 0.f;
+        }
+        float4 h, l;
+        split_tf32(v.x, h.x, l.x);
+        split_tf32(v.y, h.y, l.y);
+        split_tf32(v.z, h.z, l.z);
+        split_tf32(v.w, h.w, l.w);
+        *reinterpret_cast<float4 *>(hi + o) = h;
+        if (three) *reinterpret_cast<float4 *>(lo + o) = l;
+    }
+}
+
+template <int MB>
+__device__ __forceinline__ void matvec(const float *P, const float (&v)[MB], float (&out)[MB]) {
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < MB; ++j) acc = fmaf(P[i * MB + j], v[j], acc);
+        out[i] = acc;
+    }
+}
+
+// Per-warp staging of row-major chunks: the warp owns chunks (rows) 32w .. 32w+31 of a
+// tile and each lane holds its row's 64 samples in registers.  Rows move through a
+// 2 KB buffer 8 at a time (16-byte pieces XOR-swizzled by row, conflict-free), so that
+// global memory sees 512-byte coalesced accesses.
+//
+// warp_store_rows: row values -> dst[base + row*L + i] for sample index < n.
+__device__ __forceinline__ void warp_store_rows(const float (&v)[kL], char *stag, float *dst,
+                                                int64_t tstart, int row0, int n, bool al16,
+                                                int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if ((lane >> 3) == q) {
+            const int r = lane & 7;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                *reinterpret_cast<float4 *>(stag + r * 256 + ((j ^ r) << 4)) =
+                    make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = 2 * p + (lane >> 4), j = lane & 15;
+            const float4 w = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ r) << 4));
+            const int sidx = (row0 + 8 * q + r) * kL + j * 4;
+            const int nv = min(max(n - sidx, 0), 4);
+            float *g = dst + tstart + sidx;
+            if (nv == 4 && al16) {
+                *reinterpret_cast<float4 *>(g) = w;
+            } else {
+                if (nv > 0) g[0] = w.x;
+                if (nv > 1) g[1] = w.y;
+                if (nv > 2) g[2] = w.z;
+                if (nv > 3) g[3] = w.w;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// warp_load_rows: src[base + row*L + i] -> row values (zero past n).
+__device__ __forceinline__ void warp_load_rows(float (&v)[kL], char *stag, const float *src,
+                                               int64_t tstart, int row0, int n, bool al16,
+                                               int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = 2 * p + (lane >> 4), j = lane & 15;
+            const int sidx = (row0 + 8 * q + r) * kL + j * 4;
+            const int nv = min(max(n - sidx, 0), 4);
+            const float *g = src + tstart + sidx;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (nv == 4 && al16) {
+                w = __ldg(reinterpret_cast<const float4 *>(g));
+            } else {
+                if (nv > 0) w.x = __ldg(g);
+                if (nv > 1) w.y = __ldg(g + 1);
+                if (nv > 2) w.z = __ldg(g + 2);
+                if (nv > 3) w.w = __ldg(g + 3);
+            }
+            *reinterpret_cast<float4 *>(stag + r * 256 + ((j ^ r) << 4)) = w;
+        }
+        __syncwarp();
+        if ((lane >> 3) == q) {
+            const int r = lane & 7;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float4 w = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ r) << 4));
+                v[4 * j] = w.x;
+                v[4 * j + 1] = w.y;
+                v[4 * j + 2] = w.z;
+                v[4 * j + 3] = w.w;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Bounded single-thread mbarrier wait; on timeout (or a peer's abort) raise the abort
+// flag and record DFILT_ERR_TIMEOUT.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, long long limit,
+                                              volatile int *abort_flag, int *status) {
+    for (long long it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            __nanosleep(32);
+        }
+    }
+    set_status(status, DFILT_ERR_TIMEOUT);
+    *abort_flag = 1;
+    return false;
+}
+
+}  // namespace pipe
+}  // namespace dfilt

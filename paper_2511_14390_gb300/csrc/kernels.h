@@ -62,6 +62,12 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                              float *ga, float *gzi, void *ws, const Batch &bt, int Mmax,
                              bool fp64_scan, int precision, int num_sms, cudaStream_t st);
 size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
+
+// Tensor map of a signal viewed as rows of one chunk (L floats), 3-D so that one box
+// {32 floats, 1 half, 128 rows} is one 128-byte-swizzled K block of a tensor-core
+// operand tile.  Returns false when the layout does not allow it (rows not aligned to
+// chunk boundaries, misaligned base) -- callers then use plain async copies.
+bool make_chunk_tmap(CUtensorMap *map, const float *base, int64_t total);
 size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
 
 }  // namespace dfilt
