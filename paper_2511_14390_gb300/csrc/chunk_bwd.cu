@@ -549,14 +549,14 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // pipeline structure run on reversed tiles:
 //   warps 0-2  converters: work (tiles of a channel from last to first), tables
 //              (B = T_h^a, O^u, scan block, coefficients; double-buffered by channel
-//              parity), gy tile -> stage s (TMA or cp.async) -> TF32 hi/lo -> full[s];
-//              L2 prefetch of the x tile the epilogue will read
+//              parity), gy tile -> stage s hi (TMA or cp.async) -> TF32 hi/lo -> full[s];
+//              once MMA(i) has read stage s, the x tile of tile i -> stage s lo (x_bar[s])
 //   warp 3     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk)
 //   warps 4-7  epilogue: reverse chunk scan of S'_c = u[(c+1)L ..], u = D + O^u S',
-//              grad_x = sum_k b_k u[n+k] (FIR on the adjoint), y recomputed from the
-//              forward's saved chunk state, lag correlations reduced into per-warp FP64
-//              accumulators; grad_x leaves through per-warp staging, coalesced
-// A stage is free as soon as its MMA completed (the epilogue only reads TMEM).
+//              y recomputed from the forward's saved chunk state and the x tile, lag
+//              correlations reduced into per-warp FP64 accumulators, grad_x = sum_k
+//              b_k u[n+k] written over the x tile in place and stored from there (TMA
+//              for full tiles); stage_free[s] once the lo slot has been read out
 // ===========================================================================
 
 template <int MB, bool F64>
@@ -571,16 +571,16 @@ struct BwSmem {
     static constexpr uint32_t T_SCAN = T_OU + kL * MB * 4;
     static constexpr uint32_t T_COEF = (T_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
     static constexpr uint32_t TSLOT = (T_COEF + (2 * MB + 1) * 4 + 1023) / 1024 * 1024;
-    static constexpr uint32_t STG = TAB0 + 2 * TSLOT;                // 4 x 2 KB warp staging
-    // FP64 reverse scan scratch (E' and S' per chunk); the stages may be refilled meanwhile
-    static constexpr uint32_t SCR = STG + 4 * 2048;
+    // FP64 reverse scan scratch (E' and S' per chunk)
+    static constexpr uint32_t SCR = TAB0 + 2 * TSLOT;
     static constexpr uint32_t ACC = SCR + (F64 ? 2 * kChunks * MB * 4 : 0);   // 4 x (2MB+1) doubles
     static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
-    static constexpr uint32_t M_BAR = MISC;                          // 14 barriers
-    static constexpr uint32_t M_TMEM = MISC + 112;
-    static constexpr uint32_t M_ABORT = MISC + 116;
-    static constexpr uint32_t M_OK = MISC + 120;
-    static constexpr uint32_t M_WT = MISC + 128;
+    static constexpr int NBAR = 16;
+    static constexpr uint32_t M_BAR = MISC;
+    static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
+    static constexpr uint32_t M_ABORT = M_TMEM + 4;
+    static constexpr uint32_t M_OK = M_TMEM + 16;   // 8 flags, one per decision point
+    static constexpr uint32_t M_WT = M_TMEM + 48;
     static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
     static constexpr uint32_t BYTES = M_RING + 8 * 48;
     static constexpr uint32_t ALLOC = BYTES + 1024;
@@ -594,7 +594,9 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         float *__restrict__ gx, float *__restrict__ gb, float *__restrict__ ga,
                         float *__restrict__ gzi, const char *__restrict__ ws,
                         unsigned long long *__restrict__ counter, Batch bt, int three, int al_mask,
-                        int use_tma, const __grid_constant__ CUtensorMap tmg) {
+                        int tma_mask, const __grid_constant__ CUtensorMap tmg,
+                        const __grid_constant__ CUtensorMap tmx,
+                        const __grid_constant__ CUtensorMap tmgx) {
     using namespace pipe;
     using Tab = ChunkTab<MB>;
     using SM = BwSmem<MB, F64>;
@@ -604,24 +606,34 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *tab_free = bars + 8,
-             *load_bar = bars + 10, *dead = bars + 12, *drain = bars + 13;
+    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *stage_free = bars + 6,
+             *tab_free = bars + 8, *load_bar = bars + 10, *x_bar = bars + 12, *dead = bars + 14,
+             *drain = bars + 15;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
+    // decision flags written by one thread and read by its role after a named barrier;
+    // each decision point has its own word, so that a late reader never sees the value
+    // of a later point (the roles must leave their loops at the same point)
     volatile int *conv_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK);
-    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 4);
+    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 16);
     float *wt = reinterpret_cast<float *>(smem + SM::M_WT);
     double *acc_s = reinterpret_cast<double *>(smem + SM::ACC);
     TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool gy_al = al_mask & 1, x_al = al_mask & 2, gx_al = al_mask & 8;
+    const bool tma_gy = tma_mask & 1, tma_x = tma_mask & 2, tma_gx = tma_mask & 4;
 
     if (warp == 0) {
         tmem_alloc(tmem_slot, 256);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 14; ++i) mbar_init(&bars[i], (i == 2 || i == 3) ? 2 : 1);
+        for (int i = 0; i < SM::NBAR; ++i) {
+            uint32_t cnt = 1;
+            if (i == 2 || i == 3) cnt = 2;                        // mma_done: commit + arrive
+            if ((i == 12 || i == 13) && !tma_x) cnt = kConvThreads;   // x_bar: cp.async arrivals
+            mbar_init(&bars[i], cnt);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -661,10 +673,9 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 cur_nt = (cc.len + kTileSamples - 1) / kTileSamples;
                 if (cur_nt == 0) {
                     // an empty channel still owes zero coefficient gradients
-                    const Channel z = cc;
-                    for (int k = 0; k <= z.N; ++k)
+                    for (int k = 0; k <= cc.N; ++k)
                         if (gb) gb[c * bt.Nstride + k] = 0.f;
-                    for (int k = 0; k < z.M; ++k) {
+                    for (int k = 0; k < cc.M; ++k) {
                         if (ga) ga[c * bt.Mstride + k] = 0.f;
                         if (gzi) gzi[c * bt.Mstride + k] = 0.f;
                     }
@@ -719,8 +730,9 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
             if (ct <= MB) coef[MB + ct] = ct <= c.N ? bco[d.ch * bt.Nstride + ct] : 0.f;
         };
-        auto issue_load = [&](const TileDesc &d, int s) {
-            if (use_tma) {
+        // gy tile of `d` -> stage s hi
+        auto issue_gy = [&](const TileDesc &d, int s) {
+            if (tma_gy) {
                 if (ct == 0) {
                     mbar_arrive_expect_tx(&load_bar[s], kTileBytes);
                     const int row = (int)(d.tstart / kL);
@@ -731,11 +743,26 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 load_tile_async<kConvThreads>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
                                               gy_al && ((d.tstart & 3) == 0), ct);
             }
-            // warm L2 with the x tile the epilogue reads (full aligned tiles only)
+            // warm L2 with the x tile that is fetched once this tile's MMA is done
             if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(x + d.tstart),
                              "r"((uint32_t)kTileBytes)
                              : "memory");
+        };
+        // x tile of `d` -> stage s lo (the stage's MMA has completed); lands on x_bar[s]
+        auto issue_x = [&](const TileDesc &d, int s) {
+            if (tma_x) {
+                if (ct == 0) {
+                    mbar_arrive_expect_tx(&x_bar[s], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + stage_lo(s), &tmx, 0, 0, row, &x_bar[s]);
+                    tma_load_3d(sbase + stage_lo(s) + kKBlock, &tmx, 0, 1, row, &x_bar[s]);
+                }
+            } else {
+                load_tile_async<kConvThreads>(sbase + stage_lo(s), x, d.tstart, d.tlen,
+                                              x_al && ((d.tstart & 3) == 0), ct);
+                cp_async_mbar_arrive_noinc(&x_bar[s]);
+            }
         };
 
         if (ct == 0) {
@@ -744,11 +771,12 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             ring[0] = d0;
         }
         named_sync(kNamedConv, kConvThreads);
+        int64_t ntiles = 0;   // tiles this CTA processed
         {
             const TileDesc d0 = ring[0];
             if (d0.ch >= 0) {
                 build_tables(d0);
-                issue_load(d0, 0);
+                issue_gy(d0, 0);
             } else if (ct == 0) {
                 mbar_arrive(&full[0]);
             }
@@ -757,39 +785,59 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             const int s = (int)(i & 1);
             const TileDesc d = ring[i & 7];
             if (d.ch < 0) break;
+            // (1) gy tile i landed; stage s lo free (tile i-2's x / grad_x read out)
             if (ct == 0) {
                 bool ok = true;
-                if (use_tma) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
-                *conv_ok = ok ? 1 : 0;
+                if (i >= 2) ok = wait1(&stage_free[s], (uint32_t)(((i >> 1) - 1) & 1));
+                if (ok && tma_gy) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
+                conv_ok[0] = ok ? 1 : 0;
             }
-            if (!use_tma) cp_async_wait_all();
+            if (!tma_gy) cp_async_wait_all();
             named_sync(kNamedConv, kConvThreads);
-            if (!*conv_ok) break;
+            if (!conv_ok[0]) break;
+            // (2) TF32 hi/lo split in place
             split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen, three != 0, ct);
             fence_proxy_async_smem();
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
+            ntiles = i + 1;
+            // (3) MMA(i-1) complete: stage s^1 is free, tile i-1's x tile goes to its lo
+            //     slot (before any wait that the epilogue of tile i-1 could hold up), and
+            //     through the MMA's wait on the TMEM buffer the epilogue has finished
+            //     tile i-3, whose ring slot is reused below
+            if (i >= 1) {
+                if (ct == 0) conv_ok[1] = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
+                named_sync(kNamedConv, kConvThreads);
+                if (!conv_ok[1]) break;
+                issue_x(ring[(i - 1) & 7], s ^ 1);
+            }
+            // (4) next descriptor; a new channel's tables wait for their slot
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
                 if (nd.ch >= 0 && nd.first && ch_seq >= 2)
                     ok = wait1(&tab_free[nd.tab], (uint32_t)(((ch_seq >> 1) - 1) & 1));
-                // MMA(i-1) complete: stage s^1 is free, and (through its wait on the TMEM
-                // buffer) the epilogue has finished tile i-3, whose ring slot is reused
-                if (ok && i >= 1) ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
                 ring[(i + 1) & 7] = nd;
-                *conv_ok = ok ? 1 : 0;
+                conv_ok[2] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
-            if (!*conv_ok) break;
+            if (!conv_ok[2]) break;
             const TileDesc dn = ring[(i + 1) & 7];
             if (dn.ch < 0) {
                 if (ct == 0) mbar_arrive(&full[s ^ 1]);
                 break;
             }
             if (dn.first) build_tables(dn);
-            issue_load(dn, s ^ 1);
+            issue_gy(dn, s ^ 1);
+        }
+        // the last tile's x, once its MMA is done
+        if (ntiles > 0) {
+            const int64_t il = ntiles - 1;
+            const int sl = (int)(il & 1);
+            if (ct == 0) conv_ok[3] = wait1(&mma_done[sl], (uint32_t)((il >> 1) & 1)) ? 1 : 0;
+            named_sync(kNamedConv, kConvThreads);
+            if (conv_ok[3]) issue_x(ring[il & 7], sl);
         }
     } else if (warp == kMmaWarp) {
         // ============================ MMA issuer ============================
@@ -850,18 +898,17 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
         __syncwarp();
     } else {
         // ============================ epilogue ==============================
-        const int et = tid - kEpiWarp0 * 32;
+        const int et = tid - kEpiWarp0 * 32;   // chunk = TMEM lane
         const int ew = warp - kEpiWarp0;
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
-        char *stag = smem + SM::STG + ew * 2048;
         float Sin[MB];   // state entering the tile from the right
         double S64a = 0.0, S64b = 0.0;
         for (int64_t i = 0;; ++i) {
             const int s = (int)(i & 1);
             const uint32_t par = (uint32_t)((i >> 1) & 1);
-            if (et == 0) *epi_ok = wait1(&mma_done[s], par) ? 1 : 0;
+            if (et == 0) epi_ok[0] = wait1(&mma_done[s], par) ? 1 : 0;
             named_sync(kNamedEpi, 128);
-            if (!*epi_ok) break;
+            if (!epi_ok[0]) break;
             tc_fence_after();
             const TileDesc pv = ring[i & 7];
             if (pv.ch < 0) break;
@@ -870,8 +917,17 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             const float *sP = reinterpret_cast<const float *>(T + SM::T_SCAN);
             const double *sAt = reinterpret_cast<const double *>(T + SM::T_SCAN);
             const float *coef = reinterpret_cast<const float *>(T + SM::T_COEF);
+            char *xs = smem + stage_lo(s);   // x tile, then grad_x (operand layout)
             const int nch = (pv.tlen + kL - 1) / kL;
             const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
+            // the forward's state entering this chunk (read early: global latency)
+            float st[MB];
+            {
+                const bool vch = et < nch;
+                const float *src = saved + (size_t)(pv.chunk0 + et) * bt.Mstride;
+#pragma unroll
+                for (int m = 0; m < MB; ++m) st[m] = (vch && m < pv.M) ? src[m] : 0.f;
+            }
             if (pv.first) {   // the channel's last tile in time: nothing to its right
 #pragma unroll
                 for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
@@ -985,35 +1041,34 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 }
             }
             tc_fence_before();
-            named_sync(kNamedEpi, 128);
-            if (et == 0) mbar_arrive(&tmem_free[s]);
             if (gzi && pv.last && et == 0) {
 #pragma unroll
                 for (int m = 0; m < MB; ++m)
                     if (m < pv.M) gzi[pv.ch * bt.Mstride + m] = u[m];
             }
+            // x tile landed in the lo slot
+            if (et == 0) epi_ok[1] = wait1(&x_bar[s], par) ? 1 : 0;
+            named_sync(kNamedEpi, 128);
+            if (et == 0) mbar_arrive(&tmem_free[s]);
+            if (!epi_ok[1]) break;
+            float w[kL];   // x of this chunk, then grad_x
+#pragma unroll
+            for (int j16 = 0; j16 < 16; ++j16) {
+                const float4 v = *reinterpret_cast<const float4 *>(xs + op_piece(et, j16));
+                w[4 * j16] = v.x;
+                w[4 * j16 + 1] = v.y;
+                w[4 * j16 + 2] = v.z;
+                w[4 * j16 + 3] = v.w;
+            }
+            if (pv.tlen < kTileSamples) {   // samples past the channel's end read as zero
+                const int nv = pv.tlen - et * kL;
+#pragma unroll
+                for (int n = 0; n < kL; ++n)
+                    if (n >= nv) w[n] = 0.f;
+            }
 #define DFILT_EXT(n) ((n) < kL ? u[(n)] : S[(n) - kL])
-            // grad_x = sum_k b_k u[n+k]
-            float w[kL];
-#pragma unroll
-            for (int n = 0; n < kL; ++n) {
-                float a = 0.f;
-#pragma unroll
-                for (int k = 0; k <= MB; ++k) a = fmaf(coef[MB + k], DFILT_EXT(n + k), a);
-                w[n] = a;
-            }
-            if (gx)
-                warp_store_rows(w, stag, gx, pv.tstart, ew * 32, pv.tlen, gx_al && ((pv.tstart & 3) == 0), lane);
-            // x rows, then y recomputed from the forward's chunk state, fused with the
-            // lag correlations grad_b[k] += u[n+k] x[n], grad_a[k] -= u[n+1+k] y[n]
-            warp_load_rows(w, stag, x, pv.tstart, ew * 32, pv.tlen, x_al && ((pv.tstart & 3) == 0), lane);
-            float st[MB];
-            {
-                const bool vch = et < nch;
-                const float *src = saved + (size_t)(pv.chunk0 + et) * bt.Mstride;
-#pragma unroll
-                for (int m = 0; m < MB; ++m) st[m] = (vch && m < pv.M) ? src[m] : 0.f;
-            }
+            // y recomputed from the forward's chunk state, fused with the lag
+            // correlations grad_b[k] += u[n+k] x[n], grad_a[k] -= u[n+1+k] y[n]
             float pb[MB + 1], pa[MB];
 #pragma unroll
             for (int k = 0; k <= MB; ++k) pb[k] = 0.f;
@@ -1031,7 +1086,20 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
 #pragma unroll
                 for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(n + 1 + k), yn, pa[k]);
             }
+            // grad_x = sum_k b_k u[n+k], over this chunk's x row
+#pragma unroll
+            for (int n = 0; n < kL; ++n) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k <= MB; ++k) a = fmaf(coef[MB + k], DFILT_EXT(n + k), a);
+                w[n] = a;
+            }
 #undef DFILT_EXT
+#pragma unroll
+            for (int j16 = 0; j16 < 16; ++j16)
+                *reinterpret_cast<float4 *>(xs + op_piece(et, j16)) =
+                    make_float4(w[4 * j16], w[4 * j16 + 1], w[4 * j16 + 2], w[4 * j16 + 3]);
+            fence_proxy_async_smem();
 #pragma unroll
             for (int k = 0; k < NACC; ++k) {
                 float v = k <= MB ? pb[k] : pa[k - MB - 1];
@@ -1039,8 +1107,43 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) acc_s[ew * NACC + k] += (double)v;
             }
-            if (pv.last) {
+            named_sync(kNamedEpi, 128);
+            const bool tma_store = tma_gx && gx && pv.tlen == kTileSamples;
+            if (tma_store) {
+                if (et == 0) {
+                    // release the lo slot as soon as the bulk store has read it
+                    const int row = (int)(pv.tstart / kL);
+                    tma_store_3d(&tmgx, 0, 0, row, sbase + stage_lo(s));
+                    tma_store_3d(&tmgx, 0, 1, row, sbase + stage_lo(s) + kKBlock);
+                    bulk_commit();
+                    bulk_wait_read0();
+                    mbar_arrive(&stage_free[s]);
+                }
+            } else {
+                if (gx) {
+                    const bool al = gx_al && ((pv.tstart & 3) == 0);
+#pragma unroll 4
+                    for (int q = 0; q < 16; ++q) {
+                        const int id = et + 128 * q;
+                        const int r = id >> 4, j16 = id & 15;
+                        const float4 v = *reinterpret_cast<const float4 *>(xs + op_piece(r, j16));
+                        const int sidx = r * kL + j16 * 4;
+                        const int nv = min(max(pv.tlen - sidx, 0), 4);
+                        float *gp = gx + pv.tstart + sidx;
+                        if (nv == 4 && al) {
+                            *reinterpret_cast<float4 *>(gp) = v;
+                        } else {
+                            if (nv > 0) gp[0] = v.x;
+                            if (nv > 1) gp[1] = v.y;
+                            if (nv > 2) gp[2] = v.z;
+                            if (nv > 3) gp[3] = v.w;
+                        }
+                    }
+                }
                 named_sync(kNamedEpi, 128);
+                if (et == 0) mbar_arrive(&stage_free[s]);
+            }
+            if (pv.last) {
                 const Channel c = channel_of(bt, pv.ch);
                 for (int k = et; k < NACC; k += 128) {
                     const double v = acc_s[k] + acc_s[NACC + k] + acc_s[2 * NACC + k] + acc_s[3 * NACC + k];
@@ -1057,6 +1160,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 if (et == 0) mbar_arrive(&tab_free[pv.tab]);
             }
         }
+        if (et == 0) bulk_wait0();   // every TMA store complete before the CTA exits
     }
     cp_async_wait_all();
     tc_fence_before();
@@ -1087,13 +1191,21 @@ cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
     const int64_t grid = bt.B < num_sms ? bt.B : num_sms;
     auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     const int mask = (al(gy) ? 1 : 0) | (al(x) ? 2 : 0) | ((gx && al(gx)) ? 8 : 0);
-    CUtensorMap tmg;
+    CUtensorMap tmg, tmx, tmgx;
     std::memset(&tmg, 0, sizeof(tmg));
-    int use_tma = 0;
-    if (!bt.offsets && bt.T % kL == 0 && make_chunk_tmap(&tmg, gy, bt.total)) use_tma = 1;
+    std::memset(&tmx, 0, sizeof(tmx));
+    std::memset(&tmgx, 0, sizeof(tmgx));
+    int tma = 0;
+    // tensor maps view a fixed-shape batch as rows of one chunk; a ragged batch, a
+    // length that is not a whole number of chunks or a misaligned base takes cp.async
+    if (!bt.offsets && bt.T % kL == 0) {
+        if (make_chunk_tmap(&tmg, gy, bt.total)) tma |= 1;
+        if (make_chunk_tmap(&tmx, x, bt.total)) tma |= 2;
+        if (gx && make_chunk_tmap(&tmgx, gx, bt.total)) tma |= 4;
+    }
     auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
     kern<<<(unsigned)grid, pipe::kPipeThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, counter,
-                                                       bt, three, mask, use_tma, tmg);
+                                                       bt, three, mask, tma, tmg, tmx, tmgx);
     return cudaGetLastError();
 }
 

@@ -504,8 +504,8 @@ struct WsSmem {
     static constexpr uint32_t M_BAR = MISC;
     static constexpr uint32_t M_TMEM = MISC + 112;
     static constexpr uint32_t M_ABORT = MISC + 116;
-    static constexpr uint32_t M_OK = MISC + 120;     // converter / epilogue broadcast words
-    static constexpr uint32_t M_WT = MISC + 128;
+    static constexpr uint32_t M_OK = MISC + 120;     // converter (2) / epilogue broadcast words
+    static constexpr uint32_t M_WT = MISC + 144;
     static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
     static constexpr uint32_t BYTES = M_RING + 4 * 48;
     static constexpr uint32_t ALLOC = BYTES + 1024;
@@ -533,8 +533,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
              *tab_free = bars + 8, *load_bar = bars + 10, *dead = bars + 12, *drain = bars + 13;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
+    // decision flags written by one thread and read by its role after a named barrier;
+    // each decision point has its own word, so that a late reader never sees the value
+    // of a later point (the roles must leave their loops at the same point)
     volatile int *conv_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK);
-    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 4);
+    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 8);
     float *wt = reinterpret_cast<float *>(smem + SM::M_WT);
     TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -693,11 +696,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                 bool ok = true;
                 if (i >= 2) ok = wait1(&stage_free[s], (uint32_t)(((i >> 1) - 1) & 1));
                 if (ok && use_tma) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
-                *conv_ok = ok ? 1 : 0;
+                conv_ok[0] = ok ? 1 : 0;
             }
             if (!use_tma) cp_async_wait_all();
             named_sync(kNamedConv, kConvThreads);
-            if (!*conv_ok) break;
+            if (!conv_ok[0]) break;
             // (2) split into TF32 hi/lo, zero past the tile's valid samples
             pipe::split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen,
                                                 three != 0, ct);
@@ -717,10 +720,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                 }
                 if (ok && dn.ch >= 0 && i >= 1)
                     ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
-                *conv_ok = ok ? 1 : 0;
+                conv_ok[1] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
-            if (!*conv_ok) break;
+            if (!conv_ok[1]) break;
             const TileDesc dn = ring[(i + 1) & 3];
             if (dn.ch < 0) {
                 if (ct == 0) mbar_arrive(&full[s ^ 1]);   // end marker for the MMA warp
