@@ -549,9 +549,9 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // pipeline structure run on reversed tiles:
 //   warps 0-2  converters: work (tiles of a channel from last to first), tables
 //              (B = T_h^a, O^u, scan block, coefficients; double-buffered by channel
-//              parity), gy tile -> stage s hi (TMA or cp.async) -> TF32 hi/lo -> full[s];
-//              once MMA(i) has read stage s, the x tile of tile i -> stage s lo (x_bar[s])
-//   warp 3     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk)
+//              parity), gy tile -> stage s hi (TMA or cp.async) -> TF32 hi/lo -> full[s]
+//   warp 3     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk); once
+//              MMA(i) has completed, the x tile of tile i -> stage s lo (x_bar[s])
 //   warps 4-7  epilogue: reverse chunk scan of S'_c = u[(c+1)L ..], u = D + O^u S',
 //              y recomputed from the forward's saved chunk state and the x tile, lag
 //              correlations reduced into per-warp FP64 accumulators, grad_x = sum_k
@@ -602,6 +602,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     using SM = BwSmem<MB, F64>;
     constexpr int NM = SM::NM;
     constexpr int NACC = 2 * MB + 1;
+    static_assert(NACC <= 32, "one lag product per lane");
     extern __shared__ char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
@@ -631,13 +632,12 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
         for (int i = 0; i < SM::NBAR; ++i) {
             uint32_t cnt = 1;
             if (i == 2 || i == 3) cnt = 2;                        // mma_done: commit + arrive
-            if ((i == 12 || i == 13) && !tma_x) cnt = kConvThreads;   // x_bar: cp.async arrivals
+            if ((i == 12 || i == 13) && !tma_x) cnt = 32;   // x_bar: the MMA warp's cp.async arrivals
             mbar_init(&bars[i], cnt);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < 4 * NACC; i += kPipeThreads) acc_s[i] = 0.0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -749,29 +749,12 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                              "r"((uint32_t)kTileBytes)
                              : "memory");
         };
-        // x tile of `d` -> stage s lo (the stage's MMA has completed); lands on x_bar[s]
-        auto issue_x = [&](const TileDesc &d, int s) {
-            if (tma_x) {
-                if (ct == 0) {
-                    mbar_arrive_expect_tx(&x_bar[s], kTileBytes);
-                    const int row = (int)(d.tstart / kL);
-                    tma_load_3d(sbase + stage_lo(s), &tmx, 0, 0, row, &x_bar[s]);
-                    tma_load_3d(sbase + stage_lo(s) + kKBlock, &tmx, 0, 1, row, &x_bar[s]);
-                }
-            } else {
-                load_tile_async<kConvThreads>(sbase + stage_lo(s), x, d.tstart, d.tlen,
-                                              x_al && ((d.tstart & 3) == 0), ct);
-                cp_async_mbar_arrive_noinc(&x_bar[s]);
-            }
-        };
-
         if (ct == 0) {
             TileDesc d0;
             next_desc(d0);
             ring[0] = d0;
         }
         named_sync(kNamedConv, kConvThreads);
-        int64_t ntiles = 0;   // tiles this CTA processed
         {
             const TileDesc d0 = ring[0];
             if (d0.ch >= 0) {
@@ -800,29 +783,22 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             fence_proxy_async_smem();
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            ntiles = i + 1;
-            // (3) MMA(i-1) complete: stage s^1 is free, tile i-1's x tile goes to its lo
-            //     slot (before any wait that the epilogue of tile i-1 could hold up), and
-            //     through the MMA's wait on the TMEM buffer the epilogue has finished
-            //     tile i-3, whose ring slot is reused below
-            if (i >= 1) {
-                if (ct == 0) conv_ok[1] = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
-                named_sync(kNamedConv, kConvThreads);
-                if (!conv_ok[1]) break;
-                issue_x(ring[(i - 1) & 7], s ^ 1);
-            }
-            // (4) next descriptor; a new channel's tables wait for their slot
+            // (3) next descriptor; a new channel's tables wait for their slot; MMA(i-1)
+            //     complete: stage s^1 takes tile i+1's gy (its lo slot is refilled with
+            //     x only after this stage's next MMA), and through the MMA's wait on the
+            //     TMEM buffer the epilogue has finished tile i-3, whose ring slot is reused
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
                 if (nd.ch >= 0 && nd.first && ch_seq >= 2)
                     ok = wait1(&tab_free[nd.tab], (uint32_t)(((ch_seq >> 1) - 1) & 1));
+                if (ok && i >= 1) ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
                 ring[(i + 1) & 7] = nd;
-                conv_ok[2] = ok ? 1 : 0;
+                conv_ok[1] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
-            if (!conv_ok[2]) break;
+            if (!conv_ok[1]) break;
             const TileDesc dn = ring[(i + 1) & 7];
             if (dn.ch < 0) {
                 if (ct == 0) mbar_arrive(&full[s ^ 1]);
@@ -830,14 +806,6 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             }
             if (dn.first) build_tables(dn);
             issue_gy(dn, s ^ 1);
-        }
-        // the last tile's x, once its MMA is done
-        if (ntiles > 0) {
-            const int64_t il = ntiles - 1;
-            const int sl = (int)(il & 1);
-            if (ct == 0) conv_ok[3] = wait1(&mma_done[sl], (uint32_t)((il >> 1) & 1)) ? 1 : 0;
-            named_sync(kNamedConv, kConvThreads);
-            if (conv_ok[3]) issue_x(ring[il & 7], sl);
         }
     } else if (warp == kMmaWarp) {
         // ============================ MMA issuer ============================
@@ -885,6 +853,24 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 mbar_arrive(&mma_done[s]);
             }
             issued = true;
+            // x tile i -> stage s lo as soon as MMA(i) has read the stage (the epilogue
+            // needs it after its scan; the converters refill the slot only after the
+            // epilogue has released it)
+            if (lane == 0) ok = wait1(&mma_done[s], par) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            if (tma_x) {
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&x_bar[s], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + stage_lo(s), &tmx, 0, 0, row, &x_bar[s]);
+                    tma_load_3d(sbase + stage_lo(s) + kKBlock, &tmx, 0, 1, row, &x_bar[s]);
+                }
+            } else {
+                load_tile_async<32>(sbase + stage_lo(s), x, d.tstart, d.tlen,
+                                    x_al && ((d.tstart & 3) == 0), lane);
+                cp_async_mbar_arrive_noinc(&x_bar[s]);
+            }
             if (bt.stall_drill) {
                 if (lane == 0) wait1(dead, 0);
                 __syncwarp();
@@ -903,6 +889,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
         float Sin[MB];   // state entering the tile from the right
         double S64a = 0.0, S64b = 0.0;
+        double accd = 0.0;   // lane k < 2MB+1: this warp's sum of lag product k over the channel
         for (int64_t i = 0;; ++i) {
             const int s = (int)(i & 1);
             const uint32_t par = (uint32_t)((i >> 1) & 1);
@@ -1100,12 +1087,16 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 *reinterpret_cast<float4 *>(xs + op_piece(et, j16)) =
                     make_float4(w[4 * j16], w[4 * j16 + 1], w[4 * j16 + 2], w[4 * j16 + 3]);
             fence_proxy_async_smem();
+            {
+                float mine = 0.f;
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) {
-                float v = k <= MB ? pb[k] : pa[k - MB - 1];
+                for (int k = 0; k < NACC; ++k) {
+                    float v = k <= MB ? pb[k] : pa[k - MB - 1];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) acc_s[ew * NACC + k] += (double)v;
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == k) mine = v;
+                }
+                accd += (double)mine;
             }
             named_sync(kNamedEpi, 128);
             const bool tma_store = tma_gx && gx && pv.tlen == kTileSamples;
@@ -1144,6 +1135,9 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 if (et == 0) mbar_arrive(&stage_free[s]);
             }
             if (pv.last) {
+                if (lane < NACC) acc_s[ew * NACC + lane] = accd;
+                accd = 0.0;
+                named_sync(kNamedEpi, 128);
                 const Channel c = channel_of(bt, pv.ch);
                 for (int k = et; k < NACC; k += 128) {
                     const double v = acc_s[k] + acc_s[NACC + k] + acc_s[2 * NACC + k] + acc_s[3 * NACC + k];
@@ -1154,8 +1148,6 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         if (ga && m < c.M) ga[pv.ch * bt.Mstride + m] = (float)(-v);
                     }
                 }
-                named_sync(kNamedEpi, 128);
-                for (int k = et; k < 4 * NACC; k += 128) acc_s[k] = 0.0;
                 named_sync(kNamedEpi, 128);
                 if (et == 0) mbar_arrive(&tab_free[pv.tab]);
             }

@@ -474,8 +474,8 @@ struct TileDesc {
 // ===========================================================================
 // Warp-specialised forward (state buckets whose double-buffered layout fits).
 //
-// Roles (256 threads), decoupled by mbarriers, two pipeline stages s = i & 1:
-//   warps 0-2  converters: fetch work; build per-channel tables (double-buffered by
+// Roles (384 threads), decoupled by mbarriers, two pipeline stages s = i & 1:
+//   warps 0-2, 8-11  converters: fetch work; build per-channel tables (double-buffered by
 //              channel parity); the signal tile arrives in stage s's hi slot (TMA
 //              tensor load into the 128-byte-swizzled operand layout, or cp.async when
 //              the layout has no chunk-aligned rows); split it into TF32 hi/lo
@@ -488,12 +488,15 @@ struct TileDesc {
 //              written by a TMA tensor store (full tiles) or plain stores
 //                                                   -> tmem_free[s], stage_free[s]
 // ===========================================================================
-using pipe::kConvThreads;
+// The forward's epilogue needs few registers, so this pipeline runs 12 warps: the
+// converters are warps 0-2 and 8-11 (224 threads), the MMA issuer warp 3 and the
+// epilogue warps 4-7 (one per TMEM lane quarter).
+constexpr int kConvThreads = 224;
+constexpr int kFwdThreads = 384;
 using pipe::kEpiWarp0;
 using pipe::kMmaWarp;
 using pipe::kNamedConv;
 using pipe::kNamedEpi;
-using pipe::kPipeThreads;
 using pipe::named_sync;
 
 template <int MB, bool F64>
@@ -514,7 +517,7 @@ struct WsSmem {
 using pipe::op_piece;
 
 template <int MB, bool F64>
-__global__ void __launch_bounds__(kPipeThreads, 1)
+__global__ void __launch_bounds__(kFwdThreads, 1)
     chunk_fwd_ws_kernel(const float *__restrict__ x, const float *__restrict__ zi,
                         float *__restrict__ y, float *__restrict__ saved,
                         const char *__restrict__ ws, unsigned long long *__restrict__ counter,
@@ -574,9 +577,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         return false;
     };
 
-    if (warp < kMmaWarp) {
+    if (warp < kMmaWarp || warp >= 8) {
         // ============================ converters ============================
-        const int ct = tid;   // 0..kConvThreads-1
+        const int ct = warp < kMmaWarp ? tid : tid - 160;   // 0..kConvThreads-1
         int64_t cur_ch = -1, cur_t = 0, cur_nt = 0, cur_off = 0, cur_len = 0;
         int cur_M = 1, ch_seq = -1;
         // thread 0: describe tile i in ring[i & 3]; returns false when the work is done
@@ -1023,7 +1026,7 @@ cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *save
         make_chunk_tmap(&tmy, y, bt.total))
         use_tma = 1;
     auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
-    kern<<<(unsigned)grid, kPipeThreads, SM::ALLOC, st>>>(x, zi, y, saved, ws, counter, bt, three, x_al,
+    kern<<<(unsigned)grid, kFwdThreads, SM::ALLOC, st>>>(x, zi, y, saved, ws, counter, bt, three, x_al,
                                                        y_al, use_tma, tmx, tmy);
     return cudaGetLastError();
 }
