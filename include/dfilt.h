@@ -92,7 +92,8 @@ dfilt_status dfilt_default_opts(dfilt_opts *opts);
  * Byte sizes the caller must provide for a fixed-shape batch x[B,T]:
  *   fwd_ws     -- workspace of dfilt_forward
  *   saved      -- buffer dfilt_forward fills for dfilt_backward (chunk-boundary
- *                 states; 0 for the sequential algorithm, which re-reads y)
+ *                 states and the backward's per-channel coefficient tables; 0 for
+ *                 the sequential algorithm, which re-reads y)
  *   bwd_ws     -- workspace of dfilt_backward
  * opts may be NULL (defaults).  Output pointers may be NULL (not wanted).
  */
@@ -107,7 +108,8 @@ dfilt_status dfilt_workspace_size(int64_t B, int64_t T, int N, int M, const dfil
  *   zi  [B,M]      initial TDF-II state; NULL = zero
  *   y   [B,T]      output (must not alias any input)
  *   saved          NULL, or at least `saved` bytes from dfilt_workspace_size: filled
- *                  with what dfilt_backward needs to recompute y per chunk
+ *                  with what dfilt_backward needs to recompute y per chunk and the
+ *                  backward's coefficient tables (so the backward skips its setup)
  *   ws, ws_bytes   workspace of at least `fwd_ws` bytes (may be NULL when 0)
  * Returns DFILT_OK once all work is enqueued on `stream`.
  */
@@ -128,8 +130,10 @@ dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const
  *   gx  [B,T], gb [B,N+1], ga [B,M], gzi [B,M]   gradients; each may be NULL (not
  *                  wanted)
  *   ws, ws_bytes   workspace of at least `bwd_ws` bytes
- * opts must select the same algorithm and chunk length as the forward that
- * filled `saved`.
+ * With `saved`, b and a must be the forward's (the tables in `saved` were formed
+ * from them) and opts must select the same algorithm, chunk length and scan
+ * precision as the forward that filled `saved`.  The call may be repeated with the
+ * same `saved`.
  */
 dfilt_status dfilt_backward(const float *gy, const float *x, const float *y,
                             const float *b, const float *a, const float *zi, const void *saved,

@@ -89,7 +89,7 @@ void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, size_t *fwd, s
     size_t f = 0, s = 0, w = 0;
     if (r.algo == DFILT_ALGO_CHUNKED) {
         f = chunk_fwd_ws_bytes(B, Mmax, r.fp64_scan);
-        s = chunk_saved_bytes(B, total, Mmax);
+        s = chunk_saved_bytes(B, total, Mmax, r.fp64_scan);
         w = chunk_bwd_ws_bytes(B, Mmax, r.fp64_scan);
     }
     if (fwd) *fwd = f;

@@ -46,7 +46,10 @@ struct ChunkTab {
 // Workspace header: a 256-byte block holding the work counter, then the records.
 constexpr size_t kWsHeader = 256;
 
-cudaError_t launch_chunk_setup(const float *b, const float *a, void *ws, const Batch &bt, int MB,
-                               bool fp64_scan, bool backward, cudaStream_t st);
+// Per-channel records: forward records at fwd_tabs, backward records at bwd_tabs
+// (either may be null, not both); zeroes *counter (nullable) for the main kernel.
+cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, char *bwd_tabs,
+                               unsigned long long *counter, const Batch &bt, int MB,
+                               bool fp64_scan, cudaStream_t st);
 
 }  // namespace dfilt

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      const float *__restrict__ y, const float *__restrict__ b,
                      const float *__restrict__ a, const float *__restrict__ saved,
                      float *__restrict__ gx, float *__restrict__ gb, float *__restrict__ ga,
-                     float *__restrict__ gzi, const char *__restrict__ ws,
+                     float *__restrict__ gzi, const char *__restrict__ tabs,
                      unsigned long long *__restrict__ counter, Batch bt, int three, int al_mask) {
     using Tab = ChunkTab<MB>;
     using SM = BwdSmem<MB, F64, READ_Y>;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t ch = *ch_slot;
         if (ch >= bt.B) break;
         const Channel c = channel_of(bt, ch);
-        const char *R = ws + kWsHeader + (size_t)ch * rec;
+        const char *R = tabs + (size_t)ch * rec;
         {
             const float *g = reinterpret_cast<const float *>(R + Tab::B_G);
             const float *h = reinterpret_cast<const float *>(R + Tab::B_H);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int MB, bool F64, bool READ_Y>
 cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const float *b,
                          const float *a, const float *saved, float *gx, float *gb, float *ga,
-                         float *gzi, const char *ws, const Batch &bt, int three, int num_sms,
+                         float *gzi, const char *tabs, unsigned long long *counter, const Batch &bt, int three, int num_sms,
                          cudaStream_t st) {
     using SM = BwdSmem<MB, F64, READ_Y>;
     static_assert(SM::ALLOC <= 232448, "shared memory budget");
@@ -537,8 +537,7 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
     const int64_t grid = bt.B < slots ? bt.B : slots;
     auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     const int mask = (al(gy) ? 1 : 0) | (al(x) ? 2 : 0) | ((y && al(y)) ? 4 : 0) | ((gx && al(gx)) ? 8 : 0);
-    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
-    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws,
+    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(gy, x, y, b, a, saved, gx, gb, ga, gzi, tabs,
                                                       counter, bt, three, mask);
     return cudaGetLastError();
 }
@@ -592,7 +591,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         const float *__restrict__ bco, const float *__restrict__ aco,
                         const float *__restrict__ saved,
                         float *__restrict__ gx, float *__restrict__ gb, float *__restrict__ ga,
-                        float *__restrict__ gzi, const char *__restrict__ ws,
+                        float *__restrict__ gzi, const char *__restrict__ tabs,
                         unsigned long long *__restrict__ counter, Batch bt, int three, int al_mask,
                         int tma_mask, const __grid_constant__ CUtensorMap tmg,
                         const __grid_constant__ CUtensorMap tmx,
@@ -696,7 +695,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             d.last = cur_t == cur_nt;
         };
         auto build_tables = [&](const TileDesc &d) {
-            const char *R = ws + kWsHeader + (size_t)d.ch * rec;
+            const char *R = tabs + (size_t)d.ch * rec;
             const float *__restrict__ h = reinterpret_cast<const float *>(R + Tab::B_H);
             char *T = smem + tslot(d.tab);
             // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, half of the rows)
@@ -1166,7 +1165,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
 template <int MB, bool F64>
 cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
                           const float *a, const float *saved, float *gx, float *gb, float *ga,
-                          float *gzi, const char *ws, const Batch &bt, int three, int num_sms,
+                          float *gzi, const char *tabs, unsigned long long *counter, const Batch &bt, int three, int num_sms,
                           cudaStream_t st) {
     using SM = BwSmem<MB, F64>;
     static_assert(SM::ALLOC <= pipe::kSmemMax, "shared memory budget");
@@ -1195,8 +1194,7 @@ cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
         if (make_chunk_tmap(&tmx, x, bt.total)) tma |= 2;
         if (gx && make_chunk_tmap(&tmgx, gx, bt.total)) tma |= 4;
     }
-    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
-    kern<<<(unsigned)grid, pipe::kPipeThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, counter,
+    kern<<<(unsigned)grid, pipe::kPipeThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter,
                                                        bt, three, mask, tma, tmg, tmx, tmgx);
     return cudaGetLastError();
 }
@@ -1206,14 +1204,14 @@ cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
 template <int MB>
 cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const float *b,
                          const float *a, const float *saved, float *gx, float *gb, float *ga,
-                         float *gzi, const char *ws, const Batch &bt, bool fp64_scan, bool read_y,
+                         float *gzi, const char *tabs, unsigned long long *counter, const Batch &bt, bool fp64_scan, bool read_y,
                          int three, int num_sms, cudaStream_t st) {
-#define ARGS gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st
+#define ARGS gy, x, y, b, a, saved, gx, gb, ga, gzi, tabs, counter, bt, three, num_sms, st
     if constexpr (MB <= 8) {
         // warp-specialised kernel (recomputes y from the saved chunk states)
         if (!read_y) {
-            if (fp64_scan) return launch_bwd_ws<MB, true>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st);
-            return launch_bwd_ws<MB, false>(gy, x, b, a, saved, gx, gb, ga, gzi, ws, bt, three, num_sms, st);
+            if (fp64_scan) return launch_bwd_ws<MB, true>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter, bt, three, num_sms, st);
+            return launch_bwd_ws<MB, false>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter, bt, three, num_sms, st);
         }
     }
     if (read_y) {
@@ -1231,7 +1229,8 @@ cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const 
 
 template cudaError_t chunk_bwd_mb<DFILT_MB>(const float *, const float *, const float *,
                                             const float *, const float *, const float *, float *,
-                                            float *, float *, float *, const char *, const Batch &,
-                                            bool, bool, int, int, cudaStream_t);
+                                            float *, float *, float *, const char *,
+                                            unsigned long long *, const Batch &, bool, bool, int,
+                                            int, cudaStream_t);
 
 }  // namespace dfilt

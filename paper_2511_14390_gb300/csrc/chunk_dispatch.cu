@@ -13,8 +13,8 @@ namespace dfilt {
                                                 cudaStream_t);                                   \
     extern template cudaError_t chunk_bwd_mb<V>(                                                 \
         const float *, const float *, const float *, const float *, const float *,              \
-        const float *, float *, float *, float *, float *, const char *, const Batch &, bool,    \
-        bool, int, int, cudaStream_t);
+        const float *, float *, float *, float *, float *, const char *, unsigned long long *,  \
+        const Batch &, bool, bool, int, int, cudaStream_t);
 DFILT_CHUNK_BUCKETS(DFILT_EXTERN)
 #undef DFILT_EXTERN
 
@@ -82,14 +82,24 @@ size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan) {
     return kWsHeader + (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).bwd_tab;
 }
 
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, bool fp64_scan) {
+    return chunk_saved_state_bytes(B, total, Mmax) +
+           (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).bwd_tab;
+}
+
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
                              bool fp64_scan, int precision, int num_sms, cudaStream_t st) {
     const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
-    cudaError_t e = launch_chunk_setup(b, a, ws, bt, l.MB, l.fp64_scan, false, st);
+    // with a saved buffer, the same launch also writes the backward's tables into it
+    char *w = static_cast<char *>(ws);
+    char *btabs = saved ? reinterpret_cast<char *>(saved) + chunk_saved_state_bytes(bt.B, bt.total, Mmax)
+                        : nullptr;
+    cudaError_t e = launch_chunk_setup(b, a, w + kWsHeader, btabs,
+                                       reinterpret_cast<unsigned long long *>(w), bt, l.MB,
+                                       l.fp64_scan, st);
     if (e != cudaSuccess) return e;
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
-    const char *w = static_cast<const char *>(ws);
     switch (l.MB) {
 #define X(V) \
     case V: return chunk_fwd_mb<V>(x, zi, y, saved, w, bt, l.fp64_scan, three, num_sms, st);
@@ -106,15 +116,25 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
     const bool read_y = saved == nullptr;   // y is recomputed whenever the chunk states exist
     if (read_y && (!y || l.MB > 32)) return cudaErrorNotSupported;
-    cudaError_t e = launch_chunk_setup(b, a, ws, bt, l.MB, l.fp64_scan, true, st);
+    char *wsc = static_cast<char *>(ws);
+    auto *counter = reinterpret_cast<unsigned long long *>(wsc);
+    const char *w;
+    cudaError_t e;
+    if (saved) {
+        // the forward's setup left the backward tables behind the chunk states
+        w = reinterpret_cast<const char *>(saved) + chunk_saved_state_bytes(bt.B, bt.total, Mmax);
+        e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    } else {
+        w = wsc + kWsHeader;
+        e = launch_chunk_setup(b, a, nullptr, wsc + kWsHeader, counter, bt, l.MB, l.fp64_scan, st);
+    }
     if (e != cudaSuccess) return e;
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
-    const char *w = static_cast<const char *>(ws);
     switch (l.MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
-        return chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, bt, l.fp64_scan,     \
-                               read_y, three, num_sms, st);
+        return chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, counter, bt,         \
+                               l.fp64_scan, read_y, three, num_sms, st);
         DFILT_CHUNK_BUCKETS(X)
 #undef X
     }

@@ -1,21 +1,22 @@
-// Coefficient setup of the chunked algorithm: per channel, in FP64, the impulse
-// responses, the free-response and end-state blocks, and the chunk transition of the
-// chunk algebra (see chunk.cuh).  FP64 because companion-matrix powers of high-order
-// filters grow transiently by orders of magnitude before they decay; the transition
-// is formed by L successive companion products (no repeated squaring, which loses
-// accuracy on those filters).
+// Coefficient setup of the chunked algorithm: per channel, the impulse responses, the
+// free-response and end-state blocks, and the chunk transition of the chunk algebra
+// (see chunk.cuh), formed in extended precision and rounded to the operand precision.
+// One launch writes the forward records, the backward records, or both (grid.y).
 //
 // GB300's FP64 pipe is narrow and a warp-wide FP64 instruction costs it the same
 // whether 1 or 32 lanes are active, so both variants keep every lane busy:
-//   * low orders (MB <= 4): one channel per thread, everything in registers, in
-//     double-word arithmetic (dword.cuh) on the full-rate FP32 pipes;
-//   * higher orders: one block per channel, thread m evolves column m of F^i
+//   * low orders (MB <= 4): one warp per channel in double-word arithmetic
+//     (dword.cuh) on the full-rate FP32 pipes; one serial recurrence for the
+//     all-pole impulse response, then every table entry as a short sum over it;
+//   * higher orders: FP64, one block per channel, thread m evolves column m of F^i
 //     (i = 0..L) and every table is read off those columns in parallel:
 //       O_L[i][m] = (F^i e_m)[0],  g[n] = sum_m Gv_m O_L[n-1][m] (n >= 1),
 //       h[n] likewise with the all-pole input vector, R_L[:, L-1-i] = F^i Gv
-//       (a reduction over the columns held in shared memory), Abar = F^L.
-//     The backward's O^u columns run the anti-causal all-pole recursion from a
-//     unit future state, one column per thread.
+//       (a reduction over the columns held in shared memory), Abar = F^L
+//     (L successive companion products: companion-matrix powers of high-order
+//     filters grow transiently by orders of magnitude, and repeated squaring loses
+//     accuracy on them).  The backward's O^u columns run the anti-causal all-pole
+//     recursion from a unit future state, one column per thread.
 #include "chunk.cuh"
 #include "dword.cuh"
 
@@ -24,163 +25,167 @@ namespace dfilt {
 namespace {
 
 // ---------------------------------------------------------------------------
-// low orders: one channel per thread, double-word arithmetic on the FP32 pipes
+// low orders: one warp per channel, double-word arithmetic on the FP32 pipes.
+// Every table is a short sum over the all-pole impulse response h (the impulse
+// response of 1/A) and the coefficients, so after one serial recurrence for h
+// (lane 0) the lanes fill the tables in parallel, with coalesced stores.  With the
+// TDF-II state s_k[n] = sum_{j>k} (b_j x[n+k-j] - a_j y[n+k-j]) (n >= M):
+//   g[n]        = sum_k b_k h[n-k]                       (impulse response of B/A)
+//   O_L[i][m]   = h[i-m]                                 (zi enters as an injected input)
+//   R_L[k][j]   = b_t - sum_{l>k} a_l g[t-l],   t = L+k-j
+//   Abar[k][m]  = -sum_{l>k} a_l h[L+k-l-m]
+//   O^u[n][m]   = -sum_{j<=min(L-1-n, MB-1-m)} a_{j+1+m} h[L-1-n-j]
+//                 (the adjoint recursion in reversed time, its future values turned
+//                  into injected inputs)
+//   O^gx[n][m]  = sum_k b_k U(n+k, m),  U(p, m) = O^u[p][m] (p < L), [p-L == m] else
+//   Abar'[k][m] = O^u[k][m]
 // ---------------------------------------------------------------------------
+constexpr int kSmallWarps = 4;   // channels per block
+
 template <int MB>
-__global__ void __launch_bounds__(64) setup_small_kernel(const float *__restrict__ b,
-                                                         const float *__restrict__ a,
-                                                         char *__restrict__ ws, Batch bt,
-                                                         bool f64, bool backward) {
+struct SmallScratch {
+    float hhi[kL + MB], hlo[kL + MB];   // h[0 .. L+MB)
+    float ghi[kL], glo[kL];             // g[0 .. L)
+    float uhi[kL * MB], ulo[kL * MB];   // O^u (backward)
+    float ahi[2][MB * MB], alo[2][MB * MB];
+};
+
+template <int MB>
+__global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
+    const float *__restrict__ b, const float *__restrict__ a, char *__restrict__ fwd_tabs,
+    char *__restrict__ bwd_tabs, unsigned long long *__restrict__ counter, Batch bt, bool f64) {
     using Tab = ChunkTab<MB>;
     constexpr int L = kL;
-    const int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ch == 0) *reinterpret_cast<unsigned long long *>(ws) = 0ull;   // work counter
+    __shared__ SmallScratch<MB> scr_all[kSmallWarps];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    SmallScratch<MB> &sc = scr_all[wib];
+    const int64_t ch = (int64_t)blockIdx.x * kSmallWarps + wib;
+    if (counter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *counter = 0ull;
+    // grid.y selects the record: forward tables, backward tables, or both
+    const bool backward = fwd_tabs == nullptr || blockIdx.y == 1;
     if (ch >= bt.B) return;
     const Channel c = channel_of(bt, ch);
-    dw av[MB], bp[MB + 1], G[MB];
+    dw av[MB], bp[MB + 1];   // av[k] = a_{k+1}; zero past the channel's orders
 #pragma unroll
     for (int k = 0; k < MB; ++k) av[k] = dw_make(k < c.M ? a[ch * bt.Mstride + k] : 0.f);
 #pragma unroll
     for (int k = 0; k <= MB; ++k) bp[k] = dw_make(k <= c.N ? b[ch * bt.Nstride + k] : 0.f);
+    auto H = [&](int n) -> dw { return n >= 0 ? dw{sc.hhi[n], sc.hlo[n]} : dw_make(0.f); };
+    auto G = [&](int n) -> dw { return n >= 0 ? dw{sc.ghi[n], sc.glo[n]} : dw_make(0.f); };
+    // h by the all-pole difference equation (the one serial chain)
+    if (lane == 0) {
+        dw wh[MB];
 #pragma unroll
-    for (int k = 0; k < MB; ++k) G[k] = bp[k + 1] - av[k] * bp[0];
+        for (int k = 0; k < MB; ++k) wh[k] = dw_make(0.f);
+        for (int n = 0; n < L + MB; ++n) {
+            dw yh = dw_make(n == 0 ? 1.f : 0.f);
+#pragma unroll
+            for (int k = 0; k < MB; ++k) yh = yh - av[k] * wh[k];
+#pragma unroll
+            for (int k = MB - 1; k > 0; --k) wh[k] = wh[k - 1];
+            wh[0] = yh;
+            sc.hhi[n] = yh.hi;
+            sc.hlo[n] = yh.lo;
+        }
+    }
+    __syncwarp();
     const size_t rec = backward ? Tab::bwd_rec(f64) : Tab::fwd_rec(f64);
-    char *R = ws + kWsHeader + (size_t)ch * rec;
-    dw A[MB][MB];   // chunk transition
+    char *R = (backward ? bwd_tabs : fwd_tabs) + (size_t)ch * rec;
+    float *g = reinterpret_cast<float *>(R + (backward ? Tab::B_G : Tab::F_G));
+    for (int n = lane; n < L; n += 32) {
+        dw acc = dw_make(0.f);
+#pragma unroll
+        for (int k = 0; k <= MB; ++k) acc = acc + bp[k] * H(n - k);
+        sc.ghi[n] = acc.hi;
+        sc.glo[n] = acc.lo;
+        g[n] = dw_to_float(acc);
+    }
+    __syncwarp();
     if (!backward) {
-        float *g = reinterpret_cast<float *>(R + Tab::F_G);
         float *RL = reinterpret_cast<float *>(R + Tab::F_RL);
         float *OL = reinterpret_cast<float *>(R + Tab::F_OL);
-        // r = e1^T F^i (rows of O_L), v = F^i Gv (columns of R_L, g[i+1] = v_0)
-        dw r[MB], v[MB];
-#pragma unroll
-        for (int k = 0; k < MB; ++k) {
-            r[k] = dw_make(k == 0 ? 1.f : 0.f);
-            v[k] = G[k];
+        for (int idx = lane; idx < L * MB; idx += 32) {
+            const int i = idx / MB, m = idx % MB;
+            OL[idx] = dw_to_float(H(i - m));
         }
-        // rows[j] = e1^T F^(L-j), j = 0..MB, for the rows of Abar = F^L (below)
-        dw rows[MB + 1][MB];
-        g[0] = dw_to_float(bp[0]);
-        for (int i = 0; i < L; ++i) {
+        for (int idx = lane; idx < MB * L; idx += 32) {
+            const int k = idx / L, j = idx % L, t = L + k - j;
+            dw acc = dw_make(0.f);
 #pragma unroll
-            for (int m = 0; m < MB; ++m) OL[i * MB + m] = dw_to_float(r[m]);
-            if (i + 1 < L) g[i + 1] = dw_to_float(v[0]);
+            for (int l = 1; l <= MB; ++l)
+                if (l == t) acc = bp[l];
 #pragma unroll
-            for (int k = 0; k < MB; ++k) RL[k * L + (L - 1 - i)] = dw_to_float(v[k]);
-#pragma unroll
-            for (int j = 1; j <= MB; ++j)
-                if (i == L - j) {
-#pragma unroll
-                    for (int k = 0; k < MB; ++k) rows[j][k] = r[k];
-                }
-            // (F v)_k = v_{k+1} - a_{k+1} v_0 ;  (r F)_0 = -sum_k r_k a_{k+1}, (r F)_j = r_{j-1}
-            const dw v0 = v[0];
-#pragma unroll
-            for (int k = 0; k < MB; ++k) v[k] = (k + 1 < MB ? v[k + 1] : dw_make(0.f)) - av[k] * v0;
-            dw r0 = dw_make(0.f);
-#pragma unroll
-            for (int k = 0; k < MB; ++k) r0 = r0 - r[k] * av[k];
-#pragma unroll
-            for (int k = MB - 1; k > 0; --k) r[k] = r[k - 1];
-            r[0] = r0;
+            for (int l = 1; l <= MB; ++l)
+                if (l > k) acc = acc - av[l - 1] * G(t - l);
+            RL[idx] = dw_to_float(acc);
         }
+        if (lane < MB * MB) {
+            const int k = lane / MB, m = lane % MB;
+            dw acc = dw_make(0.f);
 #pragma unroll
-        for (int k = 0; k < MB; ++k) rows[0][k] = r[k];
-        // Rows of F^L from e_k^T F = -a_{k+1} e_0^T + e_{k+1}^T:
-        //   e_k^T F^L = -sum_{j=0}^{MB-1-k} a_{k+1+j} e_0^T F^(L-1-j)   (k >= 1)
-#pragma unroll
-        for (int m = 0; m < MB; ++m) A[0][m] = rows[0][m];
-#pragma unroll
-        for (int k = 1; k < MB; ++k)
-#pragma unroll
-            for (int m = 0; m < MB; ++m) {
-                dw acc = dw_make(0.f);
-#pragma unroll
-                for (int j = 0; j <= MB - 1 - k; ++j) acc = acc - av[k + j] * rows[1 + j][m];
-                A[k][m] = acc;
-            }
+            for (int l = 1; l <= MB; ++l)
+                if (l > k) acc = acc - av[l - 1] * H(L + k - l - m);
+            sc.ahi[0][lane] = acc.hi;
+            sc.alo[0][lane] = acc.lo;
+        }
     } else {
-        float *g = reinterpret_cast<float *>(R + Tab::B_G);
         float *h = reinterpret_cast<float *>(R + Tab::B_H);
         float *Ou = reinterpret_cast<float *>(R + Tab::B_OU);
         float *Ogx = reinterpret_cast<float *>(R + Tab::B_OGX);
-        // impulse responses by the difference equation, sliding windows of MB outputs
-        dw wg[MB], wh[MB];
+        for (int n = lane; n < L; n += 32) h[n] = dw_to_float(H(n));
+        for (int idx = lane; idx < L * MB; idx += 32) {
+            const int n = idx / MB, m = idx % MB;
+            dw acc = dw_make(0.f);
 #pragma unroll
-        for (int k = 0; k < MB; ++k) wg[k] = wh[k] = dw_make(0.f);
-        for (int n = 0; n < L; ++n) {
-            dw yg = dw_make(0.f), yh = dw_make(n == 0 ? 1.f : 0.f);
-#pragma unroll
-            for (int k = 0; k <= MB; ++k)
-                if (n == k) yg = bp[k];   // numerator input b_n (zero past order MB)
-#pragma unroll
-            for (int k = 0; k < MB; ++k) {
-                yg = yg - av[k] * wg[k];
-                yh = yh - av[k] * wh[k];
-            }
-#pragma unroll
-            for (int k = MB - 1; k > 0; --k) {
-                wg[k] = wg[k - 1];
-                wh[k] = wh[k - 1];
-            }
-            wg[0] = yg;
-            wh[0] = yh;
-            g[n] = dw_to_float(yg);
-            h[n] = dw_to_float(yh);
+            for (int j = 0; j < MB; ++j)
+                if (j <= L - 1 - n && j <= MB - 1 - m) acc = acc - av[j + m] * H(L - 1 - n - j);
+            sc.uhi[idx] = acc.hi;
+            sc.ulo[idx] = acc.lo;
+            Ou[idx] = dw_to_float(acc);
         }
-        // O^u and O^gx columns: anti-causal all-pole recursion from u[L+m] = delta
+        __syncwarp();
+        for (int idx = lane; idx < L * MB; idx += 32) {
+            const int n = idx / MB, m = idx % MB;
+            dw acc = dw_make(0.f);
 #pragma unroll
-        for (int m = 0; m < MB; ++m) {
-            dw e[MB + 1];   // e[j] = u[n + j], j = 0..MB
-#pragma unroll
-            for (int j = 0; j <= MB; ++j) e[j] = dw_make(j == m + 1 ? 1.f : 0.f);
-            for (int n = L - 1; n >= 0; --n) {
-                dw un = dw_make(0.f);
-#pragma unroll
-                for (int k = 1; k <= MB; ++k) un = un - av[k - 1] * e[k];
-                e[0] = un;
-                dw gxn = dw_make(0.f);
-#pragma unroll
-                for (int k = 0; k <= MB; ++k) gxn = gxn + bp[k] * e[k];
-                Ou[n * MB + m] = dw_to_float(un);
-                Ogx[n * MB + m] = dw_to_float(gxn);
-#pragma unroll
-                for (int k = 0; k < MB; ++k)
-                    if (n == k) A[k][m] = un;
-#pragma unroll
-                for (int j = MB; j > 0; --j) e[j] = e[j - 1];
+            for (int k = 0; k <= MB; ++k) {
+                const int p = n + k;
+                if (p < L) acc = acc + bp[k] * dw{sc.uhi[p * MB + m], sc.ulo[p * MB + m]};
+                else if (p - L == m) acc = acc + bp[k];
             }
+            Ogx[idx] = dw_to_float(acc);
+        }
+        if (lane < MB * MB) {
+            sc.ahi[0][lane] = sc.uhi[lane];   // Abar'[k][m] = O^u[k][m], k < MB
+            sc.alo[0][lane] = sc.ulo[lane];
         }
     }
+    __syncwarp();
     char *S = R + (backward ? Tab::B_SCAN : Tab::F_SCAN);
     if (f64) {
         double *At = reinterpret_cast<double *>(S);
-#pragma unroll
-        for (int j = 0; j < MB; ++j)
-#pragma unroll
-            for (int m = 0; m < MB; ++m) At[j * MB + m] = dw_to_double(A[m][j]);
+        if (lane < MB * MB) {
+            const int j = lane / MB, m = lane % MB;   // At[j][m] = A[m][j]
+            At[lane] = dw_to_double(dw{sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]});
+        }
     } else {
         float *P = reinterpret_cast<float *>(S);
+        int cur = 0;
         for (int kp = 0; kp < Tab::NPOW; ++kp) {
-#pragma unroll
-            for (int i = 0; i < MB; ++i)
-#pragma unroll
-                for (int j = 0; j < MB; ++j) P[(kp * MB + i) * MB + j] = dw_to_float(A[i][j]);
+            if (lane < MB * MB) P[kp * MB * MB + lane] = dw_to_float(dw{sc.ahi[cur][lane], sc.alo[cur][lane]});
             if (kp + 1 == Tab::NPOW) break;
-            dw Q[MB][MB];
+            if (lane < MB * MB) {
+                const int i = lane / MB, j = lane % MB;
+                dw acc = dw_make(0.f);
 #pragma unroll
-            for (int i = 0; i < MB; ++i)
-#pragma unroll
-                for (int j = 0; j < MB; ++j) {
-                    dw acc = dw_make(0.f);
-#pragma unroll
-                    for (int k = 0; k < MB; ++k) acc = acc + A[i][k] * A[k][j];
-                    Q[i][j] = acc;
-                }
-#pragma unroll
-            for (int i = 0; i < MB; ++i)
-#pragma unroll
-                for (int j = 0; j < MB; ++j) A[i][j] = Q[i][j];
+                for (int k = 0; k < MB; ++k)
+                    acc = acc + dw{sc.ahi[cur][i * MB + k], sc.alo[cur][i * MB + k]} *
+                                    dw{sc.ahi[cur][k * MB + j], sc.alo[cur][k * MB + j]};
+                sc.ahi[cur ^ 1][lane] = acc.hi;
+                sc.alo[cur ^ 1][lane] = acc.lo;
+            }
+            __syncwarp();
+            cur ^= 1;
         }
     }
 }
@@ -194,10 +199,9 @@ constexpr size_t setup_large_smem() {
 }
 
 template <int MB>
-__global__ void __launch_bounds__(MB) setup_large_kernel(const float *__restrict__ b,
-                                                         const float *__restrict__ a,
-                                                         char *__restrict__ ws, Batch bt,
-                                                         bool f64, bool backward) {
+__global__ void __launch_bounds__(MB) setup_large_kernel(
+    const float *__restrict__ b, const float *__restrict__ a, char *__restrict__ fwd_tabs,
+    char *__restrict__ bwd_tabs, unsigned long long *__restrict__ counter, Batch bt, bool f64) {
     using Tab = ChunkTab<MB>;
     constexpr int L = kL;
     extern __shared__ double sdyn[];
@@ -209,7 +213,9 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(const float *__restrict
 
     const int64_t ch = blockIdx.x;
     const int m = threadIdx.x;
-    if (ch == 0 && m == 0) *reinterpret_cast<unsigned long long *>(ws) = 0ull;
+    if (counter && ch == 0 && blockIdx.y == 0 && m == 0) *counter = 0ull;
+    // grid.y selects the record: forward tables, backward tables, or both
+    const bool backward = fwd_tabs == nullptr || blockIdx.y == 1;
     const Channel c = channel_of(bt, ch);
     sa[m] = m < c.M ? (double)a[ch * bt.Mstride + m] : 0.0;
     sbp[m] = m <= c.N ? (double)b[ch * bt.Nstride + m] : 0.0;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(const float *__restrict
     sG[m] = sbp[m + 1] - sa[m] * sbp[0];
     sGh[m] = -sa[m];   // input vector of the all-pole filter (b = [1])
     const size_t rec = backward ? Tab::bwd_rec(f64) : Tab::fwd_rec(f64);
-    char *R = ws + kWsHeader + (size_t)ch * rec;
+    char *R = (backward ? bwd_tabs : fwd_tabs) + (size_t)ch * rec;
     __syncthreads();
 
     if (!backward) {
@@ -332,30 +338,35 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(const float *__restrict
 
 }  // namespace
 
-cudaError_t launch_chunk_setup(const float *b, const float *a, void *ws, const Batch &bt, int MB,
-                               bool fp64_scan, bool backward, cudaStream_t st) {
-    char *w = static_cast<char *>(ws);
-    const unsigned small_grid = (unsigned)((bt.B + 63) / 64);
-    const unsigned large_grid = (unsigned)bt.B;
+cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, char *bwd_tabs,
+                               unsigned long long *counter, const Batch &bt, int MB,
+                               bool fp64_scan, cudaStream_t st) {
+    if (!fwd_tabs && !bwd_tabs) return cudaErrorInvalidValue;
+    const unsigned gy = (fwd_tabs && bwd_tabs) ? 2u : 1u;
+    const dim3 small_grid((unsigned)((bt.B + kSmallWarps - 1) / kSmallWarps), gy);
+    const dim3 large_grid((unsigned)bt.B, gy);
+    auto small = [&](auto kern) -> cudaError_t {
+        kern<<<small_grid, 32 * kSmallWarps, 0, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan);
+        return cudaGetLastError();
+    };
     auto large = [&](auto kern, int mb, size_t smem) -> cudaError_t {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<large_grid, mb, smem, st>>>(b, a, w, bt, fp64_scan, backward);
+        kern<<<large_grid, mb, smem, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan);
         return cudaGetLastError();
     };
     switch (MB) {
-        case 2: setup_small_kernel<2><<<small_grid, 64, 0, st>>>(b, a, w, bt, fp64_scan, backward); break;
-        case 4: setup_small_kernel<4><<<small_grid, 64, 0, st>>>(b, a, w, bt, fp64_scan, backward); break;
+        case 2: return small(setup_small_kernel<2>);
+        case 4: return small(setup_small_kernel<4>);
         case 8: return large(setup_large_kernel<8>, 8, setup_large_smem<8>());
         case 16: return large(setup_large_kernel<16>, 16, setup_large_smem<16>());
         case 32: return large(setup_large_kernel<32>, 32, setup_large_smem<32>());
         case 64: return large(setup_large_kernel<64>, 64, setup_large_smem<64>());
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace dfilt

@@ -35,11 +35,14 @@ struct ChunkLayout {
 };
 ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt);
 
-// Chunk-state buffer (`saved`): channel i's chunks start at chunk index
-// offsets[i] / L + i; each chunk stores Mstride floats.
-inline size_t chunk_saved_bytes(int64_t B, int64_t total, int Mstride) {
-    return (size_t)(total / kL + B + 1) * (size_t)Mstride * sizeof(float);
+// Forward-to-backward buffer (`saved`): the chunk states (channel i's chunks start at
+// chunk index offsets[i] / L + i; each chunk stores Mstride floats), then, 256-byte
+// aligned, the backward's per-channel tables, which the forward's setup writes so
+// that the backward needs no setup of its own.
+inline size_t chunk_saved_state_bytes(int64_t B, int64_t total, int Mstride) {
+    return ((size_t)(total / kL + B + 1) * (size_t)Mstride * sizeof(float) + 255) / 256 * 256;
 }
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, bool fp64_scan);
 
 // Per-bucket launchers (one translation unit per bucket, compiled with -DDFILT_MB=<MB>).
 template <int MB>
@@ -48,8 +51,9 @@ cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved
 template <int MB>
 cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const float *b,
                          const float *a, const float *saved, float *gx, float *gb, float *ga,
-                         float *gzi, const char *ws, const Batch &bt, bool fp64_scan, bool read_y,
-                         int three, int num_sms, cudaStream_t st);
+                         float *gzi, const char *tabs, unsigned long long *counter,
+                         const Batch &bt, bool fp64_scan, bool read_y, int three, int num_sms,
+                         cudaStream_t st);
 #define DFILT_CHUNK_BUCKETS(X) X(2) X(4) X(8) X(16) X(32) X(64)
 // Largest bucket whose FP32 Hillis-Steele scan tables fit (and are used at all).
 constexpr int kMaxF32ScanBucket = 16;
