@@ -35,7 +35,7 @@ FALLBACK_HBM = 6800.0
 def args_():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="biquad_1024x48000")
@@ -43,6 +43,8 @@ def args_():
     p.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel leg")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--channels", type=int, default=0,
+                   help="override the workload's channel count (smaller profiling cases)")
     return p.parse_args()
 
 
@@ -73,7 +75,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -162,6 +164,42 @@ def run_reference(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def kernel_name(direction, M):
+    """Main kernel of the chunked path for a state bucket (the warp-specialised kernels
+    serve the buckets whose layouts fit; see the dispatch in csrc/chunk_*.cu)."""
+    mb = next(v for v in (2, 4, 8, 16, 32, 64) if M <= v)
+    f64 = 1 if M > 4 else 0
+    if direction == "forward":
+        return f"chunk_fwd_ws_kernel<{mb}, {f64}>"
+    return f"chunk_bwd_ws_kernel<{mb}, {f64}>" if mb <= 8 else f"chunk_bwd_kernel<{mb}, {f64}, 0>"
+
+
+def profiled_traffic(kname, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kname`
+    from the committed ncu summary of this workload, scaled to one full launch; None
+    when there is no summary or the kernel source changed since it was captured."""
+    import glob
+    import hashlib
+    import re
+    base = kname.split("<")[0]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{base}_*.md"))):
+        txt = open(path).read()
+        m = re.search(r"<!-- traffic kernel=(\S+) workload=(\S+) bytes_per_launch=([0-9.e+]+) "
+                      r"sources=(\S+) sha256=([0-9a-f]+) -->", txt)
+        if not m or m.group(1) != kname.replace(" ", "") or m.group(2) != workload:
+            continue
+        h = hashlib.sha256()
+        for rel in m.group(4).split(","):
+            src = os.path.join(ROOT, rel)
+            if not os.path.exists(src):
+                return None
+            h.update(open(src, "rb").read())
+        if h.hexdigest() != m.group(5):
+            return None   # stale: the kernel changed since the counters were taken
+        return float(m.group(3))
+    return None
+
+
 def workload_config(w, name, algo):
     return {"workload": name, "B": int(w.B), "T": int(w.x.shape[1]), "M": int(w.M),
             "N": int(w.N), "algo": algo,
@@ -185,7 +223,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = inputs.make(a.workload)
+    w = inputs.make(a.workload, **({"B": a.channels} if a.channels > 0 else {}))
     B, T = w.x.shape
     N, M = w.N, w.M
     dev = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).cuda()
@@ -222,7 +260,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def timed(st, steps, warmup):
+    def timed(st, steps, warmup, kernel_timing=False):
         for _ in range(warmup):
             fwd(st)
             bwd(st)
@@ -230,6 +268,8 @@ def main():
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
         barrier()
         torch.cuda.synchronize()
+        if kernel_timing:   # event pairs around each call's main kernel, on this stream
+            dfilt.dfilt_kernel_timing(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(steps):
@@ -241,10 +281,15 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        kern = None
+        if kernel_timing:
+            (fm, fn), (bm, bn) = dfilt.dfilt_kernel_timing_read()
+            dfilt.dfilt_kernel_timing(False)
+            kern = (fm / max(fn, 1), bm / max(bn, 1), fn, bn)
         tot = e0.elapsed_time(e1)
         tf = [e[0].elapsed_time(e[1]) for e in ev]
         tb = [e[1].elapsed_time(e[2]) for e in ev]
-        return tot / steps, statistics.mean(tf), statistics.mean(tb)
+        return tot / steps, statistics.mean(tf), statistics.mean(tb), kern
 
     def maxrank(v):
         if world == 1:
@@ -256,7 +301,7 @@ def main():
     algo = a.algo
     st = setup(algo)
     clk = Clocks(gpu_uuid(torch))
-    ms, ms_f, ms_b = timed(st, a.steps, a.warmup)
+    ms, ms_f, ms_b, kern = timed(st, a.steps, a.warmup, kernel_timing=True)
     clocks = clk.stop()
     ms = maxrank(ms)
     samples_all = B * T * world
@@ -285,7 +330,7 @@ def main():
     seq = None
     if not a.no_seq and algo == "chunked":
         sst = setup("sequential")
-        sms, sf, sb = timed(sst, max(3, a.steps // 4), 2)
+        sms, sf, sb, _ = timed(sst, max(3, min(50, a.steps // 4)), 3)
         sms = maxrank(sms)
         seq = {"value": samples_all / (sms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": sms,
                "ms_fwd": sf, "ms_bwd": sb}
@@ -312,11 +357,11 @@ def main():
                            (ogz, st["gz"])):
                 h_.copy_(d_, non_blocking=True)
 
-        for _ in range(2):
+        for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
-        k = max(3, a.steps // 4)
+        k = max(3, min(50, a.steps // 4))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k):
@@ -336,24 +381,35 @@ def main():
         hbm, src = peaks()
         # algorithmic bytes per sample: forward reads x, writes y; backward reads gy and
         # x, writes grad_x (y is recomputed from M floats of chunk state per 64 samples)
-        bytes_f = (8.0 + (4.0 * M / 64.0)) * B * T
-        bytes_b = (12.0 + (4.0 * M / 64.0)) * B * T
-        dom_b, dom_ms, dom = ((bytes_b, ms_b, "backward") if ms_b >= ms_f
-                              else (bytes_f, ms_f, "forward"))
+        # (the sequential kernel re-reads y in the backward)
+        if algo == "chunked":
+            bytes_f = (8.0 + (4.0 * M / 64.0)) * B * T
+            bytes_b = (12.0 + (4.0 * M / 64.0)) * B * T
+        else:
+            bytes_f, bytes_b = 8.0 * B * T, 16.0 * B * T
+        kf, kb, kfn, kbn = kern
+        dom_b, dom_ms, dom = ((bytes_b, kb, "backward") if kb >= kf else (bytes_f, kf, "forward"))
         achieved = dom_b / (dom_ms / 1e3) / 1e9
+        kname = kernel_name(dom, M) if algo == "chunked" else ("seq_fwd_kernel" if dom == "forward" else "seq_bwd_kernel")
+        traffic = profiled_traffic(kname, a.workload)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "precision": "tf32x3" if algo == "chunked" else "fp32",
             "data": "synthetic", "config": workload_config(w, a.workload, algo),
-            "ms_fwd": ms_f, "ms_bwd": ms_b, "rel_err_vs_fp64": rel_err, "sequential": seq,
+            "ms_fwd": ms_f, "ms_bwd": ms_b, "ms_fwd_kernel": kf, "ms_bwd_kernel": kb,
+            "rel_err_vs_fp64": rel_err, "sequential": seq,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": f"chunked {dom} (setup + main kernel, one C-ABI call)",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes": dom_b,
+                         "kernel": f"{kname} ({dom} main kernel, CUDA events around each of "
+                                   f"its {kfn if dom == 'forward' else kbn} launches)",
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                         else "fallback"},
+                         else "fallback (6.8 TB/s)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 4 * a.steps,
+            # per step: forward = setup + main kernel, backward = main kernel (its work
+            # counter is cleared by a memset)
+            "gpu_launches": 3 * a.steps if algo == "chunked" else 2 * a.steps,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -178,6 +178,20 @@ dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float 
 dfilt_status dfilt_sync_status(void *stream);
 
 /*
+ * Kernel timing (a measurement aid; the paper has no counterpart).
+ * dfilt_kernel_timing(1) makes every later forward/backward call record a pair of
+ * CUDA events on its stream around its main kernel (not the coefficient setup), up
+ * to 4096 pending pairs; dfilt_kernel_timing(0) stops recording.  Either call
+ * discards pairs not yet read.  dfilt_kernel_timing_read waits for the recorded
+ * pairs, returns the summed durations (milliseconds) and the number of calls per
+ * direction (each output pointer may be NULL), and discards them.  Recording must
+ * be off while a stream is being captured into a CUDA graph.
+ */
+dfilt_status dfilt_kernel_timing(int enable);
+dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
+                                      int *bwd_calls);
+
+/*
  * Test hook for the bounded device-side waits (no waits are unbounded).
  *   iters > 0   cap every wait at `iters` polls
  *   iters == 0  restore the default cap

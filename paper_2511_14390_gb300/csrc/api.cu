@@ -123,8 +123,12 @@ dfilt_status do_forward(const float *x, const float *b, const float *a, const fl
                         void *saved, void *ws, size_t ws_bytes, const Batch &bt, int Mmax,
                         const Resolved &r, const DevInfo &di, cudaStream_t st) {
     if (bt.B == 0 || bt.total == 0) return DFILT_OK;
-    if (r.algo == DFILT_ALGO_SEQUENTIAL)
-        return cuda_status(launch_seq_fwd(x, b, a, zi, y, bt, Mmax, st));
+    if (r.algo == DFILT_ALGO_SEQUENTIAL) {
+        timing_mark(0, 0, st);
+        const cudaError_t e = launch_seq_fwd(x, b, a, zi, y, bt, Mmax, st);
+        timing_mark(0, 1, st);
+        return cuda_status(e);
+    }
     size_t need = chunk_fwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
     if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
@@ -139,7 +143,10 @@ dfilt_status do_backward(const float *gy, const float *x, const float *y, const 
     if (bt.B == 0) return DFILT_OK;
     if (r.algo == DFILT_ALGO_SEQUENTIAL) {
         if (!y) return DFILT_ERR_INVALID_ARG;
-        return cuda_status(launch_seq_bwd(gy, x, y, b, a, gx, gb, ga, gzi, bt, Mmax, st));
+        timing_mark(1, 0, st);
+        const cudaError_t e = launch_seq_bwd(gy, x, y, b, a, gx, gb, ga, gzi, bt, Mmax, st);
+        timing_mark(1, 1, st);
+        return cuda_status(e);
     }
     if (!y && !saved) return DFILT_ERR_INVALID_ARG;
     size_t need = chunk_bwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
@@ -150,7 +157,58 @@ dfilt_status do_backward(const float *gy, const float *x, const float *y, const 
                                         di.num_sms, st));
 }
 
+// ---- kernel timing: event pairs around each call's main kernel --------------------
+constexpr int kTimingSlots = 4096;
+struct TimingSlot {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int dev = -1;
+    int dir = 0;
+    int state = 0;   // 0 free, 1 started, 2 complete
+};
+std::mutex g_tmu;
+bool g_timing_on = false;
+TimingSlot g_slots[kTimingSlots];
+thread_local int t_pending[2] = {-1, -1};
+
 }  // namespace
+
+namespace dfilt {
+void timing_mark(int dir, int phase, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (!g_timing_on) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (phase == 0) {
+        t_pending[dir] = -1;
+        for (int i = 0; i < kTimingSlots; ++i) {
+            TimingSlot &sl = g_slots[i];
+            if (sl.state != 0) continue;
+            if (sl.dev != dev) {
+                if (sl.e0) cudaEventDestroy(sl.e0);
+                if (sl.e1) cudaEventDestroy(sl.e1);
+                sl.e0 = sl.e1 = nullptr;
+                if (cudaEventCreate(&sl.e0) != cudaSuccess || cudaEventCreate(&sl.e1) != cudaSuccess)
+                    return;
+                sl.dev = dev;
+            }
+            if (cudaEventRecord(sl.e0, st) != cudaSuccess) return;
+            sl.dir = dir;
+            sl.state = 1;
+            t_pending[dir] = i;
+            return;
+        }
+    } else {
+        const int i = t_pending[dir];
+        t_pending[dir] = -1;
+        if (i < 0 || g_slots[i].state != 1) return;
+        if (cudaEventRecord(g_slots[i].e1, st) != cudaSuccess) {
+            g_slots[i].state = 0;
+            return;
+        }
+        g_slots[i].state = 2;
+    }
+}
+}  // namespace dfilt
 
 namespace dfilt {
 // Status word, SM count and wait settings of the current device, for entry points
@@ -300,6 +358,42 @@ dfilt_status dfilt_sync_status(void *stream) {
         return DFILT_ERR_CUDA;
     if (v != 0 && cudaMemset(di.status, 0, sizeof(int)) != cudaSuccess) return DFILT_ERR_CUDA;
     return static_cast<dfilt_status>(v);
+}
+
+dfilt_status dfilt_kernel_timing(int enable) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing_on = enable != 0;
+    for (TimingSlot &sl : g_slots)
+        if (sl.state != 0) sl.state = 0;
+    return DFILT_OK;
+}
+
+dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
+                                      int *bwd_calls) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    double ms[2] = {0.0, 0.0};
+    int n[2] = {0, 0};
+    dfilt_status st = DFILT_OK;
+    for (TimingSlot &sl : g_slots) {
+        if (sl.state != 2) {
+            sl.state = 0;
+            continue;
+        }
+        float t = 0.f;
+        if (cudaEventSynchronize(sl.e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, sl.e0, sl.e1) != cudaSuccess) {
+            st = DFILT_ERR_CUDA;
+        } else {
+            ms[sl.dir] += t;
+            ++n[sl.dir];
+        }
+        sl.state = 0;
+    }
+    if (fwd_ms) *fwd_ms = ms[0];
+    if (fwd_calls) *fwd_calls = n[0];
+    if (bwd_ms) *bwd_ms = ms[1];
+    if (bwd_calls) *bwd_calls = n[1];
+    return st;
 }
 
 dfilt_status dfilt_set_wait_limit(int64_t iters) {

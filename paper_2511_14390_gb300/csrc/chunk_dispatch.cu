@@ -100,13 +100,17 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                                        l.fp64_scan, st);
     if (e != cudaSuccess) return e;
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
+    timing_mark(0, 0, st);
     switch (l.MB) {
-#define X(V) \
-    case V: return chunk_fwd_mb<V>(x, zi, y, saved, w, bt, l.fp64_scan, three, num_sms, st);
+#define X(V)                                                                        \
+    case V: e = chunk_fwd_mb<V>(x, zi, y, saved, w, bt, l.fp64_scan, three, num_sms, st); \
+        break;
         DFILT_CHUNK_BUCKETS(X)
 #undef X
+        default: e = cudaErrorInvalidValue;
     }
-    return cudaErrorInvalidValue;
+    timing_mark(0, 1, st);
+    return e;
 }
 
 cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
@@ -130,15 +134,19 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     }
     if (e != cudaSuccess) return e;
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
+    timing_mark(1, 0, st);
     switch (l.MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
-        return chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, counter, bt,         \
-                               l.fp64_scan, read_y, three, num_sms, st);
+        e = chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, counter, bt,            \
+                            l.fp64_scan, read_y, three, num_sms, st);                          \
+        break;
         DFILT_CHUNK_BUCKETS(X)
 #undef X
+        default: e = cudaErrorInvalidValue;
     }
-    return cudaErrorInvalidValue;
+    timing_mark(1, 1, st);
+    return e;
 }
 
 }  // namespace dfilt

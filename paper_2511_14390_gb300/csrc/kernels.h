@@ -58,6 +58,11 @@ cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const 
 // Largest bucket whose FP32 Hillis-Steele scan tables fit (and are used at all).
 constexpr int kMaxF32ScanBucket = 16;
 
+// Optional timing of each call's main kernel (the C ABI's kernel-timing switch): the
+// launchers call it with phase 0 just before and phase 1 just after the main kernel
+// (direction 0 forward, 1 backward).  A no-op while timing is off.
+void timing_mark(int direction, int phase, cudaStream_t st);
+
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
                              bool fp64_scan, int precision, int num_sms, cudaStream_t st);

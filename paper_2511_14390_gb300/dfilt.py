@@ -28,7 +28,8 @@ STATUS = {0: "DFILT_OK", 1: "DFILT_ERR_INVALID_ARG", 2: "DFILT_ERR_UNSUPPORTED",
 EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_workspace_size",
            "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
-           "dfilt_set_wait_limit", "dfilt_forward_noalloc"]
+           "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
+           "dfilt_kernel_timing_read"]
 
 
 class DfiltError(RuntimeError):
@@ -84,6 +85,9 @@ def lib():
             L.dfilt_sync_status.argtypes = [P]
             L.dfilt_set_wait_limit.argtypes = [i64]
             L.dfilt_forward_noalloc.argtypes = [P, P, P, P, P, i64, i64, i32, i32, PO, P]
+            L.dfilt_kernel_timing.argtypes = [i32]
+            PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+            L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i32
             L.dfilt_status_string.restype = ctypes.c_char_p
@@ -239,6 +243,20 @@ def dfilt_sync_status(stream=None) -> int:
 
 def dfilt_set_wait_limit(iters: int):
     _check(lib().dfilt_set_wait_limit(int(iters)), "dfilt_set_wait_limit")
+
+
+def dfilt_kernel_timing(enable: bool):
+    """Start (True) or stop (False) event timing of each call's main kernel."""
+    _check(lib().dfilt_kernel_timing(1 if enable else 0), "dfilt_kernel_timing")
+
+
+def dfilt_kernel_timing_read():
+    """Wait for the recorded calls; return ((fwd_ms_total, fwd_calls), (bwd_ms_total, bwd_calls))."""
+    fm, bm = ctypes.c_double(), ctypes.c_double()
+    fn, bn = ctypes.c_int(), ctypes.c_int()
+    _check(lib().dfilt_kernel_timing_read(ctypes.byref(fm), ctypes.byref(fn), ctypes.byref(bm),
+                                          ctypes.byref(bn)), "dfilt_kernel_timing_read")
+    return (fm.value, fn.value), (bm.value, bn.value)
 
 
 # ---------------------------------------------------------------------------

@@ -39,6 +39,14 @@ def test_host_only_calls(L):
     assert (o.algo, o.precision, o.chunk_len, o.fp64_scan) == (0, 3, 0, -1)
 
 
+def test_kernel_timing_without_calls(L):
+    """Timing switch and read are host-side; with no recorded call the sums are zero."""
+    dfilt.dfilt_kernel_timing(True)
+    assert dfilt.dfilt_kernel_timing_read() == ((0.0, 0), (0.0, 0))
+    dfilt.dfilt_kernel_timing(False)
+    assert dfilt.dfilt_kernel_timing_read() == ((0.0, 0), (0.0, 0))
+
+
 def test_workspace_sizes(L):
     f, s, w = dfilt.dfilt_workspace_size(1024, 48000, 2, 2)
     assert f > 0 and w > 0 and s >= 1024 * 48000 // 64 * 2 * 4

@@ -194,6 +194,47 @@ def test_full_size_biquad_sampled():
         assert e.max() < 1e-5, (nm, e.max())
 
 
+def test_backward_repeatable_with_same_saved():
+    """The backward reads its tables from `saved` and clears its own work counter, so a
+    second call with the same saved buffer gives bit-identical gradients."""
+    w = inputs.make("biquad_1024x48000", B=40, T=20705)
+    o = dfilt.make_opts(algo="chunked")
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o)
+    g1 = [t.clone() for t in dfilt.dfilt_backward(gy, x, None, b, a, zi, saved, opts=o)]
+    g2 = dfilt.dfilt_backward(gy, x, None, b, a, zi, saved, opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    for t1, t2 in zip(g1, g2):
+        assert torch.equal(t1, t2)
+    yr, gr = oracle_fixed(w)
+    assert rel_rows(g2[0].cpu().numpy(), gr[0]).max() < 1e-5
+
+
+@pytest.mark.parametrize("mode", ["seq", "chunk3"])
+def test_kernel_timing(mode):
+    """Event timing of the main kernels: one record per call and direction, each no
+    longer than the whole call."""
+    w = inputs.make("biquad_1024x48000", B=64, T=48000)
+    o = dfilt.make_opts(**OPTS[mode])
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dfilt.dfilt_kernel_timing(True)
+    try:
+        e0.record()
+        y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o)
+        dfilt.dfilt_backward(gy, x, y if saved is None else None, b, a, zi, saved, opts=o)
+        e1.record()
+        (fm, fn), (bm, bn) = dfilt.dfilt_kernel_timing_read()
+    finally:
+        dfilt.dfilt_kernel_timing(False)
+    torch.cuda.synchronize()
+    assert dfilt.dfilt_sync_status() == 0
+    assert (fn, bn) == (1, 1)
+    assert 0.0 < fm and 0.0 < bm and fm + bm <= e0.elapsed_time(e1) * 1.01 + 1e-3
+
+
 def test_timeout_path_reports_status():
     """A bounded device wait that runs out is reported, and the context stays usable."""
     w = inputs.make("biquad_1024x48000", B=4, T=20000)
