@@ -65,8 +65,11 @@ __device__ __forceinline__ void load_tile_async(uint32_t dst, const float *src, 
     cp_async_commit();
 }
 
-// Split an operand tile in place into TF32 hi and (at lo_off) lo, zeroing samples past
-// `n`.  Thread `t` of NT handles pieces t, t+NT, ...
+// Split an operand tile into TF32 hi and lo, zeroing samples past `n`.  The tensor
+// cores read a TF32 operand from the upper 19 bits of its 32-bit word, i.e. they
+// truncate, which is what split_tf32's hi is; so the raw tile already is the hi part
+// and only pieces that need zeroing are written back.  Thread `t` of NT handles
+// pieces t, t+NT, ...
 template <int NT>
 __device__ __forceinline__ void split_tile_tf32(char *hi, char *lo, int n, bool three, int t) {
 #pragma unroll 4
@@ -82,14 +85,16 @@ __device__ __forceinline__ void split_tile_tf32(char *hi, char *lo, int n, bool 
             if (sidx + 1 >= n) v.y = 0.f;
             if (sidx + 2 >= n) v.z = 0.f;
             if (sidx + 3 >= n) v.w = 0.f;
+            *reinterpret_cast<float4 *>(hi + o) = v;
         }
-        float4 h, l;
-        split_tf32(v.x, h.x, l.x);
-        split_tf32(v.y, h.y, l.y);
-        split_tf32(v.z, h.z, l.z);
-        split_tf32(v.w, h.w, l.w);
-        *reinterpret_cast<float4 *>(hi + o) = h;
-        if (three) *reinterpret_cast<float4 *>(lo + o) = l;
+        if (three) {
+            float4 h, l;
+            split_tf32(v.x, h.x, l.x);
+            split_tf32(v.y, h.y, l.y);
+            split_tf32(v.z, h.z, l.z);
+            split_tf32(v.w, h.w, l.w);
+            *reinterpret_cast<float4 *>(lo + o) = l;
+        }
     }
 }
 
