@@ -439,17 +439,21 @@ cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved
 
 
 // ===========================================================================
-// Shared-memory layout of the pipelined forward: two stages (signal tile hi | lo)
-// and two per-channel table slots (B operand hi | lo, O_L, scan block, S_in).
+// Shared-memory layout of the pipelined forward: NST signal-tile stages (the raw tile
+// is the TF32 hi operand; its lo part lives in TMEM), one y staging buffer, and two
+// per-channel table slots (B operand hi | lo, O_L, scan block, S_in).
 // ===========================================================================
 
-template <int MB, bool F64>
+// (layouts are also instantiated only to test whether they fit, so some of their
+// members go unreferenced)
+#pragma nv_diag_suppress 177
+template <int MB, bool F64, int NST>
 struct PipeSmem {
     using Tab = ChunkTab<MB>;
     static constexpr int NM = Tab::NFWD;
-    static constexpr uint32_t STAGE = 2 * kTileBytes;              // hi | lo
-    static constexpr uint32_t ST0 = 0;                              // stages at 0, STAGE
-    static constexpr uint32_t TAB0 = 2 * STAGE;
+    static constexpr uint32_t XS0 = 0;                              // NST x tiles
+    static constexpr uint32_t YS = NST * kTileBytes;                // y staging
+    static constexpr uint32_t TAB0 = YS + kTileBytes;
     // per table slot: B hi | B lo | O_L | scan block | S_in (doubles)
     static constexpr uint32_t T_BHI = 0;
     static constexpr uint32_t T_BLO = T_BHI + NM * 256;
@@ -476,17 +480,17 @@ struct TileDesc {
 //
 // Roles (384 threads), decoupled by mbarriers, two pipeline stages s = i & 1:
 //   warps 0-2, 8-11  converters: fetch work; build per-channel tables (double-buffered by
-//              channel parity); the signal tile arrives in stage s's hi slot (TMA
+//              channel parity); the signal tile arrives in stage s's x buffer (TMA
 //              tensor load into the 128-byte-swizzled operand layout, or cp.async when
-//              the layout has no chunk-aligned rows); split it into TF32 hi/lo
-//                                                   -> full[s]
-//              then prefetch tile i+1 into the other stage once MMA(i-1) released it
+//              the layout has no chunk-aligned rows); the raw tile is the TF32 hi
+//              operand, and warps 8-11 write its lo part into TMEM   -> full[s]
+//              then load tile i+1 into the other stage once MMA(i-1) released it
 //   warp 3     MMA issuer: full[s], tmem_free[s] -> tcgen05.mma into TMEM buffer s
-//                                                   -> mma_done[s] (tcgen05.commit)
+//              (A_hi from shared memory, A_lo from TMEM)  -> mma_done[s] (commit)
 //   warps 4-7  epilogue: mma_done[s] -> chunk-state scan, y = D + O_L S, saved
-//              states; y staged in stage s's lo slot in the operand layout and
+//              states; y staged in stage s's y buffer in the operand layout and
 //              written by a TMA tensor store (full tiles) or plain stores
-//                                                   -> tmem_free[s], stage_free[s]
+//                                                   -> tmem_free[s]
 // ===========================================================================
 // The forward's epilogue needs few registers, so this pipeline runs 12 warps: the
 // converters are warps 0-2 and 8-11 (224 threads), the MMA issuer warp 3 and the
@@ -499,24 +503,33 @@ using pipe::kNamedConv;
 using pipe::kNamedEpi;
 using pipe::named_sync;
 
-template <int MB, bool F64>
+template <int MB, bool F64, int NST>
 struct WsSmem {
-    using P = PipeSmem<MB, F64>;
+    using P = PipeSmem<MB, F64, NST>;
     static constexpr uint32_t MISC = P::MISC;
-    // barriers: full[2] mma[2] tfree[2] sfree[2] tabfree[2] load[2] dead drain (14 x 8)
+    // barriers: full[3] stage_done[3] load[3] mma_done[2] tmem_free[2] tab_free[2] dead
+    // drain (17, 20 slots)
+    static constexpr int NBAR = 20;
     static constexpr uint32_t M_BAR = MISC;
-    static constexpr uint32_t M_TMEM = MISC + 112;
-    static constexpr uint32_t M_ABORT = MISC + 116;
-    static constexpr uint32_t M_OK = MISC + 120;     // converter (2) / epilogue broadcast words
-    static constexpr uint32_t M_WT = MISC + 144;
+    static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
+    static constexpr uint32_t M_ABORT = M_TMEM + 4;
+    static constexpr uint32_t M_OK = M_TMEM + 8;      // converter (2) / epilogue broadcast words
+    static constexpr uint32_t M_WT = M_TMEM + 32;
     static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
-    static constexpr uint32_t BYTES = M_RING + 4 * 48;
+    static constexpr int RING = 8;
+    static constexpr uint32_t BYTES = M_RING + RING * 48;
     static constexpr uint32_t ALLOC = BYTES + 1024;
 };
+// three signal-tile stages (two tiles of loads in flight) where they fit, else two
+template <int MB, bool F64>
+constexpr int fwd_stages() {
+    return WsSmem<MB, F64, 3>::ALLOC <= kSmemMax ? 3 : 2;
+}
+#pragma nv_diag_default 177
 
 using pipe::op_piece;
 
-template <int MB, bool F64>
+template <int MB, bool F64, int NST>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     chunk_fwd_ws_kernel(const float *__restrict__ x, const float *__restrict__ zi,
                         float *__restrict__ y, float *__restrict__ saved,
@@ -525,15 +538,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         const __grid_constant__ CUtensorMap tmx,
                         const __grid_constant__ CUtensorMap tmy) {
     using Tab = ChunkTab<MB>;
-    using PS = PipeSmem<MB, F64>;
-    using SM = WsSmem<MB, F64>;
+    using PS = PipeSmem<MB, F64, NST>;
+    using SM = WsSmem<MB, F64, NST>;
     constexpr int NM = PS::NM;
+    constexpr int LA = NST - 1;          // tiles loaded ahead of the one being converted
+    constexpr int RING = SM::RING;
     extern __shared__ char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *stage_free = bars + 6,
-             *tab_free = bars + 8, *load_bar = bars + 10, *dead = bars + 12, *drain = bars + 13;
+    uint64_t *full = bars + 0, *stage_done = bars + 3, *load_bar = bars + 6, *mma_done = bars + 9,
+             *tmem_free = bars + 11, *tab_free = bars + 13, *dead = bars + 15, *drain = bars + 16;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
     // decision flags written by one thread and read by its role after a named barrier;
@@ -546,11 +561,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
-        tmem_alloc(tmem_slot, 256);
+        tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 14; ++i) mbar_init(&bars[i], (i == 2 || i == 3) ? 2 : 1);
+        for (int i = 0; i < SM::NBAR; ++i) mbar_init(&bars[i], (i == 9 || i == 10) ? 2 : 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -560,9 +575,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const size_t rec = Tab::fwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
-    auto stage_hi = [&](int s) { return (uint32_t)(PS::ST0 + s * PS::STAGE); };
-    auto stage_lo = [&](int s) { return (uint32_t)(PS::ST0 + s * PS::STAGE + kTileBytes); };
+    auto stage_hi = [&](int s) { return (uint32_t)(PS::XS0 + s * kTileBytes); };
     auto tslot = [&](int p) { return (uint32_t)(PS::TAB0 + p * PS::TSLOT); };
+    // TMEM columns of stage s's A_lo (128 lanes = chunks x 64 columns = samples)
+    auto alo_col = [&](int s) { return (uint32_t)(256 + 64 * s); };
     // bounded wait by one thread; on timeout (or a peer's abort) raise the abort flag
     auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
         for (long long it = 0; it < bt.wait_limit; ++it) {
@@ -582,9 +598,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const int ct = warp < kMmaWarp ? tid : tid - 160;   // 0..kConvThreads-1
         int64_t cur_ch = -1, cur_t = 0, cur_nt = 0, cur_off = 0, cur_len = 0;
         int cur_M = 1, ch_seq = -1;
-        // thread 0: describe tile i in ring[i & 3]; returns false when the work is done
-        auto next_desc = [&](int64_t i) {
-            TileDesc &d = ring[i & 3];
+        // thread 0: describe the next tile into `d` (published to the ring by the caller)
+        auto next_desc = [&](TileDesc &d) {
             while (cur_ch < 0 || cur_t >= cur_nt) {
                 const int64_t c = (int64_t)atomicAdd(counter, 1ull);
                 if (c >= bt.B) {
@@ -678,90 +693,139 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             }
         };
 
-        // prologue: tile 0
-        if (ct == 0) next_desc(0);
-        named_sync(kNamedConv, kConvThreads);
-        {
-            const TileDesc d0 = ring[0];
-            if (d0.ch >= 0) {
-                build_tables(d0);
-                issue_load(d0, 0);
-            } else if (ct == 0) {
-                mbar_arrive(&full[0]);   // no work: end marker
+        // lo part x - trunc(x) of stage s's tile into TMEM (warps 8-11, one TMEM lane
+        // quarter each, thread = chunk row); samples past the tile's end are zeroed in the
+        // shared-memory tile too (a TMA load may bring in the next channel's samples)
+        auto lo_to_tmem = [&](int n, int s) {
+            const int q = warp & 3;
+            const int r = 32 * q + lane;
+            char *hi = smem + stage_hi(s);
+            const int nv = n - r * kL;   // valid samples of this row
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(s);
+#pragma unroll
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v16[16];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int j16 = cb * 4 + p;
+                    float4 v = *reinterpret_cast<float4 *>(hi + op_piece(r, j16));
+                    if (4 * j16 + 4 > nv) {
+                        if (4 * j16 + 0 >= nv) v.x = 0.f;
+                        if (4 * j16 + 1 >= nv) v.y = 0.f;
+                        if (4 * j16 + 2 >= nv) v.z = 0.f;
+                        if (4 * j16 + 3 >= nv) v.w = 0.f;
+                        *reinterpret_cast<float4 *>(hi + op_piece(r, j16)) = v;
+                    }
+                    float h;
+                    split_tf32(v.x, h, v16[4 * p + 0]);
+                    split_tf32(v.y, h, v16[4 * p + 1]);
+                    split_tf32(v.z, h, v16[4 * p + 2]);
+                    split_tf32(v.w, h, v16[4 * p + 3]);
+                }
+                if (three) tmem_st16(ta + cb * 16, v16);
+            }
+            if (three) tmem_wait_st();
+            if (n < kTileSamples) fence_proxy_async_smem();
+            tc_fence_before();
+        };
+
+        // prologue: tiles 0 .. LA-1 described, their tables built and loads issued
+        if (ct == 0) {
+            for (int j = 0; j < LA; ++j) {
+                TileDesc dj;
+                next_desc(dj);
+                ring[j] = dj;
             }
         }
+        named_sync(kNamedConv, kConvThreads);
+        int64_t issued_upto = -1;   // last tile whose load this thread has issued
+        for (int j = 0; j < LA; ++j) {
+            const TileDesc dj = ring[j];
+            if (dj.ch < 0) break;
+            if (dj.first) build_tables(dj);   // channel slots 0 / 1: not in use yet
+            issue_load(dj, j);
+            issued_upto = j;
+        }
         for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
-            const TileDesc d = ring[i & 3];
-            if (d.ch < 0) break;
-            // (1) tile i landed; lo slot free (tile i-2's y staging consumed)
+            const int s = (int)(i % NST);
+            const uint32_t ph = (uint32_t)((i / NST) & 1);
+            const TileDesc d = ring[i & (RING - 1)];
+            if (d.ch < 0) {
+                if (ct == 0) mbar_arrive(&full[s]);   // end marker for the MMA warp
+                break;
+            }
+            // (1) tile i landed in stage s
             if (ct == 0) {
                 bool ok = true;
-                if (i >= 2) ok = wait1(&stage_free[s], (uint32_t)(((i >> 1) - 1) & 1));
-                if (ok && use_tma) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
+                if (use_tma) ok = wait1(&load_bar[s], ph);
                 conv_ok[0] = ok ? 1 : 0;
             }
-            if (!use_tma) cp_async_wait_all();
+            if (!use_tma) {
+                if (issued_upto > i) cp_async_wait_1();
+                else cp_async_wait_all();
+            }
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[0]) break;
-            // (2) split into TF32 hi/lo, zero past the tile's valid samples
-            pipe::split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen,
-                                                three != 0, ct);
-            fence_proxy_async_smem();
+            // (2) A_lo into TMEM; the raw tile in shared memory is A_hi (the tensor cores
+            //     truncate a TF32 operand to its upper 19 bits)
+            if (warp >= 8) lo_to_tmem(d.tlen, s);
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) next tile: descriptor, tables of a new channel, prefetch into stage s^1
-            //     once MMA(i-1) has finished reading it
+            // (3) tile i+LA: descriptor, tables of a new channel, load into its stage once
+            //     MMA(i-1), the stage's previous user, is done (through the MMA's wait on
+            //     the TMEM buffer the epilogue has also started tile i-3; ring slots are
+            //     reused 8 tiles apart)
             if (ct == 0) {
-                next_desc(i + 1);
-                const TileDesc &dn = ring[(i + 1) & 3];
+                TileDesc nd;
+                next_desc(nd);
                 bool ok = true;
-                if (dn.ch >= 0 && dn.first) {
-                    // slot dn.tab was last used two channels ago
+                if (nd.ch >= 0 && nd.first) {
+                    // slot nd.tab was last used two channels ago
                     const int seq = ch_seq;
-                    if (seq >= 2) ok = wait1(&tab_free[dn.tab], (uint32_t)(((seq >> 1) - 1) & 1));
+                    if (seq >= 2) ok = wait1(&tab_free[nd.tab], (uint32_t)(((seq >> 1) - 1) & 1));
                 }
-                if (ok && dn.ch >= 0 && i >= 1)
-                    ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
+                if (ok && nd.ch >= 0 && i + LA >= NST)
+                    ok = wait1(&stage_done[(i + LA) % NST], (uint32_t)(((i + LA - NST) / NST) & 1));
+                ring[(i + LA) & (RING - 1)] = nd;
                 conv_ok[1] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[1]) break;
-            const TileDesc dn = ring[(i + 1) & 3];
-            if (dn.ch < 0) {
-                if (ct == 0) mbar_arrive(&full[s ^ 1]);   // end marker for the MMA warp
-                break;
+            const TileDesc dn = ring[(i + LA) & (RING - 1)];
+            if (dn.ch >= 0) {
+                if (dn.first) build_tables(dn);
+                issue_load(dn, (int)((i + LA) % NST));
+                issued_upto = i + LA;
             }
-            if (dn.first) build_tables(dn);
-            issue_load(dn, s ^ 1);
         }
     } else if (warp == kMmaWarp) {
         // ============================ MMA issuer ============================
         bool issued = false;
         for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
+            const int s = (int)(i % NST);        // signal-tile stage
+            const int tb_ = (int)(i & 1);         // TMEM accumulator buffer
             const uint32_t par = (uint32_t)((i >> 1) & 1);
             int ok = 1;
-            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            if (lane == 0) ok = wait1(&full[s], (uint32_t)((i / NST) & 1)) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
-            const TileDesc d = ring[i & 3];
-            // TMEM buffer s free (epilogue done with tile i-2); the end marker waits too,
-            // or its arrivals could complete a second phase of mma_done[s] before the
+            const TileDesc d = ring[i & (RING - 1)];
+            // TMEM buffer free (epilogue done with tile i-2); the end marker waits too,
+            // or its arrivals could complete a second phase of mma_done before the
             // epilogue has observed tile i-2's (a parity wait cannot tell them apart)
-            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[s], par ^ 1u) ? 1 : 0;
+            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[tb_], par ^ 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             if (d.ch < 0) {
                 if (lane == 0) {
-                    mbar_arrive(&mma_done[s]);   // end marker for the epilogue (2 arrivals)
-                    mbar_arrive(&mma_done[s]);
+                    mbar_arrive(&mma_done[tb_]);   // end marker for the epilogue (2 arrivals)
+                    mbar_arrive(&mma_done[tb_]);
                 }
                 break;
             }
             if (lane == 0) {
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
+                const uint32_t d_tmem = tmem + (uint32_t)(tb_ * 128);
                 const uint32_t tb = tslot(d.tab);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
@@ -771,14 +835,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const uint64_t bhi = sdesc_sw128(sbase + tb + PS::T_BHI + kb);
                     mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
-                        const uint64_t alo = sdesc_sw128(sbase + stage_lo(s) + ka);
                         const uint64_t blo = sdesc_sw128(sbase + tb + PS::T_BLO + kb);
                         mma_tf32(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32(d_tmem, alo, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(s) + 8 * kk, bhi, idesc, 1u);
                     }
                 }
-                mma_commit(&mma_done[s]);
-                mbar_arrive(&mma_done[s]);   // orders the descriptor reads before the epilogue's
+                mma_commit(&mma_done[tb_]);
+                mbar_arrive(&mma_done[tb_]);   // orders the descriptor reads before the epilogue's
+                mma_commit(&stage_done[s]);    // the stage (shared tile and TMEM A_lo) is free
             }
             issued = true;
             if (bt.stall_drill) {
@@ -809,7 +873,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             named_sync(kNamedEpi, 128);
             if (!*epi_ok) break;
             tc_fence_after();
-            const TileDesc pv = ring[i & 3];
+            const TileDesc pv = ring[i & (RING - 1)];
             if (pv.ch < 0) break;
             const char *T = smem + tslot(pv.tab);
             const float *sOL = reinterpret_cast<const float *>(T + PS::T_OL);
@@ -837,7 +901,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     if (cb * 16 + q < MB) E[cb * 16 + q] = v[q];
             }
             float S[MB];
-            char *lo = smem + stage_lo(s);   // consumed by MMA(i): scan scratch, then y staging
+            // the y buffer: FP64 scan scratch, then y staging (free once the bulk store of
+            // the previous tile has read it)
+            char *lo = smem + PS::YS;
             if constexpr (!F64) {
                 // two-level scan: warp-local Hillis-Steele, then carries across the 4 warps
 #pragma unroll
@@ -891,10 +957,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const float wprev = __shfl_up_sync(0xffffffffu, E[m], 1);
                     S[m] = v[m] + (lane > 0 ? wprev : 0.f);
                 }
-                named_sync(kNamedEpi, 128);   // wt reusable
+                if (et == 0) bulk_wait_read0();   // the y buffer's previous store has read it
+                named_sync(kNamedEpi, 128);       // wt reusable, y buffer writable
             } else {
                 float *xbuf = reinterpret_cast<float *>(lo);
                 float *sbuf = reinterpret_cast<float *>(lo + 16384);
+                if (et == 0) bulk_wait_read0();   // the y buffer's previous store has read it
+                named_sync(kNamedEpi, 128);
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
                 named_sync(kNamedEpi, 128);
@@ -953,14 +1022,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (et == 0) {
                 mbar_arrive(&tmem_free[s]);
                 if (tma_store) {
-                    // the converters need this lo slot for tile i+2: release it as soon as
-                    // the bulk store has read it (the write to global continues async)
+                    // asynchronous: the next tile waits for the read of this buffer
                     const int row = (int)(pv.tstart / kL);
-                    tma_store_3d(&tmy, 0, 0, row, sbase + stage_lo(s));
-                    tma_store_3d(&tmy, 0, 1, row, sbase + stage_lo(s) + kKBlock);
+                    tma_store_3d(&tmy, 0, 0, row, sbase + PS::YS);
+                    tma_store_3d(&tmy, 0, 1, row, sbase + PS::YS + kKBlock);
                     bulk_commit();
-                    bulk_wait_read0();
-                    mbar_arrive(&stage_free[s]);
                 }
                 if (pv.last) mbar_arrive(&tab_free[pv.tab]);
             }
@@ -983,8 +1049,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         if (nv > 3) gp[3] = v.w;
                     }
                 }
-                named_sync(kNamedEpi, 128);
-                if (et == 0) mbar_arrive(&stage_free[s]);
             }
         }
         if (et == 0) bulk_wait0();   // every TMA store complete before the CTA exits
@@ -995,16 +1059,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, 512);
     }
 }
 
 template <int MB, bool F64>
 cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *saved, const char *ws,
                           const Batch &bt, int three, int num_sms, cudaStream_t st) {
-    using SM = WsSmem<MB, F64>;
+    constexpr int NST = fwd_stages<MB, F64>();
+    using SM = WsSmem<MB, F64, NST>;
     static_assert(SM::ALLOC <= kSmemMax, "shared memory budget");
-    auto kern = chunk_fwd_ws_kernel<MB, F64>;
+    auto kern = chunk_fwd_ws_kernel<MB, F64, NST>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1037,9 +1102,10 @@ template <int MB>
 cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *ws,
                          const Batch &bt, bool fp64_scan, int three, int num_sms, cudaStream_t st) {
     // pipelined kernel wherever its double-buffered layout fits the shared memory
-    if constexpr (WsSmem<MB, true>::ALLOC <= kSmemMax)
+    if constexpr (WsSmem<MB, true, fwd_stages<MB, true>()>::ALLOC <= kSmemMax)
         if (fp64_scan) return launch_fwd_ws<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
-    if constexpr (MB <= kMaxF32ScanBucket && WsSmem<MB, false>::ALLOC <= kSmemMax)
+    if constexpr (MB <= kMaxF32ScanBucket &&
+                  WsSmem<MB, false, fwd_stages<MB, false>()>::ALLOC <= kSmemMax)
         if (!fp64_scan) return launch_fwd_ws<MB, false>(x, zi, y, saved, ws, bt, three, num_sms, st);
     if (fp64_scan) return launch_fwd_t<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
     if constexpr (MB <= kMaxF32ScanBucket)
