@@ -548,22 +548,26 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // pipeline structure run on reversed tiles:
 //   warps 0-2  converters: work (tiles of a channel from last to first), tables
 //              (B = T_h^a, O^u, scan block, coefficients; double-buffered by channel
-//              parity), gy tile -> stage s hi (TMA or cp.async) -> TF32 hi/lo -> full[s]
-//   warp 3     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk); once
-//              MMA(i) has completed, the x tile of tile i -> stage s lo (x_bar[s])
+//              parity); the x tile of tile i into x buffer i&1 once the epilogue has
+//              released it (x_bar; issued after full[s]); the gy tile into stage s (TMA
+//              or cp.async; the raw tile is the TF32 hi operand) -> gy_landed[s]; the lo
+//              part of rows 0-95 into TMEM -> full[s]
+//   warp 3     MMA: the lo part of rows 96-127 into TMEM (its TMEM lane quarter), then
+//              D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk)
 //   warps 4-7  epilogue: reverse chunk scan of S'_c = u[(c+1)L ..], u = D + O^u S',
 //              y recomputed from the forward's saved chunk state and the x tile, lag
 //              correlations reduced into per-warp FP64 accumulators, grad_x = sum_k
 //              b_k u[n+k] written over the x tile in place and stored from there (TMA
-//              for full tiles); stage_free[s] once the lo slot has been read out
+//              for full tiles); the x buffer is released once that store has read it
 // ===========================================================================
 
 template <int MB, bool F64>
 struct BwSmem {
     using Tab = ChunkTab<MB>;
     static constexpr int NM = kL;                                    // MMA N: T_h^a rows
-    static constexpr uint32_t STAGE = 2 * pipe::kTileBytes;          // hi | lo
-    static constexpr uint32_t TAB0 = 2 * STAGE;
+    static constexpr uint32_t GS0 = 0;                               // 2 gy stages (hi)
+    static constexpr uint32_t XB0 = 2 * pipe::kTileBytes;            // 2 x / grad_x buffers
+    static constexpr uint32_t TAB0 = 4 * pipe::kTileBytes;
     static constexpr uint32_t T_BHI = 0;
     static constexpr uint32_t T_BLO = NM * 256;
     static constexpr uint32_t T_OU = 2 * NM * 256;
@@ -574,7 +578,7 @@ struct BwSmem {
     static constexpr uint32_t SCR = TAB0 + 2 * TSLOT;
     static constexpr uint32_t ACC = SCR + (F64 ? 2 * kChunks * MB * 4 : 0);   // 4 x (2MB+1) doubles
     static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
-    static constexpr int NBAR = 16;
+    static constexpr int NBAR = 18;
     static constexpr uint32_t M_BAR = MISC;
     static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
     static constexpr uint32_t M_ABORT = M_TMEM + 4;
@@ -606,9 +610,9 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *stage_free = bars + 6,
-             *tab_free = bars + 8, *load_bar = bars + 10, *x_bar = bars + 12, *dead = bars + 14,
-             *drain = bars + 15;
+    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *x_free = bars + 6,
+             *tab_free = bars + 8, *load_bar = bars + 10, *x_bar = bars + 12, *gy_landed = bars + 14,
+             *dead = bars + 16, *drain = bars + 17;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
     // decision flags written by one thread and read by its role after a named barrier;
@@ -624,14 +628,14 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     const bool tma_gy = tma_mask & 1, tma_x = tma_mask & 2, tma_gx = tma_mask & 4;
 
     if (warp == 0) {
-        tmem_alloc(tmem_slot, 256);
+        tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
     if (tid == 0) {
         for (int i = 0; i < SM::NBAR; ++i) {
             uint32_t cnt = 1;
-            if (i == 2 || i == 3) cnt = 2;                        // mma_done: commit + arrive
-            if ((i == 12 || i == 13) && !tma_x) cnt = 32;   // x_bar: the MMA warp's cp.async arrivals
+            if (i == 2 || i == 3) cnt = 2;                                 // mma_done: commit + arrive
+            if ((i == 12 || i == 13) && !tma_x) cnt = kConvThreads;       // x_bar: cp.async arrivals
             mbar_init(&bars[i], cnt);
         }
         *abort_flag = 0;
@@ -643,11 +647,47 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const size_t rec = Tab::bwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
-    auto stage_hi = [&](int s) { return (uint32_t)(s * SM::STAGE); };
-    auto stage_lo = [&](int s) { return (uint32_t)(s * SM::STAGE + kTileBytes); };
+    auto stage_hi = [&](int s) { return (uint32_t)(SM::GS0 + s * kTileBytes); };
+    auto xbuf = [&](int j) { return (uint32_t)(SM::XB0 + j * kTileBytes); };
     auto tslot = [&](int p) { return (uint32_t)(SM::TAB0 + p * SM::TSLOT); };
+    // TMEM: accumulator buffers at columns 0 / 128, stage s's A_lo at 256 + 64 s
+    auto alo_col = [&](int s) { return (uint32_t)(256 + 64 * s); };
     auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
         return wait_or_abort(bar, parity, bt.wait_limit, abort_flag, bt.status);
+    };
+    // lo part x - trunc(x) of the rows of TMEM lane quarter `q` of stage s's gy tile into
+    // TMEM (one warp, thread = chunk row); samples past the tile's end are zeroed in the
+    // shared-memory tile too
+    auto lo_to_tmem = [&](int q, int n, int s) {
+        const int r = 32 * q + lane;
+        char *hi = smem + stage_hi(s);
+        const int nv = n - r * kL;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(s);
+#pragma unroll
+        for (int cb = 0; cb < kL / 16; ++cb) {
+            float v16[16];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int j16 = cb * 4 + p;
+                float4 v = *reinterpret_cast<float4 *>(hi + op_piece(r, j16));
+                if (4 * j16 + 4 > nv) {
+                    if (4 * j16 + 0 >= nv) v.x = 0.f;
+                    if (4 * j16 + 1 >= nv) v.y = 0.f;
+                    if (4 * j16 + 2 >= nv) v.z = 0.f;
+                    if (4 * j16 + 3 >= nv) v.w = 0.f;
+                    *reinterpret_cast<float4 *>(hi + op_piece(r, j16)) = v;
+                }
+                float h;
+                split_tf32(v.x, h, v16[4 * p + 0]);
+                split_tf32(v.y, h, v16[4 * p + 1]);
+                split_tf32(v.z, h, v16[4 * p + 2]);
+                split_tf32(v.w, h, v16[4 * p + 3]);
+            }
+            if (three) tmem_st16(ta + cb * 16, v16);
+        }
+        if (three) tmem_wait_st();
+        if (n < kTileSamples) fence_proxy_async_smem();
+        tc_fence_before();
     };
 
     if (warp < kMmaWarp) {
@@ -729,7 +769,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
             if (ct <= MB) coef[MB + ct] = ct <= c.N ? bco[d.ch * bt.Nstride + ct] : 0.f;
         };
-        // gy tile of `d` -> stage s hi
+        // gy tile of `d` -> stage s
         auto issue_gy = [&](const TileDesc &d, int s) {
             if (tma_gy) {
                 if (ct == 0) {
@@ -742,12 +782,23 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 load_tile_async<kConvThreads>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
                                               gy_al && ((d.tstart & 3) == 0), ct);
             }
-            // warm L2 with the x tile that is fetched once this tile's MMA is done
-            if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(x + d.tstart),
-                             "r"((uint32_t)kTileBytes)
-                             : "memory");
         };
+        // x tile of `d` -> x buffer j; lands on x_bar[j]
+        auto issue_x = [&](const TileDesc &d, int j) {
+            if (tma_x) {
+                if (ct == 0) {
+                    mbar_arrive_expect_tx(&x_bar[j], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + xbuf(j), &tmx, 0, 0, row, &x_bar[j]);
+                    tma_load_3d(sbase + xbuf(j) + kKBlock, &tmx, 0, 1, row, &x_bar[j]);
+                }
+            } else {
+                load_tile_async<kConvThreads>(sbase + xbuf(j), x, d.tstart, d.tlen,
+                                              x_al && ((d.tstart & 3) == 0), ct);
+                cp_async_mbar_arrive_noinc(&x_bar[j]);
+            }
+        };
+
         if (ct == 0) {
             TileDesc d0;
             next_desc(d0);
@@ -759,33 +810,43 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             if (d0.ch >= 0) {
                 build_tables(d0);
                 issue_gy(d0, 0);
-            } else if (ct == 0) {
-                mbar_arrive(&full[0]);
             }
         }
         for (int64_t i = 0;; ++i) {
             const int s = (int)(i & 1);
+            const uint32_t par = (uint32_t)((i >> 1) & 1);
             const TileDesc d = ring[i & 7];
-            if (d.ch < 0) break;
-            // (1) gy tile i landed; stage s lo free (tile i-2's x / grad_x read out)
+            if (d.ch < 0) {
+                if (ct == 0) mbar_arrive(&gy_landed[s]);   // end marker for the MMA warp
+                break;
+            }
+            // (1) gy tile i landed
             if (ct == 0) {
                 bool ok = true;
-                if (i >= 2) ok = wait1(&stage_free[s], (uint32_t)(((i >> 1) - 1) & 1));
-                if (ok && tma_gy) ok = wait1(&load_bar[s], (uint32_t)((i >> 1) & 1));
-                conv_ok[0] = ok ? 1 : 0;
+                if (tma_gy) ok = wait1(&load_bar[s], par);
+                conv_ok[1] = ok ? 1 : 0;
             }
             if (!tma_gy) cp_async_wait_all();
             named_sync(kNamedConv, kConvThreads);
-            if (!conv_ok[0]) break;
-            // (2) TF32 hi/lo split in place
-            split_tile_tf32<kConvThreads>(smem + stage_hi(s), smem + stage_lo(s), d.tlen, three != 0, ct);
-            fence_proxy_async_smem();
+            if (!conv_ok[1]) break;
+            if (ct == 0) mbar_arrive(&gy_landed[s]);   // the MMA warp converts its quarter
+            // (2) A_lo of rows 0-95 into TMEM (stage s's previous MMA, tile i-2, completed
+            //     before its gy load was issued)
+            lo_to_tmem(warp, d.tlen, s);
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) next descriptor; a new channel's tables wait for their slot; MMA(i-1)
-            //     complete: stage s^1 takes tile i+1's gy (its lo slot is refilled with
-            //     x only after this stage's next MMA), and through the MMA's wait on the
-            //     TMEM buffer the epilogue has finished tile i-3, whose ring slot is reused
+            // (3) the x tile into x buffer s once the epilogue of tile i-2 has released it
+            //     (after full[s], so that tile i's MMA never waits on the epilogue)
+            if (i >= 2) {
+                if (ct == 0) conv_ok[0] = wait1(&x_free[s], par ^ 1u) ? 1 : 0;
+                named_sync(kNamedConv, kConvThreads);
+                if (!conv_ok[0]) break;
+            }
+            issue_x(d, s);
+            // (4) next descriptor; a new channel's tables wait for their slot; MMA(i-1)
+            //     complete: stage s^1 takes tile i+1's gy, and through the MMA's wait on
+            //     the TMEM buffer the epilogue has finished tile i-3, whose ring slot is
+            //     reused
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
@@ -794,17 +855,15 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                     ok = wait1(&tab_free[nd.tab], (uint32_t)(((ch_seq >> 1) - 1) & 1));
                 if (ok && i >= 1) ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
                 ring[(i + 1) & 7] = nd;
-                conv_ok[1] = ok ? 1 : 0;
+                conv_ok[2] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
-            if (!conv_ok[1]) break;
+            if (!conv_ok[2]) break;
             const TileDesc dn = ring[(i + 1) & 7];
-            if (dn.ch < 0) {
-                if (ct == 0) mbar_arrive(&full[s ^ 1]);
-                break;
+            if (dn.ch >= 0) {
+                if (dn.first) build_tables(dn);
+                issue_gy(dn, s ^ 1);
             }
-            if (dn.first) build_tables(dn);
-            issue_gy(dn, s ^ 1);
         }
     } else if (warp == kMmaWarp) {
         // ============================ MMA issuer ============================
@@ -813,13 +872,14 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             const int s = (int)(i & 1);
             const uint32_t par = (uint32_t)((i >> 1) & 1);
             int ok = 1;
-            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            if (lane == 0) ok = wait1(&gy_landed[s], par) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             const TileDesc d = ring[i & 7];
-            // TMEM buffer s free (epilogue done with tile i-2); the end marker waits too,
-            // or its arrivals could complete a second phase of mma_done[s] before the
-            // epilogue has observed tile i-2's (a parity wait cannot tell them apart)
+            // TMEM buffer s free (epilogue done with tile i-2, hence MMA(i-2) done and
+            // stage s's A_lo free); the end marker waits too, or its arrivals could
+            // complete a second phase of mma_done[s] before the epilogue has observed
+            // tile i-2's (a parity wait cannot tell them apart)
             if (lane == 0 && i >= 2) ok = wait1(&tmem_free[s], par ^ 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
@@ -830,6 +890,13 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 }
                 break;
             }
+            // A_lo of rows 96-127 (this warp's TMEM lane quarter)
+            tc_fence_after();
+            lo_to_tmem(3, d.tlen, s);
+            __syncwarp();
+            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             if (lane == 0) {
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
@@ -842,34 +909,15 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                     const uint64_t bhi = sdesc_sw128(sbase + tb + SM::T_BHI + kb);
                     mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
-                        const uint64_t alo = sdesc_sw128(sbase + stage_lo(s) + ka);
                         const uint64_t blo = sdesc_sw128(sbase + tb + SM::T_BLO + kb);
                         mma_tf32(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32(d_tmem, alo, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(s) + 8 * kk, bhi, idesc, 1u);
                     }
                 }
                 mma_commit(&mma_done[s]);
                 mbar_arrive(&mma_done[s]);
             }
             issued = true;
-            // x tile i -> stage s lo as soon as MMA(i) has read the stage (the epilogue
-            // needs it after its scan; the converters refill the slot only after the
-            // epilogue has released it)
-            if (lane == 0) ok = wait1(&mma_done[s], par) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            if (tma_x) {
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&x_bar[s], kTileBytes);
-                    const int row = (int)(d.tstart / kL);
-                    tma_load_3d(sbase + stage_lo(s), &tmx, 0, 0, row, &x_bar[s]);
-                    tma_load_3d(sbase + stage_lo(s) + kKBlock, &tmx, 0, 1, row, &x_bar[s]);
-                }
-            } else {
-                load_tile_async<32>(sbase + stage_lo(s), x, d.tstart, d.tlen,
-                                    x_al && ((d.tstart & 3) == 0), lane);
-                cp_async_mbar_arrive_noinc(&x_bar[s]);
-            }
             if (bt.stall_drill) {
                 if (lane == 0) wait1(dead, 0);
                 __syncwarp();
@@ -889,10 +937,18 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
         float Sin[MB];   // state entering the tile from the right
         double S64a = 0.0, S64b = 0.0;
         double accd = 0.0;   // lane k < 2MB+1: this warp's sum of lag product k over the channel
+        bool store_pending = false;   // (thread 0) the previous tile's bulk store may still read
         for (int64_t i = 0;; ++i) {
             const int s = (int)(i & 1);
             const uint32_t par = (uint32_t)((i >> 1) & 1);
-            if (et == 0) epi_ok[0] = wait1(&mma_done[s], par) ? 1 : 0;
+            if (et == 0) {
+                epi_ok[0] = wait1(&mma_done[s], par) ? 1 : 0;
+                if (store_pending) {   // release the previous tile's x buffer once read
+                    bulk_wait_read0();
+                    mbar_arrive(&x_free[s ^ 1]);
+                    store_pending = false;
+                }
+            }
             named_sync(kNamedEpi, 128);
             if (!epi_ok[0]) break;
             tc_fence_after();
@@ -903,7 +959,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             const float *sP = reinterpret_cast<const float *>(T + SM::T_SCAN);
             const double *sAt = reinterpret_cast<const double *>(T + SM::T_SCAN);
             const float *coef = reinterpret_cast<const float *>(T + SM::T_COEF);
-            char *xs = smem + stage_lo(s);   // x tile, then grad_x (operand layout)
+            char *xs = smem + xbuf(s);   // x tile, then grad_x (operand layout)
             const int nch = (pv.tlen + kL - 1) / kL;
             const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
             // the forward's state entering this chunk (read early: global latency)
@@ -1032,7 +1088,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 for (int m = 0; m < MB; ++m)
                     if (m < pv.M) gzi[pv.ch * bt.Mstride + m] = u[m];
             }
-            // x tile landed in the lo slot
+            // x tile landed in x buffer s
             if (et == 0) epi_ok[1] = wait1(&x_bar[s], par) ? 1 : 0;
             named_sync(kNamedEpi, 128);
             if (et == 0) mbar_arrive(&tmem_free[s]);
@@ -1101,13 +1157,12 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
             const bool tma_store = tma_gx && gx && pv.tlen == kTileSamples;
             if (tma_store) {
                 if (et == 0) {
-                    // release the lo slot as soon as the bulk store has read it
+                    // asynchronous; the buffer is released at the next tile (or exit)
                     const int row = (int)(pv.tstart / kL);
-                    tma_store_3d(&tmgx, 0, 0, row, sbase + stage_lo(s));
-                    tma_store_3d(&tmgx, 0, 1, row, sbase + stage_lo(s) + kKBlock);
+                    tma_store_3d(&tmgx, 0, 0, row, sbase + xbuf(s));
+                    tma_store_3d(&tmgx, 0, 1, row, sbase + xbuf(s) + kKBlock);
                     bulk_commit();
-                    bulk_wait_read0();
-                    mbar_arrive(&stage_free[s]);
+                    store_pending = true;
                 }
             } else {
                 if (gx) {
@@ -1131,7 +1186,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                     }
                 }
                 named_sync(kNamedEpi, 128);
-                if (et == 0) mbar_arrive(&stage_free[s]);
+                if (et == 0) mbar_arrive(&x_free[s]);
             }
             if (pv.last) {
                 if (lane < NACC) acc_s[ew * NACC + lane] = accd;
@@ -1158,7 +1213,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, 512);
     }
 }
 
