@@ -545,52 +545,67 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 
 // ===========================================================================
 // Warp-specialised backward (state buckets whose layout fits), the forward's
-// pipeline structure run on reversed tiles:
-//   warps 0-2  converters: work (tiles of a channel from last to first), tables
-//              (B = T_h^a, O^u, scan block, coefficients; double-buffered by channel
-//              parity); the x tile of tile i into x buffer i&1 once the epilogue has
-//              released it (x_bar; issued after full[s]); the gy tile into stage s (TMA
-//              or cp.async; the raw tile is the TF32 hi operand) -> gy_landed[s]; the lo
-//              part of rows 0-95 into TMEM -> full[s]
-//   warp 3     MMA: the lo part of rows 96-127 into TMEM (its TMEM lane quarter), then
-//              D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk)
-//   warps 4-7  epilogue: reverse chunk scan of S'_c = u[(c+1)L ..], u = D + O^u S',
-//              y recomputed from the forward's saved chunk state and the x tile, lag
-//              correlations reduced into per-warp FP64 accumulators, grad_x = sum_k
-//              b_k u[n+k] written over the x tile in place and stored from there (TMA
-//              for full tiles); the x buffer is released once that store has read it
+// pipeline structure run on reversed tiles, with two epilogue warpgroups:
+//   warps 0-2   converters: work (tiles of a channel from last to first), tables (the
+//               B operand T_h^a, single-buffered: rebuilt once the channel's last MMA
+//               is done; O^u, scan block, coefficients double-buffered by channel
+//               parity); gy tiles two ahead into three stages (TMA or cp.async; the
+//               raw tile is the TF32 hi operand) -> gy_landed[s]; the lo part of rows
+//               0-95 into TMEM -> full[s]; the tile's x is prefetched into L2
+//   warp 3      MMA: the lo part of rows 96-127 into TMEM (its TMEM lane quarter), then
+//               D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk) into TMEM
+//               buffer i&1
+//   warps 4-7   epilogue group 0 (even tiles), warps 8-11 group 1 (odd tiles): reverse
+//               chunk scan of S'_c = u[(c+1)L ..] (each group loads its tile's x into its
+//               own buffer first; the state entering from the right
+//               is the other group's carry), u = D + O^u S', then streamed over the
+//               chunk row: y recomputed from the forward's saved chunk state and the
+//               x tile, lag correlations, grad_x = sum_k b_k u[n+k] written over the
+//               x tile and stored from there (TMA for full tiles); lag sums added per
+//               channel in shared FP64, finished by the group that completes the
+//               channel's last tile
 // ===========================================================================
+
+constexpr int kBwThreads = 384;
+constexpr int kBwNS = 3;   // gy stages (two tiles of gy loads in flight)
+constexpr int kBwNX = 2;   // x / grad_x buffers (one per epilogue group)
 
 template <int MB, bool F64>
 struct BwSmem {
     using Tab = ChunkTab<MB>;
     static constexpr int NM = kL;                                    // MMA N: T_h^a rows
-    static constexpr uint32_t GS0 = 0;                               // 2 gy stages (hi)
-    static constexpr uint32_t XB0 = 2 * pipe::kTileBytes;            // 2 x / grad_x buffers
-    static constexpr uint32_t TAB0 = 4 * pipe::kTileBytes;
-    static constexpr uint32_t T_BHI = 0;
-    static constexpr uint32_t T_BLO = NM * 256;
-    static constexpr uint32_t T_OU = 2 * NM * 256;
-    static constexpr uint32_t T_SCAN = T_OU + kL * MB * 4;
-    static constexpr uint32_t T_COEF = (T_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
-    static constexpr uint32_t TSLOT = (T_COEF + (2 * MB + 1) * 4 + 1023) / 1024 * 1024;
-    // FP64 reverse scan scratch (E' and S' per chunk)
-    static constexpr uint32_t SCR = TAB0 + 2 * TSLOT;
-    static constexpr uint32_t ACC = SCR + (F64 ? 2 * kChunks * MB * 4 : 0);   // 4 x (2MB+1) doubles
-    static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
-    static constexpr int NBAR = 18;
+    static constexpr int NACC = 2 * MB + 1;
+    static constexpr uint32_t GS0 = 0;                               // gy stages (hi)
+    static constexpr uint32_t XB0 = kBwNS * pipe::kTileBytes;        // x / grad_x buffers
+    static constexpr uint32_t TB = XB0 + kBwNX * pipe::kTileBytes;   // B operand hi | lo
+    static constexpr uint32_t T_BHI = TB;
+    static constexpr uint32_t T_BLO = TB + NM * 256;
+    static constexpr uint32_t SMALL0 = TB + 2 * NM * 256;            // 2 slots: O^u | scan | coef
+    static constexpr uint32_t S_OU = 0;
+    static constexpr uint32_t S_SCAN = kL * MB * 4;
+    static constexpr uint32_t S_COEF = (S_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
+    static constexpr uint32_t SSLOT = (S_COEF + (2 * MB + 1) * 4 + 15) / 16 * 16;
+    // FP64 reverse scan scratch per group (E' and S' per chunk)
+    static constexpr uint32_t SCR = SMALL0 + 2 * SSLOT;
+    static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 : 0;
+    static constexpr uint32_t ACC = (SCR + 2 * SCR_G + 7) / 8 * 8;   // [2 slots][NACC] doubles
+    static constexpr uint32_t CNT = ACC + 2 * NACC * 8;              // tiles done [2 slots]
+    static constexpr uint32_t CARRY = CNT + 16;                      // [2][MB] floats
+    static constexpr uint32_t CARRY64 = (CARRY + 2 * MB * 4 + 7) / 8 * 8;   // [2][MB] doubles
+    static constexpr uint32_t MISC = (CARRY64 + 2 * MB * 8 + 15) / 16 * 16;
+    static constexpr int NBAR = 25;
     static constexpr uint32_t M_BAR = MISC;
     static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
     static constexpr uint32_t M_ABORT = M_TMEM + 4;
-    static constexpr uint32_t M_OK = M_TMEM + 16;   // 8 flags, one per decision point
-    static constexpr uint32_t M_WT = M_TMEM + 48;
-    static constexpr uint32_t M_RING = (M_WT + 4 * MB * 4 + 15) / 16 * 16;
+    static constexpr uint32_t M_OK = M_TMEM + 16;    // 12 flags: converters 4, groups 4 + 4
+    static constexpr uint32_t M_WT = M_OK + 48;      // [2 groups][4 warps][MB] floats
+    static constexpr uint32_t M_RING = (M_WT + 2 * 4 * MB * 4 + 15) / 16 * 16;
     static constexpr uint32_t BYTES = M_RING + 8 * 48;
     static constexpr uint32_t ALLOC = BYTES + 1024;
 };
 
 template <int MB, bool F64>
-__global__ void __launch_bounds__(pipe::kPipeThreads, 1)
+__global__ void __launch_bounds__(kBwThreads, 1)
     chunk_bwd_ws_kernel(const float *__restrict__ gy, const float *__restrict__ x,
                         const float *__restrict__ bco, const float *__restrict__ aco,
                         const float *__restrict__ saved,
@@ -604,24 +619,25 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     using Tab = ChunkTab<MB>;
     using SM = BwSmem<MB, F64>;
     constexpr int NM = SM::NM;
-    constexpr int NACC = 2 * MB + 1;
+    constexpr int NACC = SM::NACC;
     static_assert(NACC <= 32, "one lag product per lane");
     extern __shared__ char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *mma_done = bars + 2, *tmem_free = bars + 4, *x_free = bars + 6,
-             *tab_free = bars + 8, *load_bar = bars + 10, *x_bar = bars + 12, *gy_landed = bars + 14,
-             *dead = bars + 16, *drain = bars + 17;
+    uint64_t *full = bars + 0, *gy_landed = bars + 3, *load_bar = bars + 6, *mma_done = bars + 9,
+             *tmem_free = bars + 13, *x_bar = bars + 17, *tab_free = bars + 19, *carry_bar = bars + 21,
+             *dead = bars + 23, *drain = bars + 24;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
     // decision flags written by one thread and read by its role after a named barrier;
     // each decision point has its own word, so that a late reader never sees the value
     // of a later point (the roles must leave their loops at the same point)
     volatile int *conv_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK);
-    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 16);
-    float *wt = reinterpret_cast<float *>(smem + SM::M_WT);
-    double *acc_s = reinterpret_cast<double *>(smem + SM::ACC);
+    double *acc_ch = reinterpret_cast<double *>(smem + SM::ACC);
+    unsigned *tiles_done = reinterpret_cast<unsigned *>(smem + SM::CNT);
+    float *carry = reinterpret_cast<float *>(smem + SM::CARRY);
+    double *carry64 = reinterpret_cast<double *>(smem + SM::CARRY64);
     TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool gy_al = al_mask & 1, x_al = al_mask & 2, gx_al = al_mask & 8;
@@ -634,13 +650,15 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < SM::NBAR; ++i) {
             uint32_t cnt = 1;
-            if (i == 2 || i == 3) cnt = 2;                                 // mma_done: commit + arrive
-            if ((i == 12 || i == 13) && !tma_x) cnt = kConvThreads;       // x_bar: cp.async arrivals
+            if (i >= 9 && i < 13) cnt = 2;                                    // mma_done: commit + arrive
+            if (i >= 17 && i < 19 && !tma_x) cnt = 128;                       // x_bar: a group's cp.async arrivals
             mbar_init(&bars[i], cnt);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
+    for (int i = tid; i < 2 * NACC; i += kBwThreads) acc_ch[i] = 0.0;
+    if (tid < 2) tiles_done[tid] = 0u;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -649,20 +667,21 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
     auto stage_hi = [&](int s) { return (uint32_t)(SM::GS0 + s * kTileBytes); };
     auto xbuf = [&](int j) { return (uint32_t)(SM::XB0 + j * kTileBytes); };
-    auto tslot = [&](int p) { return (uint32_t)(SM::TAB0 + p * SM::TSLOT); };
-    // TMEM: accumulator buffers at columns 0 / 128, stage s's A_lo at 256 + 64 s
+    auto sslot = [&](int p) { return (uint32_t)(SM::SMALL0 + p * SM::SSLOT); };
+    // TMEM: accumulator buffer j (tile i uses j = i & 3) at columns 64 j, A_lo slot
+    // p (tile i uses p = i & 1) at 256 + 64 p
     auto alo_col = [&](int s) { return (uint32_t)(256 + 64 * s); };
     auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
         return wait_or_abort(bar, parity, bt.wait_limit, abort_flag, bt.status);
     };
     // lo part x - trunc(x) of the rows of TMEM lane quarter `q` of stage s's gy tile into
-    // TMEM (one warp, thread = chunk row); samples past the tile's end are zeroed in the
-    // shared-memory tile too
-    auto lo_to_tmem = [&](int q, int n, int s) {
+    // TMEM A_lo slot p (one warp, thread = chunk row); samples past the tile's end are
+    // zeroed in the shared-memory tile too
+    auto lo_to_tmem = [&](int q, int n, int s, int p) {
         const int r = 32 * q + lane;
         char *hi = smem + stage_hi(s);
         const int nv = n - r * kL;
-        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(s);
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(p);
 #pragma unroll
         for (int cb = 0; cb < kL / 16; ++cb) {
             float v16[16];
@@ -729,47 +748,50 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                                                                      : kTileSamples);
             d.chunk0 = cur_off / kL + cur_ch + t * kChunks;
             d.tab = ch_seq & 1;
+            d.seq = ch_seq;
             d.first = cur_t == 0;
             d.M = cur_M;
             ++cur_t;
             d.last = cur_t == cur_nt;
         };
+        // B operand (single slot) and the channel-parity slot of the small tables
         auto build_tables = [&](const TileDesc &d) {
             const char *R = tabs + (size_t)d.ch * rec;
             const float *__restrict__ h = reinterpret_cast<const float *>(R + Tab::B_H);
-            char *T = smem + tslot(d.tab);
             // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, half of the rows)
-            for (int item = ct; item < 128; item += kConvThreads) {
-                const int k = item & 63, hh = item >> 6;
-                float hv[32];
+            for (int item = ct; item < 512; item += kConvThreads) {
+                const int k = item & 63, r0 = (item >> 6) * 8;   // column k, rows r0 .. r0+7
+                float hv[8];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int r = 32 * hh + q;
+                for (int q = 0; q < 8; ++q) {
+                    const int r = r0 + q;
                     hv[q] = k >= r ? __ldg(h + (k - r)) : 0.f;
                 }
                 const uint32_t kb = (k >> 5) * (NM * 128);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int r = 32 * hh + q;
+                for (int q = 0; q < 8; ++q) {
                     float hi, lo;
                     split_tf32(hv[q], hi, lo);
-                    const uint32_t o = kb + sw128_off(r, k & 31);
-                    *reinterpret_cast<float *>(T + SM::T_BHI + o) = hi;
-                    *reinterpret_cast<float *>(T + SM::T_BLO + o) = lo;
+                    const uint32_t o = kb + sw128_off(r0 + q, k & 31);
+                    *reinterpret_cast<float *>(smem + SM::T_BHI + o) = hi;
+                    *reinterpret_cast<float *>(smem + SM::T_BLO + o) = lo;
                 }
             }
+            char *T = smem + sslot(d.tab);
             const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
-            float4 *sOu = reinterpret_cast<float4 *>(T + SM::T_OU);
+            float4 *sOu = reinterpret_cast<float4 *>(T + SM::S_OU);
             for (int idx = ct; idx < kL * MB / 4; idx += kConvThreads) sOu[idx] = __ldg(Ou + idx);
             const float4 *src = reinterpret_cast<const float4 *>(R + Tab::B_SCAN);
-            float4 *dst = reinterpret_cast<float4 *>(T + SM::T_SCAN);
+            float4 *dst = reinterpret_cast<float4 *>(T + SM::S_SCAN);
             for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kConvThreads) dst[idx] = __ldg(src + idx);
-            float *coef = reinterpret_cast<float *>(T + SM::T_COEF);   // a[0..MB) | b[0..MB]
+            float *coef = reinterpret_cast<float *>(T + SM::S_COEF);   // a[0..MB) | b[0..MB]
             const Channel c = channel_of(bt, d.ch);
             if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
             if (ct <= MB) coef[MB + ct] = ct <= c.N ? bco[d.ch * bt.Nstride + ct] : 0.f;
+            fence_proxy_async_smem();   // B is read by the tensor cores
         };
-        // gy tile of `d` -> stage s
+        // gy tile of `d` -> stage s; the same tile of x is prefetched into L2 for the
+        // epilogue group that will load it
         auto issue_gy = [&](const TileDesc &d, int s) {
             if (tma_gy) {
                 if (ct == 0) {
@@ -782,140 +804,154 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 load_tile_async<kConvThreads>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
                                               gy_al && ((d.tstart & 3) == 0), ct);
             }
-        };
-        // x tile of `d` -> x buffer j; lands on x_bar[j]
-        auto issue_x = [&](const TileDesc &d, int j) {
-            if (tma_x) {
-                if (ct == 0) {
-                    mbar_arrive_expect_tx(&x_bar[j], kTileBytes);
-                    const int row = (int)(d.tstart / kL);
-                    tma_load_3d(sbase + xbuf(j), &tmx, 0, 0, row, &x_bar[j]);
-                    tma_load_3d(sbase + xbuf(j) + kKBlock, &tmx, 0, 1, row, &x_bar[j]);
-                }
-            } else {
-                load_tile_async<kConvThreads>(sbase + xbuf(j), x, d.tstart, d.tlen,
-                                              x_al && ((d.tstart & 3) == 0), ct);
-                cp_async_mbar_arrive_noinc(&x_bar[j]);
-            }
+            if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(x + d.tstart),
+                             "r"((uint32_t)kTileBytes)
+                             : "memory");
         };
 
         if (ct == 0) {
-            TileDesc d0;
+            // every slot starts as an end marker: the MMA warp ends both epilogue
+            // groups (indices E and E+1) when the work runs out at index E
+            for (int j = 0; j < 8; ++j) ring[j].ch = -1;
+            TileDesc d0, d1;
             next_desc(d0);
+            next_desc(d1);
             ring[0] = d0;
+            ring[1] = d1;
         }
         named_sync(kNamedConv, kConvThreads);
+        int64_t issued_upto = -1;   // last tile whose gy load this thread has issued
         {
-            const TileDesc d0 = ring[0];
+            const TileDesc d0 = ring[0], d1 = ring[1];
             if (d0.ch >= 0) {
                 build_tables(d0);
                 issue_gy(d0, 0);
+                issued_upto = 0;
+                if (d1.ch >= 0) {   // its tables (if it starts a channel) wait for MMA(0)
+                    issue_gy(d1, 1);
+                    issued_upto = 1;
+                }
             }
         }
         for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
-            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            const int s = (int)(i % kBwNS);
+            const uint32_t ph = (uint32_t)((i / kBwNS) & 1);
             const TileDesc d = ring[i & 7];
             if (d.ch < 0) {
                 if (ct == 0) mbar_arrive(&gy_landed[s]);   // end marker for the MMA warp
                 break;
             }
-            // (1) gy tile i landed
+            // (1) gy tile i landed (tile i+1's copies may still be in flight)
             if (ct == 0) {
                 bool ok = true;
-                if (tma_gy) ok = wait1(&load_bar[s], par);
+                if (tma_gy) ok = wait1(&load_bar[s], ph);
                 conv_ok[1] = ok ? 1 : 0;
             }
-            if (!tma_gy) cp_async_wait_all();
+            if (!tma_gy) {
+                if (issued_upto > i) cp_async_wait_1();
+                else cp_async_wait_all();
+            }
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[1]) break;
             if (ct == 0) mbar_arrive(&gy_landed[s]);   // the MMA warp converts its quarter
-            // (2) A_lo of rows 0-95 into TMEM (stage s's previous MMA, tile i-2, completed
-            //     before its gy load was issued)
-            lo_to_tmem(warp, d.tlen, s);
+            // (2) A_lo of rows 0-95 into TMEM slot i&1 (its previous reader MMA(i-2) was
+            //     waited for in the previous iteration)
+            lo_to_tmem(warp, d.tlen, s, (int)(i & 1));
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) the x tile into x buffer s once the epilogue of tile i-2 has released it
-            //     (after full[s], so that tile i's MMA never waits on the epilogue)
-            if (i >= 2) {
-                if (ct == 0) conv_ok[0] = wait1(&x_free[s], par ^ 1u) ? 1 : 0;
-                named_sync(kNamedConv, kConvThreads);
-                if (!conv_ok[0]) break;
-            }
-            issue_x(d, s);
-            // (4) next descriptor; a new channel's tables wait for their slot; MMA(i-1)
-            //     complete: stage s^1 takes tile i+1's gy, and through the MMA's wait on
-            //     the TMEM buffer the epilogue has finished tile i-3, whose ring slot is
-            //     reused
+            // (3) tile i+2's descriptor; MMA(i-1) complete frees stage (i+2)%3 (and, through
+            //     the MMA's wait on the accumulator buffer, the epilogue has started tile
+            //     i-5; ring slots are reused 8 apart).  If tile i+1 starts a channel, its
+            //     small tables wait for their slot and its B operand for MMA(i), the last
+            //     reader of the single B slot.
+            const TileDesc dn1 = ring[(i + 1) & 7];
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
-                if (nd.ch >= 0 && nd.first && ch_seq >= 2)
-                    ok = wait1(&tab_free[nd.tab], (uint32_t)(((ch_seq >> 1) - 1) & 1));
-                if (ok && i >= 1) ok = wait1(&mma_done[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
-                ring[(i + 1) & 7] = nd;
+                if (i >= 1) ok = wait1(&mma_done[(i - 1) & 3], (uint32_t)(((i - 1) >> 2) & 1));
+                if (ok && dn1.ch >= 0 && dn1.first) {
+                    if (dn1.seq >= 2) ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
+                    if (ok) ok = wait1(&mma_done[i & 3], (uint32_t)((i >> 2) & 1));
+                }
+                ring[(i + 2) & 7] = nd;
+                if (nd.ch < 0) ring[(i + 3) & 7] = nd;   // the other group's end marker
                 conv_ok[2] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[2]) break;
-            const TileDesc dn = ring[(i + 1) & 7];
-            if (dn.ch >= 0) {
-                if (dn.first) build_tables(dn);
-                issue_gy(dn, s ^ 1);
+            if (dn1.ch >= 0 && dn1.first) build_tables(dn1);
+            const TileDesc dn2 = ring[(i + 2) & 7];
+            if (dn2.ch >= 0) {
+                issue_gy(dn2, (int)((i + 2) % kBwNS));
+                issued_upto = i + 2;
             }
         }
     } else if (warp == kMmaWarp) {
         // ============================ MMA issuer ============================
         bool issued = false;
         for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
-            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            const int s = (int)(i % kBwNS);                  // gy stage
+            const uint32_t ph = (uint32_t)((i / kBwNS) & 1);
+            const int pl = (int)(i & 1);                      // A_lo slot
             int ok = 1;
-            if (lane == 0) ok = wait1(&gy_landed[s], par) ? 1 : 0;
+            if (lane == 0) ok = wait1(&gy_landed[s], ph) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             const TileDesc d = ring[i & 7];
-            // TMEM buffer s free (epilogue done with tile i-2, hence MMA(i-2) done and
-            // stage s's A_lo free); the end marker waits too, or its arrivals could
-            // complete a second phase of mma_done[s] before the epilogue has observed
-            // tile i-2's (a parity wait cannot tell them apart)
-            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[s], par ^ 1u) ? 1 : 0;
+            const int tb = (int)(i & 3);   // TMEM accumulator buffer
+            const uint32_t tpar = (uint32_t)((i >> 2) & 1);
+            // accumulator buffer free (its group done with tile i-4); end markers wait
+            // too, or their arrivals could complete a second phase of mma_done before the
+            // group has observed the previous one (a parity wait cannot tell them apart)
+            if (lane == 0 && i >= 4) ok = wait1(&tmem_free[tb], tpar ^ 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             if (d.ch < 0) {
+                // end markers for both groups: index i for group i & 1, i+1 for the other
                 if (lane == 0) {
-                    mbar_arrive(&mma_done[s]);
-                    mbar_arrive(&mma_done[s]);
+                    mbar_arrive(&mma_done[tb]);
+                    mbar_arrive(&mma_done[tb]);
+                    const int tb1 = (int)((i + 1) & 3);
+                    bool ok2 = true;
+                    if (i + 1 >= 4) ok2 = wait1(&tmem_free[tb1], (uint32_t)((((i + 1) >> 2) & 1) ^ 1u));
+                    if (ok2) {
+                        mbar_arrive(&mma_done[tb1]);
+                        mbar_arrive(&mma_done[tb1]);
+                    }
                 }
                 break;
             }
-            // A_lo of rows 96-127 (this warp's TMEM lane quarter)
+            // A_lo of rows 96-127 (this warp's TMEM lane quarter) once MMA(i-2), the slot's
+            // previous reader, is done (this warp's own commit)
+            if (lane == 0 && i >= 2) ok = wait1(&mma_done[(i - 2) & 3], (uint32_t)(((i - 2) >> 2) & 1)) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             tc_fence_after();
-            lo_to_tmem(3, d.tlen, s);
+            lo_to_tmem(3, d.tlen, s, pl);
             __syncwarp();
-            if (lane == 0) ok = wait1(&full[s], par) ? 1 : 0;
+            if (lane == 0) ok = wait1(&full[s], ph) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             if (lane == 0) {
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(s * 128);
-                const uint32_t tb = tslot(d.tab);
+                const uint32_t d_tmem = tmem + (uint32_t)(tb * 64);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
                     const uint32_t ka = (kk >> 2) * kKBlock + (kk & 3) * 32;
                     const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
                     const uint64_t ahi = sdesc_sw128(sbase + stage_hi(s) + ka);
-                    const uint64_t bhi = sdesc_sw128(sbase + tb + SM::T_BHI + kb);
+                    const uint64_t bhi = sdesc_sw128(sbase + SM::T_BHI + kb);
                     mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
-                        const uint64_t blo = sdesc_sw128(sbase + tb + SM::T_BLO + kb);
+                        const uint64_t blo = sdesc_sw128(sbase + SM::T_BLO + kb);
                         mma_tf32(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(s) + 8 * kk, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(pl) + 8 * kk, bhi, idesc, 1u);
                     }
                 }
-                mma_commit(&mma_done[s]);
-                mbar_arrive(&mma_done[s]);
+                mma_commit(&mma_done[tb]);
+                mbar_arrive(&mma_done[tb]);
             }
             issued = true;
             if (bt.stall_drill) {
@@ -930,38 +966,48 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
         }
         __syncwarp();
     } else {
-        // ============================ epilogue ==============================
-        const int et = tid - kEpiWarp0 * 32;   // chunk = TMEM lane
-        const int ew = warp - kEpiWarp0;
+        // ====================== epilogue (two groups) =======================
+        const int eg = (warp - kEpiWarp0) >> 2;            // group: tiles i with i & 1 == eg
+        const int ew = (warp - kEpiWarp0) & 3;             // TMEM lane quarter (warp % 4)
+        const int et = tid - (kEpiWarp0 + 4 * eg) * 32;    // chunk = TMEM lane
+        const int bar_id = kNamedEpi + eg;
+        volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 16 + 16 * eg);
+        float *wt = reinterpret_cast<float *>(smem + SM::M_WT) + eg * 4 * MB;
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
-        float Sin[MB];   // state entering the tile from the right
-        double S64a = 0.0, S64b = 0.0;
-        double accd = 0.0;   // lane k < 2MB+1: this warp's sum of lag product k over the channel
-        bool store_pending = false;   // (thread 0) the previous tile's bulk store may still read
-        for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
-            const uint32_t par = (uint32_t)((i >> 1) & 1);
+        for (int64_t i = eg;; i += 2) {
+            const int s = (int)(i & 1);   // == eg
+            const int tb = (int)(i & 3);  // TMEM accumulator buffer
+            const int xj = eg;            // this group's x buffer
             if (et == 0) {
-                epi_ok[0] = wait1(&mma_done[s], par) ? 1 : 0;
-                if (store_pending) {   // release the previous tile's x buffer once read
-                    bulk_wait_read0();
-                    mbar_arrive(&x_free[s ^ 1]);
-                    store_pending = false;
-                }
+                epi_ok[0] = wait1(&mma_done[tb], (uint32_t)((i >> 2) & 1)) ? 1 : 0;
+                bulk_wait_read0();   // the previous tile's grad_x store has read the x buffer
             }
-            named_sync(kNamedEpi, 128);
+            named_sync(bar_id, 128);
             if (!epi_ok[0]) break;
             tc_fence_after();
             const TileDesc pv = ring[i & 7];
             if (pv.ch < 0) break;
-            const char *T = smem + tslot(pv.tab);
-            const float *sOu = reinterpret_cast<const float *>(T + SM::T_OU);
-            const float *sP = reinterpret_cast<const float *>(T + SM::T_SCAN);
-            const double *sAt = reinterpret_cast<const double *>(T + SM::T_SCAN);
-            const float *coef = reinterpret_cast<const float *>(T + SM::T_COEF);
-            char *xs = smem + xbuf(s);   // x tile, then grad_x (operand layout)
+            const char *T = smem + sslot(pv.tab);
+            const float *sOu = reinterpret_cast<const float *>(T + SM::S_OU);
+            const float *sP = reinterpret_cast<const float *>(T + SM::S_SCAN);
+            const double *sAt = reinterpret_cast<const double *>(T + SM::S_SCAN);
+            const float *coef = reinterpret_cast<const float *>(T + SM::S_COEF);
+            char *xs = smem + xbuf(xj);   // x tile, then grad_x (operand layout)
+            // this tile's x (prefetched into L2 with its gy tile) into the group's buffer
+            if (tma_x) {
+                if (et == 0) {
+                    mbar_arrive_expect_tx(&x_bar[xj], kTileBytes);
+                    const int row = (int)(pv.tstart / kL);
+                    tma_load_3d(sbase + xbuf(xj), &tmx, 0, 0, row, &x_bar[xj]);
+                    tma_load_3d(sbase + xbuf(xj) + kKBlock, &tmx, 0, 1, row, &x_bar[xj]);
+                }
+            } else {
+                load_tile_async<128>(sbase + xbuf(xj), x, pv.tstart, pv.tlen,
+                                     x_al && ((pv.tstart & 3) == 0), et);
+                cp_async_mbar_arrive_noinc(&x_bar[xj]);
+            }
             const int nch = (pv.tlen + kL - 1) / kL;
-            const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
+            const uint32_t taddr = tmem + lane_off + (uint32_t)(tb * 64);
             // the forward's state entering this chunk (read early: global latency)
             float st[MB];
             {
@@ -969,11 +1015,6 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                 const float *src = saved + (size_t)(pv.chunk0 + et) * bt.Mstride;
 #pragma unroll
                 for (int m = 0; m < MB; ++m) st[m] = (vch && m < pv.M) ? src[m] : 0.f;
-            }
-            if (pv.first) {   // the channel's last tile in time: nothing to its right
-#pragma unroll
-                for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
-                S64a = S64b = 0.0;
             }
             float E[MB];
             {
@@ -983,8 +1024,18 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) E[m] = v[m];
             }
+            // the state entering the tile from the right: the previous tile's carry
+            // (always waited for, which keeps the carry barriers' phases in step)
+            if (i >= 1) {
+                if (et == 0) epi_ok[2] = wait1(&carry_bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
+                named_sync(bar_id, 128);
+                if (!epi_ok[2]) break;
+            }
             float S[MB];   // S'_c = u[(c+1)L + m]
             if constexpr (!F64) {
+                float Sin[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) Sin[m] = (pv.first || i == 0) ? 0.f : carry[(s ^ 1) * MB + m];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const int dd = 1 << k;
@@ -1002,7 +1053,7 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
 #pragma unroll
                     for (int m = 0; m < MB; ++m) wt[ew * MB + m] = E[m];
                 }
-                named_sync(kNamedEpi, 128);
+                named_sync(bar_id, 128);
                 float C[MB];
 #pragma unroll
                 for (int m = 0; m < MB; ++m) C[m] = Sin[m];
@@ -1017,8 +1068,11 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
 #pragma unroll
                     for (int m = 0; m < MB; ++m) C[m] = w2[m] + wt[ww * MB + m];
                 }
+                if (et == 0) {   // carry for the next tile (the other group)
 #pragma unroll
-                for (int m = 0; m < MB; ++m) Sin[m] = C[m];
+                    for (int m = 0; m < MB; ++m) carry[s * MB + m] = C[m];
+                    mbar_arrive(&carry_bar[s]);
+                }
                 float v[MB];
 #pragma unroll
                 for (int m = 0; m < MB; ++m) v[m] = S[m];
@@ -1037,20 +1091,23 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                     const float wn = __shfl_down_sync(0xffffffffu, E[m], 1);
                     S[m] = v[m] + (lane < 31 ? wn : 0.f);
                 }
-                named_sync(kNamedEpi, 128);
+                named_sync(bar_id, 128);   // wt reusable
             } else {
-                // serial FP64 reverse scan by the first epilogue warp
-                float *xbuf = reinterpret_cast<float *>(smem + SM::SCR);
-                float *sbuf = xbuf + kChunks * MB;
+                // serial FP64 reverse scan by the group's first warp
+                float *xbuf_s = reinterpret_cast<float *>(smem + SM::SCR + eg * SM::SCR_G);
+                float *sbuf = xbuf_s + kChunks * MB;
 #pragma unroll
-                for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
-                named_sync(kNamedEpi, 128);
+                for (int m = 0; m < MB; ++m) xbuf_s[et * MB + m] = E[m];
+                named_sync(bar_id, 128);
                 if (ew == 0) {
+                    const bool z = pv.first || i == 0;
+                    double S64a = (!z && lane < MB) ? carry64[(s ^ 1) * MB + lane] : 0.0;
+                    double S64b = (!z && lane + 32 < MB) ? carry64[(s ^ 1) * MB + lane + 32] : 0.0;
                     for (int cc = nch - 1; cc >= 0; --cc) {
                         if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
                         if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
-                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
-                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
+                        double acc_a = lane < MB ? (double)xbuf_s[cc * MB + lane] : 0.0;
+                        double acc_b = lane + 32 < MB ? (double)xbuf_s[cc * MB + lane + 32] : 0.0;
 #pragma unroll 8
                         for (int j = 0; j < MB; ++j) {
                             const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
@@ -1060,87 +1117,91 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         S64a = acc_a;
                         S64b = acc_b;
                     }
+                    if (lane < MB) carry64[s * MB + lane] = S64a;
+                    if (lane + 32 < MB) carry64[s * MB + lane + 32] = S64b;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&carry_bar[s]);   // carry for the next tile
                 }
-                named_sync(kNamedEpi, 128);
+                named_sync(bar_id, 128);
 #pragma unroll
                 for (int m = 0; m < MB; ++m) S[m] = et < nch ? sbuf[et * MB + m] : 0.f;
-                named_sync(kNamedEpi, 128);
+                named_sync(bar_id, 128);
             }
-            // adjoint u for this chunk (TMEM zero-state part + free response)
-            float u[kL];
-#pragma unroll
-            for (int cb = 0; cb < kL / 16; ++cb) {
+            // x tile landed in the group's buffer
+            if (et == 0) epi_ok[1] = wait1(&x_bar[xj], (uint32_t)((i >> 1) & 1)) ? 1 : 0;
+            named_sync(bar_id, 128);
+            if (!epi_ok[1]) break;
+            // Streamed over the chunk row, 16 columns of the adjoint at a time (u = TMEM
+            // zero-state part + free response O^u S'), 4 samples per x piece: y
+            // recomputed from the forward's chunk state, the lag correlations
+            // grad_b[k] += u[n+k] x[n] and grad_a[k] -= u[n+1+k] y[n], and
+            // grad_x = sum_k b_k u[n+k] written over x
+            auto u_block = [&](int bb, float (&ub)[16]) {
                 float v[16];
-                tmem_ld16(taddr + cb * 16, v);
+                tmem_ld16(taddr + bb * 16, v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int n = cb * 16 + q;
+                    const int n = bb * 16 + q;
                     float a = v[q];
 #pragma unroll
                     for (int m = 0; m < MB; ++m) a = fmaf(sOu[n * MB + m], S[m], a);
-                    u[n] = a;
+                    ub[q] = a;
                 }
-            }
-            tc_fence_before();
+            };
+            float ucur[16], unext[16];
+            u_block(0, ucur);
             if (gzi && pv.last && et == 0) {
 #pragma unroll
                 for (int m = 0; m < MB; ++m)
-                    if (m < pv.M) gzi[pv.ch * bt.Mstride + m] = u[m];
+                    if (m < pv.M) gzi[pv.ch * bt.Mstride + m] = ucur[m];
             }
-            // x tile landed in x buffer s
-            if (et == 0) epi_ok[1] = wait1(&x_bar[s], par) ? 1 : 0;
-            named_sync(kNamedEpi, 128);
-            if (et == 0) mbar_arrive(&tmem_free[s]);
-            if (!epi_ok[1]) break;
-            float w[kL];   // x of this chunk, then grad_x
-#pragma unroll
-            for (int j16 = 0; j16 < 16; ++j16) {
-                const float4 v = *reinterpret_cast<const float4 *>(xs + op_piece(et, j16));
-                w[4 * j16] = v.x;
-                w[4 * j16 + 1] = v.y;
-                w[4 * j16 + 2] = v.z;
-                w[4 * j16 + 3] = v.w;
-            }
-            if (pv.tlen < kTileSamples) {   // samples past the channel's end read as zero
-                const int nv = pv.tlen - et * kL;
-#pragma unroll
-                for (int n = 0; n < kL; ++n)
-                    if (n >= nv) w[n] = 0.f;
-            }
-#define DFILT_EXT(n) ((n) < kL ? u[(n)] : S[(n) - kL])
-            // y recomputed from the forward's chunk state, fused with the lag
-            // correlations grad_b[k] += u[n+k] x[n], grad_a[k] -= u[n+1+k] y[n]
             float pb[MB + 1], pa[MB];
 #pragma unroll
             for (int k = 0; k <= MB; ++k) pb[k] = 0.f;
 #pragma unroll
             for (int k = 0; k < MB; ++k) pa[k] = 0.f;
+            const int nvalid = pv.tlen - et * kL;   // samples past the channel's end read as zero
+#pragma unroll 1
+            for (int bb = 0; bb < kL / 16; ++bb) {
+                if (bb + 1 < kL / 16) {
+                    u_block(bb + 1, unext);
+                } else {
 #pragma unroll
-            for (int n = 0; n < kL; ++n) {
-                const float xn = w[n];
-                const float yn = fmaf(coef[MB], xn, st[0]);
+                    for (int q = 0; q < 16; ++q) unext[q] = q < MB ? S[q] : 0.f;   // u[L + m] = S'_m
+                }
+#define DFILT_EXT(nn) ((nn) < 16 ? ucur[(nn)] : unext[(nn) - 16])
 #pragma unroll
-                for (int k = 0; k < MB; ++k)
-                    st[k] = fmaf(-coef[k], yn, fmaf(coef[MB + 1 + k], xn, k + 1 < MB ? st[k + 1] : 0.f));
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    const int j16 = bb * 4 + p4;
+                    const float4 xv = *reinterpret_cast<const float4 *>(xs + op_piece(et, j16));
+                    const float xq[4] = {xv.x, xv.y, xv.z, xv.w};
+                    float gq[4];
 #pragma unroll
-                for (int k = 0; k <= MB; ++k) pb[k] = fmaf(DFILT_EXT(n + k), xn, pb[k]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int nn = 4 * p4 + q;        // within the block
+                        const int n = bb * 16 + nn;       // within the chunk
+                        const float xn = n < nvalid ? xq[q] : 0.f;
+                        const float yn = fmaf(coef[MB], xn, st[0]);
 #pragma unroll
-                for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(n + 1 + k), yn, pa[k]);
-            }
-            // grad_x = sum_k b_k u[n+k], over this chunk's x row
+                        for (int k = 0; k < MB; ++k)
+                            st[k] = fmaf(-coef[k], yn, fmaf(coef[MB + 1 + k], xn, k + 1 < MB ? st[k + 1] : 0.f));
 #pragma unroll
-            for (int n = 0; n < kL; ++n) {
-                float a = 0.f;
+                        for (int k = 0; k <= MB; ++k) pb[k] = fmaf(DFILT_EXT(nn + k), xn, pb[k]);
 #pragma unroll
-                for (int k = 0; k <= MB; ++k) a = fmaf(coef[MB + k], DFILT_EXT(n + k), a);
-                w[n] = a;
-            }
+                        for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(nn + 1 + k), yn, pa[k]);
+                        float g = 0.f;
+#pragma unroll
+                        for (int k = 0; k <= MB; ++k) g = fmaf(coef[MB + k], DFILT_EXT(nn + k), g);
+                        gq[q] = g;
+                    }
+                    *reinterpret_cast<float4 *>(xs + op_piece(et, j16)) = make_float4(gq[0], gq[1], gq[2], gq[3]);
+                }
 #undef DFILT_EXT
 #pragma unroll
-            for (int j16 = 0; j16 < 16; ++j16)
-                *reinterpret_cast<float4 *>(xs + op_piece(et, j16)) =
-                    make_float4(w[4 * j16], w[4 * j16 + 1], w[4 * j16 + 2], w[4 * j16 + 3]);
+                for (int q = 0; q < 16; ++q) ucur[q] = unext[q];
+            }
+            tc_fence_before();
             fence_proxy_async_smem();
             {
                 float mine = 0.f;
@@ -1151,18 +1212,18 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                     if (lane == k) mine = v;
                 }
-                accd += (double)mine;
+                if (lane < NACC) atomicAdd(&acc_ch[pv.tab * NACC + lane], (double)mine);
             }
-            named_sync(kNamedEpi, 128);
+            named_sync(bar_id, 128);
+            if (et == 0) mbar_arrive(&tmem_free[tb]);
             const bool tma_store = tma_gx && gx && pv.tlen == kTileSamples;
             if (tma_store) {
                 if (et == 0) {
-                    // asynchronous; the buffer is released at the next tile (or exit)
+                    // asynchronous: the group's next tile waits for the read of its buffer
                     const int row = (int)(pv.tstart / kL);
-                    tma_store_3d(&tmgx, 0, 0, row, sbase + xbuf(s));
-                    tma_store_3d(&tmgx, 0, 1, row, sbase + xbuf(s) + kKBlock);
+                    tma_store_3d(&tmgx, 0, 0, row, sbase + xbuf(xj));
+                    tma_store_3d(&tmgx, 0, 1, row, sbase + xbuf(xj) + kKBlock);
                     bulk_commit();
-                    store_pending = true;
                 }
             } else {
                 if (gx) {
@@ -1185,16 +1246,43 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         }
                     }
                 }
-                named_sync(kNamedEpi, 128);
-                if (et == 0) mbar_arrive(&x_free[s]);
+                named_sync(bar_id, 128);
+            }
+            // this tile's lag sums are in: count it for its channel
+            if (et == 0) {
+                __threadfence_block();
+                atomicAdd(&tiles_done[pv.tab], 1u);
             }
             if (pv.last) {
-                if (lane < NACC) acc_s[ew * NACC + lane] = accd;
-                accd = 0.0;
-                named_sync(kNamedEpi, 128);
+                // the channel's other tiles (the other group's included) have added theirs
+                if (et == 0) {
+                    const Channel c = channel_of(bt, pv.ch);
+                    const unsigned nt = (unsigned)((c.len + kTileSamples - 1) / kTileSamples);
+                    volatile unsigned *cnt = tiles_done + pv.tab;
+                    bool ok = false;
+                    for (long long it = 0; it < bt.wait_limit; ++it) {
+                        if (*cnt >= nt) {
+                            ok = true;
+                            break;
+                        }
+                        if ((it & 63) == 63) {
+                            if (*abort_flag) break;
+                            __nanosleep(32);
+                        }
+                    }
+                    if (!ok && !*abort_flag) {
+                        set_status(bt.status, DFILT_ERR_TIMEOUT);
+                        *abort_flag = 1;
+                    }
+                    __threadfence_block();
+                    epi_ok[3] = ok ? 1 : 0;
+                }
+                named_sync(bar_id, 128);
+                if (!epi_ok[3]) break;
                 const Channel c = channel_of(bt, pv.ch);
                 for (int k = et; k < NACC; k += 128) {
-                    const double v = acc_s[k] + acc_s[NACC + k] + acc_s[2 * NACC + k] + acc_s[3 * NACC + k];
+                    const double v = acc_ch[pv.tab * NACC + k];
+                    acc_ch[pv.tab * NACC + k] = 0.0;
                     if (k <= MB) {
                         if (gb && k <= c.N) gb[pv.ch * bt.Nstride + k] = (float)v;
                     } else {
@@ -1202,7 +1290,8 @@ __global__ void __launch_bounds__(pipe::kPipeThreads, 1)
                         if (ga && m < c.M) ga[pv.ch * bt.Mstride + m] = (float)(-v);
                     }
                 }
-                named_sync(kNamedEpi, 128);
+                if (et == 0) tiles_done[pv.tab] = 0u;
+                named_sync(bar_id, 128);
                 if (et == 0) mbar_arrive(&tab_free[pv.tab]);
             }
         }
@@ -1249,7 +1338,7 @@ cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
         if (make_chunk_tmap(&tmx, x, bt.total)) tma |= 2;
         if (gx && make_chunk_tmap(&tmgx, gx, bt.total)) tma |= 4;
     }
-    kern<<<(unsigned)grid, pipe::kPipeThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter,
+    kern<<<(unsigned)grid, kBwThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter,
                                                        bt, three, mask, tma, tmg, tmx, tmgx);
     return cudaGetLastError();
 }

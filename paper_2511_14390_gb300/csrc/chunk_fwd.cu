@@ -677,6 +677,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kConvThreads) dst[idx] = __ldg(src + idx);
             double *sin = reinterpret_cast<double *>(T + PS::T_SIN);
             if (ct < MB) sin[ct] = (zi && ct < d.M) ? (double)zi[d.ch * bt.Mstride + ct] : 0.0;
+            fence_proxy_async_smem();   // B is read by the tensor cores
         };
         // tile i's signal into stage s's hi slot (TMA by thread 0, or cp.async by all)
         auto issue_load = [&](const TileDesc &d, int s) {

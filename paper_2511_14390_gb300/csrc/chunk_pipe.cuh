@@ -28,7 +28,9 @@ struct TileDesc {
     int32_t first;     // first tile of its channel (in processing order)
     int32_t M;         // channel order
     int32_t last;      // last tile of its channel (in processing order)
+    int32_t seq;       // the channel's position among this CTA's channels (table slot = seq & 1)
 };
+static_assert(sizeof(TileDesc) == 48, "ring slots are 48 bytes");
 
 __device__ __forceinline__ void named_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
