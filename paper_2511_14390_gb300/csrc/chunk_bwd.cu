@@ -550,11 +550,12 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 //               B operand T_h^a, single-buffered: rebuilt once the channel's last MMA
 //               is done; O^u, scan block, coefficients double-buffered by channel
 //               parity); gy tiles two ahead into three stages (TMA or cp.async; the
-//               raw tile is the TF32 hi operand) -> gy_landed[s]; the lo part of rows
-//               0-95 into TMEM -> full[s]; the tile's x is prefetched into L2
-//   warp 3      MMA: the lo part of rows 96-127 into TMEM (its TMEM lane quarter), then
-//               D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk) into TMEM
-//               buffer i&1
+//               raw words are the TF32 hi operand) -> gy_landed[s]; the TF32 operand
+//               (hi and lo) of rows 0-95 into TMEM -> full[s]; the stage is free once
+//               converted; the tile's x is prefetched into L2
+//   warp 3      MMA: the operand of rows 96-127 into TMEM (its TMEM lane quarter), then
+//               D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk; A from TMEM, the
+//               B operand from shared memory) into TMEM accumulator i&3
 //   warps 4-7   epilogue group 0 (even tiles), warps 8-11 group 1 (odd tiles): reverse
 //               chunk scan of S'_c = u[(c+1)L ..] (each group loads its tile's x into its
 //               own buffer first; the state entering from the right
@@ -650,6 +651,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < SM::NBAR; ++i) {
             uint32_t cnt = 1;
+            if (i < 3) cnt = 2;                                               // full: converters + MMA warp
             if (i >= 9 && i < 13) cnt = 2;                                    // mma_done: commit + arrive
             if (i >= 17 && i < 19 && !tma_x) cnt = 128;                       // x_bar: a group's cp.async arrivals
             mbar_init(&bars[i], cnt);
@@ -668,44 +670,42 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     auto stage_hi = [&](int s) { return (uint32_t)(SM::GS0 + s * kTileBytes); };
     auto xbuf = [&](int j) { return (uint32_t)(SM::XB0 + j * kTileBytes); };
     auto sslot = [&](int p) { return (uint32_t)(SM::SMALL0 + p * SM::SSLOT); };
-    // TMEM: accumulator buffer j (tile i uses j = i & 3) at columns 64 j, A_lo slot
-    // p (tile i uses p = i & 1) at 256 + 64 p
-    auto alo_col = [&](int s) { return (uint32_t)(256 + 64 * s); };
+    // TMEM: accumulator buffer j (tile i uses j = i & 3) at columns 64 j; operand slot p
+    // (tile i uses p = i & 1): A_hi at 256 + 128 p, A_lo at 256 + 128 p + 64
+    auto ahi_col = [&](int p) { return (uint32_t)(256 + 128 * p); };
+    auto alo_col = [&](int p) { return (uint32_t)(256 + 128 * p + 64); };
     auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
         return wait_or_abort(bar, parity, bt.wait_limit, abort_flag, bt.status);
     };
-    // lo part x - trunc(x) of the rows of TMEM lane quarter `q` of stage s's gy tile into
-    // TMEM A_lo slot p (one warp, thread = chunk row); samples past the tile's end are
-    // zeroed in the shared-memory tile too
-    auto lo_to_tmem = [&](int q, int n, int s, int p) {
+    // The TF32 operand of the rows of TMEM lane quarter `q` of stage s's gy tile into TMEM
+    // operand slot p (one warp, thread = chunk row): the raw word as A_hi (the tensor
+    // cores truncate a TF32 operand to its upper 19 bits) and x - trunc(x) as A_lo;
+    // samples past the tile's end are zero
+    auto a_to_tmem = [&](int q, int n, int s, int p) {
         const int r = 32 * q + lane;
-        char *hi = smem + stage_hi(s);
+        const char *hi = smem + stage_hi(s);
         const int nv = n - r * kL;
-        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(p);
+        const uint32_t lrow = (uint32_t)(32 * q) << 16;
 #pragma unroll
         for (int cb = 0; cb < kL / 16; ++cb) {
-            float v16[16];
+            float vh[16], vl[16];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const int j16 = cb * 4 + p;
-                float4 v = *reinterpret_cast<float4 *>(hi + op_piece(r, j16));
-                if (4 * j16 + 4 > nv) {
-                    if (4 * j16 + 0 >= nv) v.x = 0.f;
-                    if (4 * j16 + 1 >= nv) v.y = 0.f;
-                    if (4 * j16 + 2 >= nv) v.z = 0.f;
-                    if (4 * j16 + 3 >= nv) v.w = 0.f;
-                    *reinterpret_cast<float4 *>(hi + op_piece(r, j16)) = v;
+            for (int p4 = 0; p4 < 4; ++p4) {
+                const int j16 = cb * 4 + p4;
+                const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float xv = 4 * j16 + c < nv ? e[c] : 0.f;
+                    float h;
+                    split_tf32(xv, h, vl[4 * p4 + c]);
+                    vh[4 * p4 + c] = xv;
                 }
-                float h;
-                split_tf32(v.x, h, v16[4 * p + 0]);
-                split_tf32(v.y, h, v16[4 * p + 1]);
-                split_tf32(v.z, h, v16[4 * p + 2]);
-                split_tf32(v.w, h, v16[4 * p + 3]);
             }
-            if (three) tmem_st16(ta + cb * 16, v16);
+            tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
+            if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
         }
-        if (three) tmem_wait_st();
-        if (n < kTileSamples) fence_proxy_async_smem();
+        tmem_wait_st();
         tc_fence_before();
     };
 
@@ -842,10 +842,12 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (ct == 0) mbar_arrive(&gy_landed[s]);   // end marker for the MMA warp
                 break;
             }
-            // (1) gy tile i landed (tile i+1's copies may still be in flight)
+            // (1) gy tile i landed (tile i+1's copies may still be in flight); operand slot
+            //     i&1 free once MMA(i-2), its previous reader, is done
             if (ct == 0) {
                 bool ok = true;
                 if (tma_gy) ok = wait1(&load_bar[s], ph);
+                if (ok && i >= 2) ok = wait1(&mma_done[(i - 2) & 3], (uint32_t)(((i - 2) >> 2) & 1));
                 conv_ok[1] = ok ? 1 : 0;
             }
             if (!tma_gy) {
@@ -855,22 +857,22 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[1]) break;
             if (ct == 0) mbar_arrive(&gy_landed[s]);   // the MMA warp converts its quarter
-            // (2) A_lo of rows 0-95 into TMEM slot i&1 (its previous reader MMA(i-2) was
-            //     waited for in the previous iteration)
-            lo_to_tmem(warp, d.tlen, s, (int)(i & 1));
+            // (2) operand rows 0-95 into TMEM slot i&1
+            tc_fence_after();
+            a_to_tmem(warp, d.tlen, s, (int)(i & 1));
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) tile i+2's descriptor; MMA(i-1) complete frees stage (i+2)%3 (and, through
-            //     the MMA's wait on the accumulator buffer, the epilogue has started tile
-            //     i-5; ring slots are reused 8 apart).  If tile i+1 starts a channel, its
-            //     small tables wait for their slot and its B operand for MMA(i), the last
-            //     reader of the single B slot.
+            // (3) tile i+2's descriptor; stage (i+2)%3 is free once both converter sets have
+            //     read tile i-1 out of it (full[(i-1)%3]; ring slots are reused 8 apart, far
+            //     behind every reader).  If tile i+1 starts a channel, its small tables wait
+            //     for their slot and its B operand for MMA(i), the last reader of the single
+            //     B slot.
             const TileDesc dn1 = ring[(i + 1) & 7];
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
-                if (i >= 1) ok = wait1(&mma_done[(i - 1) & 3], (uint32_t)(((i - 1) >> 2) & 1));
+                if (i >= 1) ok = wait1(&full[(i - 1) % kBwNS], (uint32_t)(((i - 1) / kBwNS) & 1));
                 if (ok && dn1.ch >= 0 && dn1.first) {
                     if (dn1.seq >= 2) ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
                     if (ok) ok = wait1(&mma_done[i & 3], (uint32_t)((i >> 2) & 1));
@@ -923,15 +925,18 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
                 break;
             }
-            // A_lo of rows 96-127 (this warp's TMEM lane quarter) once MMA(i-2), the slot's
+            // operand rows 96-127 (this warp's TMEM lane quarter) once MMA(i-2), the slot's
             // previous reader, is done (this warp's own commit)
             if (lane == 0 && i >= 2) ok = wait1(&mma_done[(i - 2) & 3], (uint32_t)(((i - 2) >> 2) & 1)) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            lo_to_tmem(3, d.tlen, s, pl);
+            a_to_tmem(3, d.tlen, s, pl);
             __syncwarp();
-            if (lane == 0) ok = wait1(&full[s], ph) ? 1 : 0;
+            if (lane == 0) {
+                mbar_arrive(&full[s]);
+                ok = wait1(&full[s], ph) ? 1 : 0;
+            }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             if (lane == 0) {
@@ -939,14 +944,13 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 const uint32_t d_tmem = tmem + (uint32_t)(tb * 64);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
-                    const uint32_t ka = (kk >> 2) * kKBlock + (kk & 3) * 32;
                     const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
-                    const uint64_t ahi = sdesc_sw128(sbase + stage_hi(s) + ka);
+                    const uint32_t ahi = tmem + ahi_col(pl) + 8 * kk;
                     const uint64_t bhi = sdesc_sw128(sbase + SM::T_BHI + kb);
-                    mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_tmem_a(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
                         const uint64_t blo = sdesc_sw128(sbase + SM::T_BLO + kb);
-                        mma_tf32(d_tmem, ahi, blo, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, ahi, blo, idesc, 1u);
                         mma_tf32_tmem_a(d_tmem, tmem + alo_col(pl) + 8 * kk, bhi, idesc, 1u);
                     }
                 }
