@@ -478,19 +478,19 @@ struct TileDesc {
 // ===========================================================================
 // Warp-specialised forward (state buckets whose double-buffered layout fits).
 //
-// Roles (384 threads), decoupled by mbarriers, two pipeline stages s = i & 1:
+// Roles (384 threads), decoupled by mbarriers; signal tiles in NST shared-memory
+// stages (s = i % NST), TMEM operand slots and accumulators alternating (i & 1):
 //   warps 0-2, 8-11  converters: fetch work; build per-channel tables (double-buffered by
-//              channel parity); the signal tile arrives in stage s's x buffer (TMA
-//              tensor load into the 128-byte-swizzled operand layout, or cp.async when
-//              the layout has no chunk-aligned rows); the raw tile is the TF32 hi
-//              operand, and warps 8-11 write its lo part into TMEM   -> full[s]
-//              then load tile i+1 into the other stage once MMA(i-1) released it
-//   warp 3     MMA issuer: full[s], tmem_free[s] -> tcgen05.mma into TMEM buffer s
-//              (A_hi from shared memory, A_lo from TMEM)  -> mma_done[s] (commit)
-//   warps 4-7  epilogue: mma_done[s] -> chunk-state scan, y = D + O_L S, saved
-//              states; y staged in stage s's y buffer in the operand layout and
-//              written by a TMA tensor store (full tiles) or plain stores
-//                                                   -> tmem_free[s]
+//              channel parity); signal tiles arrive NST-1 ahead (TMA tensor load into
+//              the 128-byte-swizzled operand layout, or cp.async when the layout has no
+//              chunk-aligned rows); warps 8-11 write the TF32 operand (the raw words as
+//              hi, x - trunc(x) as lo) into TMEM operand slot i&1 once MMA(i-2) is done
+//                                                   -> full[s]; the stage is then free
+//   warp 3     MMA issuer: full[s], tmem_free -> tcgen05.mma (A from TMEM, the B operand
+//              from shared memory) into TMEM accumulator i&1  -> mma_done (commit)
+//   warps 4-7  epilogue: mma_done -> chunk-state scan, y = D + O_L S, saved states; y
+//              staged in the y buffer in the operand layout and written by a TMA tensor
+//              store (full tiles) or plain stores     -> tmem_free
 // ===========================================================================
 // The forward's epilogue needs few registers, so this pipeline runs 12 warps: the
 // converters are warps 0-2 and 8-11 (224 threads), the MMA issuer warp 3 and the
@@ -507,7 +507,7 @@ template <int MB, bool F64, int NST>
 struct WsSmem {
     using P = PipeSmem<MB, F64, NST>;
     static constexpr uint32_t MISC = P::MISC;
-    // barriers: full[3] stage_done[3] load[3] mma_done[2] tmem_free[2] tab_free[2] dead
+    // barriers: full[3] (unused)[3] load[3] mma_done[2] tmem_free[2] tab_free[2] dead
     // drain (17, 20 slots)
     static constexpr int NBAR = 20;
     static constexpr uint32_t M_BAR = MISC;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *stage_done = bars + 3, *load_bar = bars + 6, *mma_done = bars + 9,
+    uint64_t *full = bars + 0, *load_bar = bars + 6, *mma_done = bars + 9,
              *tmem_free = bars + 11, *tab_free = bars + 13, *dead = bars + 15, *drain = bars + 16;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
@@ -578,7 +578,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     auto stage_hi = [&](int s) { return (uint32_t)(PS::XS0 + s * kTileBytes); };
     auto tslot = [&](int p) { return (uint32_t)(PS::TAB0 + p * PS::TSLOT); };
     // TMEM columns of stage s's A_lo (128 lanes = chunks x 64 columns = samples)
-    auto alo_col = [&](int s) { return (uint32_t)(256 + 64 * s); };
+    auto ahi_col = [&](int p) { return (uint32_t)(256 + 128 * p); };
+    auto alo_col = [&](int p) { return (uint32_t)(256 + 128 * p + 64); };
     // bounded wait by one thread; on timeout (or a peer's abort) raise the abort flag
     auto wait1 = [&](uint64_t *bar, uint32_t parity) -> bool {
         for (long long it = 0; it < bt.wait_limit; ++it) {
@@ -694,39 +695,36 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             }
         };
 
-        // lo part x - trunc(x) of stage s's tile into TMEM (warps 8-11, one TMEM lane
-        // quarter each, thread = chunk row); samples past the tile's end are zeroed in the
-        // shared-memory tile too (a TMA load may bring in the next channel's samples)
-        auto lo_to_tmem = [&](int n, int s) {
+        // TF32 operand of stage s's tile into TMEM operand slot p (warps 8-11, one TMEM
+        // lane quarter each, thread = chunk row): the raw word as A_hi (the tensor cores
+        // truncate a TF32 operand to its upper 19 bits) and x - trunc(x) as A_lo; samples
+        // past the tile's end are zero (a TMA load may bring in the next channel's)
+        auto a_to_tmem = [&](int n, int s, int p) {
             const int q = warp & 3;
             const int r = 32 * q + lane;
-            char *hi = smem + stage_hi(s);
+            const char *hi = smem + stage_hi(s);
             const int nv = n - r * kL;   // valid samples of this row
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + alo_col(s);
+            const uint32_t lrow = (uint32_t)(32 * q) << 16;
 #pragma unroll
             for (int cb = 0; cb < kL / 16; ++cb) {
-                float v16[16];
+                float vh[16], vl[16];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int j16 = cb * 4 + p;
-                    float4 v = *reinterpret_cast<float4 *>(hi + op_piece(r, j16));
-                    if (4 * j16 + 4 > nv) {
-                        if (4 * j16 + 0 >= nv) v.x = 0.f;
-                        if (4 * j16 + 1 >= nv) v.y = 0.f;
-                        if (4 * j16 + 2 >= nv) v.z = 0.f;
-                        if (4 * j16 + 3 >= nv) v.w = 0.f;
-                        *reinterpret_cast<float4 *>(hi + op_piece(r, j16)) = v;
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    const int j16 = cb * 4 + p4;
+                    const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
+                    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float xv = 4 * j16 + c < nv ? e[c] : 0.f;
+                        float h;
+                        split_tf32(xv, h, vl[4 * p4 + c]);
+                        vh[4 * p4 + c] = xv;
                     }
-                    float h;
-                    split_tf32(v.x, h, v16[4 * p + 0]);
-                    split_tf32(v.y, h, v16[4 * p + 1]);
-                    split_tf32(v.z, h, v16[4 * p + 2]);
-                    split_tf32(v.w, h, v16[4 * p + 3]);
                 }
-                if (three) tmem_st16(ta + cb * 16, v16);
+                tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
+                if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
             }
-            if (three) tmem_wait_st();
-            if (n < kTileSamples) fence_proxy_async_smem();
+            tmem_wait_st();
             tc_fence_before();
         };
 
@@ -755,10 +753,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 if (ct == 0) mbar_arrive(&full[s]);   // end marker for the MMA warp
                 break;
             }
-            // (1) tile i landed in stage s
+            // (1) tile i landed in stage s; TMEM operand slot i&1 free once MMA(i-2), its
+            //     previous reader, is done
             if (ct == 0) {
                 bool ok = true;
                 if (use_tma) ok = wait1(&load_bar[s], ph);
+                if (ok && i >= 2) ok = wait1(&mma_done[i & 1], (uint32_t)(((i - 2) >> 1) & 1));
                 conv_ok[0] = ok ? 1 : 0;
             }
             if (!use_tma) {
@@ -767,15 +767,16 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             }
             named_sync(kNamedConv, kConvThreads);
             if (!conv_ok[0]) break;
-            // (2) A_lo into TMEM; the raw tile in shared memory is A_hi (the tensor cores
-            //     truncate a TF32 operand to its upper 19 bits)
-            if (warp >= 8) lo_to_tmem(d.tlen, s);
+            // (2) the operand into TMEM; the stage is free from here on
+            if (warp >= 8) {
+                tc_fence_after();
+                a_to_tmem(d.tlen, s, (int)(i & 1));
+            }
             named_sync(kNamedConv, kConvThreads);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) tile i+LA: descriptor, tables of a new channel, load into its stage once
-            //     MMA(i-1), the stage's previous user, is done (through the MMA's wait on
-            //     the TMEM buffer the epilogue has also started tile i-3; ring slots are
-            //     reused 8 tiles apart)
+            // (3) tile i+LA: descriptor, tables of a new channel, load into its stage (tile
+            //     i-1's, converted in the previous iteration).  Ring slots are reused 8 tiles
+            //     apart; through the waits above the epilogue has started tile i-4.
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
@@ -785,8 +786,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     const int seq = ch_seq;
                     if (seq >= 2) ok = wait1(&tab_free[nd.tab], (uint32_t)(((seq >> 1) - 1) & 1));
                 }
-                if (ok && nd.ch >= 0 && i + LA >= NST)
-                    ok = wait1(&stage_done[(i + LA) % NST], (uint32_t)(((i + LA - NST) / NST) & 1));
                 ring[(i + LA) & (RING - 1)] = nd;
                 conv_ok[1] = ok ? 1 : 0;
             }
@@ -830,20 +829,18 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 const uint32_t tb = tslot(d.tab);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
-                    const uint32_t ka = (kk >> 2) * kKBlock + (kk & 3) * 32;
                     const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
-                    const uint64_t ahi = sdesc_sw128(sbase + stage_hi(s) + ka);
+                    const uint32_t ahi = tmem + ahi_col(tb_) + 8 * kk;
                     const uint64_t bhi = sdesc_sw128(sbase + tb + PS::T_BHI + kb);
-                    mma_tf32(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_tmem_a(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
                         const uint64_t blo = sdesc_sw128(sbase + tb + PS::T_BLO + kb);
-                        mma_tf32(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(s) + 8 * kk, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, ahi, blo, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(tb_) + 8 * kk, bhi, idesc, 1u);
                     }
                 }
                 mma_commit(&mma_done[tb_]);
                 mbar_arrive(&mma_done[tb_]);   // orders the descriptor reads before the epilogue's
-                mma_commit(&stage_done[s]);    // the stage (shared tile and TMEM A_lo) is free
             }
             issued = true;
             if (bt.stall_drill) {
