@@ -1,7 +1,7 @@
 // Coefficient setup of the chunked algorithm: per channel, the impulse responses, the
 // free-response and end-state blocks, and the chunk transition of the chunk algebra
 // (see chunk.cuh), formed in extended precision and rounded to the operand precision.
-// One launch writes the forward records, the backward records, or both (grid.y).
+// One launch writes the forward records, the backward records, or both.
 //
 // GB300's FP64 pipe is narrow and a warp-wide FP64 instruction costs it the same
 // whether 1 or 32 lanes are active, so both variants keep every lane busy:
@@ -60,9 +60,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     SmallScratch<MB> &sc = scr_all[wib];
     const int64_t ch = (int64_t)blockIdx.x * kSmallWarps + wib;
-    if (counter && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *counter = 0ull;
-    // grid.y selects the record: forward tables, backward tables, or both
-    const bool backward = fwd_tabs == nullptr || blockIdx.y == 1;
+    if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
     if (ch >= bt.B) return;
     const Channel c = channel_of(bt, ch);
     dw av[MB], bp[MB + 1];   // av[k] = a_{k+1}; zero past the channel's orders
@@ -72,7 +70,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
     for (int k = 0; k <= MB; ++k) bp[k] = dw_make(k <= c.N ? b[ch * bt.Nstride + k] : 0.f);
     auto H = [&](int n) -> dw { return n >= 0 ? dw{sc.hhi[n], sc.hlo[n]} : dw_make(0.f); };
     auto G = [&](int n) -> dw { return n >= 0 ? dw{sc.ghi[n], sc.glo[n]} : dw_make(0.f); };
-    // h by the all-pole difference equation (the one serial chain)
+    // h by the all-pole difference equation (the one serial chain; the oldest terms
+    // first, so that only the newest product and difference lie on the chain)
     if (lane == 0) {
         dw wh[MB];
 #pragma unroll
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
         for (int n = 0; n < L + MB; ++n) {
             dw yh = dw_make(n == 0 ? 1.f : 0.f);
 #pragma unroll
-            for (int k = 0; k < MB; ++k) yh = yh - av[k] * wh[k];
+            for (int k = MB - 1; k >= 0; --k) yh = yh - av[k] * wh[k];
 #pragma unroll
             for (int k = MB - 1; k > 0; --k) wh[k] = wh[k - 1];
             wh[0] = yh;
@@ -89,21 +88,52 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
         }
     }
     __syncwarp();
-    const size_t rec = backward ? Tab::bwd_rec(f64) : Tab::fwd_rec(f64);
-    char *R = (backward ? bwd_tabs : fwd_tabs) + (size_t)ch * rec;
-    float *g = reinterpret_cast<float *>(R + (backward ? Tab::B_G : Tab::F_G));
+    char *RF = fwd_tabs ? fwd_tabs + (size_t)ch * Tab::fwd_rec(f64) : nullptr;
+    char *RB = bwd_tabs ? bwd_tabs + (size_t)ch * Tab::bwd_rec(f64) : nullptr;
     for (int n = lane; n < L; n += 32) {
         dw acc = dw_make(0.f);
 #pragma unroll
         for (int k = 0; k <= MB; ++k) acc = acc + bp[k] * H(n - k);
         sc.ghi[n] = acc.hi;
         sc.glo[n] = acc.lo;
-        g[n] = dw_to_float(acc);
+        const float gv = dw_to_float(acc);
+        if (RF) reinterpret_cast<float *>(RF + Tab::F_G)[n] = gv;
+        if (RB) reinterpret_cast<float *>(RB + Tab::B_G)[n] = gv;
     }
     __syncwarp();
-    if (!backward) {
-        float *RL = reinterpret_cast<float *>(R + Tab::F_RL);
-        float *OL = reinterpret_cast<float *>(R + Tab::F_OL);
+    // the scan block of a record from the transition in sc.a[0]
+    auto write_scan = [&](char *S) {
+        if (f64) {
+            double *At = reinterpret_cast<double *>(S);
+            if (lane < MB * MB) {
+                const int j = lane / MB, m = lane % MB;   // At[j][m] = A[m][j]
+                At[lane] = dw_to_double(dw{sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]});
+            }
+        } else {
+            float *P = reinterpret_cast<float *>(S);
+            int cur = 0;
+            for (int kp = 0; kp < Tab::NPOW; ++kp) {
+                if (lane < MB * MB) P[kp * MB * MB + lane] = dw_to_float(dw{sc.ahi[cur][lane], sc.alo[cur][lane]});
+                if (kp + 1 == Tab::NPOW) break;
+                if (lane < MB * MB) {
+                    const int i = lane / MB, j = lane % MB;
+                    dw acc = dw_make(0.f);
+#pragma unroll
+                    for (int k = 0; k < MB; ++k)
+                        acc = acc + dw{sc.ahi[cur][i * MB + k], sc.alo[cur][i * MB + k]} *
+                                        dw{sc.ahi[cur][k * MB + j], sc.alo[cur][k * MB + j]};
+                    sc.ahi[cur ^ 1][lane] = acc.hi;
+                    sc.alo[cur ^ 1][lane] = acc.lo;
+                }
+                __syncwarp();
+                cur ^= 1;
+            }
+        }
+        __syncwarp();
+    };
+    if (RF) {
+        float *RL = reinterpret_cast<float *>(RF + Tab::F_RL);
+        float *OL = reinterpret_cast<float *>(RF + Tab::F_OL);
         for (int idx = lane; idx < L * MB; idx += 32) {
             const int i = idx / MB, m = idx % MB;
             OL[idx] = dw_to_float(H(i - m));
@@ -128,10 +158,13 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
             sc.ahi[0][lane] = acc.hi;
             sc.alo[0][lane] = acc.lo;
         }
-    } else {
-        float *h = reinterpret_cast<float *>(R + Tab::B_H);
-        float *Ou = reinterpret_cast<float *>(R + Tab::B_OU);
-        float *Ogx = reinterpret_cast<float *>(R + Tab::B_OGX);
+        __syncwarp();
+        write_scan(RF + Tab::F_SCAN);
+    }
+    if (RB) {
+        float *h = reinterpret_cast<float *>(RB + Tab::B_H);
+        float *Ou = reinterpret_cast<float *>(RB + Tab::B_OU);
+        float *Ogx = reinterpret_cast<float *>(RB + Tab::B_OGX);
         for (int n = lane; n < L; n += 32) h[n] = dw_to_float(H(n));
         for (int idx = lane; idx < L * MB; idx += 32) {
             const int n = idx / MB, m = idx % MB;
@@ -159,34 +192,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
             sc.ahi[0][lane] = sc.uhi[lane];   // Abar'[k][m] = O^u[k][m], k < MB
             sc.alo[0][lane] = sc.ulo[lane];
         }
-    }
-    __syncwarp();
-    char *S = R + (backward ? Tab::B_SCAN : Tab::F_SCAN);
-    if (f64) {
-        double *At = reinterpret_cast<double *>(S);
-        if (lane < MB * MB) {
-            const int j = lane / MB, m = lane % MB;   // At[j][m] = A[m][j]
-            At[lane] = dw_to_double(dw{sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]});
-        }
-    } else {
-        float *P = reinterpret_cast<float *>(S);
-        int cur = 0;
-        for (int kp = 0; kp < Tab::NPOW; ++kp) {
-            if (lane < MB * MB) P[kp * MB * MB + lane] = dw_to_float(dw{sc.ahi[cur][lane], sc.alo[cur][lane]});
-            if (kp + 1 == Tab::NPOW) break;
-            if (lane < MB * MB) {
-                const int i = lane / MB, j = lane % MB;
-                dw acc = dw_make(0.f);
-#pragma unroll
-                for (int k = 0; k < MB; ++k)
-                    acc = acc + dw{sc.ahi[cur][i * MB + k], sc.alo[cur][i * MB + k]} *
-                                    dw{sc.ahi[cur][k * MB + j], sc.alo[cur][k * MB + j]};
-                sc.ahi[cur ^ 1][lane] = acc.hi;
-                sc.alo[cur ^ 1][lane] = acc.lo;
-            }
-            __syncwarp();
-            cur ^= 1;
-        }
+        __syncwarp();
+        write_scan(RB + Tab::B_SCAN);
     }
 }
 
@@ -343,7 +350,7 @@ cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, c
                                bool fp64_scan, cudaStream_t st) {
     if (!fwd_tabs && !bwd_tabs) return cudaErrorInvalidValue;
     const unsigned gy = (fwd_tabs && bwd_tabs) ? 2u : 1u;
-    const dim3 small_grid((unsigned)((bt.B + kSmallWarps - 1) / kSmallWarps), gy);
+    const dim3 small_grid((unsigned)((bt.B + kSmallWarps - 1) / kSmallWarps), 1);   // both records per warp
     const dim3 large_grid((unsigned)bt.B, gy);
     auto small = [&](auto kern) -> cudaError_t {
         kern<<<small_grid, 32 * kSmallWarps, 0, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan);
