@@ -546,28 +546,30 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // ===========================================================================
 // Warp-specialised backward (state buckets whose layout fits), the forward's
 // pipeline structure run on reversed tiles, with two epilogue warpgroups:
-//   warps 0-2   converters: work (tiles of a channel from last to first), tables (the
+//   warps 0-3   converters: work (tiles of a channel from last to first), tables (the
 //               B operand T_h^a, single-buffered: rebuilt once the channel's last MMA
 //               is done; O^u, scan block, coefficients double-buffered by channel
-//               parity); gy tiles two ahead into three stages (TMA or cp.async; the
-//               raw words are the TF32 hi operand) -> gy_landed[s]; the TF32 operand
-//               (hi and lo) of rows 0-95 into TMEM -> full[s]; the stage is free once
-//               converted; the tile's x is prefetched into L2
-//   warp 3      MMA: the operand of rows 96-127 into TMEM (its TMEM lane quarter), then
-//               D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk; A from TMEM, the
-//               B operand from shared memory) into TMEM accumulator i&3
+//               parity); gy tiles two ahead into three stages (TMA or cp.async); warp w
+//               writes the TF32 operand of rows 32w .. 32w+31 (the raw words as hi,
+//               x - trunc(x) as lo) into TMEM operand slot i&1 -> full[s], after which
+//               the stage is free; the tile's x is prefetched into L2
+//   warp 12     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk; A from
+//               TMEM, the B operand from shared memory) into TMEM accumulator i&3
 //   warps 4-7   epilogue group 0 (even tiles), warps 8-11 group 1 (odd tiles): reverse
 //               chunk scan of S'_c = u[(c+1)L ..] (each group loads its tile's x into its
-//               own buffer first; the state entering from the right
-//               is the other group's carry), u = D + O^u S', then streamed over the
-//               chunk row: y recomputed from the forward's saved chunk state and the
-//               x tile, lag correlations, grad_x = sum_k b_k u[n+k] written over the
-//               x tile and stored from there (TMA for full tiles); lag sums added per
-//               channel in shared FP64, finished by the group that completes the
-//               channel's last tile
+//               own buffer first; the state entering from the right is the other group's
+//               carry), u = D + O^u S', then streamed over the chunk row: y recomputed
+//               from the forward's saved chunk state and the x tile, lag correlations,
+//               grad_x = sum_k b_k u[n+k] written over the x tile and stored from there
+//               (TMA for full tiles); lag sums added per channel in shared FP64, finished
+//               by the group that completes the channel's last tile
 // ===========================================================================
 
-constexpr int kBwThreads = 384;
+// 13 warps: converters 0-3 (one per TMEM lane quarter), epilogue groups 4-7 and 8-11,
+// MMA issuer 12
+constexpr int kBwThreads = 416;
+constexpr int kBwConv = 128;     // converter threads
+constexpr int kBwMmaWarp = 12;
 constexpr int kBwNS = 3;   // gy stages (two tiles of gy loads in flight)
 constexpr int kBwNX = 2;   // x / grad_x buffers (one per epilogue group)
 
@@ -626,7 +628,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
-    uint64_t *full = bars + 0, *gy_landed = bars + 3, *load_bar = bars + 6, *mma_done = bars + 9,
+    uint64_t *full = bars + 0, *load_bar = bars + 6, *mma_done = bars + 9,
              *tmem_free = bars + 13, *x_bar = bars + 17, *tab_free = bars + 19, *carry_bar = bars + 21,
              *dead = bars + 23, *drain = bars + 24;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
@@ -651,7 +653,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < SM::NBAR; ++i) {
             uint32_t cnt = 1;
-            if (i < 3) cnt = 2;                                               // full: converters + MMA warp
             if (i >= 9 && i < 13) cnt = 2;                                    // mma_done: commit + arrive
             if (i >= 17 && i < 19 && !tma_x) cnt = 128;                       // x_bar: a group's cp.async arrivals
             mbar_init(&bars[i], cnt);
@@ -709,7 +710,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         tc_fence_before();
     };
 
-    if (warp < kMmaWarp) {
+    if (warp < 4) {
         // ============================ converters ============================
         const int ct = tid;
         int64_t cur_ch = -1, cur_t = 0, cur_nt = 0, cur_off = 0, cur_len = 0;
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             const char *R = tabs + (size_t)d.ch * rec;
             const float *__restrict__ h = reinterpret_cast<const float *>(R + Tab::B_H);
             // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, half of the rows)
-            for (int item = ct; item < 512; item += kConvThreads) {
+            for (int item = ct; item < 512; item += kBwConv) {
                 const int k = item & 63, r0 = (item >> 6) * 8;   // column k, rows r0 .. r0+7
                 float hv[8];
 #pragma unroll
@@ -780,10 +781,10 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             char *T = smem + sslot(d.tab);
             const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
             float4 *sOu = reinterpret_cast<float4 *>(T + SM::S_OU);
-            for (int idx = ct; idx < kL * MB / 4; idx += kConvThreads) sOu[idx] = __ldg(Ou + idx);
+            for (int idx = ct; idx < kL * MB / 4; idx += kBwConv) sOu[idx] = __ldg(Ou + idx);
             const float4 *src = reinterpret_cast<const float4 *>(R + Tab::B_SCAN);
             float4 *dst = reinterpret_cast<float4 *>(T + SM::S_SCAN);
-            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kConvThreads) dst[idx] = __ldg(src + idx);
+            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kBwConv) dst[idx] = __ldg(src + idx);
             float *coef = reinterpret_cast<float *>(T + SM::S_COEF);   // a[0..MB) | b[0..MB]
             const Channel c = channel_of(bt, d.ch);
             if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     tma_load_3d(sbase + stage_hi(s) + kKBlock, &tmg, 0, 1, row, &load_bar[s]);
                 }
             } else {
-                load_tile_async<kConvThreads>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
+                load_tile_async<kBwConv>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
                                               gy_al && ((d.tstart & 3) == 0), ct);
             }
             if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             ring[0] = d0;
             ring[1] = d1;
         }
-        named_sync(kNamedConv, kConvThreads);
+        named_sync(kNamedConv, kBwConv);
         int64_t issued_upto = -1;   // last tile whose gy load this thread has issued
         {
             const TileDesc d0 = ring[0], d1 = ring[1];
@@ -839,7 +840,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             const uint32_t ph = (uint32_t)((i / kBwNS) & 1);
             const TileDesc d = ring[i & 7];
             if (d.ch < 0) {
-                if (ct == 0) mbar_arrive(&gy_landed[s]);   // end marker for the MMA warp
+                if (ct == 0) mbar_arrive(&full[s]);   // end marker for the MMA warp
                 break;
             }
             // (1) gy tile i landed (tile i+1's copies may still be in flight); operand slot
@@ -854,26 +855,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (issued_upto > i) cp_async_wait_1();
                 else cp_async_wait_all();
             }
-            named_sync(kNamedConv, kConvThreads);
+            named_sync(kNamedConv, kBwConv);
             if (!conv_ok[1]) break;
-            if (ct == 0) mbar_arrive(&gy_landed[s]);   // the MMA warp converts its quarter
-            // (2) operand rows 0-95 into TMEM slot i&1
+            // (2) the operand into TMEM slot i&1 (warp w: rows 32w .. 32w+31)
             tc_fence_after();
             a_to_tmem(warp, d.tlen, s, (int)(i & 1));
-            named_sync(kNamedConv, kConvThreads);
+            named_sync(kNamedConv, kBwConv);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) tile i+2's descriptor; stage (i+2)%3 is free once both converter sets have
-            //     read tile i-1 out of it (full[(i-1)%3]; ring slots are reused 8 apart, far
-            //     behind every reader).  If tile i+1 starts a channel, its small tables wait
-            //     for their slot and its B operand for MMA(i), the last reader of the single
-            //     B slot.
+            // (3) tile i+2's descriptor; its stage (i+2)%3 held tile i-1, converted in the
+            //     previous iteration (ring slots are reused 8 apart, far behind every
+            //     reader).  If tile i+1 starts a channel, its small tables wait for their
+            //     slot and its B operand for MMA(i), the last reader of the single B slot.
             const TileDesc dn1 = ring[(i + 1) & 7];
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
-                if (i >= 1) ok = wait1(&full[(i - 1) % kBwNS], (uint32_t)(((i - 1) / kBwNS) & 1));
-                if (ok && dn1.ch >= 0 && dn1.first) {
+                if (dn1.ch >= 0 && dn1.first) {
                     if (dn1.seq >= 2) ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
                     if (ok) ok = wait1(&mma_done[i & 3], (uint32_t)((i >> 2) & 1));
                 }
@@ -881,7 +879,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (nd.ch < 0) ring[(i + 3) & 7] = nd;   // the other group's end marker
                 conv_ok[2] = ok ? 1 : 0;
             }
-            named_sync(kNamedConv, kConvThreads);
+            named_sync(kNamedConv, kBwConv);
             if (!conv_ok[2]) break;
             if (dn1.ch >= 0 && dn1.first) build_tables(dn1);
             const TileDesc dn2 = ring[(i + 2) & 7];
@@ -890,7 +888,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 issued_upto = i + 2;
             }
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == kBwMmaWarp) {
         // ============================ MMA issuer ============================
         bool issued = false;
         for (int64_t i = 0;; ++i) {
@@ -898,7 +896,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             const uint32_t ph = (uint32_t)((i / kBwNS) & 1);
             const int pl = (int)(i & 1);                      // A_lo slot
             int ok = 1;
-            if (lane == 0) ok = wait1(&gy_landed[s], ph) ? 1 : 0;
+            if (lane == 0) ok = wait1(&full[s], ph) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             const TileDesc d = ring[i & 7];
@@ -925,20 +923,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
                 break;
             }
-            // operand rows 96-127 (this warp's TMEM lane quarter) once MMA(i-2), the slot's
-            // previous reader, is done (this warp's own commit)
-            if (lane == 0 && i >= 2) ok = wait1(&mma_done[(i - 2) & 3], (uint32_t)(((i - 2) >> 2) & 1)) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
-            a_to_tmem(3, d.tlen, s, pl);
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&full[s]);
-                ok = wait1(&full[s], ph) ? 1 : 0;
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
             if (lane == 0) {
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(tb * 64);
