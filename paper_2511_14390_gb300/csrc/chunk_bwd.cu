@@ -587,7 +587,8 @@ struct BwSmem {
     static constexpr uint32_t S_OU = 0;
     static constexpr uint32_t S_SCAN = kL * MB * 4;
     static constexpr uint32_t S_COEF = (S_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
-    static constexpr uint32_t SSLOT = (S_COEF + (2 * MB + 1) * 4 + 15) / 16 * 16;
+    static constexpr uint32_t S_H = (S_COEF + (2 * MB + 1) * 4 + 15) / 16 * 16;   // h, staged
+    static constexpr uint32_t SSLOT = S_H + kL * 4;
     // FP64 reverse scan scratch per group (E' and S' per chunk)
     static constexpr uint32_t SCR = SMALL0 + 2 * SSLOT;
     static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 : 0;
@@ -758,15 +759,19 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         // B operand (single slot) and the channel-parity slot of the small tables
         auto build_tables = [&](const TileDesc &d) {
             const char *R = tabs + (size_t)d.ch * rec;
-            const float *__restrict__ h = reinterpret_cast<const float *>(R + Tab::B_H);
-            // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, half of the rows)
+            char *T = smem + sslot(d.tab);
+            // h into shared memory once (coalesced), then the Toeplitz block from there
+            float *hs = reinterpret_cast<float *>(T + SM::S_H);
+            if (ct < kL) hs[ct] = __ldg(reinterpret_cast<const float *>(R + Tab::B_H) + ct);
+            named_sync(kNamedConv, kBwConv);
+            // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, 8 of the rows)
             for (int item = ct; item < 512; item += kBwConv) {
                 const int k = item & 63, r0 = (item >> 6) * 8;   // column k, rows r0 .. r0+7
                 float hv[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int r = r0 + q;
-                    hv[q] = k >= r ? __ldg(h + (k - r)) : 0.f;
+                    hv[q] = k >= r ? hs[k - r] : 0.f;
                 }
                 const uint32_t kb = (k >> 5) * (NM * 128);
 #pragma unroll
@@ -778,7 +783,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     *reinterpret_cast<float *>(smem + SM::T_BLO + o) = lo;
                 }
             }
-            char *T = smem + sslot(d.tab);
             const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
             float4 *sOu = reinterpret_cast<float4 *>(T + SM::S_OU);
             for (int idx = ct; idx < kL * MB / 4; idx += kBwConv) sOu[idx] = __ldg(Ou + idx);
