@@ -170,7 +170,10 @@ def kernel_name(direction, M):
     mb = next(v for v in (2, 4, 8, 16, 32, 64) if M <= v)
     f64 = 1 if M > 4 else 0
     if direction == "forward":
-        return f"chunk_fwd_ws_kernel<{mb}, {f64}>"
+        if mb >= 32:
+            return f"chunk_fwd_kernel<{mb}, {f64}>"
+        stages = 2 if (mb == 16 and not f64) else 3   # signal stages that fit shared memory
+        return f"chunk_fwd_ws_kernel<{mb}, {f64}, {stages}>"
     return f"chunk_bwd_ws_kernel<{mb}, {f64}>" if mb <= 8 else f"chunk_bwd_kernel<{mb}, {f64}, 0>"
 
 
