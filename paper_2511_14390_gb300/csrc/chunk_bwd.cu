@@ -547,9 +547,9 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // Warp-specialised backward (state buckets whose layout fits), the forward's
 // pipeline structure run on reversed tiles, with two epilogue warpgroups:
 //   warps 0-3   converters: work (tiles of a channel from last to first), tables (the
-//               B operand T_h^a, single-buffered: rebuilt once the channel's last MMA
-//               is done; O^u, scan block, coefficients double-buffered by channel
-//               parity); gy tiles two ahead into three stages (TMA or cp.async); warp w
+//               B operand T_h^a, O^u, scan block, coefficients; double-buffered by
+//               channel parity); gy tiles two ahead into two stages (TMA or cp.async;
+//               a stage is free once converted); warp w
 //               writes the TF32 operand of rows 32w .. 32w+31 (the raw words as hi,
 //               x - trunc(x) as lo) into TMEM operand slot i&1 -> full[s], after which
 //               the stage is free; the tile's x is prefetched into L2
@@ -570,7 +570,7 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 constexpr int kBwThreads = 416;
 constexpr int kBwConv = 128;     // converter threads
 constexpr int kBwMmaWarp = 12;
-constexpr int kBwNS = 3;   // gy stages (two tiles of gy loads in flight)
+constexpr int kBwNS = 2;   // gy stages (a stage is free once converted; loads run two ahead)
 constexpr int kBwNX = 2;   // x / grad_x buffers (one per epilogue group)
 
 template <int MB, bool F64>
@@ -580,10 +580,11 @@ struct BwSmem {
     static constexpr int NACC = 2 * MB + 1;
     static constexpr uint32_t GS0 = 0;                               // gy stages (hi)
     static constexpr uint32_t XB0 = kBwNS * pipe::kTileBytes;        // x / grad_x buffers
-    static constexpr uint32_t TB = XB0 + kBwNX * pipe::kTileBytes;   // B operand hi | lo
-    static constexpr uint32_t T_BHI = TB;
-    static constexpr uint32_t T_BLO = TB + NM * 256;
-    static constexpr uint32_t SMALL0 = TB + 2 * NM * 256;            // 2 slots: O^u | scan | coef
+    static constexpr uint32_t TB = XB0 + kBwNX * pipe::kTileBytes;   // 2 slots: B operand hi | lo
+    static constexpr uint32_t T_BHI = 0;                             // within a B slot
+    static constexpr uint32_t T_BLO = NM * 256;
+    static constexpr uint32_t BSLOT = 2 * NM * 256;
+    static constexpr uint32_t SMALL0 = TB + 2 * BSLOT;               // 2 slots: O^u | scan | coef | h
     static constexpr uint32_t S_OU = 0;
     static constexpr uint32_t S_SCAN = kL * MB * 4;
     static constexpr uint32_t S_COEF = (S_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
@@ -779,8 +780,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     float hi, lo;
                     split_tf32(hv[q], hi, lo);
                     const uint32_t o = kb + sw128_off(r0 + q, k & 31);
-                    *reinterpret_cast<float *>(smem + SM::T_BHI + o) = hi;
-                    *reinterpret_cast<float *>(smem + SM::T_BLO + o) = lo;
+                    *reinterpret_cast<float *>(smem + SM::TB + d.tab * SM::BSLOT + SM::T_BHI + o) = hi;
+                    *reinterpret_cast<float *>(smem + SM::TB + d.tab * SM::BSLOT + SM::T_BLO + o) = lo;
                 }
             }
             const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
@@ -866,19 +867,16 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             a_to_tmem(warp, d.tlen, s, (int)(i & 1));
             named_sync(kNamedConv, kBwConv);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) tile i+2's descriptor; its stage (i+2)%3 held tile i-1, converted in the
-            //     previous iteration (ring slots are reused 8 apart, far behind every
-            //     reader).  If tile i+1 starts a channel, its small tables wait for their
-            //     slot and its B operand for MMA(i), the last reader of the single B slot.
+            // (3) tile i+2's descriptor; its stage held tile i, converted above (ring slots
+            //     are reused 8 apart, far behind every reader).  If tile i+1 starts a
+            //     channel, its table slot waits for the channel two back to be finished.
             const TileDesc dn1 = ring[(i + 1) & 7];
             if (ct == 0) {
                 TileDesc nd;
                 next_desc(nd);
                 bool ok = true;
-                if (dn1.ch >= 0 && dn1.first) {
-                    if (dn1.seq >= 2) ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
-                    if (ok) ok = wait1(&mma_done[i & 3], (uint32_t)((i >> 2) & 1));
-                }
+                if (dn1.ch >= 0 && dn1.first && dn1.seq >= 2)
+                    ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
                 ring[(i + 2) & 7] = nd;
                 if (nd.ch < 0) ring[(i + 3) & 7] = nd;   // the other group's end marker
                 conv_ok[2] = ok ? 1 : 0;
@@ -934,10 +932,10 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 for (int kk = 0; kk < kL / 8; ++kk) {
                     const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
                     const uint32_t ahi = tmem + ahi_col(pl) + 8 * kk;
-                    const uint64_t bhi = sdesc_sw128(sbase + SM::T_BHI + kb);
+                    const uint64_t bhi = sdesc_sw128(sbase + SM::TB + d.tab * SM::BSLOT + SM::T_BHI + kb);
                     mma_tf32_tmem_a(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
                     if (three) {
-                        const uint64_t blo = sdesc_sw128(sbase + SM::T_BLO + kb);
+                        const uint64_t blo = sdesc_sw128(sbase + SM::TB + d.tab * SM::BSLOT + SM::T_BLO + kb);
                         mma_tf32_tmem_a(d_tmem, ahi, blo, idesc, 1u);
                         mma_tf32_tmem_a(d_tmem, tmem + alo_col(pl) + 8 * kk, bhi, idesc, 1u);
                     }
