@@ -43,6 +43,8 @@ def args_():
     p.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel leg")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--graph", action="store_true",
+                   help="also time the step captured in a CUDA graph (launch-bound workloads)")
     p.add_argument("--channels", type=int, default=0,
                    help="override the workload's channel count (smaller profiling cases)")
     return p.parse_args()
@@ -229,6 +231,8 @@ def main():
     w = inputs.make(a.workload, **({"B": a.channels} if a.channels > 0 else {}))
     B, T = w.x.shape
     N, M = w.N, w.M
+    if w.zi is None:   # zero initial conditions, passed explicitly so grad_zi has a buffer
+        w.zi = np.zeros((B, M), dtype=np.float32)
     dev = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).cuda()
     x, b, av, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
     L = dfilt.lib()
@@ -247,17 +251,17 @@ def main():
 
     P = dfilt._ptr
 
-    def fwd(st):
+    def fwd(st, sp=None):
         dfilt._check(L.dfilt_forward(P(x), P(b), P(av), P(zi), P(st["y"]), P(st["saved"]),
                                      P(st["wf"]), st["fws"], B, T, N, M, ctypes.byref(st["o"]),
-                                     sptr), "dfilt_forward")
+                                     sp or sptr), "dfilt_forward")
 
-    def bwd(st):
+    def bwd(st, sp=None):
         yarg = None if st["saved"] is not None else st["y"]
         dfilt._check(L.dfilt_backward(P(gy), P(x), P(yarg), P(b), P(av), P(zi), P(st["saved"]),
                                       P(st["gx"]), P(st["gb"]), P(st["ga"]), P(st["gz"]),
                                       P(st["wb"]), st["bws"], B, T, N, M, ctypes.byref(st["o"]),
-                                      sptr), "dfilt_backward")
+                                      sp or sptr), "dfilt_backward")
 
     def barrier():
         if world > 1:
@@ -308,6 +312,37 @@ def main():
     clocks = clk.stop()
     ms = maxrank(ms)
     samples_all = B * T * world
+
+    # the same step captured once in a CUDA graph and replayed (removes launch gaps)
+    graph = None
+    if a.graph:
+        gs = torch.cuda.Stream()
+        gptr = ctypes.c_void_p(gs.cuda_stream)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            for _ in range(3):
+                fwd(st, gptr)
+                bwd(st, gptr)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=gs):
+            fwd(st, gptr)
+            bwd(st, gptr)
+        for _ in range(a.warmup):
+            cg.replay()
+        torch.cuda.synchronize()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(a.steps):
+            cg.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        gms = maxrank(g0.elapsed_time(g1) / a.steps)
+        graph = {"value": samples_all / (gms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": gms,
+                 "steps": a.steps}
+        del cg
     value = samples_all / (ms / 1e3) / 1e9
     status = dfilt.dfilt_sync_status()
     if status != 0:
@@ -409,7 +444,7 @@ def main():
                                    f"its {kfn if dom == 'forward' else kbn} launches)",
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
                          else "fallback (6.8 TB/s)"},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "graph_replay": graph,
             # per step: forward = setup + main kernel, backward = main kernel (its work
             # counter is cleared by a memset)
             "gpu_launches": 3 * a.steps if algo == "chunked" else 2 * a.steps,

@@ -47,7 +47,7 @@ bool dev_info(DevInfo *out) {
 struct Resolved {
     int algo;
     int precision;
-    bool fp64_scan;
+    int fp64_opt;   // chunk-state scan option: -1 automatic per state bucket, 0 FP32, 1 FP64
 };
 
 dfilt_status resolve(const dfilt_opts *o, int Mmax, Resolved *r) {
@@ -66,7 +66,7 @@ dfilt_status resolve(const dfilt_opts *o, int Mmax, Resolved *r) {
                o->precision != DFILT_PREC_TF32X3) {
         return DFILT_ERR_INVALID_ARG;
     }
-    r->fp64_scan = chunk_layout(Mmax, o->fp64_scan).fp64_scan;
+    r->fp64_opt = o->fp64_scan;
     return DFILT_OK;
 }
 
@@ -84,13 +84,13 @@ dfilt_status cuda_status(cudaError_t e) {
     return DFILT_ERR_CUDA;
 }
 
-void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, size_t *fwd, size_t *saved,
-           size_t *bwd) {
+void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, bool ragged, size_t *fwd,
+           size_t *saved, size_t *bwd) {
     size_t f = 0, s = 0, w = 0;
     if (r.algo == DFILT_ALGO_CHUNKED) {
-        f = chunk_fwd_ws_bytes(B, Mmax, r.fp64_scan);
-        s = chunk_saved_bytes(B, total, Mmax, r.fp64_scan);
-        w = chunk_bwd_ws_bytes(B, Mmax, r.fp64_scan);
+        f = chunk_fwd_ws_bytes(B, Mmax, r.fp64_opt, ragged);
+        s = chunk_saved_bytes(B, total, Mmax, r.fp64_opt, ragged);
+        w = chunk_bwd_ws_bytes(B, Mmax, r.fp64_opt, ragged);
     }
     if (fwd) *fwd = f;
     if (saved) *saved = s;
@@ -111,6 +111,10 @@ Batch make_batch(const DevInfo &di, const int64_t *offsets, const int *Ms, const
     bt.Mstride = Mmax;
     bt.Nstride = Nmax + 1;
     bt.status = di.status;
+    bt.list = nullptr;
+    bt.list_range = nullptr;
+    bt.fwd_stride = 0;
+    bt.bwd_stride = 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         bt.wait_limit = g_wait_limit;
@@ -129,11 +133,12 @@ dfilt_status do_forward(const float *x, const float *b, const float *a, const fl
         timing_mark(0, 1, st);
         return cuda_status(e);
     }
-    size_t need = chunk_fwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
+    const bool ragged = bt.offsets != nullptr;
+    size_t need = chunk_fwd_ws_bytes(bt.B, Mmax, r.fp64_opt, ragged);
     if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
     return cuda_status(launch_chunk_fwd(x, b, a, zi, y, static_cast<float *>(saved), ws, bt, Mmax,
-                                        r.fp64_scan, r.precision, di.num_sms, st));
+                                        r.fp64_opt, r.precision, di.num_sms, st));
 }
 
 dfilt_status do_backward(const float *gy, const float *x, const float *y, const float *b,
@@ -149,11 +154,12 @@ dfilt_status do_backward(const float *gy, const float *x, const float *y, const 
         return cuda_status(e);
     }
     if (!y && !saved) return DFILT_ERR_INVALID_ARG;
-    size_t need = chunk_bwd_ws_bytes(bt.B, Mmax, r.fp64_scan);
+    const bool ragged = bt.offsets != nullptr;
+    size_t need = chunk_bwd_ws_bytes(bt.B, Mmax, r.fp64_opt, ragged);
     if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
     return cuda_status(launch_chunk_bwd(gy, x, y, b, a, static_cast<const float *>(saved), gx, gb,
-                                        ga, gzi, ws, bt, Mmax, r.fp64_scan, r.precision,
+                                        ga, gzi, ws, bt, Mmax, r.fp64_opt, r.precision,
                                         di.num_sms, st));
 }
 
@@ -258,7 +264,7 @@ dfilt_status dfilt_workspace_size(int64_t B, int64_t T, int N, int M, const dfil
     if (s) return s;
     Resolved r;
     if ((s = resolve(opts, M, &r))) return s;
-    sizes(r, B, B * T, M, fwd_ws, saved, bwd_ws);
+    sizes(r, B, B * T, M, false, fwd_ws, saved, bwd_ws);
     return DFILT_OK;
 }
 
@@ -270,7 +276,7 @@ dfilt_status dfilt_workspace_size_ragged(int64_t B, int64_t total, int Nmax, int
     if (s) return s;
     Resolved r;
     if ((s = resolve(opts, Mmax, &r))) return s;
-    sizes(r, B, total, Mmax, fwd_ws, saved, bwd_ws);
+    sizes(r, B, total, Mmax, true, fwd_ws, saved, bwd_ws);
     return DFILT_OK;
 }
 

@@ -191,15 +191,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
     bool alive = true;
-    const size_t rec = Tab::bwd_rec(F64);
+    const size_t rec = bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
     const bool gy_al = al_mask & 1, x_al = al_mask & 2, y_al = al_mask & 4, gx_al = al_mask & 8;
 
     while (alive) {
-        if (tid == 0) *ch_slot = (int64_t)atomicAdd(counter, 1ull);
+        if (tid == 0) {
+            int64_t cw = -1;
+            if (!work_channel(bt, (int64_t)atomicAdd(counter, 1ull), &cw)) cw = -1;
+            *ch_slot = cw;
+        }
         __syncthreads();
         const int64_t ch = *ch_slot;
-        if (ch >= bt.B) break;
+        if (ch < 0) break;
         const Channel c = channel_of(bt, ch);
         const char *R = tabs + (size_t)ch * rec;
         {
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const size_t rec = Tab::bwd_rec(F64);
+    const size_t rec = bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
     auto stage_hi = [&](int s) { return (uint32_t)(SM::GS0 + s * kTileBytes); };
     auto xbuf = [&](int j) { return (uint32_t)(SM::XB0 + j * kTileBytes); };
@@ -720,8 +724,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         // thread 0: describe the next tile into `d` (published to the ring by the caller)
         auto next_desc = [&](TileDesc &d) {
             while (cur_ch < 0 || cur_t >= cur_nt) {
-                const int64_t c = (int64_t)atomicAdd(counter, 1ull);
-                if (c >= bt.B) {
+                int64_t c;
+                if (!work_channel(bt, (int64_t)atomicAdd(counter, 1ull), &c)) {
                     d.ch = -1;
                     return;
                 }
@@ -877,8 +881,10 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 bool ok = true;
                 if (dn1.ch >= 0 && dn1.first && dn1.seq >= 2)
                     ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
+                // (an end marker at index E is followed by one at E+1, the other group's
+                // end: the next iteration describes E+1 only after waiting MMA(E-3), so
+                // that group has read the slot's previous tile E-7 by then)
                 ring[(i + 2) & 7] = nd;
-                if (nd.ch < 0) ring[(i + 3) & 7] = nd;   // the other group's end marker
                 conv_ok[2] = ok ? 1 : 0;
             }
             named_sync(kNamedConv, kBwConv);

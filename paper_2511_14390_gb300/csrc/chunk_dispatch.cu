@@ -9,8 +9,8 @@ namespace dfilt {
 
 #define DFILT_EXTERN(V)                                                                          \
     extern template cudaError_t chunk_fwd_mb<V>(const float *, const float *, float *, float *, \
-                                                const char *, const Batch &, bool, int, int,    \
-                                                cudaStream_t);                                   \
+                                                const char *, unsigned long long *, const Batch &, \
+                                                bool, int, int, cudaStream_t);                   \
     extern template cudaError_t chunk_bwd_mb<V>(                                                 \
         const float *, const float *, const float *, const float *, const float *,              \
         const float *, float *, float *, float *, float *, const char *, unsigned long long *,  \
@@ -74,40 +74,127 @@ ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt) {
     return l;
 }
 
-size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan) {
-    return kWsHeader + (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).fwd_tab;
+// Per-bucket plan: a fixed-shape batch is one bucket; a ragged batch runs every state
+// bucket up to its largest order as its own launch pair (setup + main kernel) over the
+// channels of that bucket, with records at a common stride.
+ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged) {
+    ChunkPlan p{};
+    p.ragged = ragged;
+    if (!ragged) {
+        p.nb = 1;
+        p.lay[0] = chunk_layout(Mmax, fp64_opt);
+    } else {
+        const int top = chunk_bucket(Mmax);
+        p.nb = 0;
+        for (int mb : {2, 4, 8, 16, 32, 64})
+            if (mb <= top) p.lay[p.nb++] = chunk_layout(mb, fp64_opt);
+    }
+    for (int j = 0; j < p.nb; ++j) {
+        p.fstride = p.lay[j].fwd_tab > p.fstride ? p.lay[j].fwd_tab : p.fstride;
+        p.bstride = p.lay[j].bwd_tab > p.bstride ? p.lay[j].bwd_tab : p.bstride;
+    }
+    return p;
 }
 
-size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan) {
-    return kWsHeader + (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).bwd_tab;
+// channel list of a ragged batch: B bucket-sorted channel indices, then nb+1 bucket starts
+static size_t list_bytes(int64_t B, bool ragged) {
+    return ragged ? ((size_t)(B + 16) * sizeof(int) + 255) / 256 * 256 : 0;
 }
 
-size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, bool fp64_scan) {
-    return chunk_saved_state_bytes(B, total, Mmax) +
-           (size_t)B * chunk_layout(Mmax, fp64_scan ? 1 : 0).bwd_tab;
+size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged) {
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    return kWsHeader + (size_t)B * p.fstride + list_bytes(B, ragged);
 }
+
+size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged) {
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    return kWsHeader + (size_t)B * p.bstride + list_bytes(B, ragged);
+}
+
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged) {
+    return chunk_saved_state_bytes(B, total, Mmax) + (size_t)B * chunk_plan(Mmax, fp64_opt, ragged).bstride;
+}
+
+namespace {
+
+// Sort the channels of a ragged batch by state bucket (one block; order within a bucket
+// is arbitrary, which no result depends on): list[starts[j] .. starts[j+1]) are the
+// channels of bucket j (orders up to 2 << j; the last bucket takes the rest).
+__global__ void __launch_bounds__(1024) bucket_channels_kernel(const int *__restrict__ Ms, int64_t B,
+                                                               int Mstride, int nb,
+                                                               int *__restrict__ list,
+                                                               int *__restrict__ starts) {
+    __shared__ int cnt[8], pos[8];
+    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [&](int64_t i) {
+        int m = Ms[i];
+        m = m < 1 ? 1 : (m > Mstride ? Mstride : m);
+        int j = 0;
+        while (j < nb - 1 && m > (2 << j)) ++j;
+        return j;
+    };
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int j = 0; j <= nb; ++j) {
+            starts[j] = acc;
+            if (j < nb) {
+                pos[j] = acc;
+                acc += cnt[j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) list[atomicAdd(&pos[bucket(i)], 1)] = (int)i;
+}
+
+}  // namespace
 
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
-                             bool fp64_scan, int precision, int num_sms, cudaStream_t st) {
-    const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
-    // with a saved buffer, the same launch also writes the backward's tables into it
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st) {
+    const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
     char *w = static_cast<char *>(ws);
+    auto *counters = reinterpret_cast<unsigned long long *>(w);   // one per bucket
+    // with a saved buffer, the same setup launch also writes the backward's tables into it
     char *btabs = saved ? reinterpret_cast<char *>(saved) + chunk_saved_state_bytes(bt.B, bt.total, Mmax)
                         : nullptr;
-    cudaError_t e = launch_chunk_setup(b, a, w + kWsHeader, btabs,
-                                       reinterpret_cast<unsigned long long *>(w), bt, l.MB,
-                                       l.fp64_scan, st);
-    if (e != cudaSuccess) return e;
+    Batch bb[8];
+    int *list = reinterpret_cast<int *>(w + kWsHeader + (size_t)bt.B * p.fstride);
+    if (ragged) {
+        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, list, list + bt.B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int j = 0; j < p.nb; ++j) {
+        bb[j] = bt;
+        if (ragged) {
+            bb[j].list = list;
+            bb[j].list_range = list + bt.B + j;
+            bb[j].fwd_stride = (int64_t)p.fstride;
+            bb[j].bwd_stride = (int64_t)p.bstride;
+        }
+        const cudaError_t e = launch_chunk_setup(b, a, w + kWsHeader, btabs, counters + j, bb[j],
+                                                 p.lay[j].MB, p.lay[j].fp64_scan, st);
+        if (e != cudaSuccess) return e;
+    }
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
+    cudaError_t e = cudaSuccess;
     timing_mark(0, 0, st);
-    switch (l.MB) {
-#define X(V)                                                                        \
-    case V: e = chunk_fwd_mb<V>(x, zi, y, saved, w, bt, l.fp64_scan, three, num_sms, st); \
+    for (int j = 0; j < p.nb && e == cudaSuccess; ++j) {
+        switch (p.lay[j].MB) {
+#define X(V)                                                                                   \
+    case V:                                                                                    \
+        e = chunk_fwd_mb<V>(x, zi, y, saved, w + kWsHeader, counters + j, bb[j],               \
+                            p.lay[j].fp64_scan, three, num_sms, st);                           \
         break;
-        DFILT_CHUNK_BUCKETS(X)
+            DFILT_CHUNK_BUCKETS(X)
 #undef X
-        default: e = cudaErrorInvalidValue;
+            default: e = cudaErrorInvalidValue;
+        }
     }
     timing_mark(0, 1, st);
     return e;
@@ -115,35 +202,55 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
 
 cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
                              const float *a, const float *saved, float *gx, float *gb, float *ga,
-                             float *gzi, void *ws, const Batch &bt, int Mmax, bool fp64_scan,
+                             float *gzi, void *ws, const Batch &bt, int Mmax, int fp64_opt,
                              int precision, int num_sms, cudaStream_t st) {
-    const ChunkLayout l = chunk_layout(Mmax, fp64_scan ? 1 : 0);
+    const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
     const bool read_y = saved == nullptr;   // y is recomputed whenever the chunk states exist
-    if (read_y && (!y || l.MB > 32)) return cudaErrorNotSupported;
+    if (read_y && (!y || chunk_bucket(Mmax) > 32)) return cudaErrorNotSupported;
     char *wsc = static_cast<char *>(ws);
-    auto *counter = reinterpret_cast<unsigned long long *>(wsc);
-    const char *w;
-    cudaError_t e;
-    if (saved) {
-        // the forward's setup left the backward tables behind the chunk states
-        w = reinterpret_cast<const char *>(saved) + chunk_saved_state_bytes(bt.B, bt.total, Mmax);
-        e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-    } else {
-        w = wsc + kWsHeader;
-        e = launch_chunk_setup(b, a, nullptr, wsc + kWsHeader, counter, bt, l.MB, l.fp64_scan, st);
+    auto *counters = reinterpret_cast<unsigned long long *>(wsc);   // one per bucket
+    // the forward's setup left the backward tables behind the chunk states
+    const char *tabs = saved ? reinterpret_cast<const char *>(saved) +
+                                   chunk_saved_state_bytes(bt.B, bt.total, Mmax)
+                             : wsc + kWsHeader;
+    Batch bb[8];
+    int *list = reinterpret_cast<int *>(wsc + kWsHeader + (size_t)bt.B * p.bstride);
+    cudaError_t e = cudaSuccess;
+    if (ragged) {
+        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, list, list + bt.B);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
+    if (saved) e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * p.nb, st);
     if (e != cudaSuccess) return e;
+    for (int j = 0; j < p.nb; ++j) {
+        bb[j] = bt;
+        if (ragged) {
+            bb[j].list = list;
+            bb[j].list_range = list + bt.B + j;
+            bb[j].fwd_stride = (int64_t)p.fstride;
+            bb[j].bwd_stride = (int64_t)p.bstride;
+        }
+        if (!saved) {
+            e = launch_chunk_setup(b, a, nullptr, wsc + kWsHeader, counters + j, bb[j], p.lay[j].MB,
+                                   p.lay[j].fp64_scan, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
     timing_mark(1, 0, st);
-    switch (l.MB) {
+    for (int j = 0; j < p.nb && e == cudaSuccess; ++j) {
+        switch (p.lay[j].MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
-        e = chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, w, counter, bt,            \
-                            l.fp64_scan, read_y, three, num_sms, st);                          \
+        e = chunk_bwd_mb<V>(gy, x, y, b, a, saved, gx, gb, ga, gzi, tabs, counters + j, bb[j], \
+                            p.lay[j].fp64_scan, read_y, three, num_sms, st);                   \
         break;
-        DFILT_CHUNK_BUCKETS(X)
+            DFILT_CHUNK_BUCKETS(X)
 #undef X
-        default: e = cudaErrorInvalidValue;
+            default: e = cudaErrorInvalidValue;
+        }
     }
     timing_mark(1, 1, st);
     return e;

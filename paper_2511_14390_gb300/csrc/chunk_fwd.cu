@@ -130,7 +130,7 @@ __device__ __forceinline__ void matvec_f32(const float *P, const float (&v)[MB],
 template <int MB, bool F64>
 __global__ void __launch_bounds__(kThreads, 1)
     chunk_fwd_kernel(const float *__restrict__ x, const float *__restrict__ zi,
-                     float *__restrict__ y, float *__restrict__ saved, const char *__restrict__ ws,
+                     float *__restrict__ y, float *__restrict__ saved, const char *__restrict__ tabs,
                      unsigned long long *__restrict__ counter, Batch bt, int three, int x_al,
                      int y_al) {
     using Tab = ChunkTab<MB>;
@@ -166,16 +166,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
     bool alive = true;
-    const size_t rec = Tab::fwd_rec(F64);
+    const size_t rec = bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
 
     while (alive) {
-        if (tid == 0) *ch_slot = (int64_t)atomicAdd(counter, 1ull);
+        if (tid == 0) {
+            int64_t cw = -1;
+            if (!work_channel(bt, (int64_t)atomicAdd(counter, 1ull), &cw)) cw = -1;
+            *ch_slot = cw;
+        }
         __syncthreads();
         const int64_t ch = *ch_slot;
-        if (ch >= bt.B) break;
+        if (ch < 0) break;
         const Channel c = channel_of(bt, ch);
-        const char *R = ws + kWsHeader + (size_t)ch * rec;
+        const char *R = tabs + (size_t)ch * rec;
         // ---- per-channel operand tables ----
         {
             const float *g = reinterpret_cast<const float *>(R + Tab::F_G);
@@ -402,7 +406,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int MB, bool F64>
-cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved, const char *ws,
+cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved, const char *tabs,
+                         unsigned long long *counter,
                          const Batch &bt, int three, int num_sms, cudaStream_t st) {
     using SM = FwdSmem<MB, F64>;
     auto kern = chunk_fwd_kernel<MB, F64>;
@@ -432,8 +437,7 @@ cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved
     const int64_t grid = bt.B < slots ? bt.B : slots;
     const int x_al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
     const int y_al = (reinterpret_cast<uintptr_t>(y) & 15) == 0;
-    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
-    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(x, zi, y, saved, ws, counter, bt, three, x_al, y_al);
+    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(x, zi, y, saved, tabs, counter, bt, three, x_al, y_al);
     return cudaGetLastError();
 }
 
@@ -533,7 +537,7 @@ template <int MB, bool F64, int NST>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     chunk_fwd_ws_kernel(const float *__restrict__ x, const float *__restrict__ zi,
                         float *__restrict__ y, float *__restrict__ saved,
-                        const char *__restrict__ ws, unsigned long long *__restrict__ counter,
+                        const char *__restrict__ tabs, unsigned long long *__restrict__ counter,
                         Batch bt, int three, int x_al, int y_al, int use_tma,
                         const __grid_constant__ CUtensorMap tmx,
                         const __grid_constant__ CUtensorMap tmy) {
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const size_t rec = Tab::fwd_rec(F64);
+    const size_t rec = bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(F64);
     constexpr uint32_t idesc = idesc_tf32_m128(NM);
     auto stage_hi = [&](int s) { return (uint32_t)(PS::XS0 + s * kTileBytes); };
     auto tslot = [&](int p) { return (uint32_t)(PS::TAB0 + p * PS::TSLOT); };
@@ -602,8 +606,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         // thread 0: describe the next tile into `d` (published to the ring by the caller)
         auto next_desc = [&](TileDesc &d) {
             while (cur_ch < 0 || cur_t >= cur_nt) {
-                const int64_t c = (int64_t)atomicAdd(counter, 1ull);
-                if (c >= bt.B) {
+                int64_t c;
+                if (!work_channel(bt, (int64_t)atomicAdd(counter, 1ull), &c)) {
                     d.ch = -1;
                     return;
                 }
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         // all converters: per-channel tables into slot d.tab (column-parallel expansion
         // of the Toeplitz block: thread handles column k, half h of the rows)
         auto build_tables = [&](const TileDesc &d) {
-            const char *R = ws + kWsHeader + (size_t)d.ch * rec;
+            const char *R = tabs + (size_t)d.ch * rec;
             const float *__restrict__ g = reinterpret_cast<const float *>(R + Tab::F_G);
             const float *__restrict__ RL = reinterpret_cast<const float *>(R + Tab::F_RL);
             char *T = smem + tslot(d.tab);
@@ -1062,7 +1066,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 }
 
 template <int MB, bool F64>
-cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *saved, const char *ws,
+cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *saved, const char *tabs,
+                          unsigned long long *counter,
                           const Batch &bt, int three, int num_sms, cudaStream_t st) {
     constexpr int NST = fwd_stages<MB, F64>();
     using SM = WsSmem<MB, F64, NST>;
@@ -1088,8 +1093,7 @@ cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *save
     if (!bt.offsets && bt.T % kL == 0 && make_chunk_tmap(&tmx, x, bt.total) &&
         make_chunk_tmap(&tmy, y, bt.total))
         use_tma = 1;
-    auto *counter = reinterpret_cast<unsigned long long *>(const_cast<char *>(ws));
-    kern<<<(unsigned)grid, kFwdThreads, SM::ALLOC, st>>>(x, zi, y, saved, ws, counter, bt, three, x_al,
+    kern<<<(unsigned)grid, kFwdThreads, SM::ALLOC, st>>>(x, zi, y, saved, tabs, counter, bt, three, x_al,
                                                        y_al, use_tma, tmx, tmy);
     return cudaGetLastError();
 }
@@ -1097,22 +1101,23 @@ cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *save
 }  // namespace
 
 template <int MB>
-cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *ws,
+cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *tabs,
+                         unsigned long long *counter,
                          const Batch &bt, bool fp64_scan, int three, int num_sms, cudaStream_t st) {
     // pipelined kernel wherever its double-buffered layout fits the shared memory
     if constexpr (WsSmem<MB, true, fwd_stages<MB, true>()>::ALLOC <= kSmemMax)
-        if (fp64_scan) return launch_fwd_ws<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
+        if (fp64_scan) return launch_fwd_ws<MB, true>(x, zi, y, saved, tabs, counter, bt, three, num_sms, st);
     if constexpr (MB <= kMaxF32ScanBucket &&
                   WsSmem<MB, false, fwd_stages<MB, false>()>::ALLOC <= kSmemMax)
-        if (!fp64_scan) return launch_fwd_ws<MB, false>(x, zi, y, saved, ws, bt, three, num_sms, st);
-    if (fp64_scan) return launch_fwd_t<MB, true>(x, zi, y, saved, ws, bt, three, num_sms, st);
+        if (!fp64_scan) return launch_fwd_ws<MB, false>(x, zi, y, saved, tabs, counter, bt, three, num_sms, st);
+    if (fp64_scan) return launch_fwd_t<MB, true>(x, zi, y, saved, tabs, counter, bt, three, num_sms, st);
     if constexpr (MB <= kMaxF32ScanBucket)
-        return launch_fwd_t<MB, false>(x, zi, y, saved, ws, bt, three, num_sms, st);
+        return launch_fwd_t<MB, false>(x, zi, y, saved, tabs, counter, bt, three, num_sms, st);
     return cudaErrorNotSupported;
 }
 
 template cudaError_t chunk_fwd_mb<DFILT_MB>(const float *, const float *, float *, float *,
-                                            const char *, const Batch &, bool, int, int,
-                                            cudaStream_t);
+                                            const char *, unsigned long long *, const Batch &, bool,
+                                            int, int, cudaStream_t);
 
 }  // namespace dfilt

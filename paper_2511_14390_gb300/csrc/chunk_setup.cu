@@ -59,9 +59,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
     __shared__ SmallScratch<MB> scr_all[kSmallWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     SmallScratch<MB> &sc = scr_all[wib];
-    const int64_t ch = (int64_t)blockIdx.x * kSmallWarps + wib;
     if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
-    if (ch >= bt.B) return;
+    int64_t ch;
+    if (!work_channel(bt, (int64_t)blockIdx.x * kSmallWarps + wib, &ch)) return;
     const Channel c = channel_of(bt, ch);
     dw av[MB], bp[MB + 1];   // av[k] = a_{k+1}; zero past the channel's orders
 #pragma unroll
@@ -88,8 +88,10 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
         }
     }
     __syncwarp();
-    char *RF = fwd_tabs ? fwd_tabs + (size_t)ch * Tab::fwd_rec(f64) : nullptr;
-    char *RB = bwd_tabs ? bwd_tabs + (size_t)ch * Tab::bwd_rec(f64) : nullptr;
+    const size_t fstride = bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(f64);
+    const size_t bstride = bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(f64);
+    char *RF = fwd_tabs ? fwd_tabs + (size_t)ch * fstride : nullptr;
+    char *RB = bwd_tabs ? bwd_tabs + (size_t)ch * bstride : nullptr;
     for (int n = lane; n < L; n += 32) {
         dw acc = dw_make(0.f);
 #pragma unroll
@@ -218,11 +220,12 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
     double(*sA)[MB + 1] = sX + MB;
     double(*sOL)[MB + 1] = sA + MB;
 
-    const int64_t ch = blockIdx.x;
     const int m = threadIdx.x;
-    if (counter && ch == 0 && blockIdx.y == 0 && m == 0) *counter = 0ull;
+    if (counter && blockIdx.x == 0 && blockIdx.y == 0 && m == 0) *counter = 0ull;
     // grid.y selects the record: forward tables, backward tables, or both
     const bool backward = fwd_tabs == nullptr || blockIdx.y == 1;
+    int64_t ch;
+    if (!work_channel(bt, (int64_t)blockIdx.x, &ch)) return;   // uniform across the block
     const Channel c = channel_of(bt, ch);
     sa[m] = m < c.M ? (double)a[ch * bt.Mstride + m] : 0.0;
     sbp[m] = m <= c.N ? (double)b[ch * bt.Nstride + m] : 0.0;
@@ -230,7 +233,8 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
     __syncthreads();
     sG[m] = sbp[m + 1] - sa[m] * sbp[0];
     sGh[m] = -sa[m];   // input vector of the all-pole filter (b = [1])
-    const size_t rec = backward ? Tab::bwd_rec(f64) : Tab::fwd_rec(f64);
+    const size_t rec = backward ? (bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(f64))
+                                : (bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(f64));
     char *R = (backward ? bwd_tabs : fwd_tabs) + (size_t)ch * rec;
     __syncthreads();
 

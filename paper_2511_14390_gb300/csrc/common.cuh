@@ -38,6 +38,14 @@ struct Batch {
     int *status;              // device status word
     long long wait_limit;     // cap on polls of any bounded wait
     int stall_drill;          // test mode: also wait on a barrier nothing signals
+    // Optional sub-list of channels for one launch (a state-order bucket of a ragged
+    // batch): work item c is channel list[list_range[0] + c], c < list_range[1] -
+    // list_range[0].  nullptr: work item c is channel c < B.
+    const int *list;
+    const int *list_range;
+    // Byte strides of the per-channel table records (0: the launch's own record size;
+    // set when buckets of different sizes share one workspace).
+    int64_t fwd_stride, bwd_stride;
 };
 
 struct Channel {
@@ -45,6 +53,18 @@ struct Channel {
     int64_t len;
     int M, N;
 };
+
+// Channel of work item c of a launch; false once the launch's work is exhausted.
+__device__ __forceinline__ bool work_channel(const Batch &bt, int64_t c, int64_t *ch) {
+    if (!bt.list) {
+        *ch = c;
+        return c < bt.B;
+    }
+    const int lo = bt.list_range[0], hi = bt.list_range[1];
+    if (c >= (int64_t)(hi - lo)) return false;
+    *ch = bt.list[lo + c];
+    return true;
+}
 
 __device__ __forceinline__ Channel channel_of(const Batch &bt, int64_t i) {
     Channel c;

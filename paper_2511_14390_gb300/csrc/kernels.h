@@ -34,6 +34,15 @@ struct ChunkLayout {
     size_t bwd_tab;     // bytes of backward tables per channel
 };
 ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt);
+// Launch plan of one call: one bucket for a fixed-shape batch, every state bucket up to
+// the largest order for a ragged batch (records at the common strides).
+struct ChunkPlan {
+    int nb;
+    ChunkLayout lay[6];
+    size_t fstride, bstride;
+    bool ragged;
+};
+ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged);
 
 // Forward-to-backward buffer (`saved`): the chunk states (channel i's chunks start at
 // chunk index offsets[i] / L + i; each chunk stores Mstride floats), then, 256-byte
@@ -42,12 +51,13 @@ ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt);
 inline size_t chunk_saved_state_bytes(int64_t B, int64_t total, int Mstride) {
     return ((size_t)(total / kL + B + 1) * (size_t)Mstride * sizeof(float) + 255) / 256 * 256;
 }
-size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, bool fp64_scan);
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged);
 
 // Per-bucket launchers (one translation unit per bucket, compiled with -DDFILT_MB=<MB>).
 template <int MB>
-cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *ws,
-                         const Batch &bt, bool fp64_scan, int three, int num_sms, cudaStream_t st);
+cudaError_t chunk_fwd_mb(const float *x, const float *zi, float *y, float *saved, const char *tabs,
+                         unsigned long long *counter, const Batch &bt, bool fp64_scan, int three,
+                         int num_sms, cudaStream_t st);
 template <int MB>
 cudaError_t chunk_bwd_mb(const float *gy, const float *x, const float *y, const float *b,
                          const float *a, const float *saved, float *gx, float *gb, float *ga,
@@ -63,20 +73,21 @@ constexpr int kMaxF32ScanBucket = 16;
 // (direction 0 forward, 1 backward).  A no-op while timing is off.
 void timing_mark(int direction, int phase, cudaStream_t st);
 
+// fp64_opt: the caller's scan option (-1 automatic per bucket, 0 off, 1 on)
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
-                             bool fp64_scan, int precision, int num_sms, cudaStream_t st);
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st);
 cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
                              const float *a, const float *saved, float *gx, float *gb,
                              float *ga, float *gzi, void *ws, const Batch &bt, int Mmax,
-                             bool fp64_scan, int precision, int num_sms, cudaStream_t st);
-size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st);
+size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged);
+size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged);
 
 // Tensor map of a signal viewed as rows of one chunk (L floats), 3-D so that one box
 // {32 floats, 1 half, 128 rows} is one 128-byte-swizzled K block of a tensor-core
 // operand tile.  Returns false when the layout does not allow it (rows not aligned to
 // chunk boundaries, misaligned base) -- callers then use plain async copies.
 bool make_chunk_tmap(CUtensorMap *map, const float *base, int64_t total);
-size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, bool fp64_scan);
 
 }  // namespace dfilt

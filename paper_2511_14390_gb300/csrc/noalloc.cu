@@ -67,9 +67,8 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     if (o.fp64_scan < -1 || o.fp64_scan > 1) return DFILT_ERR_INVALID_ARG;
     if (o.precision != DFILT_PREC_TF32 && o.precision != DFILT_PREC_TF32X3)
         return DFILT_ERR_UNSUPPORTED;
-    const ChunkLayout l = chunk_layout(M, o.fp64_scan);
     // Capacity check before touching the device: the tables for B channels must fit.
-    if (chunk_fwd_ws_bytes(B, M, l.fp64_scan) > kNoallocScratchBytes) return DFILT_ERR_WORKSPACE;
+    if (chunk_fwd_ws_bytes(B, M, o.fp64_scan, false) > kNoallocScratchBytes) return DFILT_ERR_WORKSPACE;
     if (B == 0 || T == 0) return DFILT_OK;
     int *status = nullptr, num_sms = 0, drill = 0;
     long long wait_limit = 0;
@@ -90,7 +89,11 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     bt.status = status;
     bt.wait_limit = wait_limit;
     bt.stall_drill = drill;
-    const cudaError_t e = launch_chunk_fwd(x, b, a, zi, y, nullptr, scratch, bt, M, l.fp64_scan,
+    bt.list = nullptr;
+    bt.list_range = nullptr;
+    bt.fwd_stride = 0;
+    bt.bwd_stride = 0;
+    const cudaError_t e = launch_chunk_fwd(x, b, a, zi, y, nullptr, scratch, bt, M, o.fp64_scan,
                                            o.precision, num_sms, static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess) return DFILT_OK;
     return e == cudaErrorNotSupported ? DFILT_ERR_UNSUPPORTED : DFILT_ERR_CUDA;

@@ -147,6 +147,51 @@ def test_ragged(mode):
             assert not gb[i].any() and not ga[i].any() and not gz[i].any()
 
 
+@pytest.mark.parametrize("mode", ["chunk3", "chunk3d"])
+def test_ragged_all_buckets(mode):
+    """Orders 1..32 (the ragged workload's range) in one batch: the chunked path runs one
+    launch pair per state bucket (2, 4, 8, 16, 32) over that bucket's channels, with
+    coefficient rows wider than the smaller buckets.  Per-channel tolerance from the
+    first-order bound C u32 kappa."""
+    from tol import U32, kappa
+    w = inputs.make_ragged(B=40, T_range=(200, 40000), M_range=(1, 32), seed=17)
+    Ms = w.Ms.copy()
+    Ms[:6] = [1, 2, 4, 8, 16, 32]          # every bucket edge present
+    for i in range(6):
+        rng = np.random.default_rng(40 + i)
+        w.a[i] = 0.0
+        w.a[i, :Ms[i]], _, _ = inputs.draw_denominator(rng, int(Ms[i]), 0.5, 0.99)
+        w.Ns[i] = min(w.Ns[i], Ms[i])
+        w.b[i] = 0.0
+        w.b[i, :int(w.Ns[i]) + 1] = inputs.draw_numerator(rng, int(w.Ns[i]), True)
+        w.zi[i, Ms[i]:] = 0.0
+    w.Ms[:] = Ms
+    offs, x, gy = w.offsets, w.x, w.gy
+    o = dfilt.make_opts(**OPTS[mode])
+    y, saved = dfilt.dfilt_forward_ragged(dev(x), dev(offs), dev(w.Ms), dev(w.Ns), dev(w.b),
+                                          dev(w.a), dev(w.zi), opts=o)
+    g = dfilt.dfilt_backward_ragged(dev(gy), dev(x), None if saved is not None else y, dev(offs),
+                                    dev(w.Ms), dev(w.Ns), dev(w.b), dev(w.a), dev(w.zi), saved,
+                                    opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    yr = oracle.forward_ragged(x, offs, w.Ms, w.Ns, w.b, w.a, w.zi)
+    gr = oracle.backward_ragged(gy, x, yr, offs, w.Ms, w.Ns, w.b, w.a)
+    y = y.cpu().numpy()
+    gx, gb, ga, gz = [t.cpu().numpy() for t in g]
+    for i in range(w.B):
+        s, e = offs[i], offs[i + 1]
+        M, N = int(w.Ms[i]), int(w.Ns[i])
+        if e == s:
+            continue
+        tol = max(1e-5, 16 * U32 * float(kappa(w.a[i:i + 1, :M], e - s)[0]))
+        Sb, Sa, Su = coef_scales(gy[s:e], x[s:e], yr[s:e], w.b[i, :N + 1], w.a[i, :M])
+        assert rel_rows(y[s:e], yr[s:e])[0] < tol, (mode, i, M)
+        assert rel_rows(gx[s:e], gr[0][s:e])[0] < tol, (mode, i, M)
+        assert coef_err(gb[i, :N + 1], gr[1][i, :N + 1], Sb)[0] < tol, (mode, i, M)
+        assert coef_err(ga[i, :M], gr[2][i, :M], Sa)[0] < tol, (mode, i, M)
+        assert coef_err(gz[i, :M], gr[3][i, :M], Su)[0] < tol, (mode, i, M)
+
+
 @pytest.mark.parametrize("mode", ["seq", "chunk3"])
 @pytest.mark.parametrize("T,M,N", [(1, 2, 2), (3, 4, 1), (64, 2, 2), (65, 3, 3), (8192, 2, 0),
                                    (8193, 2, 2)])
