@@ -693,25 +693,30 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         const char *hi = smem + stage_hi(s);
         const int nv = n - r * kL;
         const uint32_t lrow = (uint32_t)(32 * q) << 16;
+        auto rows = [&](auto full) {   // full: every sample of the row is valid (no masking)
 #pragma unroll
-        for (int cb = 0; cb < kL / 16; ++cb) {
-            float vh[16], vl[16];
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float vh[16], vl[16];
 #pragma unroll
-            for (int p4 = 0; p4 < 4; ++p4) {
-                const int j16 = cb * 4 + p4;
-                const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
-                const float e[4] = {v.x, v.y, v.z, v.w};
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    const int j16 = cb * 4 + p4;
+                    const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
+                    const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float xv = 4 * j16 + c < nv ? e[c] : 0.f;
-                    float h;
-                    split_tf32(xv, h, vl[4 * p4 + c]);
-                    vh[4 * p4 + c] = xv;
+                    for (int c = 0; c < 4; ++c) {
+                        const float xv = (decltype(full)::value || 4 * j16 + c < nv) ? e[c] : 0.f;
+                        float h;
+                        split_tf32(xv, h, vl[4 * p4 + c]);
+                        vh[4 * p4 + c] = xv;
+                    }
                 }
+                tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
+                if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
             }
-            tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
-            if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
-        }
+        };
+        // warp-uniform choice: tcgen05.st is a warp-collective instruction
+        if (__all_sync(0xffffffffu, nv >= kL)) rows(BoolC<true>{});
+        else rows(BoolC<false>{});
         tmem_wait_st();
         tc_fence_before();
     };
@@ -1020,18 +1025,12 @@ __global__ void __launch_bounds__(kBwThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) E[m] = v[m];
             }
-            // the state entering the tile from the right: the previous tile's carry
-            // (always waited for, which keeps the carry barriers' phases in step)
-            if (i >= 1) {
-                if (et == 0) epi_ok[2] = wait1(&carry_bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
-                named_sync(bar_id, 128);
-                if (!epi_ok[2]) break;
-            }
+            // The state entering the tile from the right is the previous tile's carry
+            // (always waited for, which keeps the carry barriers' phases in step).  The
+            // carry chain runs through both groups tile by tile, so each group does all
+            // the work that does not need it before it waits.
             float S[MB];   // S'_c = u[(c+1)L + m]
             if constexpr (!F64) {
-                float Sin[MB];
-#pragma unroll
-                for (int m = 0; m < MB; ++m) Sin[m] = (pv.first || i == 0) ? 0.f : carry[(s ^ 1) * MB + m];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const int dd = 1 << k;
@@ -1049,10 +1048,13 @@ __global__ void __launch_bounds__(kBwThreads, 1)
 #pragma unroll
                     for (int m = 0; m < MB; ++m) wt[ew * MB + m] = E[m];
                 }
-                named_sync(bar_id, 128);
+                if (i >= 1 && et == 0)
+                    epi_ok[2] = wait1(&carry_bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
+                named_sync(bar_id, 128);   // warp totals written, carry landed
+                if (i >= 1 && !epi_ok[2]) break;
                 float C[MB];
 #pragma unroll
-                for (int m = 0; m < MB; ++m) C[m] = Sin[m];
+                for (int m = 0; m < MB; ++m) C[m] = (pv.first || i == 0) ? 0.f : carry[(s ^ 1) * MB + m];
 #pragma unroll
                 for (int ww = 3; ww >= 0; --ww) {
                     if (ww == ew) {
@@ -1089,6 +1091,11 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
                 named_sync(bar_id, 128);   // wt reusable
             } else {
+                if (i >= 1) {
+                    if (et == 0) epi_ok[2] = wait1(&carry_bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
+                    named_sync(bar_id, 128);
+                    if (!epi_ok[2]) break;
+                }
                 // serial FP64 reverse scan by the group's first warp
                 float *xbuf_s = reinterpret_cast<float *>(smem + SM::SCR + eg * SM::SCR_G);
                 float *sbuf = xbuf_s + kChunks * MB;
@@ -1127,6 +1134,22 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (et == 0) epi_ok[1] = wait1(&x_bar[xj], (uint32_t)((i >> 1) & 1)) ? 1 : 0;
             named_sync(bar_id, 128);
             if (!epi_ok[1]) break;
+            // samples past the channel's end read as zero: this row's tail zeroed in place
+            // (only a channel's last tile has one; the row is this thread's alone)
+            const int nvalid = pv.tlen - et * kL;
+            if (nvalid < kL) {
+#pragma unroll 1
+                for (int j16 = max(nvalid, 0) >> 2; j16 < 16; ++j16) {
+                    float4 *pp = reinterpret_cast<float4 *>(xs + op_piece(et, j16));
+                    float4 v = *pp;
+                    const int s0 = 4 * j16;
+                    if (s0 + 0 >= nvalid) v.x = 0.f;
+                    if (s0 + 1 >= nvalid) v.y = 0.f;
+                    if (s0 + 2 >= nvalid) v.z = 0.f;
+                    if (s0 + 3 >= nvalid) v.w = 0.f;
+                    *pp = v;
+                }
+            }
             // Streamed over the chunk row, 16 columns of the adjoint at a time (u = TMEM
             // zero-state part + free response O^u S'), 4 samples per x piece: y
             // recomputed from the forward's chunk state, the lag correlations
@@ -1157,7 +1180,24 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             for (int k = 0; k <= MB; ++k) pb[k] = 0.f;
 #pragma unroll
             for (int k = 0; k < MB; ++k) pa[k] = 0.f;
-            const int nvalid = pv.tlen - et * kL;   // samples past the channel's end read as zero
+            // low orders: the coefficients in registers (-a_1..-a_MB, b_0..b_MB), off the
+            // y recursion's dependency chain; higher orders read them from shared memory
+            constexpr bool kRegCoef = MB <= 8;
+            float cR[kRegCoef ? 2 * MB + 1 : 1];
+            if constexpr (kRegCoef) {
+#pragma unroll
+                for (int k = 0; k < MB; ++k) cR[k] = -coef[k];
+#pragma unroll
+                for (int k = 0; k <= MB; ++k) cR[MB + k] = coef[MB + k];
+            }
+            auto na = [&](int k) -> float {   // -a_{k+1}
+                if constexpr (kRegCoef) return cR[k];
+                else return -coef[k];
+            };
+            auto cb_ = [&](int k) -> float {   // b_k
+                if constexpr (kRegCoef) return cR[MB + k];
+                else return coef[MB + k];
+            };
 #pragma unroll 1
             for (int bb = 0; bb < kL / 16; ++bb) {
                 if (bb + 1 < kL / 16) {
@@ -1177,18 +1217,18 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     for (int q = 0; q < 4; ++q) {
                         const int nn = 4 * p4 + q;        // within the block
                         const int n = bb * 16 + nn;       // within the chunk
-                        const float xn = n < nvalid ? xq[q] : 0.f;
-                        const float yn = fmaf(coef[MB], xn, st[0]);
+                        const float xn = xq[q];
+                        const float yn = fmaf(cb_(0), xn, st[0]);
 #pragma unroll
                         for (int k = 0; k < MB; ++k)
-                            st[k] = fmaf(-coef[k], yn, fmaf(coef[MB + 1 + k], xn, k + 1 < MB ? st[k + 1] : 0.f));
+                            st[k] = fmaf(na(k), yn, fmaf(cb_(1 + k), xn, k + 1 < MB ? st[k + 1] : 0.f));
 #pragma unroll
                         for (int k = 0; k <= MB; ++k) pb[k] = fmaf(DFILT_EXT(nn + k), xn, pb[k]);
 #pragma unroll
                         for (int k = 0; k < MB; ++k) pa[k] = fmaf(DFILT_EXT(nn + 1 + k), yn, pa[k]);
                         float g = 0.f;
 #pragma unroll
-                        for (int k = 0; k <= MB; ++k) g = fmaf(coef[MB + k], DFILT_EXT(nn + k), g);
+                        for (int k = 0; k <= MB; ++k) g = fmaf(cb_(k), DFILT_EXT(nn + k), g);
                         gq[q] = g;
                     }
                     *reinterpret_cast<float4 *>(xs + op_piece(et, j16)) = make_float4(gq[0], gq[1], gq[2], gq[3]);

@@ -709,25 +709,30 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             const char *hi = smem + stage_hi(s);
             const int nv = n - r * kL;   // valid samples of this row
             const uint32_t lrow = (uint32_t)(32 * q) << 16;
+            auto rows = [&](auto full) {   // full: every sample of the row is valid (no masking)
 #pragma unroll
-            for (int cb = 0; cb < kL / 16; ++cb) {
-                float vh[16], vl[16];
+                for (int cb = 0; cb < kL / 16; ++cb) {
+                    float vh[16], vl[16];
 #pragma unroll
-                for (int p4 = 0; p4 < 4; ++p4) {
-                    const int j16 = cb * 4 + p4;
-                    const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
-                    const float e[4] = {v.x, v.y, v.z, v.w};
+                    for (int p4 = 0; p4 < 4; ++p4) {
+                        const int j16 = cb * 4 + p4;
+                        const float4 v = *reinterpret_cast<const float4 *>(hi + op_piece(r, j16));
+                        const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float xv = 4 * j16 + c < nv ? e[c] : 0.f;
-                        float h;
-                        split_tf32(xv, h, vl[4 * p4 + c]);
-                        vh[4 * p4 + c] = xv;
+                        for (int c = 0; c < 4; ++c) {
+                            const float xv = (decltype(full)::value || 4 * j16 + c < nv) ? e[c] : 0.f;
+                            float h;
+                            split_tf32(xv, h, vl[4 * p4 + c]);
+                            vh[4 * p4 + c] = xv;
+                        }
                     }
+                    tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
+                    if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
                 }
-                tmem_st16(tmem + lrow + ahi_col(p) + cb * 16, vh);
-                if (three) tmem_st16(tmem + lrow + alo_col(p) + cb * 16, vl);
-            }
+            };
+            // warp-uniform choice: tcgen05.st is a warp-collective instruction
+            if (__all_sync(0xffffffffu, nv >= kL)) rows(pipe::BoolC<true>{});
+            else rows(pipe::BoolC<false>{});
             tmem_wait_st();
             tc_fence_before();
         };

@@ -12,6 +12,10 @@ constexpr uint32_t kTileBytes = kChunks * kL * 4;   // 32 KB: one signal tile
 constexpr uint32_t kKBlock = kChunks * 128;         // one 32-wide K block of an operand tile
 constexpr uint32_t kSmemMax = 232448;               // opt-in shared memory per block
 constexpr int kNamedConv = 1, kNamedEpi = 2;
+template <bool B>
+struct BoolC {   // compile-time flag for generic lambdas
+    static constexpr bool value = B;
+};
 // Warp roles of the warp-specialised kernels: 8 warps, so the register file allows up
 // to 255 registers per thread (a ninth warp would cap it at 168).
 constexpr int kConvThreads = 96;   // warps 0-2: converters
