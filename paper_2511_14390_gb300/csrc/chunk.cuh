@@ -28,7 +28,8 @@ struct ChunkTab {
     static constexpr size_t F_RL = F_G + kL * 4;
     static constexpr size_t F_OL = F_RL + (size_t)MB * kL * 4;
     static constexpr size_t F_SCAN = (F_OL + (size_t)kL * MB * 4 + 15) / 16 * 16;
-    // backward record: g[L] | h[L] | Ou[L][MB] | Ogx[L][MB] | scan block
+    // backward record: g[L] | h[L] | Ou[L][MB] | Ogx[L][MB] | scan block | coefficients
+    // (a_1..a_MB, b_0..b_MB as f32, zero past the channel's orders)
     static constexpr size_t B_G = 0;
     static constexpr size_t B_H = kL * 4;
     static constexpr size_t B_OU = 2 * kL * 4;
@@ -40,7 +41,9 @@ struct ChunkTab {
     static constexpr size_t SCAN_F64 = (size_t)MB * MB * 8;
     __host__ __device__ static constexpr size_t scan_bytes(bool f64) { return f64 ? SCAN_F64 : SCAN_F32; }
     __host__ __device__ static constexpr size_t fwd_rec(bool f64) { return (F_SCAN + scan_bytes(f64) + 255) / 256 * 256; }
-    __host__ __device__ static constexpr size_t bwd_rec(bool f64) { return (B_SCAN + scan_bytes(f64) + 255) / 256 * 256; }
+    __host__ __device__ static constexpr size_t b_coef(bool f64) { return (B_SCAN + scan_bytes(f64) + 15) / 16 * 16; }
+    static constexpr size_t COEF_BYTES = ((2 * MB + 1) * 4 + 15) / 16 * 16;
+    __host__ __device__ static constexpr size_t bwd_rec(bool f64) { return (b_coef(f64) + COEF_BYTES + 255) / 256 * 256; }
 };
 
 // Workspace header: a 256-byte block holding the work counter, then the records.

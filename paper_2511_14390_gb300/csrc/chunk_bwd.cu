@@ -588,21 +588,25 @@ struct BwSmem {
     static constexpr uint32_t T_BHI = 0;                             // within a B slot
     static constexpr uint32_t T_BLO = NM * 256;
     static constexpr uint32_t BSLOT = 2 * NM * 256;
-    static constexpr uint32_t SMALL0 = TB + 2 * BSLOT;               // 2 slots: O^u | scan | coef | h
+    static constexpr uint32_t SMALL0 = TB + 2 * BSLOT;               // 2 slots: O^u | scan | coef
     static constexpr uint32_t S_OU = 0;
     static constexpr uint32_t S_SCAN = kL * MB * 4;
     static constexpr uint32_t S_COEF = (S_SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
-    static constexpr uint32_t S_H = (S_COEF + (2 * MB + 1) * 4 + 15) / 16 * 16;   // h, staged
-    static constexpr uint32_t SSLOT = S_H + kL * 4;
+    static constexpr uint32_t SSLOT = (S_COEF + (2 * MB + 1) * 4 + 15) / 16 * 16;
+    // staging of a channel's record (bulk copy): h | O^u, then scan block | coefficients
+    static constexpr uint32_t G_PART0 = (uint32_t)(Tab::B_OGX - Tab::B_H);
+    static constexpr uint32_t G_PART1 = (uint32_t)(Tab::b_coef(F64) + Tab::COEF_BYTES - Tab::B_SCAN);
+    static constexpr uint32_t G_COEF = G_PART0 + (uint32_t)(Tab::b_coef(F64) - Tab::B_SCAN);
+    static constexpr uint32_t STG = (SMALL0 + 2 * SSLOT + 127) / 128 * 128;
     // FP64 reverse scan scratch per group (E' and S' per chunk)
-    static constexpr uint32_t SCR = SMALL0 + 2 * SSLOT;
+    static constexpr uint32_t SCR = (STG + G_PART0 + G_PART1 + 15) / 16 * 16;
     static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 : 0;
     static constexpr uint32_t ACC = (SCR + 2 * SCR_G + 7) / 8 * 8;   // [2 slots][NACC] doubles
     static constexpr uint32_t CNT = ACC + 2 * NACC * 8;              // tiles done [2 slots]
     static constexpr uint32_t CARRY = CNT + 16;                      // [2][MB] floats
     static constexpr uint32_t CARRY64 = (CARRY + 2 * MB * 4 + 7) / 8 * 8;   // [2][MB] doubles
     static constexpr uint32_t MISC = (CARRY64 + 2 * MB * 8 + 15) / 16 * 16;
-    static constexpr int NBAR = 25;
+    static constexpr int NBAR = 26;
     static constexpr uint32_t M_BAR = MISC;
     static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
     static constexpr uint32_t M_ABORT = M_TMEM + 4;
@@ -636,7 +640,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
     uint64_t *full = bars + 0, *load_bar = bars + 6, *mma_done = bars + 9,
              *tmem_free = bars + 13, *x_bar = bars + 17, *tab_free = bars + 19, *carry_bar = bars + 21,
-             *dead = bars + 23, *drain = bars + 24;
+             *dead = bars + 23, *drain = bars + 24, *stg_bar = bars + 25;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
     // decision flags written by one thread and read by its role after a named barrier;
@@ -766,14 +770,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             ++cur_t;
             d.last = cur_t == cur_nt;
         };
-        // B operand (single slot) and the channel-parity slot of the small tables
-        auto build_tables = [&](const TileDesc &d) {
+        // a channel's record (h, O^u, scan block, coefficients) into the staging area:
+        // two bulk copies on stg_bar, issued by thread 0 ahead of the table build
+        bool stg_pending = false;   // thread 0: a record copy not yet waited for
+        auto prefetch_record = [&](const TileDesc &d) {
             const char *R = tabs + (size_t)d.ch * rec;
+            stg_pending = true;
+            fence_proxy_async_smem();   // the previous build's reads of the area come first
+            mbar_arrive_expect_tx(stg_bar, SM::G_PART0 + SM::G_PART1);
+            bulk_load(sbase + SM::STG, R + Tab::B_H, SM::G_PART0, stg_bar);
+            bulk_load(sbase + SM::STG + SM::G_PART0, R + Tab::B_SCAN, SM::G_PART1, stg_bar);
+        };
+        // the channel-parity slots of the B operand and of the small tables, from the
+        // staged record
+        auto build_tables = [&](const TileDesc &d) {
             char *T = smem + sslot(d.tab);
-            // h into shared memory once (coalesced), then the Toeplitz block from there
-            float *hs = reinterpret_cast<float *>(T + SM::S_H);
-            if (ct < kL) hs[ct] = __ldg(reinterpret_cast<const float *>(R + Tab::B_H) + ct);
-            named_sync(kNamedConv, kBwConv);
+            const char *G = smem + SM::STG;
+            const float *hs = reinterpret_cast<const float *>(G);
             // T_h^a[i][k] = h[k - i] (k >= i): work item = (column k, 8 of the rows)
             for (int item = ct; item < 512; item += kBwConv) {
                 const int k = item & 63, r0 = (item >> 6) * 8;   // column k, rows r0 .. r0+7
@@ -793,16 +806,15 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     *reinterpret_cast<float *>(smem + SM::TB + d.tab * SM::BSLOT + SM::T_BLO + o) = lo;
                 }
             }
-            const float4 *Ou = reinterpret_cast<const float4 *>(R + Tab::B_OU);
+            const float4 *Ou = reinterpret_cast<const float4 *>(G + (Tab::B_OU - Tab::B_H));
             float4 *sOu = reinterpret_cast<float4 *>(T + SM::S_OU);
-            for (int idx = ct; idx < kL * MB / 4; idx += kBwConv) sOu[idx] = __ldg(Ou + idx);
-            const float4 *src = reinterpret_cast<const float4 *>(R + Tab::B_SCAN);
+            for (int idx = ct; idx < kL * MB / 4; idx += kBwConv) sOu[idx] = Ou[idx];
+            const float4 *src = reinterpret_cast<const float4 *>(G + SM::G_PART0);
             float4 *dst = reinterpret_cast<float4 *>(T + SM::S_SCAN);
-            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kBwConv) dst[idx] = __ldg(src + idx);
+            for (int idx = ct; idx < (int)(Tab::scan_bytes(F64) / 16); idx += kBwConv) dst[idx] = src[idx];
             float *coef = reinterpret_cast<float *>(T + SM::S_COEF);   // a[0..MB) | b[0..MB]
-            const Channel c = channel_of(bt, d.ch);
-            if (ct < MB) coef[ct] = ct < c.M ? aco[d.ch * bt.Mstride + ct] : 0.f;
-            if (ct <= MB) coef[MB + ct] = ct <= c.N ? bco[d.ch * bt.Nstride + ct] : 0.f;
+            const float *gc = reinterpret_cast<const float *>(G + SM::G_COEF);
+            if (ct < 2 * MB + 1) coef[ct] = gc[ct];
             fence_proxy_async_smem();   // B is read by the tensor cores
         };
         // gy tile of `d` -> stage s; the same tile of x is prefetched into L2 for the
@@ -834,22 +846,35 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             next_desc(d1);
             ring[0] = d0;
             ring[1] = d1;
+            if (d0.ch >= 0) prefetch_record(d0);
         }
         named_sync(kNamedConv, kBwConv);
         int64_t issued_upto = -1;   // last tile whose gy load this thread has issued
+        int64_t waited_upto = -1;   // thread 0: last tile whose gy load it saw land
+        uint32_t stg_par = 0;       // parity of the next staging completion
+        bool conv_alive = true;
         {
             const TileDesc d0 = ring[0], d1 = ring[1];
             if (d0.ch >= 0) {
-                build_tables(d0);
-                issue_gy(d0, 0);
-                issued_upto = 0;
-                if (d1.ch >= 0) {   // its tables (if it starts a channel) wait for MMA(0)
-                    issue_gy(d1, 1);
-                    issued_upto = 1;
+                if (ct == 0) {
+                    conv_ok[3] = wait1(stg_bar, stg_par) ? 1 : 0;
+                    stg_pending = conv_ok[3] == 0;
+                }
+                stg_par ^= 1u;
+                named_sync(kNamedConv, kBwConv);
+                conv_alive = conv_ok[3] != 0;
+                if (conv_alive) {
+                    build_tables(d0);
+                    issue_gy(d0, 0);
+                    issued_upto = 0;
+                    if (d1.ch >= 0) {   // its tables (if it starts a channel) wait for MMA(0)
+                        issue_gy(d1, 1);
+                        issued_upto = 1;
+                    }
                 }
             }
         }
-        for (int64_t i = 0;; ++i) {
+        for (int64_t i = 0; conv_alive; ++i) {
             const int s = (int)(i % kBwNS);
             const uint32_t ph = (uint32_t)((i / kBwNS) & 1);
             const TileDesc d = ring[i & 7];
@@ -857,12 +882,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (ct == 0) mbar_arrive(&full[s]);   // end marker for the MMA warp
                 break;
             }
-            // (1) gy tile i landed (tile i+1's copies may still be in flight); operand slot
-            //     i&1 free once MMA(i-2), its previous reader, is done
+            // tile i+1 starts a channel (its descriptor is re-read where needed: the ring
+            // slot is not rewritten before iteration i+7)
+            const bool new1 = ring[(i + 1) & 7].ch >= 0 && ring[(i + 1) & 7].first;
+            // (1) tile i+2's descriptor and (for a new channel at i+1) the record prefetch,
+            //     while gy tile i lands; operand slot i&1 free once MMA(i-2), its previous
+            //     reader, is done.  The descriptor's ring slot held tile i-6, read by every
+            //     role once MMA(i-2) is done.  (An end marker at index E is followed by one
+            //     at E+1, the other group's end, written in the same way one tile later.)
             if (ct == 0) {
+                if (new1) prefetch_record(ring[(i + 1) & 7]);
+                TileDesc nd;
+                next_desc(nd);
                 bool ok = true;
                 if (tma_gy) ok = wait1(&load_bar[s], ph);
+                if (ok) waited_upto = i;
                 if (ok && i >= 2) ok = wait1(&mma_done[(i - 2) & 3], (uint32_t)(((i - 2) >> 2) & 1));
+                ring[(i + 2) & 7] = nd;
                 conv_ok[1] = ok ? 1 : 0;
             }
             if (!tma_gy) {
@@ -876,30 +912,36 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             a_to_tmem(warp, d.tlen, s, (int)(i & 1));
             named_sync(kNamedConv, kBwConv);
             if (ct == 0) mbar_arrive(&full[s]);
-            // (3) tile i+2's descriptor; its stage held tile i, converted above (ring slots
-            //     are reused 8 apart, far behind every reader).  If tile i+1 starts a
-            //     channel, its table slot waits for the channel two back to be finished.
-            const TileDesc dn1 = ring[(i + 1) & 7];
-            if (ct == 0) {
-                TileDesc nd;
-                next_desc(nd);
-                bool ok = true;
-                if (dn1.ch >= 0 && dn1.first && dn1.seq >= 2)
-                    ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
-                // (an end marker at index E is followed by one at E+1, the other group's
-                // end: the next iteration describes E+1 only after waiting MMA(E-3), so
-                // that group has read the slot's previous tile E-7 by then)
-                ring[(i + 2) & 7] = nd;
-                conv_ok[2] = ok ? 1 : 0;
-            }
-            named_sync(kNamedConv, kBwConv);
-            if (!conv_ok[2]) break;
-            if (dn1.ch >= 0 && dn1.first) build_tables(dn1);
+            // (3) gy tile i+2 into the stage just converted; then, if tile i+1 starts a
+            //     channel, its tables, once the channel two back (same slot) is finished
             const TileDesc dn2 = ring[(i + 2) & 7];
             if (dn2.ch >= 0) {
                 issue_gy(dn2, (int)((i + 2) % kBwNS));
                 issued_upto = i + 2;
             }
+            if (new1) {
+                const TileDesc dn1 = ring[(i + 1) & 7];
+                if (ct == 0) {
+                    bool ok = true;
+                    if (dn1.seq >= 2) ok = wait1(&tab_free[dn1.tab], (uint32_t)(((dn1.seq >> 1) - 1) & 1));
+                    if (ok) {
+                        ok = wait1(stg_bar, stg_par);
+                        stg_pending = !ok;
+                    }
+                    conv_ok[2] = ok ? 1 : 0;
+                }
+                stg_par ^= 1u;
+                named_sync(kNamedConv, kBwConv);
+                if (!conv_ok[2]) break;
+                build_tables(dn1);
+            }
+        }
+        // a failed wait can leave copies in flight: let them land before the CTA exits
+        if (ct == 0) {
+            if (tma_gy)
+                for (int64_t j = waited_upto + 1; j <= issued_upto; ++j)
+                    mbar_wait_bounded(&load_bar[j % kBwNS], (uint32_t)((j / kBwNS) & 1), kDefaultWaitLimit);
+            if (stg_pending) mbar_wait_bounded(stg_bar, stg_par, kDefaultWaitLimit);
         }
     } else if (warp == kBwMmaWarp) {
         // ============================ MMA issuer ============================
@@ -1216,7 +1258,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int nn = 4 * p4 + q;        // within the block
-                        const int n = bb * 16 + nn;       // within the chunk
                         const float xn = xq[q];
                         const float yn = fmaf(cb_(0), xn, st[0]);
 #pragma unroll

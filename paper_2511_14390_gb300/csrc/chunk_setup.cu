@@ -190,6 +190,10 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
             }
             Ogx[idx] = dw_to_float(acc);
         }
+        float *C = reinterpret_cast<float *>(RB + Tab::b_coef(f64));
+        for (int k = lane; k < 2 * MB + 1; k += 32)
+            C[k] = k < MB ? (k < c.M ? a[ch * bt.Mstride + k] : 0.f)
+                          : (k - MB <= c.N ? b[ch * bt.Nstride + (k - MB)] : 0.f);
         if (lane < MB * MB) {
             sc.ahi[0][lane] = sc.uhi[lane];   // Abar'[k][m] = O^u[k][m], k < MB
             sc.alo[0][lane] = sc.ulo[lane];
@@ -278,6 +282,10 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
         float *h = reinterpret_cast<float *>(R + Tab::B_H);
         float *Ou = reinterpret_cast<float *>(R + Tab::B_OU);
         float *Ogx = reinterpret_cast<float *>(R + Tab::B_OGX);
+        float *C = reinterpret_cast<float *>(R + Tab::b_coef(f64));
+        C[m] = (float)sa[m];
+        C[MB + m] = (float)sbp[m];
+        if (m == 0) C[2 * MB] = (float)sbp[MB];
         // first rows of F^i for g and h
         double v[MB];
 #pragma unroll
