@@ -677,7 +677,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const size_t rec = bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(F64);
-    constexpr uint32_t idesc = idesc_tf32_m128(NM);
     auto stage_hi = [&](int s) { return (uint32_t)(SM::GS0 + s * kTileBytes); };
     auto xbuf = [&](int j) { return (uint32_t)(SM::XB0 + j * kTileBytes); };
     auto sslot = [&](int p) { return (uint32_t)(SM::SMALL0 + p * SM::SSLOT); };
@@ -982,15 +981,22 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(tb * 64);
 #pragma unroll
-                for (int kk = 0; kk < kL / 8; ++kk) {
+                for (int kr = 0; kr < kL / 8; ++kr) {
+                    // T_h^a is upper triangular: samples 8kk .. 8kk+7 reach outputs
+                    // n < 8kk+8 only, so this K step covers B rows (and D columns) below
+                    // 16 ceil((kk+1)/2); K runs downwards so that the widest step (all
+                    // 64 columns) is the first, the one that overwrites the accumulator
+                    const int kk = kL / 8 - 1 - kr;
+                    const int nn = 16 * ((kk + 2) / 2);
+                    const uint32_t idn = idesc_tf32_m128(nn);
                     const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
                     const uint32_t ahi = tmem + ahi_col(pl) + 8 * kk;
                     const uint64_t bhi = sdesc_sw128(sbase + SM::TB + d.tab * SM::BSLOT + SM::T_BHI + kb);
-                    mma_tf32_tmem_a(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_tmem_a(d_tmem, ahi, bhi, idn, kr > 0 ? 1u : 0u);
                     if (three) {
                         const uint64_t blo = sdesc_sw128(sbase + SM::TB + d.tab * SM::BSLOT + SM::T_BLO + kb);
-                        mma_tf32_tmem_a(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(pl) + 8 * kk, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(d_tmem, ahi, blo, idn, 1u);
+                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(pl) + 8 * kk, bhi, idn, 1u);
                     }
                 }
                 mma_commit(&mma_done[tb]);

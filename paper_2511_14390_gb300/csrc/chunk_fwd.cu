@@ -578,7 +578,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const size_t rec = bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(F64);
-    constexpr uint32_t idesc = idesc_tf32_m128(NM);
     auto stage_hi = [&](int s) { return (uint32_t)(PS::XS0 + s * kTileBytes); };
     auto tslot = [&](int p) { return (uint32_t)(PS::TAB0 + p * PS::TSLOT); };
     // TMEM columns of stage s's A_lo (128 lanes = chunks x 64 columns = samples)
@@ -838,14 +837,20 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 const uint32_t tb = tslot(d.tab);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
-                    const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32;
+                    // T_g is lower triangular: samples 8kk .. 8kk+7 reach outputs n >= 8kk
+                    // only, so this K step covers B rows (and D columns) from n0 on; the
+                    // R_L rows behind T_g are dense and always included
+                    const int n0 = 16 * (kk / 2);
+                    const uint32_t kb = (kk >> 2) * (NM * 128) + (kk & 3) * 32 + n0 * 128;
+                    const uint32_t idn = idesc_tf32_m128(NM - n0);
+                    const uint32_t dk = d_tmem + (uint32_t)n0;
                     const uint32_t ahi = tmem + ahi_col(tb_) + 8 * kk;
                     const uint64_t bhi = sdesc_sw128(sbase + tb + PS::T_BHI + kb);
-                    mma_tf32_tmem_a(d_tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_tmem_a(dk, ahi, bhi, idn, kk > 0 ? 1u : 0u);
                     if (three) {
                         const uint64_t blo = sdesc_sw128(sbase + tb + PS::T_BLO + kb);
-                        mma_tf32_tmem_a(d_tmem, ahi, blo, idesc, 1u);
-                        mma_tf32_tmem_a(d_tmem, tmem + alo_col(tb_) + 8 * kk, bhi, idesc, 1u);
+                        mma_tf32_tmem_a(dk, ahi, blo, idn, 1u);
+                        mma_tf32_tmem_a(dk, tmem + alo_col(tb_) + 8 * kk, bhi, idn, 1u);
                     }
                 }
                 mma_commit(&mma_done[tb_]);
