@@ -57,6 +57,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(v: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: every rank passes its own, all get the maximum."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(samples_per_rank: int, world: int, ms: float) -> float:
+    """Gsamples/s of the whole job: every rank filters its own replica of the batch
+    (weak scaling), timed by the slowest rank."""
+    return samples_per_rank * world / (ms / 1e3) / 1e9
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -299,11 +316,7 @@ def main():
         return tot / steps, statistics.mean(tf), statistics.mean(tb), kern
 
     def maxrank(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, world)
 
     algo = a.algo
     st = setup(algo)
@@ -343,7 +356,7 @@ def main():
         graph = {"value": samples_all / (gms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": gms,
                  "steps": a.steps}
         del cg
-    value = samples_all / (ms / 1e3) / 1e9
+    value = whole_job_rate(B * T, world, ms)
     status = dfilt.dfilt_sync_status()
     if status != 0:
         raise RuntimeError(f"device status {dfilt.STATUS[status]}")
