@@ -483,7 +483,8 @@ struct TileDesc {
 // Warp-specialised forward (state buckets whose double-buffered layout fits).
 //
 // Roles (384 threads), decoupled by mbarriers; signal tiles in NST shared-memory
-// stages (s = i % NST), TMEM operand slots and accumulators alternating (i & 1):
+// stages (s = i % NST), TMEM operand slots alternating (i & 1), accumulators in a ring
+// of NA (i % NA; three 80-column accumulators where they fit beside the operand slots):
 //   warps 0-2, 8-11  converters: fetch work; build per-channel tables (double-buffered by
 //              channel parity); signal tiles arrive NST-1 ahead (TMA tensor load into
 //              the 128-byte-swizzled operand layout, or cp.async when the layout has no
@@ -491,7 +492,7 @@ struct TileDesc {
 //              hi, x - trunc(x) as lo) into TMEM operand slot i&1 once MMA(i-2) is done
 //                                                   -> full[s]; the stage is then free
 //   warp 3     MMA issuer: full[s], tmem_free -> tcgen05.mma (A from TMEM, the B operand
-//              from shared memory) into TMEM accumulator i&1  -> mma_done (commit)
+//              from shared memory) into TMEM accumulator i%NA -> mma_done (commit)
 //   warps 4-7  epilogue: mma_done -> chunk-state scan, y = D + O_L S, saved states; y
 //              staged in the y buffer in the operand layout and written by a TMA tensor
 //              store (full tiles) or plain stores     -> tmem_free
@@ -511,8 +512,8 @@ template <int MB, bool F64, int NST>
 struct WsSmem {
     using P = PipeSmem<MB, F64, NST>;
     static constexpr uint32_t MISC = P::MISC;
-    // barriers: full[3] (unused)[3] load[3] mma_done[2] tmem_free[2] tab_free[2] dead
-    // drain (17, 20 slots)
+    // barriers: full[3] (unused)[3] load[3] mma_done[3] tmem_free[3] tab_free[2] dead
+    // drain (19 of 20 slots)
     static constexpr int NBAR = 20;
     static constexpr uint32_t M_BAR = MISC;
     static constexpr uint32_t M_TMEM = MISC + NBAR * 8;
@@ -552,7 +553,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
     uint64_t *full = bars + 0, *load_bar = bars + 6, *mma_done = bars + 9,
-             *tmem_free = bars + 11, *tab_free = bars + 13, *dead = bars + 15, *drain = bars + 16;
+             *tmem_free = bars + 12, *tab_free = bars + 15, *dead = bars + 17, *drain = bars + 18;
+    // accumulators: NA of ACOLS columns below the operand slots (columns 256 ..)
+    constexpr int NA = 3 * NM <= 256 ? 3 : 2;
+    constexpr uint32_t ACOLS = NA == 3 ? (uint32_t)NM : 128u;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::M_TMEM);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM::M_ABORT);
     // decision flags written by one thread and read by its role after a named barrier;
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < SM::NBAR; ++i) mbar_init(&bars[i], (i == 9 || i == 10) ? 2 : 1);
+        for (int i = 0; i < SM::NBAR; ++i) mbar_init(&bars[i], (i >= 9 && i < 12) ? 2 : 1);   // mma_done: commit + arrive
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -766,7 +770,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (ct == 0) {
                 bool ok = true;
                 if (use_tma) ok = wait1(&load_bar[s], ph);
-                if (ok && i >= 2) ok = wait1(&mma_done[i & 1], (uint32_t)(((i - 2) >> 1) & 1));
+                if (ok && i >= 2) ok = wait1(&mma_done[(i - 2) % NA], (uint32_t)(((i - 2) / NA) & 1));
                 conv_ok[0] = ok ? 1 : 0;
             }
             if (!use_tma) {
@@ -811,8 +815,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         bool issued = false;
         for (int64_t i = 0;; ++i) {
             const int s = (int)(i % NST);        // signal-tile stage
-            const int tb_ = (int)(i & 1);         // TMEM accumulator buffer
-            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            const int tb_ = (int)(i & 1);          // TMEM operand slot
+            const int ab = (int)(i % NA);          // TMEM accumulator
+            const uint32_t par = (uint32_t)((i / NA) & 1);
             int ok = 1;
             if (lane == 0) ok = wait1(&full[s], (uint32_t)((i / NST) & 1)) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -821,19 +826,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             // TMEM buffer free (epilogue done with tile i-2); the end marker waits too,
             // or its arrivals could complete a second phase of mma_done before the
             // epilogue has observed tile i-2's (a parity wait cannot tell them apart)
-            if (lane == 0 && i >= 2) ok = wait1(&tmem_free[tb_], par ^ 1u) ? 1 : 0;
+            if (lane == 0 && i >= NA) ok = wait1(&tmem_free[ab], par ^ 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             if (d.ch < 0) {
                 if (lane == 0) {
-                    mbar_arrive(&mma_done[tb_]);   // end marker for the epilogue (2 arrivals)
-                    mbar_arrive(&mma_done[tb_]);
+                    mbar_arrive(&mma_done[ab]);   // end marker for the epilogue (2 arrivals)
+                    mbar_arrive(&mma_done[ab]);
                 }
                 break;
             }
             if (lane == 0) {
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(tb_ * 128);
+                const uint32_t d_tmem = tmem + (uint32_t)ab * ACOLS;
                 const uint32_t tb = tslot(d.tab);
 #pragma unroll
                 for (int kk = 0; kk < kL / 8; ++kk) {
@@ -853,8 +858,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         mma_tf32_tmem_a(dk, tmem + alo_col(tb_) + 8 * kk, bhi, idn, 1u);
                     }
                 }
-                mma_commit(&mma_done[tb_]);
-                mbar_arrive(&mma_done[tb_]);   // orders the descriptor reads before the epilogue's
+                mma_commit(&mma_done[ab]);
+                mbar_arrive(&mma_done[ab]);   // orders the descriptor reads before the epilogue's
             }
             issued = true;
             if (bt.stall_drill) {
@@ -879,8 +884,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
         for (int64_t i = 0;; ++i) {
-            const int s = (int)(i & 1);
-            const uint32_t par = (uint32_t)((i >> 1) & 1);
+            const int s = (int)(i % NA);           // TMEM accumulator
+            const uint32_t par = (uint32_t)((i / NA) & 1);
             if (et == 0) *epi_ok = wait1(&mma_done[s], par) ? 1 : 0;
             named_sync(kNamedEpi, 128);
             if (!*epi_ok) break;
@@ -893,7 +898,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             const double *sAt = reinterpret_cast<const double *>(T + PS::T_SCAN);
             const double *sin = reinterpret_cast<const double *>(T + PS::T_SIN);
             const int nch = (pv.tlen + kL - 1) / kL;
-            const uint32_t taddr = tmem + lane_off + (uint32_t)(s * 128);
+            const uint32_t taddr = tmem + lane_off + (uint32_t)s * ACOLS;
             if (pv.first) {
 #pragma unroll
                 for (int m = 0; m < MB; ++m) Sin[m] = (float)sin[m];
