@@ -35,8 +35,9 @@ struct ChunkTab {
     static constexpr size_t B_OU = 2 * kL * 4;
     static constexpr size_t B_OGX = B_OU + (size_t)kL * MB * 4;
     static constexpr size_t B_SCAN = (B_OGX + (size_t)kL * MB * 4 + 15) / 16 * 16;
-    // scan block: fp32 powers P[k][MB][MB] (row-major) or fp64 transition stored
-    // column-major (At[j][m] = A[m][j]) for the sequential FP64 scan
+    // scan block: fp32 powers P[k][MB][MB] (row-major), or for the serial scan the
+    // transition as double words (hi, lo float pairs) stored column-major
+    // (At[j][m] = A[m][j])
     static constexpr size_t SCAN_F32 = (size_t)NPOW * MB * MB * 4;
     static constexpr size_t SCAN_F64 = (size_t)MB * MB * 8;
     __host__ __device__ static constexpr size_t scan_bytes(bool f64) { return f64 ? SCAN_F64 : SCAN_F32; }

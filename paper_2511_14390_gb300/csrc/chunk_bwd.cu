@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float *sOU = reinterpret_cast<float *>(smem + SM::OU);
     float *sOGX = reinterpret_cast<float *>(smem + SM::OGX);
     const float *sP = reinterpret_cast<const float *>(smem + SM::SCAN);
-    const double *sAt = reinterpret_cast<const double *>(smem + SM::SCAN);
+    const float2 *sAt = reinterpret_cast<const float2 *>(smem + SM::SCAN);
     float *sa = reinterpret_cast<float *>(smem + SM::COEF);
     float *sb = sa + (MB + 1);
     double *sacc = reinterpret_cast<double *>(smem + SM::ACC);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
 
         float Sin[MB];   // adjoint state entering the current tile from the right
-        double S64a = 0.0, S64b = 0.0;
+        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (warp 0)
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
         const int64_t ntiles = (c.len + kTileSamples - 1) / kTileSamples;
@@ -367,18 +367,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncthreads();
                 if (warp == 0) {
                     for (int cc = nch - 1; cc >= 0; --cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
-                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
-                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
-#pragma unroll 8
-                        for (int j = 0; j < MB; ++j) {
-                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
-                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
-                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
-                        }
-                        S64a = acc_a;
-                        S64b = acc_b;
+                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
+                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
+                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
+                                               S64a, S64b, lane);
                     }
                 }
                 __syncthreads();
@@ -437,7 +430,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float au = vu[i], ag = vg[i];
 #pragma unroll
                     for (int m = 0; m < MB; ++m) {
-                        const float ou = SM::OU_FROM_AT ? (float)sAt[m * MB + n] : sOU[n * MB + m];
+                        const float ou = SM::OU_FROM_AT ? dw_to_float(dw{sAt[m * MB + n].x, sAt[m * MB + n].y})
+                                                        : sOU[n * MB + m];
                         au = fmaf(ou, S[m], au);
                         ag = fmaf(sOGX[n * MB + m], S[m], ag);
                     }
@@ -650,7 +644,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     double *acc_ch = reinterpret_cast<double *>(smem + SM::ACC);
     unsigned *tiles_done = reinterpret_cast<unsigned *>(smem + SM::CNT);
     float *carry = reinterpret_cast<float *>(smem + SM::CARRY);
-    double *carry64 = reinterpret_cast<double *>(smem + SM::CARRY64);
+    float2 *carry64 = reinterpret_cast<float2 *>(smem + SM::CARRY64);   // double-word carries
     TileDesc *ring = reinterpret_cast<TileDesc *>(smem + SM::M_RING);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool gy_al = al_mask & 1, x_al = al_mask & 2, gx_al = al_mask & 8;
@@ -1039,7 +1033,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             const char *T = smem + sslot(pv.tab);
             const float *sOu = reinterpret_cast<const float *>(T + SM::S_OU);
             const float *sP = reinterpret_cast<const float *>(T + SM::S_SCAN);
-            const double *sAt = reinterpret_cast<const double *>(T + SM::S_SCAN);
+            const float2 *sAt = reinterpret_cast<const float2 *>(T + SM::S_SCAN);
             const float *coef = reinterpret_cast<const float *>(T + SM::S_COEF);
             char *xs = smem + xbuf(xj);   // x tile, then grad_x (operand layout)
             // this tile's x (prefetched into L2 with its gy tile) into the group's buffer
@@ -1152,24 +1146,18 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 named_sync(bar_id, 128);
                 if (ew == 0) {
                     const bool z = pv.first || i == 0;
-                    double S64a = (!z && lane < MB) ? carry64[(s ^ 1) * MB + lane] : 0.0;
-                    double S64b = (!z && lane + 32 < MB) ? carry64[(s ^ 1) * MB + lane + 32] : 0.0;
+                    const float2 c0 = (!z && lane < MB) ? carry64[(s ^ 1) * MB + lane] : make_float2(0.f, 0.f);
+                    const float2 c1 = (!z && lane + 32 < MB) ? carry64[(s ^ 1) * MB + lane + 32] : make_float2(0.f, 0.f);
+                    dw S64a{c0.x, c0.y}, S64b{c1.x, c1.y};
                     for (int cc = nch - 1; cc >= 0; --cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
-                        double acc_a = lane < MB ? (double)xbuf_s[cc * MB + lane] : 0.0;
-                        double acc_b = lane + 32 < MB ? (double)xbuf_s[cc * MB + lane + 32] : 0.0;
-#pragma unroll 8
-                        for (int j = 0; j < MB; ++j) {
-                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
-                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
-                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
-                        }
-                        S64a = acc_a;
-                        S64b = acc_b;
+                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
+                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf_s[cc * MB + lane] : 0.f,
+                                               lane + 32 < MB ? xbuf_s[cc * MB + lane + 32] : 0.f,
+                                               S64a, S64b, lane);
                     }
-                    if (lane < MB) carry64[s * MB + lane] = S64a;
-                    if (lane + 32 < MB) carry64[s * MB + lane + 32] = S64b;
+                    if (lane < MB) carry64[s * MB + lane] = make_float2(S64a.hi, S64a.lo);
+                    if (lane + 32 < MB) carry64[s * MB + lane + 32] = make_float2(S64b.hi, S64b.lo);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&carry_bar[s]);   // carry for the next tile
                 }

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     double *sin_buf = reinterpret_cast<double *>(smem + SM::MISC + 48);
     float *sOL = reinterpret_cast<float *>(smem + SM::OL);
     const float *sP = reinterpret_cast<const float *>(smem + SM::SCAN);
-    const double *sAt = reinterpret_cast<const double *>(smem + SM::SCAN);
+    const float2 *sAt = reinterpret_cast<const float2 *>(smem + SM::SCAN);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
@@ -207,12 +207,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
         // per-thread carried state for the FP32 scan; warp 0 carries the FP64 one
         float Sin[MB];
-        double S64a = 0.0, S64b = 0.0;
+        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (warp 0)
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = (float)sin_buf[m];
         if (F64 && warp == 0) {
-            S64a = lane < MB ? sin_buf[lane] : 0.0;
-            S64b = lane + 32 < MB ? sin_buf[lane + 32] : 0.0;
+            S64a = dw_make(lane < MB ? (float)sin_buf[lane] : 0.f);
+            S64b = dw_make(lane + 32 < MB ? (float)sin_buf[lane + 32] : 0.f);
         }
         const int64_t ntiles = (c.len + kTileSamples - 1) / kTileSamples;
         const int64_t chunk_base = c.off / kL + ch;
@@ -334,25 +334,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 __syncthreads();
             } else {
-                // serial FP64 scan by warp 0: S_{c+1} = Abar S_c + E_c, state carried in FP64
+                // serial scan by warp 0: S_{c+1} = Abar S_c + E_c, state carried in double words
                 float *sbuf = reinterpret_cast<float *>(smem + SM::AHI);
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
                 __syncthreads();
                 if (warp == 0) {
                     for (int cc = 0; cc < nch; ++cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
-                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
-                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
-#pragma unroll 8
-                        for (int j = 0; j < MB; ++j) {
-                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
-                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
-                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
-                        }
-                        S64a = acc_a;
-                        S64b = acc_b;
+                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
+                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
+                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
+                                               S64a, S64b, lane);
                     }
                 }
                 __syncthreads();
@@ -880,7 +873,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const int ew = warp - kEpiWarp0;       // lane quarter
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
         float Sin[MB];
-        double S64a = 0.0, S64b = 0.0;
+        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (first warp)
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
         for (int64_t i = 0;; ++i) {
@@ -895,7 +888,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             const char *T = smem + tslot(pv.tab);
             const float *sOL = reinterpret_cast<const float *>(T + PS::T_OL);
             const float *sP = reinterpret_cast<const float *>(T + PS::T_SCAN);
-            const double *sAt = reinterpret_cast<const double *>(T + PS::T_SCAN);
+            const float2 *sAt = reinterpret_cast<const float2 *>(T + PS::T_SCAN);
             const double *sin = reinterpret_cast<const double *>(T + PS::T_SIN);
             const int nch = (pv.tlen + kL - 1) / kL;
             const uint32_t taddr = tmem + lane_off + (uint32_t)s * ACOLS;
@@ -903,8 +896,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) Sin[m] = (float)sin[m];
                 if (F64 && ew == 0) {
-                    S64a = lane < MB ? sin[lane] : 0.0;
-                    S64b = lane + 32 < MB ? sin[lane + 32] : 0.0;
+                    S64a = dw_make(lane < MB ? (float)sin[lane] : 0.f);
+                    S64b = dw_make(lane + 32 < MB ? (float)sin[lane + 32] : 0.f);
                 }
             }
             float E[MB];
@@ -986,18 +979,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                 named_sync(kNamedEpi, 128);
                 if (ew == 0) {
                     for (int cc = 0; cc < nch; ++cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = (float)S64a;
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = (float)S64b;
-                        double acc_a = lane < MB ? (double)xbuf[cc * MB + lane] : 0.0;
-                        double acc_b = lane + 32 < MB ? (double)xbuf[cc * MB + lane + 32] : 0.0;
-#pragma unroll 8
-                        for (int j = 0; j < MB; ++j) {
-                            const double sj = __shfl_sync(0xffffffffu, j < 32 ? S64a : S64b, j & 31);
-                            if (lane < MB) acc_a = fma(sAt[j * MB + lane], sj, acc_a);
-                            if (lane + 32 < MB) acc_b = fma(sAt[j * MB + lane + 32], sj, acc_b);
-                        }
-                        S64a = acc_a;
-                        S64b = acc_b;
+                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
+                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
+                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
+                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
+                                               S64a, S64b, lane);
                     }
                 }
                 named_sync(kNamedEpi, 128);

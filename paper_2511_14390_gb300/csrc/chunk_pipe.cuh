@@ -4,6 +4,7 @@
 #pragma once
 
 #include "chunk.cuh"
+#include "dword.cuh"
 
 namespace dfilt {
 namespace pipe {
@@ -191,6 +192,37 @@ __device__ __forceinline__ void warp_load_rows(float (&v)[kL], char *stag, const
         }
         __syncwarp();
     }
+}
+
+// One step of the serial chunk-state scan, s <- A s + e, in double-word arithmetic on
+// the FP32 pipes (GB300's FP64 pipe is narrow; double words carry about 44 significant
+// bits, far beyond what the FP32 inputs e hold).  One warp: lane r < MB holds state
+// component r in sa and (MB = 64) component r + 32 in sb.  At is the transition stored
+// column-major as (hi, lo) pairs, At[j * MB + m] = A[m][j].  Each product is split
+// exactly (FMA TwoProduct) and its high part added with TwoSum; the low parts are
+// summed plainly and folded in once at the end.
+__device__ __forceinline__ void dw_acc(float &h, float &l, float2 a, float sh, float sl) {
+    const float p = a.x * sh;
+    float e = fmaf(a.x, sh, -p);
+    e = fmaf(a.x, sl, e);
+    e = fmaf(a.y, sh, e);
+    const dw s = two_sum(h, p);
+    h = s.hi;
+    l += s.lo + e;
+}
+template <int MB>
+__device__ __forceinline__ void dw_scan_step(const float2 *__restrict__ At, float ea, float eb,
+                                             dw &sa, dw &sb, int lane) {
+    float ah = ea, al = 0.f, bh = eb, bl = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < MB; ++j) {
+        const float sh = __shfl_sync(0xffffffffu, j < 32 ? sa.hi : sb.hi, j & 31);
+        const float sl = __shfl_sync(0xffffffffu, j < 32 ? sa.lo : sb.lo, j & 31);
+        if (lane < MB) dw_acc(ah, al, At[j * MB + lane], sh, sl);
+        if (lane + 32 < MB) dw_acc(bh, bl, At[j * MB + lane + 32], sh, sl);
+    }
+    sa = fast_two_sum(ah, al);
+    sb = fast_two_sum(bh, bl);
 }
 
 // Bounded single-thread mbarrier wait; on timeout (or a peer's abort) raise the abort

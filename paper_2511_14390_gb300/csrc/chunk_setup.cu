@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
     __syncwarp();
     // the scan block of a record from the transition in sc.a[0]
     auto write_scan = [&](char *S) {
-        if (f64) {
-            double *At = reinterpret_cast<double *>(S);
+        if (f64) {   // the serial scan's transition: double words (hi, lo), column-major
+            float2 *At = reinterpret_cast<float2 *>(S);
             if (lane < MB * MB) {
                 const int j = lane / MB, m = lane % MB;   // At[j][m] = A[m][j]
-                At[lane] = dw_to_double(dw{sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]});
+                At[lane] = make_float2(sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]);
             }
         } else {
             float *P = reinterpret_cast<float *>(S);
@@ -335,8 +335,12 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
     __syncthreads();
     char *S = R + (backward ? Tab::B_SCAN : Tab::F_SCAN);
     if (f64) {
-        double *At = reinterpret_cast<double *>(S);
-        for (int j = 0; j < MB; ++j) At[j * MB + m] = sA[m][j];
+        float2 *At = reinterpret_cast<float2 *>(S);   // double words (hi, lo), column-major
+        for (int j = 0; j < MB; ++j) {
+            const double v = sA[m][j];
+            const float hi = (float)v;
+            At[j * MB + m] = make_float2(hi, (float)(v - (double)hi));
+        }
     } else {
         float *P = reinterpret_cast<float *>(S);
         for (int kp = 0; kp < Tab::NPOW; ++kp) {
