@@ -1,6 +1,6 @@
 // Device helpers shared by the warp-specialised chunked kernels (forward and
 // backward): tile descriptors, operand-tile addressing, named barriers, async tile
-// loads, the TF32 split, small mat-vecs, and per-warp staging of row-major chunks.
+// loads, small mat-vecs, the double-word serial scan step and bounded waits.
 #pragma once
 
 #include "chunk.cuh"
@@ -17,12 +17,11 @@ template <bool B>
 struct BoolC {   // compile-time flag for generic lambdas
     static constexpr bool value = B;
 };
-// Warp roles of the warp-specialised kernels: 8 warps, so the register file allows up
-// to 255 registers per thread (a ninth warp would cap it at 168).
-constexpr int kConvThreads = 96;   // warps 0-2: converters
-constexpr int kMmaWarp = 3;        // warp 3: tensor-core issuer
-constexpr int kEpiWarp0 = 4;       // warps 4-7: epilogue (one per TMEM lane quarter)
-constexpr int kPipeThreads = 256;
+// Warp roles shared by the warp-specialised kernels (each kernel adds its own
+// converter warps): the forward's tensor-core issuer is warp 3, and both kernels'
+// epilogue warps start at warp 4 (one per TMEM lane quarter, warp % 4).
+constexpr int kMmaWarp = 3;
+constexpr int kEpiWarp0 = 4;
 
 struct TileDesc {
     int64_t ch;        // channel (-1: no more work)
@@ -72,39 +71,6 @@ __device__ __forceinline__ void load_tile_async(uint32_t dst, const float *src, 
     cp_async_commit();
 }
 
-// Split an operand tile into TF32 hi and lo, zeroing samples past `n`.  The tensor
-// cores read a TF32 operand from the upper 19 bits of its 32-bit word, i.e. they
-// truncate, which is what split_tf32's hi is; so the raw tile already is the hi part
-// and only pieces that need zeroing are written back.  Thread `t` of NT handles
-// pieces t, t+NT, ...
-template <int NT>
-__device__ __forceinline__ void split_tile_tf32(char *hi, char *lo, int n, bool three, int t) {
-#pragma unroll 4
-    for (int q = 0; q < (2048 + NT - 1) / NT; ++q) {
-        const int id = t + NT * q;
-        if (id >= 2048) break;
-        const int r = id >> 4, j16 = id & 15;
-        const uint32_t o = op_piece(r, j16);
-        float4 v = *reinterpret_cast<float4 *>(hi + o);
-        const int sidx = r * kL + j16 * 4;
-        if (sidx + 4 > n) {
-            if (sidx + 0 >= n) v.x = 0.f;
-            if (sidx + 1 >= n) v.y = 0.f;
-            if (sidx + 2 >= n) v.z = 0.f;
-            if (sidx + 3 >= n) v.w = 0.f;
-            *reinterpret_cast<float4 *>(hi + o) = v;
-        }
-        if (three) {
-            float4 h, l;
-            split_tf32(v.x, h.x, l.x);
-            split_tf32(v.y, h.y, l.y);
-            split_tf32(v.z, h.z, l.z);
-            split_tf32(v.w, h.w, l.w);
-            *reinterpret_cast<float4 *>(lo + o) = l;
-        }
-    }
-}
-
 template <int MB>
 __device__ __forceinline__ void matvec(const float *P, const float (&v)[MB], float (&out)[MB]) {
 #pragma unroll
@@ -113,84 +79,6 @@ __device__ __forceinline__ void matvec(const float *P, const float (&v)[MB], flo
 #pragma unroll
         for (int j = 0; j < MB; ++j) acc = fmaf(P[i * MB + j], v[j], acc);
         out[i] = acc;
-    }
-}
-
-// Per-warp staging of row-major chunks: the warp owns chunks (rows) 32w .. 32w+31 of a
-// tile and each lane holds its row's 64 samples in registers.  Rows move through a
-// 2 KB buffer 8 at a time (16-byte pieces XOR-swizzled by row, conflict-free), so that
-// global memory sees 512-byte coalesced accesses.
-//
-// warp_store_rows: row values -> dst[base + row*L + i] for sample index < n.
-__device__ __forceinline__ void warp_store_rows(const float (&v)[kL], char *stag, float *dst,
-                                                int64_t tstart, int row0, int n, bool al16,
-                                                int lane) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if ((lane >> 3) == q) {
-            const int r = lane & 7;
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                *reinterpret_cast<float4 *>(stag + r * 256 + ((j ^ r) << 4)) =
-                    make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = 2 * p + (lane >> 4), j = lane & 15;
-            const float4 w = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ r) << 4));
-            const int sidx = (row0 + 8 * q + r) * kL + j * 4;
-            const int nv = min(max(n - sidx, 0), 4);
-            float *g = dst + tstart + sidx;
-            if (nv == 4 && al16) {
-                *reinterpret_cast<float4 *>(g) = w;
-            } else {
-                if (nv > 0) g[0] = w.x;
-                if (nv > 1) g[1] = w.y;
-                if (nv > 2) g[2] = w.z;
-                if (nv > 3) g[3] = w.w;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// warp_load_rows: src[base + row*L + i] -> row values (zero past n).
-__device__ __forceinline__ void warp_load_rows(float (&v)[kL], char *stag, const float *src,
-                                               int64_t tstart, int row0, int n, bool al16,
-                                               int lane) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = 2 * p + (lane >> 4), j = lane & 15;
-            const int sidx = (row0 + 8 * q + r) * kL + j * 4;
-            const int nv = min(max(n - sidx, 0), 4);
-            const float *g = src + tstart + sidx;
-            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (nv == 4 && al16) {
-                w = __ldg(reinterpret_cast<const float4 *>(g));
-            } else {
-                if (nv > 0) w.x = __ldg(g);
-                if (nv > 1) w.y = __ldg(g + 1);
-                if (nv > 2) w.z = __ldg(g + 2);
-                if (nv > 3) w.w = __ldg(g + 3);
-            }
-            *reinterpret_cast<float4 *>(stag + r * 256 + ((j ^ r) << 4)) = w;
-        }
-        __syncwarp();
-        if ((lane >> 3) == q) {
-            const int r = lane & 7;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float4 w = *reinterpret_cast<const float4 *>(stag + r * 256 + ((j ^ r) << 4));
-                v[4 * j] = w.x;
-                v[4 * j + 1] = w.y;
-                v[4 * j + 2] = w.z;
-                v[4 * j + 3] = w.w;
-            }
-        }
-        __syncwarp();
     }
 }
 

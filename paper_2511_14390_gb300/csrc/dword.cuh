@@ -4,7 +4,8 @@
 // TwoProduct (a * b = p + e exactly, e = fma(a, b, -p)); the combination rules are
 // the usual double-word sum and product (cf. Joldes, Muller, Popescu, "Tight and
 // rigorous error bounds for basic building blocks of double-word arithmetic", 2017).
-// Used where GB300's narrow FP64 pipe would otherwise serialise per-channel setup.
+// Used where GB300's narrow FP64 pipe would otherwise serialise the work: the
+// per-channel setup of the low-order tables and the serial high-order chunk-state scan.
 #pragma once
 
 namespace dfilt {
