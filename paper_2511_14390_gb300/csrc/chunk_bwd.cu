@@ -1131,7 +1131,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     const float wn = __shfl_down_sync(0xffffffffu, E[m], 1);
                     S[m] = v[m] + (lane < 31 ? wn : 0.f);
                 }
-                named_sync(bar_id, 128);   // wt reusable
+                // (wt is next written in the group's next tile, several group barriers on)
             } else {
                 if (i >= 1) {
                     if (et == 0) epi_ok[2] = wait1(&carry_bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1)) ? 1 : 0;
