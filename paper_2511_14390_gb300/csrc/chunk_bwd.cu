@@ -810,8 +810,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (ct < 2 * MB + 1) coef[ct] = gc[ct];
             fence_proxy_async_smem();   // B is read by the tensor cores
         };
-        // gy tile of `d` -> stage s; the same tile of x is prefetched into L2 for the
-        // epilogue group that will load it
+        // gy tile of `d` -> stage s
         auto issue_gy = [&](const TileDesc &d, int s) {
             if (tma_gy) {
                 if (ct == 0) {
@@ -824,10 +823,6 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 load_tile_async<kBwConv>(sbase + stage_hi(s), gy, d.tstart, d.tlen,
                                               gy_al && ((d.tstart & 3) == 0), ct);
             }
-            if (ct == 0 && x_al && d.tlen == kTileSamples && ((d.tstart & 3) == 0))
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(x + d.tstart),
-                             "r"((uint32_t)kTileBytes)
-                             : "memory");
         };
 
         if (ct == 0) {
@@ -1017,13 +1012,39 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + SM::M_OK + 16 + 16 * eg);
         float *wt = reinterpret_cast<float *>(smem + SM::M_WT) + eg * 4 * MB;
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+        const int xj = eg;   // this group's x buffer
+        // a tile's x into the group's buffer (TMA by one thread, or cp.async by all)
+        auto issue_x = [&](const TileDesc &d) {
+            if (tma_x) {
+                if (et == 0) {
+                    mbar_arrive_expect_tx(&x_bar[xj], kTileBytes);
+                    const int row = (int)(d.tstart / kL);
+                    tma_load_3d(sbase + xbuf(xj), &tmx, 0, 0, row, &x_bar[xj]);
+                    tma_load_3d(sbase + xbuf(xj) + kKBlock, &tmx, 0, 1, row, &x_bar[xj]);
+                }
+            } else {
+                load_tile_async<128>(sbase + xbuf(xj), x, d.tstart, d.tlen,
+                                     x_al && ((d.tstart & 3) == 0), et);
+                cp_async_mbar_arrive_noinc(&x_bar[xj]);
+            }
+        };
+        int64_t x_pending = -1;   // tile whose x load is issued but not yet waited for
         for (int64_t i = eg;; i += 2) {
             const int s = (int)(i & 1);   // == eg
             const int tb = (int)(i & 3);  // TMEM accumulator buffer
-            const int xj = eg;            // this group's x buffer
+            // TMA x of a later tile: issued before the accumulator wait (the descriptor is
+            // in the ring since the group saw MMA(i-2) done), once the previous tile's
+            // grad_x store has read the buffer; the first tile and cp.async x: below
             if (et == 0) {
+                if (tma_x && i > eg) {
+                    const TileDesc nx = ring[i & 7];
+                    bulk_wait_read0();
+                    if (nx.ch >= 0) {
+                        issue_x(nx);
+                        x_pending = i;
+                    }
+                }
                 epi_ok[0] = wait1(&mma_done[tb], (uint32_t)((i >> 2) & 1)) ? 1 : 0;
-                bulk_wait_read0();   // the previous tile's grad_x store has read the x buffer
             }
             named_sync(bar_id, 128);
             if (!epi_ok[0]) break;
@@ -1036,18 +1057,9 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             const float2 *sAt = reinterpret_cast<const float2 *>(T + SM::S_SCAN);
             const float *coef = reinterpret_cast<const float *>(T + SM::S_COEF);
             char *xs = smem + xbuf(xj);   // x tile, then grad_x (operand layout)
-            // this tile's x (prefetched into L2 with its gy tile) into the group's buffer
-            if (tma_x) {
-                if (et == 0) {
-                    mbar_arrive_expect_tx(&x_bar[xj], kTileBytes);
-                    const int row = (int)(pv.tstart / kL);
-                    tma_load_3d(sbase + xbuf(xj), &tmx, 0, 0, row, &x_bar[xj]);
-                    tma_load_3d(sbase + xbuf(xj) + kKBlock, &tmx, 0, 1, row, &x_bar[xj]);
-                }
-            } else {
-                load_tile_async<128>(sbase + xbuf(xj), x, pv.tstart, pv.tlen,
-                                     x_al && ((pv.tstart & 3) == 0), et);
-                cp_async_mbar_arrive_noinc(&x_bar[xj]);
+            if (!tma_x || i == eg) {   // (cp.async: the previous tile's plain stores have read the buffer)
+                issue_x(pv);
+                x_pending = i;
             }
             const int nch = (pv.tlen + kL - 1) / kL;
             const uint32_t taddr = tmem + lane_off + (uint32_t)(tb * 64);
@@ -1170,6 +1182,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (et == 0) epi_ok[1] = wait1(&x_bar[xj], (uint32_t)((i >> 1) & 1)) ? 1 : 0;
             named_sync(bar_id, 128);
             if (!epi_ok[1]) break;
+            x_pending = -1;
             // samples past the channel's end read as zero: this row's tail zeroed in place
             // (only a channel's last tile has one; the row is this thread's alone)
             const int nvalid = pv.tlen - et * kL;
@@ -1366,7 +1379,12 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (et == 0) mbar_arrive(&tab_free[pv.tab]);
             }
         }
-        if (et == 0) bulk_wait0();   // every TMA store complete before the CTA exits
+        if (et == 0) {
+            bulk_wait0();   // every TMA store complete before the CTA exits
+            // an x load issued for a tile the group did not reach lands first
+            if (tma_x && x_pending >= 0)
+                mbar_wait_bounded(&x_bar[xj], (uint32_t)((x_pending >> 1) & 1), kDefaultWaitLimit);
+        }
     }
     cp_async_wait_all();
     tc_fence_before();
