@@ -545,18 +545,19 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
 // Warp-specialised backward (state buckets whose layout fits), the forward's
 // pipeline structure run on reversed tiles, with two epilogue warpgroups:
 //   warps 0-3   converters: work (tiles of a channel from last to first), tables (the
-//               B operand T_h^a, O^u, scan block, coefficients; double-buffered by
-//               channel parity); gy tiles two ahead into two stages (TMA or cp.async;
-//               a stage is free once converted); warp w
-//               writes the TF32 operand of rows 32w .. 32w+31 (the raw words as hi,
-//               x - trunc(x) as lo) into TMEM operand slot i&1 -> full[s], after which
-//               the stage is free; the tile's x is prefetched into L2
+//               B operand T_h^a, O^u, scan block, coefficients, built from the channel's
+//               record staged by a bulk copy; double-buffered by channel parity); gy
+//               tiles two ahead into two stages (TMA or cp.async); warp w writes the
+//               TF32 operand of rows 32w .. 32w+31 (the raw words as hi, x - trunc(x)
+//               as lo) into TMEM operand slot i&1 -> full[s], after which the stage is
+//               free
 //   warp 12     MMA: D[128 x 64] = G T_h^a^T (zero-state adjoint u per chunk; A from
 //               TMEM, the B operand from shared memory) into TMEM accumulator i&3
 //   warps 4-7   epilogue group 0 (even tiles), warps 8-11 group 1 (odd tiles): reverse
 //               chunk scan of S'_c = u[(c+1)L ..] (each group loads its tile's x into its
-//               own buffer first; the state entering from the right is the other group's
-//               carry), u = D + O^u S', then streamed over the chunk row: y recomputed
+//               own buffer, issued before it waits for the tile's accumulator; the state
+//               entering from the right is the other group's carry), u = D + O^u S',
+//               then streamed over the chunk row: y recomputed
 //               from the forward's saved chunk state and the x tile, lag correlations,
 //               grad_x = sum_k b_k u[n+k] written over the x tile and stored from there
 //               (TMA for full tiles); lag sums added per channel in shared FP64, finished
