@@ -293,3 +293,42 @@ class DFilt(torch.autograd.Function):
 def filt(x, b, a, zi=None, **opt_kwargs):
     """Differentiable batched direct-form filter (see DFilt)."""
     return DFilt.apply(x, b, a, zi, make_opts(**opt_kwargs) if opt_kwargs else None)
+
+
+class DFiltRagged(torch.autograd.Function):
+    """y = DFiltRagged.apply(x, offsets, Ms, Ns, b, a, zi, opts): a ragged batch packed
+    into one signal (channel i is x[offsets[i]:offsets[i+1]] with orders Ms[i], Ns[i];
+    b [B, Nmax+1], a [B, Mmax], zi [B, Mmax] zero-padded rows; zi may be None); the
+    backward is the library's closed-form adjoint.  offsets, Ms and Ns get no gradient.
+    The calls allocate through torch only, so a whole training step around it can be
+    captured in a CUDA graph."""
+
+    @staticmethod
+    def forward(ctx, x, offsets, Ms, Ns, b, a, zi=None, opts: Opts | None = None):
+        opts = opts or make_opts()
+        y, saved = dfilt_forward_ragged(x, offsets, Ms, Ns, b, a, zi, opts=opts)
+        keep_y = saved is None   # without chunk states the backward re-reads y
+        ctx.opts = opts
+        ctx.has_zi = zi is not None
+        empty = x.new_empty(0)
+        ctx.save_for_backward(x, offsets, Ms, Ns, b, a, zi if zi is not None else empty,
+                              saved if saved is not None else empty, y if keep_y else empty)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, offsets, Ms, Ns, b, a, zi, saved, y = ctx.saved_tensors
+        ng = ctx.needs_input_grad
+        needs = (bool(ng[0]), bool(ng[4]), bool(ng[5]), bool(ng[6]) and ctx.has_zi)
+        gx, gb, ga, gzi = dfilt_backward_ragged(gy.contiguous(), x, y if y.numel() else None,
+                                                offsets, Ms, Ns, b, a,
+                                                zi if ctx.has_zi else None,
+                                                saved if saved.numel() else None,
+                                                opts=ctx.opts, needs=needs)
+        return gx, None, None, None, gb, ga, (gzi if ctx.has_zi else None), None
+
+
+def filt_ragged(x, offsets, Ms, Ns, b, a, zi=None, **opt_kwargs):
+    """Differentiable ragged batch of direct-form filters (see DFiltRagged)."""
+    return DFiltRagged.apply(x, offsets, Ms, Ns, b, a, zi,
+                             make_opts(**opt_kwargs) if opt_kwargs else None)

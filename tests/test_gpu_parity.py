@@ -311,6 +311,76 @@ def test_autograd(mode):
         assert rel_rows(t.grad.cpu().numpy(), r).max() < 1e-5
 
 
+def _ragged_grads_ok(w, y, gy, grads, tag):
+    """y and (grad_x, grad_b, grad_a, grad_zi) of a ragged batch against the oracle,
+    per channel, tolerance max(1e-5, 16 u32 kappa)."""
+    from tol import U32, kappa
+    offs = w.offsets
+    yr = oracle.forward_ragged(w.x, offs, w.Ms, w.Ns, w.b, w.a, w.zi)
+    gr = oracle.backward_ragged(gy, w.x, yr, offs, w.Ms, w.Ns, w.b, w.a)
+    gx, gb, ga, gz = grads
+    for i in range(w.B):
+        s, e = offs[i], offs[i + 1]
+        M, N = int(w.Ms[i]), int(w.Ns[i])
+        if e == s:
+            continue
+        tol = max(1e-5, 16 * U32 * float(kappa(w.a[i:i + 1, :M], e - s)[0]))
+        Sb, Sa, Su = coef_scales(gy[s:e], w.x[s:e], yr[s:e], w.b[i, :N + 1], w.a[i, :M])
+        assert rel_rows(y[s:e], yr[s:e])[0] < tol, (tag, i)
+        assert rel_rows(gx[s:e], gr[0][s:e])[0] < tol, (tag, i)
+        assert coef_err(gb[i, :N + 1], gr[1][i, :N + 1], Sb)[0] < tol, (tag, i)
+        assert coef_err(ga[i, :M], gr[2][i, :M], Sa)[0] < tol, (tag, i)
+        assert coef_err(gz[i, :M], gr[3][i, :M], Su)[0] < tol, (tag, i)
+
+
+def test_ragged_training_step_graph():
+    """A ragged batch (orders 1..8, so several state buckets) inside a loss.backward()
+    training step: eager, then the whole step captured in a CUDA graph and replayed
+    with a new upstream gradient."""
+    w = inputs.make_ragged(B=24, T_range=(100, 30000), M_range=(1, 8), seed=23)
+    offs, Ms, Ns = dev(w.offsets), dev(w.Ms), dev(w.Ns)
+    gy = dev(w.gy)
+
+    def leaves():
+        return [dev(t).requires_grad_() for t in (w.x, w.b, w.a, w.zi)]
+
+    def step(params):
+        x, b, a, zi = params
+        y = dfilt.filt_ragged(x, offs, Ms, Ns, b, a, zi, algo="chunked")
+        (y * gy).sum().backward()
+        return y.detach()
+
+    params = leaves()
+    y = step(params)
+    assert dfilt.dfilt_sync_status() == 0
+    _ragged_grads_ok(w, y.cpu().numpy(), w.gy, [p.grad.cpu().numpy() for p in params], "eager")
+
+    # fresh leaves first used on a side stream (their gradient accumulators then
+    # belong to that stream, not to the legacy default stream, which a capture may
+    # not depend on)
+    params = leaves()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            for p in params:
+                p.grad = None
+            step(params)
+    torch.cuda.current_stream().wait_stream(s)
+    for p in params:
+        p.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y_static = step(params)
+    gy2 = np.random.default_rng(99).standard_normal(w.gy.shape).astype(np.float32)
+    gy.copy_(dev(gy2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert dfilt.dfilt_sync_status() == 0
+    _ragged_grads_ok(w, y_static.cpu().numpy(), gy2, [p.grad.cpu().numpy() for p in params],
+                     "graph")
+
+
 def test_cuda_graph_capture():
     """Forward + backward captured once in a CUDA graph and replayed."""
     w = inputs.make("biquad_1024x48000", B=16, T=20000)
