@@ -20,6 +20,7 @@ OPTS = {
     "chunk3": dict(algo="chunked", precision="tf32x3"),
     "chunk1": dict(algo="chunked", precision="tf32"),
     "chunk3d": dict(algo="chunked", precision="tf32x3", fp64_scan=1),
+    "chunk3f": dict(algo="chunked", precision="tf32x3", fp64_scan=0),
 }
 TOL = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": 5e-3, "chunk3d": 1e-5}
 GTOL = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": 5e-3, "chunk3d": 1e-5}
@@ -109,6 +110,29 @@ def test_orders_high_radius(mode, M):
         w.b[i] = inputs.draw_numerator(rng, M, True)
     tol = np.maximum(1e-5, 16 * U32 * kappa(w.a, w.x.shape[1]))   # per channel
     check(f"highr_M{M}", mode, w, tol=tol, gtol=tol)
+
+
+def test_high_order_scan_precision():
+    """Order 16 with poles at radius 0.98-0.995 over 16 tiles: the chunk transitions
+    grow transiently to large norms, where an FP32 chunk-state scan loses accuracy.
+    The automatic (double-word) scan must stay at the sequential FP32 kernel's error
+    level and within the first-order bound; the forced FP32 scan is logged beside it."""
+    from tol import U32, kappa
+    rng = np.random.default_rng(516)
+    w = inputs.make("allpole16_256x262144", B=8, T=16 * 8192, seed=516)
+    for i in range(w.B):
+        w.a[i], w.radius[i], _ = inputs.draw_denominator(rng, 16, 0.98, 0.995)
+    yr, gref = oracle_fixed(w)
+    errs = {}
+    for mode in ("seq", "chunk3", "chunk3f"):
+        y, grads = run_fixed(w, mode, (True, False, True, False))
+        errs[mode] = grad_errors(w, y, yr, grads, gref, (True, False, True, False))
+        log_errors(f"scanprec/{mode}", **errs[mode])
+    bound = 16 * U32 * kappa(w.a, w.x.shape[1])
+    for nm in ("y", "gx"):
+        dw_err, seq_err = errs["chunk3"][nm], errs["seq"][nm]
+        assert (dw_err < np.maximum(8 * seq_err, 1e-6)).all(), (nm, dw_err, seq_err)
+        assert (dw_err < np.maximum(bound, 1e-5)).all(), (nm, dw_err, bound)
 
 
 @pytest.mark.parametrize("mode", ["seq", "chunk3", "chunk3d"])
