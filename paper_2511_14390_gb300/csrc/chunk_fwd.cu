@@ -798,9 +798,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (!conv_ok[1]) break;
             const TileDesc dn = ring[(i + LA) & (RING - 1)];
             if (dn.ch >= 0) {
-                if (dn.first) build_tables(dn);
+                // the load first: its stage is free already, and the tables (global
+                // reads of the channel's record) are needed only when its MMA runs
                 issue_load(dn, (int)((i + LA) % NST));
                 issued_upto = i + LA;
+                if (dn.first) build_tables(dn);
             }
         }
     } else if (warp == kMmaWarp) {
