@@ -73,7 +73,10 @@ typedef struct {
     int algo;        /* dfilt_algo */
     int precision;   /* dfilt_precision; ignored by the sequential algorithm */
     int chunk_len;   /* chunk length L of the chunked algorithm; 0 = default (64) */
-    int fp64_scan;   /* chunk-state scan in FP64: -1 auto, 0 off, 1 on */
+    int fp64_scan;   /* high-precision chunk-state scan (a serial scan in double-word
+                        FP32 arithmetic, about 44 bits: FP64-class accuracy without
+                        GB300's narrow FP64 pipe): -1 auto (orders above 4),
+                        0 off (FP32 two-level scan, orders <= 16), 1 on */
 } dfilt_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -84,7 +87,7 @@ const char *dfilt_status_string(dfilt_status s);
 
 /*
  * Fill *opts with the defaults: AUTO algorithm, TF32X3, default chunk length,
- * automatic FP64 scan.  opts must not be NULL.
+ * automatic scan precision.  opts must not be NULL.
  */
 dfilt_status dfilt_default_opts(dfilt_opts *opts);
 
