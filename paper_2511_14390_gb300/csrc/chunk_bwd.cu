@@ -48,7 +48,8 @@ struct BwdSmem {
     static constexpr uint32_t COEF = (SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
     static constexpr uint32_t ACC = (COEF + 2 * (MB + 1) * 4 + 15) / 16 * 16;   // 4 x (2MB+1) doubles
     static constexpr uint32_t MISC = ACC + 4 * (2 * MB + 1) * 8;
-    static constexpr uint32_t BYTES = MISC + 48;
+    static constexpr uint32_t ST = MISC + 48;                 // serial-scan state [2][MB] double words
+    static constexpr uint32_t BYTES = ST + 2 * MB * 8;
     static constexpr uint32_t ALLOC = BYTES + 1024;
 };
 
@@ -238,9 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
 
         float Sin[MB];   // adjoint state entering the current tile from the right
-        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (warp 0)
+        float2 *st = reinterpret_cast<float2 *>(smem + SM::ST);   // serial-scan state
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
+        if (F64 && tid < MB) st[tid] = make_float2(0.f, 0.f);
         const int64_t ntiles = (c.len + kTileSamples - 1) / kTileSamples;
         const int64_t chunk_base = c.off / kL + ch;
 
@@ -365,15 +367,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
                 __syncthreads();
-                if (warp == 0) {
-                    for (int cc = nch - 1; cc >= 0; --cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
-                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
-                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
-                                               S64a, S64b, lane);
-                    }
-                }
+                pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, true, tid, [] { __syncthreads(); });
+                if ((nch & 1) && tid < MB) st[tid] = st[MB + tid];   // outgoing state to st[0]
                 __syncthreads();
 #pragma unroll
                 for (int m = 0; m < MB; ++m) S[m] = tid < nch ? sbuf[tid * MB + m] : 0.f;
@@ -595,7 +590,7 @@ struct BwSmem {
     static constexpr uint32_t STG = (SMALL0 + 2 * SSLOT + 127) / 128 * 128;
     // FP64 reverse scan scratch per group (E' and S' per chunk)
     static constexpr uint32_t SCR = (STG + G_PART0 + G_PART1 + 15) / 16 * 16;
-    static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 : 0;
+    static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 + 2 * MB * 8 : 0;   // + scan state
     static constexpr uint32_t ACC = (SCR + 2 * SCR_G + 7) / 8 * 8;   // [2 slots][NACC] doubles
     static constexpr uint32_t CNT = ACC + 2 * NACC * 8;              // tiles done [2 slots]
     static constexpr uint32_t CARRY = CNT + 16;                      // [2][MB] floats
@@ -1151,30 +1146,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     named_sync(bar_id, 128);
                     if (!epi_ok[2]) break;
                 }
-                // serial FP64 reverse scan by the group's first warp
+                // serial reverse scan in double words by the whole group, from the other
+                // group's carry (zero at a channel's last tile, processed first)
                 float *xbuf_s = reinterpret_cast<float *>(smem + SM::SCR + eg * SM::SCR_G);
                 float *sbuf = xbuf_s + kChunks * MB;
+                float2 *st = reinterpret_cast<float2 *>(sbuf + kChunks * MB);   // [2][MB]
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf_s[et * MB + m] = E[m];
-                named_sync(bar_id, 128);
-                if (ew == 0) {
+                if (et < MB) {
                     const bool z = pv.first || i == 0;
-                    const float2 c0 = (!z && lane < MB) ? carry64[(s ^ 1) * MB + lane] : make_float2(0.f, 0.f);
-                    const float2 c1 = (!z && lane + 32 < MB) ? carry64[(s ^ 1) * MB + lane + 32] : make_float2(0.f, 0.f);
-                    dw S64a{c0.x, c0.y}, S64b{c1.x, c1.y};
-                    for (int cc = nch - 1; cc >= 0; --cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
-                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf_s[cc * MB + lane] : 0.f,
-                                               lane + 32 < MB ? xbuf_s[cc * MB + lane + 32] : 0.f,
-                                               S64a, S64b, lane);
-                    }
-                    if (lane < MB) carry64[s * MB + lane] = make_float2(S64a.hi, S64a.lo);
-                    if (lane + 32 < MB) carry64[s * MB + lane + 32] = make_float2(S64b.hi, S64b.lo);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&carry_bar[s]);   // carry for the next tile
+                    st[et] = z ? make_float2(0.f, 0.f) : carry64[(s ^ 1) * MB + et];
                 }
                 named_sync(bar_id, 128);
+                pipe::dw_scan_group<MB>(sAt, st, xbuf_s, sbuf, nch, true, et,
+                                        [&] { named_sync(bar_id, 128); });
+                if (et < MB) carry64[s * MB + et] = st[(nch & 1) * MB + et];
+                named_sync(bar_id, 128);
+                if (et == 0) mbar_arrive(&carry_bar[s]);   // carry for the next tile
 #pragma unroll
                 for (int m = 0; m < MB; ++m) S[m] = et < nch ? sbuf[et * MB + m] : 0.f;
                 named_sync(bar_id, 128);

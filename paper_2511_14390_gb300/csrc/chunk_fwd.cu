@@ -44,8 +44,10 @@ struct FwdSmem {
     static constexpr uint32_t OL = BLO + NM * 256;
     static constexpr uint32_t SCAN = OL + kL * MB * 4;
     static constexpr uint32_t MISC = (SCAN + (uint32_t)Tab::scan_bytes(F64) + 15) / 16 * 16;
-    // misc block: mbarrier (8) | tmem base (4) | channel (8) | flag (4) | drill mbarrier (8) | S_in (MB doubles)
-    static constexpr uint32_t BYTES = MISC + 48 + MB * 8;
+    // misc block: mbarrier (8) | tmem base (4) | channel (8) | flag (4) | drill mbarrier (8) |
+    // S_in (MB doubles) | serial-scan state (2 x MB double words)
+    static constexpr uint32_t ST = MISC + 48 + MB * 8;
+    static constexpr uint32_t BYTES = ST + 2 * MB * 8;
     static constexpr uint32_t ALLOC = BYTES + 1024;   // slack for 1024-byte alignment
 };
 
@@ -205,15 +207,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();
         __syncthreads();
 
-        // per-thread carried state for the FP32 scan; warp 0 carries the FP64 one
+        // per-thread carried state for the FP32 scan; the serial scan carries its
+        // double-word state in shared memory (st[0..MB))
         float Sin[MB];
-        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (warp 0)
+        float2 *st = reinterpret_cast<float2 *>(smem + SM::ST);
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = (float)sin_buf[m];
-        if (F64 && warp == 0) {
-            S64a = dw_make(lane < MB ? (float)sin_buf[lane] : 0.f);
-            S64b = dw_make(lane + 32 < MB ? (float)sin_buf[lane + 32] : 0.f);
-        }
+        if (F64 && tid < MB) st[tid] = make_float2((float)sin_buf[tid], 0.f);
         const int64_t ntiles = (c.len + kTileSamples - 1) / kTileSamples;
         const int64_t chunk_base = c.off / kL + ch;
 
@@ -334,20 +334,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 __syncthreads();
             } else {
-                // serial scan by warp 0: S_{c+1} = Abar S_c + E_c, state carried in double words
+                // serial scan S_{c+1} = Abar S_c + E_c by the whole CTA, state carried in
+                // double words
                 float *sbuf = reinterpret_cast<float *>(smem + SM::AHI);
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
                 __syncthreads();
-                if (warp == 0) {
-                    for (int cc = 0; cc < nch; ++cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
-                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
-                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
-                                               S64a, S64b, lane);
-                    }
-                }
+                pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, false, tid, [] { __syncthreads(); });
+                if ((nch & 1) && tid < MB) st[tid] = st[MB + tid];   // outgoing state to st[0]
                 __syncthreads();
 #pragma unroll
                 for (int m = 0; m < MB; ++m) S[m] = tid < nch ? sbuf[tid * MB + m] : 0.f;
@@ -875,7 +869,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         const int ew = warp - kEpiWarp0;       // lane quarter
         const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
         float Sin[MB];
-        dw S64a = dw_make(0.f), S64b = dw_make(0.f);   // double-word scan state (first warp)
+        // the serial scan's double-word state [2][MB], in the warp-total area (which only
+        // the FP32 scan uses)
+        float2 *st = reinterpret_cast<float2 *>(wt);
 #pragma unroll
         for (int m = 0; m < MB; ++m) Sin[m] = 0.f;
         for (int64_t i = 0;; ++i) {
@@ -897,10 +893,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             if (pv.first) {
 #pragma unroll
                 for (int m = 0; m < MB; ++m) Sin[m] = (float)sin[m];
-                if (F64 && ew == 0) {
-                    S64a = dw_make(lane < MB ? (float)sin[lane] : 0.f);
-                    S64b = dw_make(lane + 32 < MB ? (float)sin[lane + 32] : 0.f);
-                }
+                if (F64 && et < MB) st[et] = make_float2((float)sin[et], 0.f);
             }
             float E[MB];
 #pragma unroll
@@ -979,15 +972,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
                 named_sync(kNamedEpi, 128);
-                if (ew == 0) {
-                    for (int cc = 0; cc < nch; ++cc) {
-                        if (lane < MB) sbuf[cc * MB + lane] = dw_to_float(S64a);
-                        if (lane + 32 < MB) sbuf[cc * MB + lane + 32] = dw_to_float(S64b);
-                        pipe::dw_scan_step<MB>(sAt, lane < MB ? xbuf[cc * MB + lane] : 0.f,
-                                               lane + 32 < MB ? xbuf[cc * MB + lane + 32] : 0.f,
-                                               S64a, S64b, lane);
-                    }
-                }
+                pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, false, et,
+                                        [] { named_sync(kNamedEpi, 128); });
+                if ((nch & 1) && et < MB) st[et] = st[MB + et];   // outgoing state to st[0]
                 named_sync(kNamedEpi, 128);
 #pragma unroll
                 for (int m = 0; m < MB; ++m) S[m] = et < nch ? sbuf[et * MB + m] : 0.f;

@@ -82,13 +82,11 @@ __device__ __forceinline__ void matvec(const float *P, const float (&v)[MB], flo
     }
 }
 
-// One step of the serial chunk-state scan, s <- A s + e, in double-word arithmetic on
+// The serial chunk-state scan, s <- A s + e per chunk, in double-word arithmetic on
 // the FP32 pipes (GB300's FP64 pipe is narrow; double words carry about 44 significant
-// bits, far beyond what the FP32 inputs e hold).  One warp: lane r < MB holds state
-// component r in sa and (MB = 64) component r + 32 in sb.  At is the transition stored
-// column-major as (hi, lo) pairs, At[j * MB + m] = A[m][j].  Each product is split
-// exactly (FMA TwoProduct) and its high part added with TwoSum; the low parts are
-// summed plainly and folded in once at the end.
+// bits, far beyond what the FP32 inputs e hold).  Each product is split exactly (FMA
+// TwoProduct) and its high part added with TwoSum; the low parts are summed plainly
+// and folded in once per dot product.
 __device__ __forceinline__ void dw_acc(float &h, float &l, float2 a, float sh, float sl) {
     const float p = a.x * sh;
     float e = fmaf(a.x, sh, -p);
@@ -98,19 +96,56 @@ __device__ __forceinline__ void dw_acc(float &h, float &l, float2 a, float sh, f
     h = s.hi;
     l += s.lo + e;
 }
-template <int MB>
-__device__ __forceinline__ void dw_scan_step(const float2 *__restrict__ At, float ea, float eb,
-                                             dw &sa, dw &sb, int lane) {
-    float ah = ea, al = 0.f, bh = eb, bl = 0.f;
-#pragma unroll 8
-    for (int j = 0; j < MB; ++j) {
-        const float sh = __shfl_sync(0xffffffffu, j < 32 ? sa.hi : sb.hi, j & 31);
-        const float sl = __shfl_sync(0xffffffffu, j < 32 ? sa.lo : sb.lo, j & 31);
-        if (lane < MB) dw_acc(ah, al, At[j * MB + lane], sh, sl);
-        if (lane + 32 < MB) dw_acc(bh, bl, At[j * MB + lane + 32], sh, sl);
+
+// The scan over a tile's chunks by a group of 128 threads: TPR threads per state row
+// (row r = t / TPR) each sum MB / TPR terms of the dot product, the partial double
+// words are combined with shuffles (TwoSum on the high parts), and the state vector
+// moves between two shared-memory buffers, one group barrier per chunk step.
+//   st   : [2][MB] double words; st[0] holds the incoming state, and on return
+//          st[nch & 1] holds the outgoing one
+//   e    : E per chunk [nch][MB] (FP32), s_out : the state entering each chunk
+//   rev  : chunks from last to first (the backward's adjoint scan)
+//   sync : the group's barrier (all 128 threads call this function)
+template <int MB, class Sync>
+__device__ __forceinline__ void dw_scan_group(const float2 *__restrict__ At, float2 *st,
+                                              const float *e, float *s_out, int nch, bool rev,
+                                              int t, Sync sync) {
+    constexpr int TPR = (128 / MB < MB) ? 128 / MB : MB;   // threads per row
+    constexpr int JPT = MB / TPR;                          // terms per thread
+    const int r = t / TPR, part = t % TPR;
+    const bool active = t < MB * TPR;
+    for (int k = 0; k < nch; ++k) {
+        const int cc = rev ? nch - 1 - k : k;
+        const float2 *cur = st + (k & 1) * MB;
+        float2 *nxt = st + ((k + 1) & 1) * MB;
+        float h = 0.f, l = 0.f;
+        if (active) {
+            if (part == 0) {
+                s_out[cc * MB + r] = cur[r].x + cur[r].y;
+                h = e[cc * MB + r];
+            }
+#pragma unroll
+            for (int q = 0; q < JPT; ++q) {
+                const int j = part * JPT + q;
+                const float2 sj = cur[j];
+                dw_acc(h, l, At[j * MB + r], sj.x, sj.y);
+            }
+        }
+        // (every lane of the warp shuffles; rows are TPR-aligned within a warp)
+#pragma unroll
+        for (int off = TPR / 2; off > 0; off >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h, off);
+            const float ol = __shfl_down_sync(0xffffffffu, l, off);
+            const dw sm = two_sum(h, oh);
+            h = sm.hi;
+            l += ol + sm.lo;
+        }
+        if (active && part == 0) {
+            const dw v = fast_two_sum(h, l);
+            nxt[r] = make_float2(v.hi, v.lo);
+        }
+        sync();
     }
-    sa = fast_two_sum(ah, al);
-    sb = fast_two_sum(bh, bl);
 }
 
 // Bounded single-thread mbarrier wait; on timeout (or a peer's abort) raise the abort
