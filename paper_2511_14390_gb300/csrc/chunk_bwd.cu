@@ -9,7 +9,7 @@
 //   2. tcgen05.mma: D[128 x 128] = G [T_g^a | T_h^a]^T -- columns 0..63 of row c are
 //      chunk c's zero-state grad_x, columns 64..127 its zero-state adjoint u;
 //   3. reverse chunk scan of the adjoint state S'_c = u[(c+1)L .. (c+1)L+MB)
-//      (S'_{c-1} = Abar' S'_c + u_zs,c[0:MB]), FP32 Hillis-Steele or serial FP64;
+//      (S'_{c-1} = Abar' S'_c + u_zs,c[0:MB]), FP32 Hillis-Steele or serial double-word;
 //   4. fused epilogue per chunk: u = u_zs + O^u S', grad_x = gx_zs + O^gx S' (stored),
 //      y recomputed from the forward's saved chunk state (or read), and the lag
 //      correlations grad_b[k] += sum u[n+k] x[n], grad_a[k] -= sum u[n+1+k] y[n]
@@ -34,7 +34,7 @@ template <int MB, bool F64, bool READ_Y>
 struct BwdSmem {
     using Tab = ChunkTab<MB>;
     static constexpr int NM = Tab::NBWD;
-    // For MB == L with the FP64 scan, O^u is read from the FP64 transition (Abar' = O^u).
+    // For MB == L with the serial scan, O^u is read from its transition (Abar' = O^u).
     static constexpr bool OU_FROM_AT = F64 && MB == kL;
     static constexpr uint32_t AHI = 0;
     static constexpr uint32_t ALO = AHI + kTileBytes;

@@ -55,8 +55,8 @@ ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt) {
     l.MB = chunk_bucket(Mmax);
     // FP32 powers of the chunk transition stay stable for low orders; above order 4 the
     // transient growth of companion-matrix powers makes an FP32 scan diverge on some
-    // filters, so the automatic choice is the FP64 scan there (and it is the only one
-    // above the FP32 table bucket limit).
+    // filters, so the automatic choice there is the serial scan in double words
+    // (FP64-class accuracy; the only one above the FP32 table bucket limit).
     l.fp64_scan = fp64_scan_opt < 0 ? (Mmax > 4) : (fp64_scan_opt != 0);
     if (l.MB > kMaxF32ScanBucket) l.fp64_scan = true;
     size_t f = 0, b = 0;

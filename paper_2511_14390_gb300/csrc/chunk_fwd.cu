@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     if (cb * 16 + q < MB) E[cb * 16 + q] = v[q];
             }
             float S[MB];
-            // the y buffer: FP64 scan scratch, then y staging (free once the bulk store of
+            // the y buffer: serial-scan scratch, then y staging (free once the bulk store of
             // the previous tile has read it)
             char *lo = smem + PS::YS;
             if constexpr (!F64) {
