@@ -53,7 +53,7 @@ typedef enum {
     DFILT_ERR_UNSUPPORTED = 2,   /* M > 64, unsupported option or device */
     DFILT_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, copy) */
     DFILT_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
-    DFILT_ERR_NUMERIC = 5,       /* optional non-finite output check failed */
+    DFILT_ERR_NUMERIC = 5,       /* non-finite output (dfilt_set_numeric_check) */
     DFILT_ERR_WORKSPACE = 6      /* ws_bytes smaller than dfilt_workspace_size asks */
 } dfilt_status;
 
@@ -193,6 +193,15 @@ dfilt_status dfilt_sync_status(void *stream);
 dfilt_status dfilt_kernel_timing(int enable);
 dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
                                       int *bwd_calls);
+
+/*
+ * Optional output check (off by default).  With enable != 0, every later forward /
+ * backward call (dfilt_forward*, dfilt_backward*) also scans its outputs on `stream`
+ * for non-finite values and records DFILT_ERR_NUMERIC in the device status word
+ * (read by dfilt_sync_status) if it finds one.  Costs one extra read of the outputs.
+ * Applies to calls made after it on any thread of the process.
+ */
+dfilt_status dfilt_set_numeric_check(int enable);
 
 /*
  * Test hook for the bounded device-side waits (no waits are unbounded).

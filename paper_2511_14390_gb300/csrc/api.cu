@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace dfilt;
@@ -20,6 +22,42 @@ int *g_status_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 long long g_wait_limit = kDefaultWaitLimit;
 int g_stall_drill = 0;
+bool g_numeric_check = false;
+
+// NVTX range around an entry point (header-only NVTX: a no-op unless a profiler
+// attaches)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Optional output check: records DFILT_ERR_NUMERIC in the status word when any of the
+// n floats at p is not finite (grid-stride; vector loads where the pointer allows).
+__global__ void check_finite_kernel(const float *__restrict__ p, int64_t n, int *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 4; i += stride) {
+            const float4 v = __ldg(p4 + i);
+            bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+        }
+        for (int64_t i = n / 4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            bad |= !isfinite(__ldg(p + i));
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            bad |= !isfinite(__ldg(p + i));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(status, DFILT_ERR_NUMERIC);
+}
+
+cudaError_t check_finite(const float *p, int64_t n, int *status, int num_sms, cudaStream_t st) {
+    if (!p || n <= 0) return cudaSuccess;
+    const int64_t want = (n / 4 + 255) / 256;
+    const int grid = (int)(want < 4LL * num_sms ? (want > 0 ? want : 1) : 4LL * num_sms);
+    check_finite_kernel<<<grid, 256, 0, st>>>(p, n, status);
+    return cudaGetLastError();
+}
 
 struct DevInfo {
     int *status;
@@ -139,6 +177,22 @@ dfilt_status do_forward(const float *x, const float *b, const float *a, const fl
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
     return cuda_status(launch_chunk_fwd(x, b, a, zi, y, static_cast<float *>(saved), ws, bt, Mmax,
                                         r.fp64_opt, r.precision, di.num_sms, st));
+}
+
+bool numeric_check_on() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_numeric_check;
+}
+
+// the optional finite-output check after a successful enqueue
+dfilt_status checked(dfilt_status s, const float *const *outs, const int64_t *sizes, int nout,
+                     const DevInfo &di, cudaStream_t st) {
+    if (s != DFILT_OK || !numeric_check_on()) return s;
+    for (int k = 0; k < nout; ++k) {
+        const cudaError_t e = check_finite(outs[k], sizes[k], di.status, di.num_sms, st);
+        if (e != cudaSuccess) return DFILT_ERR_CUDA;
+    }
+    return DFILT_OK;
 }
 
 dfilt_status do_backward(const float *gy, const float *x, const float *y, const float *b,
@@ -283,6 +337,7 @@ dfilt_status dfilt_workspace_size_ragged(int64_t B, int64_t total, int Nmax, int
 dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const float *zi,
                            float *y, void *saved, void *ws, size_t ws_bytes, int64_t B, int64_t T,
                            int N, int M, const dfilt_opts *opts, void *stream) {
+    NvtxRange nv("dfilt_forward");
     if (B < 0 || T < 0) return DFILT_ERR_INVALID_ARG;
     dfilt_status s = check_orders(N, M);
     if (s) return s;
@@ -292,14 +347,18 @@ dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const
     DevInfo di;
     if (!dev_info(&di)) return DFILT_ERR_CUDA;
     Batch bt = make_batch(di, nullptr, nullptr, nullptr, B, T, B * T, N, M, N, M);
-    return do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, M, r, di,
-                      static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *outs[1] = {y};
+    const int64_t n[1] = {B * T};
+    return checked(do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, M, r, di, st), outs, n, 1,
+                   di, st);
 }
 
 dfilt_status dfilt_backward(const float *gy, const float *x, const float *y, const float *b,
                             const float *a, const float *zi, const void *saved, float *gx,
                             float *gb, float *ga, float *gzi, void *ws, size_t ws_bytes, int64_t B,
                             int64_t T, int N, int M, const dfilt_opts *opts, void *stream) {
+    NvtxRange nv("dfilt_backward");
     (void)zi;   // carried inside `saved` (chunk 0's entry state) when y is recomputed
     if (B < 0 || T < 0) return DFILT_ERR_INVALID_ARG;
     dfilt_status s = check_orders(N, M);
@@ -310,8 +369,11 @@ dfilt_status dfilt_backward(const float *gy, const float *x, const float *y, con
     DevInfo di;
     if (!dev_info(&di)) return DFILT_ERR_CUDA;
     Batch bt = make_batch(di, nullptr, nullptr, nullptr, B, T, B * T, N, M, N, M);
-    return do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, M, r, di,
-                       static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *outs[4] = {gx, gb, ga, gzi};
+    const int64_t n[4] = {B * T, B * (N + 1), B * M, B * M};
+    return checked(do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, M, r, di, st),
+                   outs, n, 4, di, st);
 }
 
 dfilt_status dfilt_forward_ragged(const float *x, const int64_t *offsets, const int *Ms,
@@ -319,6 +381,7 @@ dfilt_status dfilt_forward_ragged(const float *x, const int64_t *offsets, const 
                                   float *y, void *saved, void *ws, size_t ws_bytes, int64_t B,
                                   int64_t total, int Nmax, int Mmax, const dfilt_opts *opts,
                                   void *stream) {
+    NvtxRange nv("dfilt_forward_ragged");
     if (B < 0 || total < 0) return DFILT_ERR_INVALID_ARG;
     dfilt_status s = check_orders(Nmax, Mmax);
     if (s) return s;
@@ -329,8 +392,11 @@ dfilt_status dfilt_forward_ragged(const float *x, const int64_t *offsets, const 
     DevInfo di;
     if (!dev_info(&di)) return DFILT_ERR_CUDA;
     Batch bt = make_batch(di, offsets, Ms, Ns, B, 0, total, Nmax, Mmax, Nmax, Mmax);
-    return do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, Mmax, r, di,
-                      static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *outs[1] = {y};
+    const int64_t n[1] = {total};
+    return checked(do_forward(x, b, a, zi, y, saved, ws, ws_bytes, bt, Mmax, r, di, st), outs, n,
+                   1, di, st);
 }
 
 dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float *y,
@@ -339,6 +405,7 @@ dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float 
                                    const void *saved, float *gx, float *gb, float *ga, float *gzi,
                                    void *ws, size_t ws_bytes, int64_t B, int64_t total, int Nmax,
                                    int Mmax, const dfilt_opts *opts, void *stream) {
+    NvtxRange nv("dfilt_backward_ragged");
     (void)zi;
     if (B < 0 || total < 0) return DFILT_ERR_INVALID_ARG;
     dfilt_status s = check_orders(Nmax, Mmax);
@@ -350,8 +417,12 @@ dfilt_status dfilt_backward_ragged(const float *gy, const float *x, const float 
     DevInfo di;
     if (!dev_info(&di)) return DFILT_ERR_CUDA;
     Batch bt = make_batch(di, offsets, Ms, Ns, B, 0, total, Nmax, Mmax, Nmax, Mmax);
-    return do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, Mmax, r, di,
-                       static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *outs[4] = {gx, gb, ga, gzi};
+    const int64_t n[4] = {total, B * (Nmax + 1), B * Mmax, B * Mmax};
+    return checked(do_backward(gy, x, y, b, a, saved, gx, gb, ga, gzi, ws, ws_bytes, bt, Mmax, r,
+                               di, st),
+                   outs, n, 4, di, st);
 }
 
 dfilt_status dfilt_sync_status(void *stream) {
@@ -400,6 +471,12 @@ dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bw
     if (bwd_ms) *bwd_ms = ms[1];
     if (bwd_calls) *bwd_calls = n[1];
     return st;
+}
+
+dfilt_status dfilt_set_numeric_check(int enable) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_numeric_check = enable != 0;
+    return DFILT_OK;
 }
 
 dfilt_status dfilt_set_wait_limit(int64_t iters) {

@@ -29,7 +29,7 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
            "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
-           "dfilt_kernel_timing_read"]
+           "dfilt_kernel_timing_read", "dfilt_set_numeric_check"]
 
 
 class DfiltError(RuntimeError):
@@ -84,6 +84,7 @@ def lib():
                                                 i64, i64, i32, i32, PO, P]
             L.dfilt_sync_status.argtypes = [P]
             L.dfilt_set_wait_limit.argtypes = [i64]
+            L.dfilt_set_numeric_check.argtypes = [i32]
             L.dfilt_forward_noalloc.argtypes = [P, P, P, P, P, i64, i64, i32, i32, PO, P]
             L.dfilt_kernel_timing.argtypes = [i32]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
@@ -243,6 +244,11 @@ def dfilt_sync_status(stream=None) -> int:
 
 def dfilt_set_wait_limit(iters: int):
     _check(lib().dfilt_set_wait_limit(int(iters)), "dfilt_set_wait_limit")
+
+
+def dfilt_set_numeric_check(enable: bool):
+    """Scan every later call's outputs for non-finite values (DFILT_ERR_NUMERIC)."""
+    _check(lib().dfilt_set_numeric_check(1 if enable else 0), "dfilt_set_numeric_check")
 
 
 def dfilt_kernel_timing(enable: bool):

@@ -405,6 +405,30 @@ def test_ragged_training_step_graph():
                      "graph")
 
 
+def test_numeric_check():
+    """The optional finite-output check reports a NaN that reaches y and grad_x, stays
+    silent on clean data, and is off by default."""
+    w = inputs.make("biquad_1024x48000", B=4, T=8192 + 100)
+    o = dfilt.make_opts(algo="chunked")
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    xbad = x.clone()
+    xbad[2, 5000] = float("nan")
+    dfilt.dfilt_forward(xbad, b, a, zi, opts=o)
+    assert dfilt.dfilt_sync_status() == 0          # off by default
+    dfilt.dfilt_set_numeric_check(True)
+    try:
+        y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o)
+        dfilt.dfilt_backward(gy, x, None, b, a, zi, saved, opts=o)
+        assert dfilt.dfilt_sync_status() == 0
+        ybad, sbad = dfilt.dfilt_forward(xbad, b, a, zi, opts=o)
+        assert dfilt.STATUS[dfilt.dfilt_sync_status()] == "DFILT_ERR_NUMERIC"
+        gbad = dfilt.dfilt_backward(gy, xbad, None, b, a, zi, sbad, opts=o)
+        assert dfilt.STATUS[dfilt.dfilt_sync_status()] == "DFILT_ERR_NUMERIC"
+    finally:
+        dfilt.dfilt_set_numeric_check(False)
+    assert dfilt.dfilt_sync_status() == 0
+
+
 def test_cuda_graph_capture():
     """Forward + backward captured once in a CUDA graph and replayed."""
     w = inputs.make("biquad_1024x48000", B=16, T=20000)
