@@ -263,6 +263,42 @@ def test_full_size_biquad_sampled():
         assert e.max() < 1e-5, (nm, e.max())
 
 
+@pytest.mark.parametrize("M", [2, 6, 16])
+def test_backward_reads_y(M):
+    """Chunked backward given y instead of the forward's saved chunk states (it runs its
+    own coefficient setup and reads y), for a low, a mid and a high state bucket."""
+    from tol import U32, kappa
+    w = inputs.make("biquad_1024x48000", B=5, T=2 * 8192 + 777, M=M, N=M, seed=70 + M)
+    o = dfilt.make_opts(algo="chunked")
+    x, b, a, zi, gy = dev(w.x), dev(w.b), dev(w.a), dev(w.zi), dev(w.gy)
+    y, saved = dfilt.dfilt_forward(x, b, a, zi, opts=o, want_saved=False)
+    assert saved is None
+    grads = dfilt.dfilt_backward(gy, x, y, b, a, zi, None, opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    yr, gref = oracle_fixed(w)
+    errs = grad_errors(w, y.cpu().numpy(), yr, [g.cpu().numpy() for g in grads], gref)
+    log_errors(f"ready/M{M}", **errs)
+    tol = np.maximum(1e-5, 16 * U32 * kappa(w.a, w.x.shape[1]))
+    for nm in ("y", "gx", "gb", "ga", "gzi"):
+        assert (errs[nm] < tol).all(), (nm, errs[nm], tol)
+
+
+def test_ragged_backward_reads_y():
+    """The ragged chunked backward given y (no saved states): per-bucket setup and
+    y read by the backward kernels."""
+    w = inputs.make_ragged(B=21, T_range=(50, 30000), M_range=(1, 8), seed=31)
+    o = dfilt.make_opts(algo="chunked")
+    dx, dgy = dev(w.x), dev(w.gy)
+    doffs, dMs, dNs = dev(w.offsets), dev(w.Ms), dev(w.Ns)
+    db, da, dzi = dev(w.b), dev(w.a), dev(w.zi)
+    y, saved = dfilt.dfilt_forward_ragged(dx, doffs, dMs, dNs, db, da, dzi, opts=o,
+                                          want_saved=False)
+    assert saved is None
+    g = dfilt.dfilt_backward_ragged(dgy, dx, y, doffs, dMs, dNs, db, da, dzi, None, opts=o)
+    assert dfilt.dfilt_sync_status() == 0
+    _ragged_grads_ok(w, y.cpu().numpy(), w.gy, [t.cpu().numpy() for t in g], "ready")
+
+
 def test_backward_repeatable_with_same_saved():
     """The backward reads its tables from `saved` and clears its own work counter, so a
     second call with the same saved buffer gives bit-identical gradients."""
