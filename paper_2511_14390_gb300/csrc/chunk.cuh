@@ -37,9 +37,11 @@ struct ChunkTab {
     static constexpr size_t B_SCAN = (B_OGX + (size_t)kL * MB * 4 + 15) / 16 * 16;
     // scan block: fp32 powers P[k][MB][MB] (row-major), or for the serial scan the
     // transition as double words (hi, lo float pairs) stored column-major
-    // (At[j][m] = A[m][j])
+    // (At[j][m] = A[m][j]), followed for MB <= 16 by its fourth power in the same form
     static constexpr size_t SCAN_F32 = (size_t)NPOW * MB * MB * 4;
-    static constexpr size_t SCAN_F64 = (size_t)MB * MB * 8;
+    // the serial scan of MB <= 16 is blocked by four chunks and also needs Abar^4
+    static constexpr bool kBlockScan = MB <= 16;
+    static constexpr size_t SCAN_F64 = (size_t)MB * MB * 8 * (kBlockScan ? 2 : 1);
     __host__ __device__ static constexpr size_t scan_bytes(bool f64) { return f64 ? SCAN_F64 : SCAN_F32; }
     __host__ __device__ static constexpr size_t fwd_rec(bool f64) { return (F_SCAN + scan_bytes(f64) + 255) / 256 * 256; }
     __host__ __device__ static constexpr size_t b_coef(bool f64) { return (B_SCAN + scan_bytes(f64) + 15) / 16 * 16; }

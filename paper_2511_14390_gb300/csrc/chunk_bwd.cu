@@ -367,7 +367,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[tid * MB + m] = E[m];
                 __syncthreads();
-                pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, true, tid, [] { __syncthreads(); });
+                if constexpr (Tab::kBlockScan)   // scratch in the A_lo tile behind E
+                    pipe::dw_scan_group_blocked<MB>(sAt, st, xbuf, sbuf, nch, true, tid,
+                                                    [] { __syncthreads(); },
+                                                    reinterpret_cast<float2 *>(smem + SM::ALO + 8192),
+                                                    reinterpret_cast<float2 *>(smem + SM::ALO + 16384));
+                else
+                    pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, true, tid, [] { __syncthreads(); });
                 if ((nch & 1) && tid < MB) st[tid] = st[MB + tid];   // outgoing state to st[0]
                 __syncthreads();
 #pragma unroll

@@ -972,8 +972,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
                 for (int m = 0; m < MB; ++m) xbuf[et * MB + m] = E[m];
                 named_sync(kNamedEpi, 128);
-                pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, false, et,
-                                        [] { named_sync(kNamedEpi, 128); });
+                if constexpr (Tab::kBlockScan)   // scratch in the y buffer's free parts
+                    pipe::dw_scan_group_blocked<MB>(sAt, st, xbuf, sbuf, nch, false, et,
+                                                    [] { named_sync(kNamedEpi, 128); },
+                                                    reinterpret_cast<float2 *>(lo + 8192),
+                                                    reinterpret_cast<float2 *>(lo + 24576));
+                else
+                    pipe::dw_scan_group<MB>(sAt, st, xbuf, sbuf, nch, false, et,
+                                            [] { named_sync(kNamedEpi, 128); });
                 if ((nch & 1) && et < MB) st[et] = st[MB + et];   // outgoing state to st[0]
                 named_sync(kNamedEpi, 128);
 #pragma unroll

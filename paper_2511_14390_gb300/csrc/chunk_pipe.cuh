@@ -148,6 +148,107 @@ __device__ __forceinline__ void dw_scan_group(const float2 *__restrict__ At, flo
     }
 }
 
+// The same scan blocked by four chunks (MB <= 16, where the serial chain's latency is
+// the cost): with E'_k the chunks' inputs in processing order (zero past nch),
+//   pre-pass   F_g = A^3 E'_4g + A^2 E'_4g+1 + A E'_4g+2 + E'_4g+3   (Horner, all
+//              blocks at once: three group-wide steps)
+//   serial     T_0 = s_in, T_{g+1} = A^4 T_g + F_g                   (nch / 4 steps)
+//   post-pass  s_4g = T_g, s_4g+q = A s_4g+q-1 + E'_4g+q-1, q = 1..3  (all blocks at once)
+// At4 (the fourth power) follows At in the scan block.  Scratch: vb [2][32][MB] and
+// tb [33][MB] double words.  Same contract as dw_scan_group.
+template <int MB, class Sync>
+__device__ __forceinline__ void dw_scan_group_blocked(const float2 *__restrict__ At, float2 *st,
+                                                      const float *e, float *s_out, int nch,
+                                                      bool rev, int t, Sync sync, float2 *vb,
+                                                      float2 *tb) {
+    const float2 *__restrict__ At4 = At + MB * MB;
+    const int G = (nch + 3) >> 2;
+    auto chunk = [&](int k) { return rev ? nch - 1 - k : k; };   // processing order -> chunk
+    auto ein = [&](int k, int r) { return k < nch ? e[chunk(k) * MB + r] : 0.f; };
+    float2 *V0 = vb, *V1 = vb + 32 * MB;
+    // pre-pass
+    for (int it = t; it < G * MB; it += 128) V0[it] = make_float2(ein(4 * (it / MB), it % MB), 0.f);
+    sync();
+    for (int q = 1; q < 4; ++q) {
+        const float2 *Vi = (q & 1) ? V0 : V1;
+        float2 *Vo = (q & 1) ? V1 : V0;
+        for (int it = t; it < G * MB; it += 128) {
+            const int g = it / MB, r = it % MB;
+            float h = ein(4 * g + q, r), l = 0.f;
+            const float2 *v = Vi + g * MB;
+#pragma unroll 4
+            for (int j = 0; j < MB; ++j) dw_acc(h, l, At[j * MB + r], v[j].x, v[j].y);
+            const dw o = fast_two_sum(h, l);
+            Vo[it] = make_float2(o.hi, o.lo);
+        }
+        sync();
+    }
+    const float2 *F = V1;   // after the third step
+    // serial pass over the blocks, TPR threads per row as in dw_scan_group
+    constexpr int TPR = (128 / MB < MB) ? 128 / MB : MB;
+    constexpr int JPT = MB / TPR;
+    const int r = t / TPR, part = t % TPR;
+    const bool active = t < MB * TPR;
+    if (t < MB) tb[t] = st[t];
+    sync();
+    for (int g = 0; g < G; ++g) {
+        const float2 *cur = tb + g * MB;
+        float h = 0.f, l = 0.f;
+        if (active) {
+            if (part == 0) {
+                h = F[g * MB + r].x;
+                l = F[g * MB + r].y;
+            }
+#pragma unroll
+            for (int q = 0; q < JPT; ++q) {
+                const int j = part * JPT + q;
+                const float2 sj = cur[j];
+                dw_acc(h, l, At4[j * MB + r], sj.x, sj.y);
+            }
+        }
+#pragma unroll
+        for (int off = TPR / 2; off > 0; off >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h, off);
+            const float ol = __shfl_down_sync(0xffffffffu, l, off);
+            const dw sm = two_sum(h, oh);
+            h = sm.hi;
+            l += ol + sm.lo;
+        }
+        if (active && part == 0) {
+            const dw v = fast_two_sum(h, l);
+            tb[(g + 1) * MB + r] = make_float2(v.hi, v.lo);
+        }
+        sync();
+    }
+    // post-pass: the states inside each block, the outgoing one into st[nch & 1]
+    float2 *out = st + (nch & 1) * MB;
+    for (int it = t; it < G * MB; it += 128) {
+        const int g = it / MB, rr = it % MB;
+        const float2 v = tb[g * MB + rr];
+        V0[it] = v;
+        s_out[chunk(4 * g) * MB + rr] = v.x + v.y;
+    }
+    if ((nch & 3) == 0 && t < MB) out[t] = tb[G * MB + t];
+    sync();
+    for (int q = 1; q < 4; ++q) {
+        const float2 *Vi = (q & 1) ? V0 : V1;
+        float2 *Vo = (q & 1) ? V1 : V0;
+        for (int it = t; it < G * MB; it += 128) {
+            const int g = it / MB, rr = it % MB;
+            const int k = 4 * g + q;
+            float h = ein(k - 1, rr), l = 0.f;
+            const float2 *v = Vi + g * MB;
+#pragma unroll 4
+            for (int j = 0; j < MB; ++j) dw_acc(h, l, At[j * MB + rr], v[j].x, v[j].y);
+            const dw o = fast_two_sum(h, l);
+            Vo[it] = make_float2(o.hi, o.lo);
+            if (k < nch) s_out[chunk(k) * MB + rr] = o.hi + o.lo;
+            if (k == nch) out[rr] = make_float2(o.hi, o.lo);
+        }
+        sync();
+    }
+}
+
 // Bounded single-thread mbarrier wait; on timeout (or a peer's abort) raise the abort
 // flag and record DFILT_ERR_TIMEOUT.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, long long limit,

@@ -111,6 +111,28 @@ __global__ void __launch_bounds__(32 * kSmallWarps) setup_small_kernel(
                 const int j = lane / MB, m = lane % MB;   // At[j][m] = A[m][j]
                 At[lane] = make_float2(sc.ahi[0][m * MB + j], sc.alo[0][m * MB + j]);
             }
+            if constexpr (Tab::kBlockScan) {   // then A^4, by squaring twice
+                __syncwarp();
+                int cur = 0;
+                for (int sq = 0; sq < 2; ++sq) {
+                    if (lane < MB * MB) {
+                        const int i = lane / MB, j = lane % MB;
+                        dw acc = dw_make(0.f);
+#pragma unroll
+                        for (int k = 0; k < MB; ++k)
+                            acc = acc + dw{sc.ahi[cur][i * MB + k], sc.alo[cur][i * MB + k]} *
+                                            dw{sc.ahi[cur][k * MB + j], sc.alo[cur][k * MB + j]};
+                        sc.ahi[cur ^ 1][lane] = acc.hi;
+                        sc.alo[cur ^ 1][lane] = acc.lo;
+                    }
+                    __syncwarp();
+                    cur ^= 1;
+                }
+                if (lane < MB * MB) {
+                    const int j = lane / MB, m = lane % MB;
+                    At[MB * MB + lane] = make_float2(sc.ahi[cur][m * MB + j], sc.alo[cur][m * MB + j]);
+                }
+            }
         } else {
             float *P = reinterpret_cast<float *>(S);
             int cur = 0;
@@ -340,6 +362,24 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
             const double v = sA[m][j];
             const float hi = (float)v;
             At[j * MB + m] = make_float2(hi, (float)(v - (double)hi));
+        }
+        if constexpr (Tab::kBlockScan) {   // then A^4, by squaring twice in FP64
+            for (int sq = 0; sq < 2; ++sq) {
+                double row[MB];
+                for (int j = 0; j < MB; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < MB; ++k) acc += sA[m][k] * sA[k][j];
+                    row[j] = acc;
+                }
+                __syncthreads();
+                for (int j = 0; j < MB; ++j) sA[m][j] = row[j];
+                __syncthreads();
+            }
+            for (int j = 0; j < MB; ++j) {
+                const double v = sA[m][j];
+                const float hi = (float)v;
+                At[MB * MB + j * MB + m] = make_float2(hi, (float)(v - (double)hi));
+            }
         }
     } else {
         float *P = reinterpret_cast<float *>(S);
