@@ -201,7 +201,7 @@ def kernel_name(direction, M):
     if direction == "forward":
         if mb >= 32:
             return f"chunk_fwd_kernel<{mb}, {f64}>"
-        stages = 2 if (mb == 16 and not f64) else 3   # signal stages that fit shared memory
+        stages = 2 if mb == 16 else 3   # signal stages that fit shared memory
         return f"chunk_fwd_ws_kernel<{mb}, {f64}, {stages}>"
     return f"chunk_bwd_ws_kernel<{mb}, {f64}>" if mb <= 8 else f"chunk_bwd_kernel<{mb}, {f64}, 0>"
 
