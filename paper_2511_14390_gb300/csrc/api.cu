@@ -283,6 +283,16 @@ bool api_launch_context(int **status, int *num_sms, long long *wait_limit, int *
     *stall_drill = g_stall_drill;
     return true;
 }
+
+// The finite-output check for an entry point defined outside this file (one output).
+dfilt_status api_check_output(const float *out, int64_t n, cudaStream_t st) {
+    if (!numeric_check_on()) return DFILT_OK;
+    DevInfo di;
+    if (!dev_info(&di)) return DFILT_ERR_CUDA;
+    const float *outs[1] = {out};
+    const int64_t sizes[1] = {n};
+    return checked(DFILT_OK, outs, sizes, 1, di, st);
+}
 }  // namespace dfilt
 
 extern "C" {

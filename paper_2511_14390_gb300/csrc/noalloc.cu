@@ -23,6 +23,8 @@
 namespace dfilt {
 // Launch context shared with the other entry points (defined in api.cu).
 bool api_launch_context(int **status, int *num_sms, long long *wait_limit, int *stall_drill);
+// The optional finite-output check of the other entry points (a no-op while it is off).
+dfilt_status api_check_output(const float *out, int64_t n, cudaStream_t st);
 }  // namespace dfilt
 
 using namespace dfilt;
@@ -95,6 +97,6 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     bt.bwd_stride = 0;
     const cudaError_t e = launch_chunk_fwd(x, b, a, zi, y, nullptr, scratch, bt, M, o.fp64_scan,
                                            o.precision, num_sms, static_cast<cudaStream_t>(stream));
-    if (e == cudaSuccess) return DFILT_OK;
+    if (e == cudaSuccess) return api_check_output(y, B * T, static_cast<cudaStream_t>(stream));
     return e == cudaErrorNotSupported ? DFILT_ERR_UNSUPPORTED : DFILT_ERR_CUDA;
 }

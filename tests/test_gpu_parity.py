@@ -460,6 +460,12 @@ def test_numeric_check():
         assert dfilt.STATUS[dfilt.dfilt_sync_status()] == "DFILT_ERR_NUMERIC"
         gbad = dfilt.dfilt_backward(gy, xbad, None, b, a, zi, sbad, opts=o)
         assert dfilt.STATUS[dfilt.dfilt_sync_status()] == "DFILT_ERR_NUMERIC"
+        # the allocation-free forward applies the same check
+        yn = torch.empty_like(x)
+        dfilt.dfilt_forward_noalloc(x, b, a, zi, y=yn, opts=o)
+        assert dfilt.dfilt_sync_status() == 0
+        dfilt.dfilt_forward_noalloc(xbad, b, a, zi, y=yn, opts=o)
+        assert dfilt.STATUS[dfilt.dfilt_sync_status()] == "DFILT_ERR_NUMERIC"
     finally:
         dfilt.dfilt_set_numeric_check(False)
     assert dfilt.dfilt_sync_status() == 0
