@@ -12,7 +12,9 @@ Digital Filters"):
   in the TDF-II (SciPy ``lfilter``) convention; a second formulation (initial
   state injected into the all-pole input) cross-checks it;
 * backward -- the reverse-time adjoint of Sec. 3.1 (Eqs. dLdz, dLdx, dLdvBA, with
-  the boundary condition of App. A) written as scalar difference equations.
+  the boundary condition of App. A) written as scalar difference equations;
+* forward mode (JVP) -- the TDF-II recursion carried with its derivative along
+  tangents of every input (the forward-mode derivative Sec. 5 mentions).
 
 The heavy loops live in ``dfilt_oracle.c`` (plain C, FP64, OpenMP over channels);
 ``pyref.py`` holds a pure-Python FP64 restatement for tiny cases, ``statespace.py``
@@ -69,6 +71,8 @@ def _bind(lib):
     lib.oracle_forward_ragged.restype = i32
     lib.oracle_backward_ragged.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, i64, i32, i32, i32]
     lib.oracle_backward_ragged.restype = i32
+    lib.oracle_jvp.argtypes = [P, P, P, P, P, P, P, P, P, P, i64, i64, i32, i32, i32]
+    lib.oracle_jvp.restype = i32
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = i32
     return lib
@@ -133,6 +137,26 @@ def backward(gy, x, y, b, a, *, nthreads: int = 0, lib=None):
     gx, gb, ga, gzi = backward_ragged(gy.reshape(-1), x.reshape(-1), y.reshape(-1),
                                       offs, Ms, Ns, b, a, nthreads=nthreads, lib=lib)
     return gx.reshape(B, T), gb, ga, gzi
+
+
+def jvp(x, b, a, zi=None, dx=None, db=None, da=None, dzi=None, *, nthreads: int = 0,
+        lib=None):
+    """(y[B,T], dy[B,T]) in FP64: the forward and its directional derivative along the
+    tangents (dx, db, da, dzi) -- forward mode, the TDF-II recursion differentiated
+    step by step (Sec. 5 notes forward mode follows like the reverse mode).  A tangent
+    left as None is zero."""
+    lib = lib or load()
+    x, b, a = _f64(x), _f64(b), _f64(a)
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    zi, dx, db, da, dzi = (None if v is None else _f64(v) for v in (zi, dx, db, da, dzi))
+    y = np.zeros_like(x)
+    dy = np.zeros_like(x)
+    rc = lib.oracle_jvp(_ptr(x), _ptr(b), _ptr(a), _ptr(zi), _ptr(dx), _ptr(db), _ptr(da),
+                        _ptr(dzi), _ptr(y), _ptr(dy), B, T, N, M, int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle jvp: allocation failed")
+    return y, dy
 
 
 # ----------------------------------------------------------------------------

@@ -195,5 +195,77 @@ int oracle_backward_ragged(const double *g, const double *x, const double *y,
     return fail ? -1 : 0;
 }
 
+/*
+ * Forward mode (JVP): the directional derivative of the forward along tangents
+ * (dx, db, da, dzi), for the forward-mode derivative the paper notes can be derived
+ * the same way as the reverse mode (Sec. 5).  Written as the TDF-II state recursion
+ * of fwd_tdf2 carried together with its derivative (dual numbers): every primal
+ * assignment is followed by its product-rule derivative,
+ *     y[n]   = b_0 x[n] + s_0
+ *     dy[n]  = db_0 x[n] + b_0 dx[n] + ds_0
+ *     s_k   <- s_{k+1} + b_{k+1} x[n] - a_{k+1} y[n]
+ *     ds_k  <- ds_{k+1} + db_{k+1} x[n] + b_{k+1} dx[n] - da_{k+1} y[n] - a_{k+1} dy[n]
+ * starting from s = zi, ds = dzi.  A NULL tangent is zero.  s, ds are caller
+ * scratch [M].
+ */
+static void jvp_tdf2(const double *x, const double *b, const double *a, const double *zi,
+                     const double *dx, const double *db, const double *da, const double *dzi,
+                     double *y, double *dy, int64_t T, int N, int M, double *s, double *ds)
+{
+    for (int k = 0; k < M; ++k) {
+        s[k] = zi ? zi[k] : 0.0;
+        ds[k] = dzi ? dzi[k] : 0.0;
+    }
+    for (int64_t n = 0; n < T; ++n) {
+        const double xn = x[n];
+        const double dxn = dx ? dx[n] : 0.0;
+        const double yn = xn * b[0] + s[0];
+        double dyn = b[0] * dxn + ds[0];
+        if (db) dyn += db[0] * xn;
+        for (int k = 0; k < M; ++k) {
+            const double nxt = (k + 1 < M) ? s[k + 1] : 0.0;
+            const double dnxt = (k + 1 < M) ? ds[k + 1] : 0.0;
+            s[k] = nxt + xn * bcoef(b, N, k + 1) - yn * a[k];
+            double d = dnxt + bcoef(b, N, k + 1) * dxn - a[k] * dyn;
+            if (db) d += bcoef(db, N, k + 1) * xn;
+            if (da) d -= da[k] * yn;
+            ds[k] = d;
+        }
+        y[n] = yn;
+        dy[n] = dyn;
+    }
+}
+
+/*
+ * Fixed-shape batch driver of jvp_tdf2: channel i owns x + i*T (likewise dx, y, dy)
+ * and coefficient rows b + i*(N+1), a + i*M, zi + i*M (and the tangents').  Any of
+ * zi, dx, db, da, dzi may be NULL.  Returns 0, or -1 on an allocation failure.
+ */
+int oracle_jvp(const double *x, const double *b, const double *a, const double *zi,
+               const double *dx, const double *db, const double *da, const double *dzi,
+               double *y, double *dy, int64_t B, int64_t T, int N, int M, int nthreads)
+{
+    int fail = 0;
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        double *s = (double *)malloc(sizeof(double) * 2 * (size_t)(M > 0 ? M : 1));
+        if (!s) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < B; ++i) {
+            if (!s) continue;
+            const int64_t o = i * T;
+            jvp_tdf2(x + o, b + i * (N + 1), a + i * M, zi ? zi + i * M : NULL,
+                     dx ? dx + o : NULL, db ? db + i * (N + 1) : NULL, da ? da + i * M : NULL,
+                     dzi ? dzi + i * M : NULL, y + o, dy + o, T, N, M, s, s + (M > 0 ? M : 1));
+        }
+        free(s);
+    }
+    return fail ? -1 : 0;
+}
+
 /* Threads an OpenMP region actually gets (for reporting the CPU baseline). */
 int oracle_max_threads(void) { return pick_threads(0); }

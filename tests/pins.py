@@ -244,9 +244,68 @@ def pin_statespace(lib=None):
             assert _rel(got, ref) < 1e-11, ("state space", nm, M, N)
 
 
+def pin_jvp_single_pole(lib=None):
+    """Forward mode, closed form.  One pole, impulse input, x = delta, zero numerator
+    tail: y[n] = b0 (-a)^n, so dy/da = -n b0 (-a)^(n-1), dy/db0 = (-a)^n, and the
+    initial state's tangent reaches the output as dzi (-a)^n (TDF-II, M = 1)."""
+    T, b0, a1 = 40, 0.7, -0.93
+    x = np.zeros((1, T)); x[0, 0] = 1.0
+    b, a, zi = np.array([[b0, 0.0]]), np.array([[a1]]), np.zeros((1, 1))
+    n = np.arange(T, dtype=np.float64)
+    p = (-a1) ** n
+    dp = np.concatenate([[0.0], n[1:] * (-a1) ** (n[1:] - 1)])   # d/dr of r^n at r = -a1
+    one = np.ones((1, 1))
+    y, dy = oracle.jvp(x, b, a, zi, da=one, lib=lib)
+    assert _rel(y[0], b0 * p) < 1e-14, "jvp primal"
+    assert _rel(dy[0], -b0 * dp) < 1e-13, "jvp d/da"
+    _, dy = oracle.jvp(x, b, a, zi, db=np.array([[1.0, 0.0]]), lib=lib)
+    assert _rel(dy[0], p) < 1e-14, "jvp d/db0"
+    _, dy = oracle.jvp(x, b, a, zi, db=np.array([[0.0, 1.0]]), lib=lib)
+    assert _rel(dy[0], np.concatenate([[0.0], p[:-1]])) < 1e-14, "jvp d/db1"
+    _, dy = oracle.jvp(x, b, a, zi, dzi=2.5 * one, lib=lib)
+    assert _rel(dy[0], 2.5 * p) < 1e-14, "jvp d/dzi"
+    _, dy = oracle.jvp(x, b, a, zi, dx=x, lib=lib)
+    assert _rel(dy[0], b0 * p) < 1e-14, "jvp d/dx"
+
+
+def pin_jvp_finite_differences(lib=None):
+    """Forward mode against FP64 central differences of the forward along one joint
+    direction in (x, b, a, zi)."""
+    rng = np.random.default_rng(25)
+    for M, N, T in [(2, 2, 64), (5, 3, 48), (1, 0, 30), (4, 4, 3)]:
+        b, a = _random_filter(rng, M, N, rmax=0.8)
+        x = rng.standard_normal(T); zi = rng.standard_normal(M)
+        dx, db, da, dz = (rng.standard_normal(v.shape) for v in (x, b, a, zi))
+        h = 1e-6
+        f = lambda s: oracle.forward((x + s * dx)[None], (b + s * db)[None], (a + s * da)[None],
+                                     (zi + s * dz)[None], lib=lib)[0]
+        fd = (f(h) - f(-h)) / (2 * h)
+        y, dy = oracle.jvp(x[None], b[None], a[None], zi[None], dx[None], db[None], da[None],
+                           dz[None], lib=lib)
+        assert _rel(y[0], f(0.0)) < 1e-14, ("jvp primal", M, N)
+        assert _rel(dy[0], fd) < 1e-7, ("jvp fd", M, N)
+
+
+def pin_jvp_adjoint(lib=None):
+    """Forward and reverse mode are transposes of one linear map:
+    <g, J d> = <J^T g, d> with J^T g the backward's (grad_x, grad_b, grad_a, grad_zi)."""
+    rng = np.random.default_rng(26)
+    for M, N, T in [(2, 2, 200), (6, 4, 77), (3, 0, 5)]:
+        b, a = _random_filter(rng, M, N)
+        x = rng.standard_normal((1, T)); zi = rng.standard_normal((1, M))
+        g = rng.standard_normal((1, T))
+        dx, db, da, dz = (rng.standard_normal(v.shape) for v in (x, b[None], a[None], zi))
+        y, dy = oracle.jvp(x, b[None], a[None], zi, dx, db, da, dz, lib=lib)
+        gx, gb, ga, gz = oracle.backward(g, x, y, b[None], a[None], lib=lib)
+        lhs = float((g * dy).sum())
+        rhs = float((gx * dx).sum() + (gb * db).sum() + (ga * da).sum() + (gz * dz).sum())
+        assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + abs(rhs) + 1.0), ("jvp adjoint", M, N)
+
+
 ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfilter,
             pin_injection_form, pin_linearity_shift, pin_exact_forward,
-            pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace]
+            pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace,
+            pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint]
 
 
 def run_all(lib=None):

@@ -33,6 +33,12 @@ MUTATIONS = [
     ("grad_a sign", "ga[k - 1] = -acc;", "ga[k - 1] = acc;"),
     ("grad_a correlates x", "acc += u[n] * y[n - k];", "acc += u[n] * x[n - k];"),
     ("grad_zi index", "gzi[k] = (k < T) ? u[k] : 0.0;", "gzi[k] = (k + 1 < T) ? u[k + 1] : 0.0;"),
+    ("jvp feedback on the primal", "- a[k] * dyn;", "- a[k] * yn;"),
+    ("jvp denominator tangent sign", "if (da) d -= da[k] * yn;", "if (da) d += da[k] * yn;"),
+    ("jvp numerator tangent index", "if (db) d += bcoef(db, N, k + 1) * xn;",
+     "if (db) d += bcoef(db, N, k) * xn;"),
+    ("jvp drops the state tangent", "ds[k] = dzi ? dzi[k] : 0.0;", "ds[k] = 0.0;"),
+    ("jvp drops db_0", "if (db) dyn += db[0] * xn;", "if (db) dyn += 0.0 * xn;"),
 ]
 
 
