@@ -43,6 +43,7 @@ def args_():
     p.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel leg")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-jvp", action="store_true", help="skip the forward-mode (JVP) leg")
     p.add_argument("--graph", action="store_true",
                    help="also time the step captured in a CUDA graph (launch-bound workloads)")
     p.add_argument("--channels", type=int, default=0,
@@ -397,6 +398,92 @@ def main():
                "ms_fwd": sf, "ms_bwd": sb}
         del sst
 
+    # Forward mode (Jacobian-vector product) on the same workload, tangents of every
+    # input: the call runs the input step (v from x, dx, y and the coefficient tangents)
+    # and then the library's forward with numerator [1] on v.  The forward step alone is
+    # timed on the same data, so the input step's time is the difference.
+    jvp = None
+    if not a.no_jvp and algo == "chunked":
+        o = st["o"]
+        rng = np.random.default_rng(7)
+        tdx = dev(rng.standard_normal((B, T), dtype=np.float32))
+        tdb = dev((0.1 * rng.standard_normal(w.b.shape)).astype(np.float32))
+        tda = dev((0.1 * rng.standard_normal(w.a.shape)).astype(np.float32))
+        tdz = dev(rng.standard_normal(w.a.shape).astype(np.float32))
+        nws = dfilt.dfilt_jvp_workspace_size(B, T, N, M, o)
+        jws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+        dyj = torch.empty_like(x)
+        fws1 = dfilt.dfilt_workspace_size(B, T, 0, M, o)[0]
+        w1 = torch.empty(max(fws1, 16), dtype=torch.uint8, device="cuda")
+        ones = torch.ones((B, 1), dtype=torch.float32, device="cuda")
+        vview = jws[: B * T * 4].view(torch.float32)
+        dy1 = torch.empty_like(x)
+
+        def jvp_call():
+            dfilt._check(L.dfilt_jvp(P(x), P(st["y"]), P(b), P(av), P(tdx), P(tdb), P(tda),
+                                     P(tdz), P(dyj), P(jws), nws, B, T, N, M, ctypes.byref(o),
+                                     sptr), "dfilt_jvp")
+
+        def fwd1_call():
+            dfilt._check(L.dfilt_forward(P(vview), P(ones), P(av), P(tdz), P(dy1), None, P(w1),
+                                         fws1, B, T, 0, M, ctypes.byref(o), sptr), "dfilt_forward")
+
+        def time_calls(fn, n):
+            for _ in range(max(3, a.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            barrier()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(n):
+                fn()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            return maxrank(t0.elapsed_time(t1) / n)
+
+        nj = max(3, min(200, a.steps))
+        ms_j = time_calls(jvp_call, nj)
+        ms_f1 = time_calls(fwd1_call, nj)
+        jvp_call()          # dyj of the tangents, for the accuracy check below
+        status = dfilt.dfilt_sync_status()
+        if status != 0:
+            raise RuntimeError(f"device status {dfilt.STATUS[status]}")
+        hbm_j, src_j = peaks()
+        ms_in = ms_j - ms_f1
+        jvp = {"value": samples_all / (ms_j / 1e3) / 1e9, "unit": UNIT, "ms_per_call": ms_j,
+               "calls": nj, "ms_forward_step": ms_f1, "ms_input_step": ms_in,
+               "input_step_roofline": {
+                   "bound": "hbm", "unit": "GB/s", "peak": hbm_j,
+                   "achieved": 16.0 * B * T / (ms_in / 1e3) / 1e9 if ms_in > 0 else None,
+                   "frac": (16.0 * B * T / (ms_in / 1e3) / 1e9 / hbm_j) if ms_in > 0 else None,
+                   "algorithmic_bytes": 16.0 * B * T,
+                   "kernel": "jvp_input_kernel (x, dx, y read, v written; time = call - "
+                             "forward step)", "peak_source": src_j},
+               "call_roofline_frac": 16.0 * B * T / (ms_j / 1e3) / 1e9 / hbm_j,
+               "gpu_launches_per_call": 3}
+        if rank == 0:
+            import oracle
+            idx = np.linspace(0, B - 1, 8).astype(int)
+            tg = [t.cpu().numpy()[idx] for t in (tdx, tdb, tda, tdz)]
+            _, dref = oracle.jvp(w.x[idx], w.b[idx], w.a[idx], w.zi[idx], *tg)
+            got = dyj.cpu().numpy()[idx].astype(np.float64)
+            jvp["rel_err_vs_fp64"] = float((np.abs(got - dref).max(-1)
+                                            / np.abs(dref).max(-1)).max())
+            if world == 1 and not a.no_cpu:
+                sub = max(1, min(B, 64))
+                t0, reps = time.perf_counter(), 0
+                tgs = [t.cpu().numpy()[:sub] for t in (tdx, tdb, tda, tdz)]
+                while time.perf_counter() - t0 < 2.0 or reps == 0:
+                    oracle.jvp(w.x[:sub], w.b[:sub], w.a[:sub], w.zi[:sub], *tgs)
+                    reps += 1
+                dt = time.perf_counter() - t0
+                jvp["cpu_baseline"] = {"value": sub * T * reps / dt / 1e9, "unit": UNIT,
+                                       "cores": oracle.max_threads(), "kind": "oracle",
+                                       "sample": f"{sub} of the {B} channels, FP64 JVP, "
+                                                 f"repeated {reps}x over {dt:.1f} s"}
+        del jws, w1, dy1, dyj, tdx
+
     # End to end through the public API from pinned host buffers, pipelined across steps
     # the way a streaming caller would run it: step k's inputs are copied host -> device
     # on one stream while step k-1 computes and step k-2's results are copied back on a
@@ -512,6 +599,7 @@ def main():
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
                          else "fallback (6.8 TB/s)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "graph_replay": graph,
+            "jvp": jvp,
             # per step: forward = setup + main kernel, backward = main kernel (its work
             # counter is cleared by a memset)
             "gpu_launches": 3 * a.steps if algo == "chunked" else 2 * a.steps,

@@ -237,6 +237,32 @@ dfilt_status dfilt_forward_noalloc(const float *x, const float *b, const float *
                                    const float *zi, float *y, int64_t B, int64_t T, int N, int M,
                                    const dfilt_opts *opts, void *stream);
 
+/*
+ * Forward mode (Jacobian-vector product) of a fixed-shape batch: the directional
+ * derivative dy of the forward's output along tangents of its inputs.  The paper
+ * derives the reverse mode (Sec. 3.1) and notes that forward mode follows the same
+ * way (Sec. 5); differentiating A(z) y = B(z) x (+ zi injected) gives
+ *     v[n] = sum_{k=0..N} (b_k dx[n-k] + db_k x[n-k]) - sum_{k=1..M} da_k y[n-k]
+ *     dy   = the all-pole filter 1/A(z) applied to v, TDF-II initial state dzi
+ * (x, dx, y zero at negative times).
+ *   x   [B,T]      the forward's input (may be NULL when db is NULL)
+ *   y   [B,T]      the forward's output (may be NULL when da is NULL)
+ *   b   [B,N+1]    numerator (may be NULL when dx is NULL)
+ *   a   [B,M]      denominator a_1..a_M (required)
+ *   dx [B,T], db [B,N+1], da [B,M], dzi [B,M]   tangents; NULL = zero
+ *   dy  [B,T]      output (must not alias any input)
+ *   ws, ws_bytes   workspace of at least dfilt_jvp_workspace_size bytes, 16-byte
+ *                  aligned (it holds v, so it grows with B*T)
+ * opts selects the algorithm of the recursion as for dfilt_forward; the optional
+ * finite-output check applies to dy.  Asynchronous on `stream` like every entry point.
+ */
+dfilt_status dfilt_jvp_workspace_size(int64_t B, int64_t T, int N, int M,
+                                      const dfilt_opts *opts, size_t *ws_bytes);
+dfilt_status dfilt_jvp(const float *x, const float *y, const float *b, const float *a,
+                       const float *dx, const float *db, const float *da, const float *dzi,
+                       float *dy, void *ws, size_t ws_bytes, int64_t B, int64_t T, int N, int M,
+                       const dfilt_opts *opts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
            "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
-           "dfilt_kernel_timing_read", "dfilt_set_numeric_check"]
+           "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
+           "dfilt_jvp"]
 
 
 class DfiltError(RuntimeError):
@@ -87,6 +88,8 @@ def lib():
             L.dfilt_set_numeric_check.argtypes = [i32]
             L.dfilt_forward_noalloc.argtypes = [P, P, P, P, P, i64, i64, i32, i32, PO, P]
             L.dfilt_kernel_timing.argtypes = [i32]
+            L.dfilt_jvp_workspace_size.argtypes = [i64, i64, i32, i32, PO, Psz]
+            L.dfilt_jvp.argtypes = [P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32, i32, PO, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
             L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
             for name in EXPORTS:
@@ -235,6 +238,32 @@ def dfilt_forward_noalloc(x, b, a, zi=None, *, y, opts: Opts | None = None, stre
                                        b.shape[1] - 1, a.shape[1], ctypes.byref(o),
                                        _stream(stream)), "dfilt_forward_noalloc")
     return y
+
+
+def dfilt_jvp_workspace_size(B, T, N, M, opts: Opts | None = None) -> int:
+    o = opts or make_opts()
+    w = ctypes.c_size_t()
+    _check(lib().dfilt_jvp_workspace_size(B, T, N, M, ctypes.byref(o), ctypes.byref(w)),
+           "dfilt_jvp_workspace_size")
+    return w.value
+
+
+def dfilt_jvp(x, y, b, a, dx=None, db=None, da=None, dzi=None, *, opts: Opts | None = None,
+              dy=None, ws=None, stream=None):
+    """Forward-mode derivative dy[B,T] of the forward along the tangents (dx, db, da,
+    dzi); a tangent left as None is zero.  x, y are the forward's input and output."""
+    x, y, b, a = _f32(x, "x"), _f32(y, "y"), _f32(b, "b"), _f32(a, "a")
+    dx, db, da, dzi = _f32(dx, "dx"), _f32(db, "db"), _f32(da, "da"), _f32(dzi, "dzi")
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    o = opts or make_opts()
+    nws = dfilt_jvp_workspace_size(B, T, N, M, o)
+    dy = torch.empty_like(x) if dy is None else dy
+    ws = _buf(nws, x.device) if ws is None else ws
+    _check(lib().dfilt_jvp(_ptr(x), _ptr(y), _ptr(b), _ptr(a), _ptr(dx), _ptr(db), _ptr(da),
+                           _ptr(dzi), _ptr(dy), _ptr(ws), ws.numel(), B, T, N, M,
+                           ctypes.byref(o), _stream(stream)), "dfilt_jvp")
+    return dy
 
 
 def dfilt_sync_status(stream=None) -> int:

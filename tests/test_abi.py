@@ -78,3 +78,30 @@ def test_missing_pointers_rejected(L):
     o = dfilt.make_opts()
     assert L.dfilt_forward(None, None, None, None, None, None, None, 0, 4, 10, 0, 2,
                            ctypes.byref(o), None) == 1
+
+
+def test_jvp_host_checks(L):
+    """Forward-mode entry point: workspace size (holds v, B*T floats, plus the forward's
+    workspace), argument errors and the empty batch, all decided on the host."""
+    o = dfilt.make_opts()
+    nws = dfilt.dfilt_jvp_workspace_size(1024, 48000, 2, 2, o)
+    f, _, _ = dfilt.dfilt_workspace_size(1024, 48000, 0, 2, o)
+    assert nws >= 1024 * 48000 * 4 + 1024 * 4 + f
+    sz = ctypes.c_size_t()
+    for B, T, N, M, code in [(4, 10, 0, 65, 2), (4, 10, 3, 2, 1), (4, 10, 0, 0, 1),
+                             (-1, 10, 0, 2, 1), (4, -5, 0, 2, 1)]:
+        assert L.dfilt_jvp_workspace_size(B, T, N, M, ctypes.byref(o), ctypes.byref(sz)) == code
+        assert L.dfilt_jvp(None, None, None, None, None, None, None, None, None, None, 0, B, T,
+                           N, M, ctypes.byref(o), None) == code
+    # missing a / dy, a tangent without the input it multiplies, too small a workspace
+    assert L.dfilt_jvp(None, None, None, None, None, None, None, None, None, None, 0, 4, 10, 2,
+                       2, ctypes.byref(o), None) == 1
+    fake = ctypes.c_void_p(4096)    # never dereferenced: the call fails before any launch
+    assert L.dfilt_jvp(None, None, None, fake, fake, None, None, None, fake, fake, 1 << 30, 4,
+                       10, 2, 2, ctypes.byref(o), None) == 1          # dx without b
+    assert L.dfilt_jvp(None, None, fake, fake, None, None, fake, None, fake, fake, 1 << 30, 4,
+                       10, 2, 2, ctypes.byref(o), None) == 1          # da without y
+    assert L.dfilt_jvp(None, None, fake, fake, None, None, None, None, fake, fake, 16, 4, 10, 2,
+                       2, ctypes.byref(o), None) == 6                 # workspace too small
+    assert L.dfilt_jvp(None, None, None, None, None, None, None, None, None, None, 0, 0, 10, 2,
+                       2, ctypes.byref(o), None) == 0                 # empty batch
