@@ -10,8 +10,8 @@
 // (causal sums: x, dx, y are zero at negative times; y is the forward's output, which
 // already carries the zi response).  This is the forward-mode counterpart of the
 // reverse-mode gradients of Sec. 3.1, which Sec. 5 notes follows the same way.  The
-// call runs two steps: `jvp_input_kernel` forms v (a short FIR over three signals,
-// HBM-bound: 12 bytes read and 4 written per sample), then the library's own forward
+// call runs two steps: `jvp_input_kernel` (or its low-order streaming form) forms v (a
+// short FIR over three signals, HBM-bound: 12 bytes read and 4 written per sample), then the library's own forward
 // filters v with numerator [1] and state dzi, so the recursion runs on the chunked
 // tensor-core path (or the sequential kernel, as opts select).
 #include <nvtx3/nvToolsExt.h>
@@ -95,6 +95,78 @@ jvp_input_kernel(const float *__restrict__ x, const float *__restrict__ dx,
     }
 }
 
+// Low orders (max(N, M) <= 4) on rows of a multiple of 4 samples with 16-byte aligned
+// signals: a streaming kernel without shared memory.  Grid x covers the quads of a row,
+// grid y strides over rows; thread q forms the 4 outputs of quad q of its row from one
+// float4 load per signal, and the quad before it (the window's history) comes from the
+// neighbouring lane by shuffle (lane 0 loads it; it is zero at a row's start).  Same
+// terms in the same order as jvp_input_kernel.  Lanes past a row's end mirror its last
+// quad and store nothing, so the shuffles always run with the full warp.
+__device__ __forceinline__ float4 shfl_up4(float4 a) {
+    a.x = __shfl_up_sync(0xffffffffu, a.x, 1);
+    a.y = __shfl_up_sync(0xffffffffu, a.y, 1);
+    a.z = __shfl_up_sync(0xffffffffu, a.z, 1);
+    a.w = __shfl_up_sync(0xffffffffu, a.w, 1);
+    return a;
+}
+
+__global__ void __launch_bounds__(kJvpThreads, 4)
+jvp_input_vec4_kernel(const float4 *__restrict__ x, const float4 *__restrict__ dx,
+                      const float4 *__restrict__ y, const float *__restrict__ b,
+                      const float *__restrict__ db, const float *__restrict__ da,
+                      float4 *__restrict__ v, float *__restrict__ ones, int64_t B, int64_t T,
+                      int N, int M) {
+    const int64_t nqr = T / 4;                           // quads per row
+    const int64_t qr = (int64_t)blockIdx.x * kJvpThreads + threadIdx.x;
+    const bool live = qr < nqr;
+    const int64_t qc = live ? qr : nqr - 1;
+    const int lane = threadIdx.x & 31;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    __shared__ float cb[5], cdb[5], cda[5];
+    for (int64_t row = blockIdx.y; row < B; row += gridDim.y) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ones[row] = 1.0f;
+        const int64_t qq = row * nqr + qc;
+        __syncthreads();                                 // previous row's coefficients read
+        if (threadIdx.x < 5) {
+            const int k = threadIdx.x;
+            cb[k] = (dx && k <= N) ? __ldg(b + row * (N + 1) + k) : 0.0f;
+            cdb[k] = (db && k <= N) ? __ldg(db + row * (N + 1) + k) : 0.0f;
+            cda[k] = (da && k >= 1 && k <= M) ? __ldg(da + row * M + k - 1) : 0.0f;
+        }
+        const float4 cx = db ? __ldcs(x + qq) : z4;
+        const float4 cdx = dx ? __ldcs(dx + qq) : z4;
+        const float4 cy = da ? __ldcs(y + qq) : z4;
+        float4 px = shfl_up4(cx), pdx = shfl_up4(cdx), py = shfl_up4(cy);
+        if (qc == 0) {
+            px = pdx = py = z4;
+        } else if (lane == 0) {
+            px = db ? __ldg(x + qq - 1) : z4;
+            pdx = dx ? __ldg(dx + qq - 1) : z4;
+            py = da ? __ldg(y + qq - 1) : z4;
+        }
+        __syncthreads();                                 // this row's coefficients written
+        const float xw[8] = {px.x, px.y, px.z, px.w, cx.x, cx.y, cx.z, cx.w};
+        const float dxw[8] = {pdx.x, pdx.y, pdx.z, pdx.w, cdx.x, cdx.y, cdx.z, cdx.w};
+        const float yw[8] = {py.x, py.y, py.z, py.w, cy.x, cy.y, cy.z, cy.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 + j;
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k <= N) acc = fmaf(cb[k], dxw[c - k], fmaf(cdb[k], xw[c - k], acc));
+#pragma unroll
+            for (int k = 1; k < 5; ++k)
+                if (k <= M) acc = fmaf(-cda[k], yw[c - k], acc);
+            o[j] = acc;
+        }
+        if (live) v[qq] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+bool aligned16p(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 // Workspace layout: v [B*T floats] | ones [B floats] | the forward's workspace.
 struct JvpLayout {
     size_t v, ones, fwd, fwd_bytes, total;
@@ -151,11 +223,23 @@ extern "C" dfilt_status dfilt_jvp(const float *x, const float *y, const float *b
     float *v = reinterpret_cast<float *>(w + L.v);
     float *ones = reinterpret_cast<float *>(w + L.ones);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t segs = (T + kJvpSeg - 1) / kJvpSeg;
-    const int64_t blocks = B * segs;
-    if (blocks > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
-    jvp_input_kernel<<<(unsigned)blocks, kJvpThreads, 0, st>>>(x, dx, y, b, db, da, v, ones, B,
-                                                                T, N, M, segs);
+    const bool vec4 = (N > M ? N : M) <= 4 && T % 4 == 0 && aligned16p(x) && aligned16p(dx) &&
+                      aligned16p(y) && aligned16p(v);
+    if (vec4) {
+        const int64_t bx = (T / 4 + kJvpThreads - 1) / kJvpThreads;
+        if (bx > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
+        const dim3 grid((unsigned)bx, (unsigned)(B < 65535 ? B : 65535));
+        jvp_input_vec4_kernel<<<grid, kJvpThreads, 0, st>>>(
+            reinterpret_cast<const float4 *>(x), reinterpret_cast<const float4 *>(dx),
+            reinterpret_cast<const float4 *>(y), b, db, da, reinterpret_cast<float4 *>(v), ones,
+            B, T, N, M);
+    } else {
+        const int64_t segs = (T + kJvpSeg - 1) / kJvpSeg;
+        const int64_t blocks = B * segs;
+        if (blocks > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
+        jvp_input_kernel<<<(unsigned)blocks, kJvpThreads, 0, st>>>(x, dx, y, b, db, da, v, ones,
+                                                                    B, T, N, M, segs);
+    }
     if (cudaGetLastError() != cudaSuccess) return DFILT_ERR_CUDA;
     return dfilt_forward(v, ones, a, dzi, dy, nullptr, w + L.fwd, L.fwd_bytes, B, T, 0, M, opts,
                          stream);

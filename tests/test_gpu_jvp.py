@@ -92,6 +92,23 @@ def test_jvp_short_signals(T):
     check(f"T{T}", w, tangents(w, 4), "chunk3", 1e-5)
 
 
+@pytest.mark.parametrize("M,N", [(1, 0), (2, 2), (3, 1), (4, 4)])
+def test_jvp_low_order_streaming_path(M, N):
+    """Orders <= 4 on rows of a multiple of 4 samples (the float4 streaming input step):
+    all tangents, then each alone; rows spanning several blocks with a partial last one."""
+    w = inputs.make("biquad_1024x48000", B=5, T=2 * 8192 + 2048 + 20, M=M, N=N, seed=70 + M)
+    for which in (ALL,) + tuple((k,) for k in ALL):
+        check(f"vec4_M{M}_{'_'.join(which)}", w, tangents(w, 7, which), "chunk3", 1e-5)
+
+
+@pytest.mark.parametrize("B,T", [(7, 4), (70000, 8)])
+def test_jvp_low_order_short_rows(B, T):
+    """One or two quads per row, and more rows than one grid dimension holds (the
+    streaming input step strides over rows)."""
+    w = inputs.make("biquad_1024x48000", B=B, T=T, seed=80 + T)
+    check(f"vec4_rows_B{B}_T{T}", w, tangents(w, 8), "chunk3", 1e-5)
+
+
 def test_jvp_zero_tangents_and_empty():
     """No tangent at all gives dy = 0; an empty batch is a no-op."""
     w = inputs.make("biquad_1024x48000", B=3, T=5000)
