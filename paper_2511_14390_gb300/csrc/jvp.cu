@@ -110,7 +110,8 @@ __device__ __forceinline__ float4 shfl_up4(float4 a) {
     return a;
 }
 
-__global__ void __launch_bounds__(kJvpThreads, 4)
+template <int H>   // max(N, M): the history each output needs
+__global__ void __launch_bounds__(kJvpThreads, H <= 2 ? 6 : 4)
 jvp_input_vec4_kernel(const float4 *__restrict__ x, const float4 *__restrict__ dx,
                       const float4 *__restrict__ y, const float *__restrict__ b,
                       const float *__restrict__ db, const float *__restrict__ da,
@@ -122,12 +123,12 @@ jvp_input_vec4_kernel(const float4 *__restrict__ x, const float4 *__restrict__ d
     const int64_t qc = live ? qr : nqr - 1;
     const int lane = threadIdx.x & 31;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    __shared__ float cb[5], cdb[5], cda[5];
+    __shared__ float cb[H + 1], cdb[H + 1], cda[H + 1];
     for (int64_t row = blockIdx.y; row < B; row += gridDim.y) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ones[row] = 1.0f;
         const int64_t qq = row * nqr + qc;
         __syncthreads();                                 // previous row's coefficients read
-        if (threadIdx.x < 5) {
+        if (threadIdx.x <= H) {
             const int k = threadIdx.x;
             cb[k] = (dx && k <= N) ? __ldg(b + row * (N + 1) + k) : 0.0f;
             cdb[k] = (db && k <= N) ? __ldg(db + row * (N + 1) + k) : 0.0f;
@@ -154,10 +155,10 @@ jvp_input_vec4_kernel(const float4 *__restrict__ x, const float4 *__restrict__ d
             const int c = 4 + j;
             float acc = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 5; ++k)
+            for (int k = 0; k <= H; ++k)
                 if (k <= N) acc = fmaf(cb[k], dxw[c - k], fmaf(cdb[k], xw[c - k], acc));
 #pragma unroll
-            for (int k = 1; k < 5; ++k)
+            for (int k = 1; k <= H; ++k)
                 if (k <= M) acc = fmaf(-cda[k], yw[c - k], acc);
             o[j] = acc;
         }
@@ -229,7 +230,14 @@ extern "C" dfilt_status dfilt_jvp(const float *x, const float *y, const float *b
         const int64_t bx = (T / 4 + kJvpThreads - 1) / kJvpThreads;
         if (bx > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
         const dim3 grid((unsigned)bx, (unsigned)(B < 65535 ? B : 65535));
-        jvp_input_vec4_kernel<<<grid, kJvpThreads, 0, st>>>(
+        auto *kern = jvp_input_vec4_kernel<4>;
+        switch (N > M ? N : M) {
+            case 1: kern = jvp_input_vec4_kernel<1>; break;
+            case 2: kern = jvp_input_vec4_kernel<2>; break;
+            case 3: kern = jvp_input_vec4_kernel<3>; break;
+            default: break;
+        }
+        kern<<<grid, kJvpThreads, 0, st>>>(
             reinterpret_cast<const float4 *>(x), reinterpret_cast<const float4 *>(dx),
             reinterpret_cast<const float4 *>(y), b, db, da, reinterpret_cast<float4 *>(v), ones,
             B, T, N, M);
