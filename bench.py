@@ -458,8 +458,10 @@ def main():
                    "achieved": 16.0 * B * T / (ms_in / 1e3) / 1e9 if ms_in > 0 else None,
                    "frac": (16.0 * B * T / (ms_in / 1e3) / 1e9 / hbm_j) if ms_in > 0 else None,
                    "algorithmic_bytes": 16.0 * B * T,
-                   "kernel": "jvp_input_kernel (x, dx, y read, v written; time = call - "
-                             "forward step)", "peak_source": src_j},
+                   "kernel": (f"jvp_input_vec4_kernel<{max(N, M)}>" if max(N, M) <= 4
+                              and T % 4 == 0 else "jvp_input_kernel")
+                             + " (x, dx, y read, v written; time = call - forward step)",
+                   "peak_source": src_j},
                "call_roofline_frac": 16.0 * B * T / (ms_j / 1e3) / 1e9 / hbm_j,
                "gpu_launches_per_call": 3}
         if rank == 0:
