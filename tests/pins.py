@@ -302,10 +302,53 @@ def pin_jvp_adjoint(lib=None):
         assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + abs(rhs) + 1.0), ("jvp adjoint", M, N)
 
 
+def pin_recurrence_dense(lib=None):
+    """App. B operator with a dense (non-companion) A: a diagonal A gives per-component
+    geometric sums in closed form; a rotation by theta scaled by r gives
+    v(n) = r^n R(n theta) v0 for z = 0; and the backward's (grad_A, grad_v0, grad_z)
+    equal FP64 central differences of <g, v> (lib unused: numpy operator)."""
+    from oracle import statespace as ss
+    rng = np.random.default_rng(27)
+    lam = np.array([0.9, -0.6, 0.3])
+    v0 = rng.standard_normal(3); z = rng.standard_normal((25, 3))
+    v = ss.recurrence_forward(np.diag(lam), v0, z)
+    for i in range(3):
+        ref = [lam[i] ** (n + 1) * v0[i] + sum(lam[i] ** (n - k) * z[k, i] for k in range(n + 1))
+               for n in range(25)]
+        assert _rel(v[:, i], ref) < 1e-13, "recurrence diagonal"
+    r, th = 0.97, 0.4
+    Rm = r * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    w0 = np.array([1.0, -0.5])
+    v = ss.recurrence_forward(Rm, w0, np.zeros((30, 2)))
+    for n in range(30):
+        c, s_ = np.cos((n + 1) * th), np.sin((n + 1) * th)
+        ref = r ** (n + 1) * np.array([[c, -s_], [s_, c]]) @ w0
+        assert _rel(v[n], ref) < 1e-13, "recurrence rotation"
+    for M, T in [(2, 40), (4, 17)]:
+        A = 0.5 * rng.standard_normal((M, M)) / np.sqrt(M)
+        v0 = rng.standard_normal(M); z = rng.standard_normal((T, M)); g = rng.standard_normal((T, M))
+        v = ss.recurrence_forward(A, v0, z)
+        gA, gv0, gz = ss.recurrence_backward(A, v0, v, g)
+        L = lambda AA, vv, zz: float((g * ss.recurrence_forward(AA, vv, zz)).sum())
+        h = 1e-6
+        def fd(arr, which):
+            out = np.zeros_like(arr)
+            for idx in np.ndindex(arr.shape):
+                ap, am = arr.copy(), arr.copy(); ap[idx] += h; am[idx] -= h
+                kp = dict(AA=A, vv=v0, zz=z); km = dict(AA=A, vv=v0, zz=z)
+                kp[which] = ap; km[which] = am
+                out[idx] = (L(**kp) - L(**km)) / (2 * h)
+            return out
+        assert _rel(gA, fd(A, "AA")) < 1e-7, ("recurrence fd A", M)
+        assert _rel(gv0, fd(v0, "vv")) < 1e-7, ("recurrence fd v0", M)
+        assert _rel(gz, fd(z, "zz")) < 1e-7, ("recurrence fd z", M)
+
+
 ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfilter,
             pin_injection_form, pin_linearity_shift, pin_exact_forward,
             pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace,
-            pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint]
+            pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint,
+            pin_recurrence_dense]
 
 
 def run_all(lib=None):
