@@ -44,6 +44,8 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-jvp", action="store_true", help="skip the forward-mode (JVP) leg")
+    p.add_argument("--no-ss", action="store_true",
+                   help="skip the dense state-space recurrence leg (M = 2, 64 x 2^20 steps)")
     p.add_argument("--graph", action="store_true",
                    help="also time the step captured in a CUDA graph (launch-bound workloads)")
     p.add_argument("--channels", type=int, default=0,
@@ -486,6 +488,84 @@ def main():
                                                  f"repeated {reps}x over {dt:.1f} s"}
         del jws, w1, dy1, dyj, tdx
 
+    # The App. B recurrence v(n+1) = A v(n) + z(n) with a dense 2 x 2 A (the operator the
+    # paper benchmarks), batched: 64 channels x 2^20 steps, forward + backward (grad_A,
+    # grad_v0, grad_z).  Algorithmic bytes per step: forward z read + v written (16),
+    # backward gv and v read + gz written (24).
+    ssl = None
+    if not a.no_ss:
+        Bs, Ts, Ms = 64, 1 << 20, 2
+        rng = np.random.default_rng(11)
+        As = rng.standard_normal((Bs, Ms, Ms))
+        for i in range(Bs):
+            As[i] *= 0.95 / max(abs(np.linalg.eigvals(As[i])))
+        Ad = dev(As.astype(np.float32))
+        v0d = dev(rng.standard_normal((Bs, Ms)).astype(np.float32))
+        zd = torch.randn((Bs, Ts, Ms), device="cuda", generator=torch.Generator("cuda").manual_seed(12))
+        gvd = torch.randn((Bs, Ts, Ms), device="cuda", generator=torch.Generator("cuda").manual_seed(13))
+        sfw, sbw = dfilt.dfilt_ss_workspace_size(Bs, Ts, Ms)
+        sw1 = torch.empty(max(sfw, 16), dtype=torch.uint8, device="cuda")
+        sw2 = torch.empty(max(sbw, 16), dtype=torch.uint8, device="cuda")
+        vd, gzd = torch.empty_like(zd), torch.empty_like(zd)
+        gAd, gv0d = torch.empty_like(Ad), torch.empty_like(v0d)
+
+        def ss_step():
+            dfilt._check(L.dfilt_ss_forward(P(Ad), P(v0d), P(zd), P(vd), P(sw1), sfw, Bs, Ts, Ms,
+                                            sptr), "dfilt_ss_forward")
+            dfilt._check(L.dfilt_ss_backward(P(Ad), P(v0d), P(vd), P(gvd), P(gAd), P(gv0d),
+                                             P(gzd), P(sw2), sbw, Bs, Ts, Ms, sptr),
+                         "dfilt_ss_backward")
+
+        for _ in range(max(3, a.warmup)):
+            ss_step()
+        torch.cuda.synchronize()
+        barrier()
+        ns = max(3, min(100, a.steps))
+        s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s0.record(stream)
+        for _ in range(ns):
+            ss_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        sms_ = maxrank(s0.elapsed_time(s1) / ns)
+        status = dfilt.dfilt_sync_status()
+        if status != 0:
+            raise RuntimeError(f"device status {dfilt.STATUS[status]}")
+        hbm_s, src_s = peaks()
+        steps_all = Bs * Ts * world
+        ssl = {"workload": f"dense A (M = {Ms}), {Bs} channels x {Ts} steps, fwd + bwd",
+               "value": steps_all / (sms_ / 1e3) / 1e9, "unit": "Gsteps/s", "ms_per_step": sms_,
+               "calls": ns, "algorithmic_bytes": 40.0 * Bs * Ts,
+               "roofline_frac": 40.0 * Bs * Ts / (sms_ / 1e3) / 1e9 / hbm_s,
+               "peak": hbm_s, "peak_source": src_s,
+               # forward: powers, pass 1, carry, pass 2; backward: the same four on A^T
+               # plus the dL/dA partials and their final sum
+               "gpu_launches_per_step": 10}
+        if rank == 0:
+            from oracle import statespace as ossm
+            hv = vd[0, :4096].double().cpu().numpy()
+            ref = ossm.recurrence_forward(As[0].astype(np.float32).astype(np.float64),
+                                          v0d[0].double().cpu().numpy(),
+                                          zd[0, :4096].double().cpu().numpy())
+            ssl["rel_err_vs_fp64_first_4096_steps"] = float(np.abs(hv - ref).max()
+                                                           / np.abs(ref).max())
+            if world == 1 and not a.no_cpu:
+                zc, gc = zd[0].double().cpu().numpy(), gvd[0].double().cpu().numpy()
+                A0 = As[0].astype(np.float32).astype(np.float64)
+                t0, reps, nst = time.perf_counter(), 0, 1 << 16
+                while time.perf_counter() - t0 < 2.0 or reps == 0:
+                    vv = ossm.recurrence_forward(A0, np.zeros(2), zc[:nst])
+                    ossm.recurrence_backward(A0, np.zeros(2), vv, gc[:nst])
+                    reps += 1
+                dt = time.perf_counter() - t0
+                ssl["cpu_baseline"] = {"value": nst * reps / dt / 1e9, "unit": "Gsteps/s",
+                                       "cores": 1, "kind": "oracle",
+                                       "sample": f"{nst} steps of one channel, FP64 numpy "
+                                                 f"operator fwd + bwd, repeated {reps}x "
+                                                 f"over {dt:.1f} s"}
+        del zd, gvd, vd, gzd, sw1, sw2
+
     # End to end through the public API from pinned host buffers, pipelined across steps
     # the way a streaming caller would run it: step k's inputs are copied host -> device
     # on one stream while step k-1 computes and step k-2's results are copied back on a
@@ -601,7 +681,7 @@ def main():
                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
                          else "fallback (6.8 TB/s)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "graph_replay": graph,
-            "jvp": jvp,
+            "jvp": jvp, "state_space": ssl,
             # per step: forward = setup + main kernel, backward = main kernel (its work
             # counter is cleared by a memset)
             "gpu_launches": 3 * a.steps if algo == "chunked" else 2 * a.steps,

@@ -263,6 +263,34 @@ dfilt_status dfilt_jvp(const float *x, const float *y, const float *b, const flo
                        float *dy, void *ws, size_t ws_bytes, int64_t B, int64_t T, int N, int M,
                        const dfilt_opts *opts, void *stream);
 
+/*
+ * The general linear recurrence of App. B (the operator the paper benchmarks at
+ * M = 2), batched over B independent channels, each with its own dense A:
+ *     v(n+1) = A v(n) + z(n),   n = 0..T-1,   v(0) = v0
+ * and its backward (App. A, Eqs. dLdz and dLdvBA): dL/dz is the same recurrence run
+ * with A^T on the time-reversed dL/dv from a zero state; dL/dv0 = A^T dL/dz(0);
+ * dL/dA = sum_n dL/dz(n) v(n)^T with v(n) the state before step n.
+ *   A   [B,M,M]    row-major per channel (row i produces v_i)
+ *   v0  [B,M]      initial state; NULL = zero
+ *   z   [B,T,M]    inputs, step-major (the M entries of a step contiguous)
+ *   v   [B,T,M]    outputs v(1..T)
+ *   gv  [B,T,M]    upstream gradient dL/dv(1..T)
+ *   gA [B,M,M], gv0 [B,M]   gradients, each may be NULL (not wanted); v may be NULL
+ *                  when gA is NULL
+ *   gz  [B,T,M]    gradient dL/dz (required: the other two are formed from it)
+ *   ws, ws_bytes   workspace of at least fwd_ws / bwd_ws bytes, 16-byte aligned
+ * Supported 1 <= M <= 4 (DFILT_ERR_UNSUPPORTED above).  FP32 arithmetic; the powers
+ * of A the chunked scan uses are formed in FP64.  dL/dA sums in a fixed order.
+ */
+dfilt_status dfilt_ss_workspace_size(int64_t B, int64_t T, int M, size_t *fwd_ws,
+                                     size_t *bwd_ws);
+dfilt_status dfilt_ss_forward(const float *A, const float *v0, const float *z, float *v,
+                              void *ws, size_t ws_bytes, int64_t B, int64_t T, int M,
+                              void *stream);
+dfilt_status dfilt_ss_backward(const float *A, const float *v0, const float *v, const float *gv,
+                               float *gA, float *gv0, float *gz, void *ws, size_t ws_bytes,
+                               int64_t B, int64_t T, int M, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

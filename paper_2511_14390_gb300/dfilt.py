@@ -30,7 +30,7 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
            "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
            "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
-           "dfilt_jvp"]
+           "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward"]
 
 
 class DfiltError(RuntimeError):
@@ -90,6 +90,9 @@ def lib():
             L.dfilt_kernel_timing.argtypes = [i32]
             L.dfilt_jvp_workspace_size.argtypes = [i64, i64, i32, i32, PO, Psz]
             L.dfilt_jvp.argtypes = [P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32, i32, PO, P]
+            L.dfilt_ss_workspace_size.argtypes = [i64, i64, i32, Psz, Psz]
+            L.dfilt_ss_forward.argtypes = [P, P, P, P, P, sz, i64, i64, i32, P]
+            L.dfilt_ss_backward.argtypes = [P, P, P, P, P, P, P, P, sz, i64, i64, i32, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
             L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
             for name in EXPORTS:
@@ -264,6 +267,41 @@ def dfilt_jvp(x, y, b, a, dx=None, db=None, da=None, dzi=None, *, opts: Opts | N
                            _ptr(dzi), _ptr(dy), _ptr(ws), ws.numel(), B, T, N, M,
                            ctypes.byref(o), _stream(stream)), "dfilt_jvp")
     return dy
+
+
+def dfilt_ss_workspace_size(B, T, M):
+    f, w = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().dfilt_ss_workspace_size(B, T, M, ctypes.byref(f), ctypes.byref(w)),
+           "dfilt_ss_workspace_size")
+    return f.value, w.value
+
+
+def dfilt_ss_forward(A, v0, z, *, v=None, ws=None, stream=None):
+    """v(1..T) [B,T,M] of the recurrence v(n+1) = A v(n) + z(n) (App. B), batched."""
+    A, v0, z = _f32(A, "A"), _f32(v0, "v0"), _f32(z, "z")
+    B, T, M = z.shape
+    fws, _ = dfilt_ss_workspace_size(B, T, M)
+    v = torch.empty_like(z) if v is None else v
+    ws = _buf(fws, z.device) if ws is None else ws
+    _check(lib().dfilt_ss_forward(_ptr(A), _ptr(v0), _ptr(z), _ptr(v), _ptr(ws), ws.numel(),
+                                  B, T, M, _stream(stream)), "dfilt_ss_forward")
+    return v
+
+
+def dfilt_ss_backward(A, v0, v, gv, *, needs=(True, True), ws=None, stream=None):
+    """(grad_A, grad_v0, grad_z) of the recurrence (App. A); entries of `needs` select
+    grad_A and grad_v0."""
+    A, v0, v, gv = _f32(A, "A"), _f32(v0, "v0"), _f32(v, "v"), _f32(gv, "gv")
+    B, T, M = gv.shape
+    _, bws = dfilt_ss_workspace_size(B, T, M)
+    gA = torch.empty_like(A) if needs[0] else None
+    gv0 = torch.empty((B, M), dtype=torch.float32, device=gv.device) if needs[1] else None
+    gz = torch.empty_like(gv)
+    ws = _buf(bws, gv.device) if ws is None else ws
+    _check(lib().dfilt_ss_backward(_ptr(A), _ptr(v0), _ptr(v), _ptr(gv), _ptr(gA), _ptr(gv0),
+                                   _ptr(gz), _ptr(ws), ws.numel(), B, T, M, _stream(stream)),
+           "dfilt_ss_backward")
+    return gA, gv0, gz
 
 
 def dfilt_sync_status(stream=None) -> int:

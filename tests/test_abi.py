@@ -105,3 +105,19 @@ def test_jvp_host_checks(L):
                        2, ctypes.byref(o), None) == 6                 # workspace too small
     assert L.dfilt_jvp(None, None, None, None, None, None, None, None, None, None, 0, 0, 10, 2,
                        2, ctypes.byref(o), None) == 0                 # empty batch
+
+
+def test_ss_host_checks(L):
+    """State-space operator: workspace sizes and argument errors decided on the host."""
+    f, w = dfilt.dfilt_ss_workspace_size(64, 1 << 20, 2)
+    assert f > 0 and w > f
+    sz = ctypes.c_size_t()
+    assert L.dfilt_ss_workspace_size(4, 10, 5, ctypes.byref(sz), None) == 2    # M > 4
+    assert L.dfilt_ss_workspace_size(4, 10, 0, ctypes.byref(sz), None) == 1
+    assert L.dfilt_ss_workspace_size(-1, 10, 2, ctypes.byref(sz), None) == 1
+    assert L.dfilt_ss_forward(None, None, None, None, None, 0, 4, 10, 2, None) == 1
+    assert L.dfilt_ss_forward(None, None, None, None, None, 0, 0, 10, 2, None) == 0
+    assert L.dfilt_ss_backward(None, None, None, None, None, None, None, None, 0, 4, 10, 2,
+                               None) == 1
+    fake = ctypes.c_void_p(4096)    # never dereferenced: the call fails before any launch
+    assert L.dfilt_ss_forward(fake, None, fake, fake, fake, 16, 4, 10, 2, None) == 6
