@@ -120,12 +120,40 @@ ss_seg_kernel(const float *__restrict__ A, int trans, const float *__restrict__ 
     // memory positions of the segment: [p0, p0 + cnt)
     const int64_t p0 = REV ? T - g * kSsSeg - cnt : g * kSsSeg;
     const float *zb = z + (b * T + p0) * M;
-#pragma unroll 8
-    for (int f = lane; f < cnt * M; f += 32) {
+    auto slot = [&](int f) {                       // shared-memory slot of segment float f
         const int pr = f / M, m = f - pr * M;
         const int l = REV ? cnt - 1 - pr : pr;
-        zs[(l >> 5) * ROW + (l & 31) * M + m] = zb[f];
+        return (l >> 5) * ROW + (l & 31) * M + m;
+    };
+    // every segment starts on a 16-byte boundary when T*M is a multiple of 4
+    const bool vec = ((T * M) & 3) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+    const int nf = cnt * M;
+    int done = 0;
+    if (vec) {
+        constexpr int R = 8;                       // float4 loads in flight per lane
+        const float4 *z4 = reinterpret_cast<const float4 *>(zb);
+        const int n4 = nf >> 2;
+        for (int q0 = 0; q0 < n4; q0 += 32 * R) {
+            float4 r4[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int q = q0 + r * 32 + lane;
+                r4[r] = q < n4 ? __ldcs(z4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int q = q0 + r * 32 + lane;
+                if (q < n4) {
+                    zs[slot(4 * q)] = r4[r].x;
+                    zs[slot(4 * q + 1)] = r4[r].y;
+                    zs[slot(4 * q + 2)] = r4[r].z;
+                    zs[slot(4 * q + 3)] = r4[r].w;
+                }
+            }
+        }
+        done = n4 * 4;
     }
+    for (int f = done + lane; f < nf; f += 32) zs[slot(f)] = zb[f];
     __syncwarp();
 
     const int len = cnt - lane * kSsChunk < 0 ? 0 : (cnt - lane * kSsChunk > kSsChunk ? kSsChunk : cnt - lane * kSsChunk);
@@ -188,11 +216,16 @@ ss_seg_kernel(const float *__restrict__ A, int trans, const float *__restrict__ 
     }
     __syncwarp();
     float *ob = out + (b * T + p0) * M;
-    for (int f = lane; f < cnt * M; f += 32) {
-        const int pr = f / M, m = f - pr * M;
-        const int l = REV ? cnt - 1 - pr : pr;
-        ob[f] = zs[(l >> 5) * ROW + (l & 31) * M + m];
+    done = 0;
+    if (vec && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        float4 *o4 = reinterpret_cast<float4 *>(ob);
+        const int n4 = nf >> 2;
+        for (int q = lane; q < n4; q += 32)
+            o4[q] = make_float4(zs[slot(4 * q)], zs[slot(4 * q + 1)], zs[slot(4 * q + 2)],
+                                zs[slot(4 * q + 3)]);
+        done = n4 * 4;
     }
+    for (int f = done + lane; f < nf; f += 32) ob[f] = zs[slot(f)];
 }
 
 // Entry state of every segment: one warp per channel, 32 segments at a time.
