@@ -18,7 +18,7 @@
 // The powers A^(2^k), k = 5..14, are formed per channel by squaring in FP64.  z is
 // read twice and v written once (24 bytes per step at M = 2).  The backward runs the
 // same kernels on A^T in reversed time (no initial state) to get dL/dz, then a
-// reduction kernel forms dL/dA (FP32 products over 4 steps, FP64 sums after that, in
+// reduction kernel forms dL/dA (FP32 sums over 128 steps, FP64 sums after that, in
 // a fixed order) and dL/dv(0).
 #include <nvtx3/nvToolsExt.h>
 
@@ -276,8 +276,9 @@ ss_carry_kernel(const float *__restrict__ pw, const float *__restrict__ v0,
 }
 
 // dL/dA partial sums per (channel, segment of kSsSeg steps): sum_n gz(n) prev(n)^T with
-// prev(n) = v(n-1), prev(0) = v0.  Each thread sums its 4 steps in FP32, the block
-// then adds the threads' terms in FP64 in a fixed order.
+// prev(n) = v(n-1), prev(0) = v0.  Each thread sums its 4 steps in FP32, each warp
+// its 128 steps by an FP32 shuffle tree (GB300's FP64 pipe is too narrow for a tree
+// per warp), and the block adds the 8 warp sums in FP64 in a fixed order.
 template <int M>
 __global__ void __launch_bounds__(256)
 ss_grada_kernel(const float *__restrict__ gz, const float *__restrict__ v,
@@ -308,10 +309,10 @@ ss_grada_kernel(const float *__restrict__ gz, const float *__restrict__ v,
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < M * M; ++i) {
-        double d = (double)acc[i];
+        float d = acc[i];                          // FP32 tree over the warp's 128 steps
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-        if (lane == 0) red[w][i] = d;
+        if (lane == 0) red[w][i] = (double)d;
     }
     __syncthreads();
     if (threadIdx.x < M * M) {
