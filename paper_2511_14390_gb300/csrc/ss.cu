@@ -240,11 +240,17 @@ ss_carry_kernel(const float *__restrict__ pw, const float *__restrict__ v0,
     float carry[M], t[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) carry[i] = v0 ? v0[b * M + i] : 0.0f;
+    float nxt[M];                                  // aggregates of the next group, prefetched
+#pragma unroll
+    for (int i = 0; i < M; ++i) nxt[i] = lane < G ? agg[(b * G + lane) * M + i] : 0.0f;
     for (int64_t r = 0; r * 32 < G; ++r) {
         const int64_t g = r * 32 + lane;
         float e[M];
 #pragma unroll
-        for (int i = 0; i < M; ++i) e[i] = g < G ? agg[(b * G + g) * M + i] : 0.0f;
+        for (int i = 0; i < M; ++i) {
+            e[i] = nxt[i];
+            nxt[i] = g + 32 < G ? agg[(b * G + g + 32) * M + i] : 0.0f;
+        }
         if (lane == 0) {
             matvec<M>(Q, carry, t);
 #pragma unroll
@@ -331,10 +337,14 @@ __global__ void ss_grada_final_kernel(const double *__restrict__ part, const flo
     if (id >= B * M * M) return;
     const int64_t b = id / (M * M);
     const int e = (int)(id - b * M * M);
-    if (gA) {
-        double d = 0.0;
-        for (int64_t g = 0; g < G; ++g) d += part[(b * G + g) * M * M + e];
-        gA[id] = (float)d;
+    if (gA) {                                      // four interleaved chains, fixed order
+        double d[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t g = 0;
+        for (; g + 4 <= G; g += 4)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] += part[(b * G + g + k) * M * M + e];
+        for (; g < G; ++g) d[0] += part[(b * G + g) * M * M + e];
+        gA[id] = (float)((d[0] + d[1]) + (d[2] + d[3]));
     }
     if (gv0 && e < M) {                            // row e of A^T = column e of A
         float acc = 0.0f;
