@@ -14,7 +14,9 @@ Digital Filters"):
 * backward -- the reverse-time adjoint of Sec. 3.1 (Eqs. dLdz, dLdx, dLdvBA, with
   the boundary condition of App. A) written as scalar difference equations;
 * forward mode (JVP) -- the TDF-II recursion carried with its derivative along
-  tangents of every input (the forward-mode derivative Sec. 5 mentions).
+  tangents of every input (the forward-mode derivative Sec. 5 mentions);
+* direct-form initial conditions -- the difference equation extended into negative
+  time with given past inputs and outputs, and its gradients.
 
 The heavy loops live in ``dfilt_oracle.c`` (plain C, FP64, OpenMP over channels);
 ``pyref.py`` holds a pure-Python FP64 restatement for tiny cases, ``statespace.py``
@@ -73,6 +75,11 @@ def _bind(lib):
     lib.oracle_backward_ragged.restype = i32
     lib.oracle_jvp.argtypes = [P, P, P, P, P, P, P, P, P, P, i64, i64, i32, i32, i32]
     lib.oracle_jvp.restype = i32
+    lib.oracle_forward_df1.argtypes = [P, P, P, P, P, P, i64, i64, i32, i32, i32]
+    lib.oracle_forward_df1.restype = i32
+    lib.oracle_backward_df1.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, i64, i64, i32, i32,
+                                        i32]
+    lib.oracle_backward_df1.restype = i32
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = i32
     return lib
@@ -157,6 +164,40 @@ def jvp(x, b, a, zi=None, dx=None, db=None, da=None, dzi=None, *, nthreads: int 
     if rc != 0:
         raise MemoryError("oracle jvp: allocation failed")
     return y, dy
+
+
+def forward_df1(x, b, a, xpast, ypast, *, nthreads: int = 0, lib=None):
+    """y[B,T] in FP64 with direct-form initial conditions: past inputs xpast[B,N]
+    (x[-1], x[-2], ...) and past outputs ypast[B,M] (y[-1], ...), the difference
+    equation of Eq. rtf extended into negative time."""
+    lib = lib or load()
+    x, b, a, ypast = _f64(x), _f64(b), _f64(a), _f64(ypast)
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    xpast = None if (xpast is None or N == 0) else _f64(xpast)
+    y = np.zeros_like(x)
+    lib.oracle_forward_df1(_ptr(x), _ptr(b), _ptr(a), _ptr(xpast), _ptr(ypast), _ptr(y), B, T,
+                           N, M, int(nthreads))
+    return y
+
+
+def backward_df1(gy, x, y, b, a, xpast, ypast, *, nthreads: int = 0, lib=None):
+    """(grad_x, grad_b, grad_a, grad_xpast, grad_ypast) in FP64 for forward_df1."""
+    lib = lib or load()
+    gy, x, y, b, a, ypast = _f64(gy), _f64(x), _f64(y), _f64(b), _f64(a), _f64(ypast)
+    B, T = x.shape
+    N, M = b.shape[1] - 1, a.shape[1]
+    xpast = None if (xpast is None or N == 0) else _f64(xpast)
+    gx = np.zeros_like(x)
+    gb, ga = np.zeros((B, N + 1)), np.zeros((B, M))
+    gxp, gyp = np.zeros((B, N)), np.zeros((B, M))
+    rc = lib.oracle_backward_df1(_ptr(gy), _ptr(x), _ptr(y), _ptr(b), _ptr(a), _ptr(xpast),
+                                 _ptr(ypast), _ptr(gx), _ptr(gb), _ptr(ga),
+                                 _ptr(gxp) if N > 0 else None, _ptr(gyp), B, T, N, M,
+                                 int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle backward_df1: allocation failed")
+    return gx, gb, ga, gxp, gyp
 
 
 # ----------------------------------------------------------------------------

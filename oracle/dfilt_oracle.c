@@ -267,5 +267,109 @@ int oracle_jvp(const double *x, const double *b, const double *a, const double *
     return fail ? -1 : 0;
 }
 
+/*
+ * Direct-form initial conditions (the DF-I state: past inputs x[-1..-N] and past
+ * outputs y[-1..-M], the convention of SciPy's lfiltic and MATLAB's filtic), the
+ * counterpart of the TDF-II state that Sec. 2 pairs with the direct form.  Forward:
+ * the difference equation of Eq. rtf over the signals extended into negative time,
+ *     xe(i) = x[i] (i >= 0), xpast[-i-1] (i < 0);   ye likewise with ypast
+ *     y[n]  = sum_{k=0..N} b_k xe(n-k) - sum_{k=1..M} a_k ye(n-k)
+ * Backward: with the adjoint u of bwd_channel (same recursion), the gradients of the
+ * same equation with respect to every quantity in it:
+ *     grad_b[k]       = sum_{n>=0} u[n] xe(n-k)        (past inputs included)
+ *     grad_a[k]       = -sum_{n>=0} u[n] ye(n-k)       (past outputs included)
+ *     grad_xpast[j-1] = sum_{k=j..N} b_k u[k-j]        (x[-j] enters y[k-j] via b_k)
+ *     grad_ypast[j-1] = -sum_{k=j..M} a_k u[k-j]
+ * (u[n] = 0 for n >= T).  grad_x is unchanged.  xpast may be NULL when N = 0.
+ */
+static double xe_at(const double *x, const double *xp, int64_t i)
+{
+    return i >= 0 ? x[i] : (xp ? xp[-i - 1] : 0.0);
+}
+
+static void fwd_df1_past(const double *x, const double *b, const double *a, const double *xp,
+                         const double *yp, double *y, int64_t T, int N, int M)
+{
+    for (int64_t n = 0; n < T; ++n) {
+        double acc = 0.0;
+        for (int k = 0; k <= N; ++k) acc += b[k] * xe_at(x, xp, n - k);
+        for (int k = 1; k <= M; ++k) acc -= a[k - 1] * (n - k >= 0 ? y[n - k] : yp[k - n - 1]);
+        y[n] = acc;
+    }
+}
+
+static void bwd_df1_past(const double *g, const double *x, const double *y, const double *b,
+                         const double *a, const double *xp, const double *yp, double *gx,
+                         double *gb, double *ga, double *gxp, double *gyp, int64_t T, int N,
+                         int M, double *u)
+{
+    bwd_channel(g, x, y, b, a, gx, NULL, NULL, NULL, T, N, M, u);
+    for (int k = 0; k <= N; ++k) {
+        double sum = 0.0;
+        for (int64_t n = 0; n < T; ++n) sum += u[n] * xe_at(x, xp, n - k);
+        gb[k] = sum;
+    }
+    for (int k = 1; k <= M; ++k) {
+        double sum = 0.0;
+        for (int64_t n = 0; n < T; ++n) sum += u[n] * (n - k >= 0 ? y[n - k] : yp[k - n - 1]);
+        ga[k - 1] = -sum;
+    }
+    for (int j = 1; j <= N; ++j) {
+        double sum = 0.0;
+        for (int k = j; k <= N; ++k)
+            if (k - j < T) sum += b[k] * u[k - j];
+        gxp[j - 1] = sum;
+    }
+    for (int j = 1; j <= M; ++j) {
+        double sum = 0.0;
+        for (int k = j; k <= M; ++k)
+            if (k - j < T) sum += a[k - 1] * u[k - j];
+        gyp[j - 1] = -sum;
+    }
+}
+
+/*
+ * Fixed-shape drivers: x, y, g [B,T]; b [B,N+1]; a [B,M]; xpast [B,N] (NULL if N = 0);
+ * ypast [B,M].  Returns 0, or -1 on an allocation failure.
+ */
+int oracle_forward_df1(const double *x, const double *b, const double *a, const double *xp,
+                       const double *yp, double *y, int64_t B, int64_t T, int N, int M,
+                       int nthreads)
+{
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+    for (int64_t i = 0; i < B; ++i)
+        fwd_df1_past(x + i * T, b + i * (N + 1), a + i * M, (xp && N > 0) ? xp + i * N : NULL,
+                     yp + i * M, y + i * T, T, N, M);
+    return 0;
+}
+
+int oracle_backward_df1(const double *g, const double *x, const double *y, const double *b,
+                        const double *a, const double *xp, const double *yp, double *gx,
+                        double *gb, double *ga, double *gxp, double *gyp, int64_t B, int64_t T,
+                        int N, int M, int nthreads)
+{
+    int fail = 0;
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        double *u = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+        if (!u) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < B; ++i) {
+            if (!u) continue;
+            bwd_df1_past(g + i * T, x + i * T, y + i * T, b + i * (N + 1), a + i * M,
+                         (xp && N > 0) ? xp + i * N : NULL, yp + i * M, gx + i * T,
+                         gb + i * (N + 1), ga + i * M, gxp ? gxp + i * (N > 0 ? N : 0) : NULL,
+                         gyp + i * M, T, N, M, u);
+        }
+        free(u);
+    }
+    return fail ? -1 : 0;
+}
+
 /* Threads an OpenMP region actually gets (for reporting the CPU baseline). */
 int oracle_max_threads(void) { return pick_threads(0); }

@@ -344,11 +344,46 @@ def pin_recurrence_dense(lib=None):
         assert _rel(gz, fd(z, "zz")) < 1e-7, ("recurrence fd z", M)
 
 
+def pin_df1_initial_conditions(lib=None):
+    """Direct-form initial conditions (past inputs and outputs): the forward equals
+    SciPy's lfiltic + lfilter (library routines); zero past values reduce to the
+    zero-state filter; the gradients equal FP64 central differences of <g, y> with
+    respect to x, b, a, xpast and ypast."""
+    import scipy.signal as ss
+    rng = np.random.default_rng(28)
+    for M, N, T in [(2, 2, 60), (5, 3, 40), (3, 0, 25), (4, 4, 3)]:
+        b, a = _random_filter(rng, M, N, rmax=0.8)
+        x = rng.standard_normal(T); xp = rng.standard_normal(N); yp = rng.standard_normal(M)
+        af = np.concatenate([[1.0], a])
+        y = oracle.forward_df1(x[None], b[None], a[None], xp[None], yp[None], lib=lib)[0]
+        ref, _ = ss.lfilter(b, af, x, zi=ss.lfiltic(b, af, yp, xp if N else None))
+        assert _rel(y, ref) < 1e-12, ("df1 lfiltic", M, N)
+        y0 = oracle.forward_df1(x[None], b[None], a[None], np.zeros((1, N)), np.zeros((1, M)),
+                                lib=lib)[0]
+        assert _rel(y0, ss.lfilter(b, af, x)) < 1e-12, ("df1 zero past", M, N)
+        g = rng.standard_normal(T)
+        gx, gb, ga, gxp, gyp = oracle.backward_df1(g[None], x[None], y[None], b[None], a[None],
+                                                   xp[None], yp[None], lib=lib)
+        L = lambda xx, bb, aa, xq, yq: float(g @ oracle.forward_df1(
+            xx[None], bb[None], aa[None], xq[None], yq[None], lib=lib)[0])
+        h = 1e-6
+        args = dict(xx=x, bb=b, aa=a, xq=xp, yq=yp)
+        for nm, got in [("xx", gx[0]), ("bb", gb[0]), ("aa", ga[0]), ("xq", gxp[0]),
+                        ("yq", gyp[0])]:
+            vec = args[nm]
+            fd = np.zeros_like(vec)
+            for i in range(vec.size):
+                vp, vm = vec.copy(), vec.copy(); vp[i] += h; vm[i] -= h
+                fd[i] = (L(**{**args, nm: vp}) - L(**{**args, nm: vm})) / (2 * h)
+            if vec.size:
+                assert _rel(got, fd) < 1e-7, ("df1 fd", nm, M, N)
+
+
 ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfilter,
             pin_injection_form, pin_linearity_shift, pin_exact_forward,
             pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace,
             pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint,
-            pin_recurrence_dense]
+            pin_recurrence_dense, pin_df1_initial_conditions]
 
 
 def run_all(lib=None):

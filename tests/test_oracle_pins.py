@@ -39,6 +39,15 @@ MUTATIONS = [
      "if (db) d += bcoef(db, N, k) * xn;"),
     ("jvp drops the state tangent", "ds[k] = dzi ? dzi[k] : 0.0;", "ds[k] = 0.0;"),
     ("jvp drops db_0", "if (db) dyn += db[0] * xn;", "if (db) dyn += 0.0 * xn;"),
+    ("df1 forward drops past outputs",
+     "acc -= a[k - 1] * (n - k >= 0 ? y[n - k] : yp[k - n - 1]);",
+     "acc -= a[k - 1] * (n - k >= 0 ? y[n - k] : 0.0);"),
+    ("df1 grad_a drops past outputs",
+     "sum += u[n] * (n - k >= 0 ? y[n - k] : yp[k - n - 1]);",
+     "sum += u[n] * (n - k >= 0 ? y[n - k] : 0.0);"),
+    ("df1 grad_xpast coefficient index", "if (k - j < T) sum += b[k] * u[k - j];",
+     "if (k - j < T) sum += b[k - 1] * u[k - j];"),
+    ("df1 grad_ypast sign", "gyp[j - 1] = -sum;", "gyp[j - 1] = sum;"),
 ]
 
 
