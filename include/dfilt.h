@@ -291,6 +291,28 @@ dfilt_status dfilt_ss_backward(const float *A, const float *v0, const float *v, 
                                float *gA, float *gv0, float *gz, void *ws, size_t ws_bytes,
                                int64_t B, int64_t T, int M, void *stream);
 
+/*
+ * Direct-form initial conditions: past inputs xpast[B,N] = (x[-1], ..., x[-N]) and past
+ * outputs ypast[B,M] = (y[-1], ..., y[-M]) (the convention of SciPy's lfiltic and
+ * MATLAB's filtic) mapped to the TDF-II state zi[B,M] that dfilt_forward takes (Sec. 2
+ * pairs the direct form with its transposed form):
+ *     zi[m] = sum_{k=m+1..N} b_k x[m-k] - sum_{k=m+1..M} a_k y[m-k]
+ * xpast or ypast may be NULL (zero).  dfilt_ic_df1_backward is the adjoint of that map:
+ * from gzi = dL/dzi (dfilt_backward's grad_zi) it writes
+ *     gxpast[j-1] = sum_m gzi[m] b_{m+j},   gypast[j-1] = -sum_m gzi[m] a_{m+j}
+ * and ADDS the past values' terms to the filter's coefficient gradients:
+ *     gb[k] += sum_{m<k} gzi[m] x[m-k],   ga[k-1] -= sum_{m<k} gzi[m] y[m-k]
+ * so that gb, ga from dfilt_backward become the gradients of the filter with past
+ * values.  Each output may be NULL (not wanted).  Device pointers; asynchronous.
+ */
+dfilt_status dfilt_ic_df1(const float *b, const float *a, const float *xpast,
+                          const float *ypast, float *zi, int64_t B, int N, int M,
+                          void *stream);
+dfilt_status dfilt_ic_df1_backward(const float *b, const float *a, const float *xpast,
+                                   const float *ypast, const float *gzi, float *gxpast,
+                                   float *gypast, float *gb, float *ga, int64_t B, int N, int M,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
            "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
            "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
-           "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward"]
+           "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward",
+           "dfilt_ic_df1", "dfilt_ic_df1_backward"]
 
 
 class DfiltError(RuntimeError):
@@ -93,6 +94,8 @@ def lib():
             L.dfilt_ss_workspace_size.argtypes = [i64, i64, i32, Psz, Psz]
             L.dfilt_ss_forward.argtypes = [P, P, P, P, P, sz, i64, i64, i32, P]
             L.dfilt_ss_backward.argtypes = [P, P, P, P, P, P, P, P, sz, i64, i64, i32, P]
+            L.dfilt_ic_df1.argtypes = [P, P, P, P, P, i64, i32, i32, P]
+            L.dfilt_ic_df1_backward.argtypes = [P, P, P, P, P, P, P, P, P, i64, i32, i32, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
             L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
             for name in EXPORTS:
@@ -304,6 +307,33 @@ def dfilt_ss_backward(A, v0, v, gv, *, needs=(True, True), ws=None, stream=None)
     return gA, gv0, gz
 
 
+def dfilt_ic_df1(b, a, xpast, ypast, *, zi=None, stream=None):
+    """TDF-II state zi[B,M] equivalent to past inputs xpast[B,N] and outputs ypast[B,M]."""
+    b, a, xpast, ypast = _f32(b, "b"), _f32(a, "a"), _f32(xpast, "xpast"), _f32(ypast, "ypast")
+    B, M = a.shape
+    N = b.shape[1] - 1
+    zi = torch.empty((B, M), dtype=torch.float32, device=a.device) if zi is None else zi
+    _check(lib().dfilt_ic_df1(_ptr(b), _ptr(a), _ptr(xpast), _ptr(ypast), _ptr(zi), B, N, M,
+                              _stream(stream)), "dfilt_ic_df1")
+    return zi
+
+
+def dfilt_ic_df1_backward(b, a, xpast, ypast, gzi, gb=None, ga=None, *,
+                          needs=(True, True), stream=None):
+    """(grad_xpast, grad_ypast) from grad_zi; adds the past values' terms to gb, ga
+    (the filter backward's coefficient gradients) in place when given."""
+    b, a, xpast, ypast = _f32(b, "b"), _f32(a, "a"), _f32(xpast, "xpast"), _f32(ypast, "ypast")
+    gzi = _f32(gzi, "gzi")
+    B, M = a.shape
+    N = b.shape[1] - 1
+    gxp = torch.empty((B, N), dtype=torch.float32, device=a.device) if needs[0] else None
+    gyp = torch.empty((B, M), dtype=torch.float32, device=a.device) if needs[1] else None
+    _check(lib().dfilt_ic_df1_backward(_ptr(b), _ptr(a), _ptr(xpast), _ptr(ypast), _ptr(gzi),
+                                       _ptr(gxp), _ptr(gyp), _ptr(gb), _ptr(ga), B, N, M,
+                                       _stream(stream)), "dfilt_ic_df1_backward")
+    return gxp, gyp
+
+
 def dfilt_sync_status(stream=None) -> int:
     """Synchronise the stream; return (and clear) the device status word."""
     return int(lib().dfilt_sync_status(_stream(stream)))
@@ -366,6 +396,40 @@ class DFilt(torch.autograd.Function):
 def filt(x, b, a, zi=None, **opt_kwargs):
     """Differentiable batched direct-form filter (see DFilt)."""
     return DFilt.apply(x, b, a, zi, make_opts(**opt_kwargs) if opt_kwargs else None)
+
+
+class DFiltDF1(torch.autograd.Function):
+    """y = DFiltDF1.apply(x, b, a, xpast, ypast, opts): the filter started from
+    direct-form initial conditions (past inputs xpast[B,N], past outputs ypast[B,M]),
+    through the library's map to the TDF-II state and its adjoint."""
+
+    @staticmethod
+    def forward(ctx, x, b, a, xpast, ypast, opts: Opts | None = None):
+        opts = opts or make_opts()
+        zi = dfilt_ic_df1(b, a, xpast, ypast)
+        y, saved = dfilt_forward(x, b, a, zi, opts=opts)
+        ctx.opts = opts
+        empty = x.new_empty(0)
+        ctx.save_for_backward(x, b, a, xpast, ypast, zi, saved if saved is not None else empty,
+                              y if saved is None else empty)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, b, a, xpast, ypast, zi, saved, y = ctx.saved_tensors
+        ng = ctx.needs_input_grad
+        needs = (bool(ng[0]), bool(ng[1]), bool(ng[2]), True)
+        gx, gb, ga, gzi = dfilt_backward(gy.contiguous(), x, y if y.numel() else None, b, a, zi,
+                                         saved if saved.numel() else None, opts=ctx.opts,
+                                         needs=needs)
+        gxp, gyp = dfilt_ic_df1_backward(b, a, xpast, ypast, gzi, gb, ga,
+                                         needs=(bool(ng[3]), bool(ng[4])))
+        return gx, gb, ga, gxp, gyp, None
+
+
+def filt_df1(x, b, a, xpast, ypast, **opt_kwargs):
+    """Differentiable filter with direct-form initial conditions (see DFiltDF1)."""
+    return DFiltDF1.apply(x, b, a, xpast, ypast, make_opts(**opt_kwargs) if opt_kwargs else None)
 
 
 class DFiltRagged(torch.autograd.Function):

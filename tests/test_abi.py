@@ -121,3 +121,15 @@ def test_ss_host_checks(L):
                                None) == 1
     fake = ctypes.c_void_p(4096)    # never dereferenced: the call fails before any launch
     assert L.dfilt_ss_forward(fake, None, fake, fake, fake, 16, 4, 10, 2, None) == 6
+
+
+def test_ic_df1_host_checks(L):
+    """Direct-form initial conditions: argument errors and the empty batch on the host."""
+    assert L.dfilt_ic_df1(None, None, None, None, None, 4, 2, 65, None) == 2
+    assert L.dfilt_ic_df1(None, None, None, None, None, 4, 3, 2, None) == 1
+    assert L.dfilt_ic_df1(None, None, None, None, None, 4, 2, 2, None) == 1     # zi missing
+    assert L.dfilt_ic_df1(None, None, None, None, None, 0, 2, 2, None) == 0
+    assert L.dfilt_ic_df1_backward(None, None, None, None, None, None, None, None, None, 4, 2,
+                                   2, None) == 1                                  # gzi missing
+    assert L.dfilt_ic_df1_backward(None, None, None, None, None, None, None, None, None, 0, 2,
+                                   2, None) == 0
