@@ -49,16 +49,22 @@ def test_df1_forward_and_gradients(algo, M, N):
     gx, gb, ga, gxp, gyp = oracle.backward_df1(w.gy, w.x, yr, w.b, w.a, xp, yp)
     h = lambda t: t.detach().cpu().numpy().astype(np.float64)
     tol = np.maximum(1e-5, 16 * U32 * kappa(w.a, T))
-    # coefficient and past-value gradients against the natural scale of their sums
-    u = oracle.backward(w.gy, w.x, yr, np.ones((B, 1)), w.a)[0]
-    su = np.abs(u).sum(1, keepdims=True)
-    sx = np.abs(np.concatenate([xp[:, ::-1], w.x], 1)).max(1, keepdims=True) if N else 1.0
-    sy = np.abs(np.concatenate([yp[:, ::-1], yr], 1)).max(1, keepdims=True)
+    # each coefficient / past-value gradient against the sum of its terms' magnitudes
+    u = np.abs(oracle.backward(w.gy, w.x, yr, np.ones((B, 1)), w.a)[0])
+    xe = np.abs(np.concatenate([xp[:, ::-1], w.x], 1))     # xe[:, N + i] = |x[i]|, i >= -N
+    ye = np.abs(np.concatenate([yp[:, ::-1], yr], 1))      # ye[:, M + i] = |y[i]|, i >= -M
+    Sb = np.stack([(u * xe[:, N - k: N - k + T]).sum(1) for k in range(N + 1)], 1)
+    Sa = np.stack([(u * ye[:, M - k: M - k + T]).sum(1) for k in range(1, M + 1)], 1)
+    ab, aa = np.abs(w.b).astype(np.float64), np.abs(w.a).astype(np.float64)
+    Syp = np.stack([sum(aa[:, k - 1] * u[:, k - j] for k in range(j, M + 1))
+                    for j in range(1, M + 1)], 1)
     errs = {"y": rel_rows(h(y), yr), "gx": rel_rows(h(x.grad), gx),
-            "gb": coef_err(h(b.grad), gb, su * sx), "ga": coef_err(h(a.grad), ga, su * sy),
-            "gypast": coef_err(h(ypd.grad), gyp, su * np.abs(w.a).max(1, keepdims=True))}
+            "gb": coef_err(h(b.grad), gb, Sb), "ga": coef_err(h(a.grad), ga, Sa),
+            "gypast": coef_err(h(ypd.grad), gyp, Syp)}
     if N:
-        errs["gxpast"] = coef_err(h(xpd.grad), gxp, su * np.abs(w.b).max(1, keepdims=True))
+        Sxp = np.stack([sum(ab[:, k] * u[:, k - j] for k in range(j, N + 1))
+                        for j in range(1, N + 1)], 1)
+        errs["gxpast"] = coef_err(h(xpd.grad), gxp, Sxp)
     log_errors(f"df1_{algo}_M{M}_N{N}", **errs)
     for k, e in errs.items():
         assert (e < tol).all(), (k, e, tol)
