@@ -133,3 +133,13 @@ def test_ic_df1_host_checks(L):
                                    2, None) == 1                                  # gzi missing
     assert L.dfilt_ic_df1_backward(None, None, None, None, None, None, None, None, None, 0, 2,
                                    2, None) == 0
+
+
+@pytest.mark.parametrize("precision", [2, 4])
+def test_bf16_precisions_unsupported(L, precision):
+    """BF16 and split-BF16 operands are not built: the chunked path reports
+    DFILT_ERR_UNSUPPORTED for them, decided on the host."""
+    o = dfilt.Opts(2, precision, 0, -1)
+    sz = ctypes.c_size_t()
+    assert L.dfilt_workspace_size(4, 100, 2, 2, ctypes.byref(o), ctypes.byref(sz), None,
+                                  None) == 2
