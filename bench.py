@@ -196,6 +196,25 @@ def run_reference(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+RADIUS_BINS = [(0.5, 0.9), (0.9, 0.99), (0.99, 0.999)]
+
+
+def radius_bins(per_channel: dict, radius) -> dict:
+    """Max and median of per-channel errors in each pole-radius bin (the channels'
+    largest drawn pole radius); channels outside every bin are reported as "other"."""
+    radius = np.asarray(radius, dtype=np.float64)
+    masks = {f"[{lo}, {hi})": (radius >= lo) & (radius < hi) for lo, hi in RADIUS_BINS}
+    masks["other"] = ~np.any(np.stack(list(masks.values())), axis=0)
+    out = {}
+    for name, m in masks.items():
+        if m.any():
+            out[name] = {"channels": int(m.sum())}
+            for k, v in per_channel.items():
+                v = np.asarray(v, dtype=np.float64)[m]
+                out[name][k] = {"max": float(v.max()), "median": float(np.median(v))}
+    return out
+
+
 def kernel_name(direction, M):
     """Main kernel of the chunked path for a state bucket (the warp-specialised kernels
     serve the buckets whose layouts fit; see the dispatch in csrc/chunk_*.cu)."""
@@ -378,17 +397,20 @@ def main():
     rel_err = None
     if rank == 0:
         import oracle
-        idx = np.linspace(0, B - 1, 8).astype(int)
+        idx = np.unique(np.linspace(0, B - 1, 32).astype(int))
         sub = inputs.Workload(x=w.x[idx], b=w.b[idx], a=w.a[idx], zi=w.zi[idx], gy=w.gy[idx],
                               M=M, N=N, radius=w.radius[idx])
         yr = oracle.forward(sub.x, sub.b, sub.a, sub.zi)
         gr = oracle.backward(sub.gy, sub.x, yr, sub.b, sub.a)
-        rel = lambda g, r: float((np.abs(g.cpu().numpy()[idx].astype(np.float64) - r).max(-1)
-                                  / np.abs(r).max(-1)).max())
-        rel_err = {"y": rel(st["y"], yr), "grad_x": rel(st["gx"], gr[0]),
-                   "grad_b": rel(st["gb"], gr[1]), "grad_a": rel(st["ga"], gr[2]),
-                   "grad_zi": rel(st["gz"], gr[3]), "channels_checked": len(idx),
-                   "metric": "per-channel max|err| / max|ref|, max over checked channels"}
+        rel = lambda g, r: (np.abs(g.cpu().numpy()[idx].astype(np.float64) - r).max(-1)
+                            / np.abs(r).max(-1))
+        per = {"y": rel(st["y"], yr), "grad_x": rel(st["gx"], gr[0]),
+               "grad_b": rel(st["gb"], gr[1]), "grad_a": rel(st["ga"], gr[2]),
+               "grad_zi": rel(st["gz"], gr[3])}
+        rel_err = {k: float(v.max()) for k, v in per.items()}
+        rel_err.update({"channels_checked": len(idx),
+                        "metric": "per-channel max|err| / max|ref|, max over checked channels",
+                        "by_pole_radius": radius_bins(per, w.radius[idx])})
 
     # sequential-kernel leg (the baseline the chunked form is compared with)
     seq = None
