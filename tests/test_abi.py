@@ -143,3 +143,12 @@ def test_bf16_precisions_unsupported(L, precision):
     sz = ctypes.c_size_t()
     assert L.dfilt_workspace_size(4, 100, 2, 2, ctypes.byref(o), ctypes.byref(sz), None,
                                   None) == 2
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No fallback: with libdfilt.so absent the binding raises instead of computing
+    anything another way."""
+    monkeypatch.setattr(dfilt, "LIB_PATH", str(tmp_path / "libdfilt.so"))
+    monkeypatch.setattr(dfilt, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        dfilt.lib()
