@@ -77,7 +77,23 @@ typedef struct {
                         FP32 arithmetic, about 44 bits: FP64-class accuracy without
                         GB300's narrow FP64 pipe): -1 auto (orders above 4),
                         0 off (FP32 two-level scan, orders <= 16), 1 on */
+    int path;        /* chunked algorithm, orders above 8 (state buckets 16..64) with the
+                        high-precision scan: DFILT_PATH_AUTO, DFILT_PATH_FUSED or
+                        DFILT_PATH_DECOUPLED (below); lower orders always run fused */
+    int span_tiles;  /* decoupled path: 8192-sample tiles per scan span (a power of two,
+                        1..4096) -- a channel longer than one span is scanned by several
+                        CTAs joined by a look-back; 0 = automatic (tuning table, else a
+                        rule on the batch shape) */
 } dfilt_opts;
+
+typedef enum {
+    DFILT_PATH_AUTO = 0,         /* decoupled where a `saved` buffer is given, else fused */
+    DFILT_PATH_FUSED = 1,        /* one persistent kernel per call: tiles of a channel in
+                                    order on one SM, the chunk-state scan inside it */
+    DFILT_PATH_DECOUPLED = 2     /* separate launches: tensor-core E pass, chunk-state scan
+                                    over spans of channels on many SMs (bounded look-back),
+                                    tensor-core output pass; needs `saved` */
+} dfilt_path;
 
 /* Library version (major*10000 + minor*100 + patch). */
 int dfilt_version(void);

@@ -17,14 +17,17 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfilt.so")
 BUCKETS = [2, 4, 8, 16, 32, 64]
+HI_BUCKETS = [16, 32, 64]   # the decoupled high-order path
 # (object name, source, extra defines): the chunked kernels compile once per state bucket
 UNITS = ([("api", "api.cu", []), ("seq", "seq.cu", []), ("chunk_setup", "chunk_setup.cu", []),
           ("chunk_dispatch", "chunk_dispatch.cu", []), ("noalloc", "noalloc.cu", []),
           ("jvp", "jvp.cu", []), ("ss", "ss.cu", []),
           ("ic", "ic.cu", [])]
          + [(f"chunk_fwd_{m}", "chunk_fwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS]
-         + [(f"chunk_bwd_{m}", "chunk_bwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS])
-HEADERS = ["common.cuh", "kernels.h", "chunk.cuh", "chunk_pipe.cuh", "dword.cuh"]
+         + [(f"chunk_bwd_{m}", "chunk_bwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS]
+         + [(f"hi_tc_{m}", "hi_tc.cu", [f"-DDFILT_MB={m}"]) for m in HI_BUCKETS]
+         + [(f"hi_scan_{m}", "hi_scan.cu", [f"-DDFILT_MB={m}"]) for m in HI_BUCKETS])
+HEADERS = ["common.cuh", "kernels.h", "chunk.cuh", "chunk_pipe.cuh", "dword.cuh", "hi.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=true",
               "-I", os.path.join(ROOT, "include")]

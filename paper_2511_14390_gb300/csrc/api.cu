@@ -86,6 +86,7 @@ struct Resolved {
     int algo;
     int precision;
     int fp64_opt;   // chunk-state scan option: -1 automatic per state bucket, 0 FP32, 1 FP64
+    HiOpt hi;       // high-order path and scan span length
 };
 
 dfilt_status resolve(const dfilt_opts *o, int Mmax, Resolved *r) {
@@ -95,6 +96,11 @@ dfilt_status resolve(const dfilt_opts *o, int Mmax, Resolved *r) {
     if (o->algo < DFILT_ALGO_AUTO || o->algo > DFILT_ALGO_CHUNKED) return DFILT_ERR_INVALID_ARG;
     if (o->chunk_len != 0 && o->chunk_len != kL) return DFILT_ERR_UNSUPPORTED;
     if (o->fp64_scan < -1 || o->fp64_scan > 1) return DFILT_ERR_INVALID_ARG;
+    if (o->path < DFILT_PATH_AUTO || o->path > DFILT_PATH_DECOUPLED) return DFILT_ERR_INVALID_ARG;
+    if (o->span_tiles < 0 || o->span_tiles > 4096 || (o->span_tiles & (o->span_tiles - 1)) != 0)
+        return DFILT_ERR_INVALID_ARG;
+    r->hi.path = o->path;
+    r->hi.span_tiles = o->span_tiles;
     r->algo = o->algo == DFILT_ALGO_AUTO ? DFILT_ALGO_CHUNKED : o->algo;
     r->precision = o->precision;
     if (r->algo == DFILT_ALGO_CHUNKED) {
@@ -126,9 +132,9 @@ void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, bool ragged, s
            size_t *saved, size_t *bwd) {
     size_t f = 0, s = 0, w = 0;
     if (r.algo == DFILT_ALGO_CHUNKED) {
-        f = chunk_fwd_ws_bytes(B, Mmax, r.fp64_opt, ragged);
+        f = chunk_fwd_ws_bytes(B, total, Mmax, r.fp64_opt, ragged, r.hi);
         s = chunk_saved_bytes(B, total, Mmax, r.fp64_opt, ragged);
-        w = chunk_bwd_ws_bytes(B, Mmax, r.fp64_opt, ragged);
+        w = chunk_bwd_ws_bytes(B, total, Mmax, r.fp64_opt, ragged, r.hi);
     }
     if (fwd) *fwd = f;
     if (saved) *saved = s;
@@ -172,11 +178,11 @@ dfilt_status do_forward(const float *x, const float *b, const float *a, const fl
         return cuda_status(e);
     }
     const bool ragged = bt.offsets != nullptr;
-    size_t need = chunk_fwd_ws_bytes(bt.B, Mmax, r.fp64_opt, ragged);
+    size_t need = chunk_fwd_ws_bytes(bt.B, bt.total, Mmax, r.fp64_opt, ragged, r.hi);
     if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
     return cuda_status(launch_chunk_fwd(x, b, a, zi, y, static_cast<float *>(saved), ws, bt, Mmax,
-                                        r.fp64_opt, r.precision, di.num_sms, st));
+                                        r.fp64_opt, r.precision, di.num_sms, st, r.hi));
 }
 
 bool numeric_check_on() {
@@ -209,12 +215,12 @@ dfilt_status do_backward(const float *gy, const float *x, const float *y, const 
     }
     if (!y && !saved) return DFILT_ERR_INVALID_ARG;
     const bool ragged = bt.offsets != nullptr;
-    size_t need = chunk_bwd_ws_bytes(bt.B, Mmax, r.fp64_opt, ragged);
+    size_t need = chunk_bwd_ws_bytes(bt.B, bt.total, Mmax, r.fp64_opt, ragged, r.hi);
     if (ws_bytes < need || (need && !ws)) return DFILT_ERR_WORKSPACE;
     if (!aligned16(ws) || (saved && !aligned16(saved))) return DFILT_ERR_INVALID_ARG;
     return cuda_status(launch_chunk_bwd(gy, x, y, b, a, static_cast<const float *>(saved), gx, gb,
                                         ga, gzi, ws, bt, Mmax, r.fp64_opt, r.precision,
-                                        di.num_sms, st));
+                                        di.num_sms, st, r.hi));
 }
 
 // ---- kernel timing: event pairs around each call's main kernel --------------------
@@ -318,6 +324,8 @@ dfilt_status dfilt_default_opts(dfilt_opts *o) {
     o->precision = DFILT_PREC_TF32X3;
     o->chunk_len = 0;
     o->fp64_scan = -1;
+    o->path = DFILT_PATH_AUTO;
+    o->span_tiles = 0;
     return DFILT_OK;
 }
 

@@ -46,7 +46,12 @@ struct ChunkTab {
     __host__ __device__ static constexpr size_t fwd_rec(bool f64) { return (F_SCAN + scan_bytes(f64) + 255) / 256 * 256; }
     __host__ __device__ static constexpr size_t b_coef(bool f64) { return (B_SCAN + scan_bytes(f64) + 15) / 16 * 16; }
     static constexpr size_t COEF_BYTES = ((2 * MB + 1) * 4 + 15) / 16 * 16;
-    __host__ __device__ static constexpr size_t bwd_rec(bool f64) { return (b_coef(f64) + COEF_BYTES + 255) / 256 * 256; }
+    // then (orders above 4) O_L[L][MB] f32, so that a backward can recompute y from the
+    // forward's chunk states with the backward record alone
+    __host__ __device__ static constexpr size_t b_ol(bool f64) { return b_coef(f64) + COEF_BYTES; }
+    __host__ __device__ static constexpr size_t bwd_rec(bool f64) {
+        return (b_ol(f64) + (MB > 4 ? (size_t)kL * MB * 4 : 0) + 255) / 256 * 256;
+    }
 };
 
 // Workspace header: a 256-byte block holding the work counter, then the records.

@@ -597,8 +597,10 @@ struct BwSmem {
     // FP64 reverse scan scratch per group (E' and S' per chunk)
     static constexpr uint32_t SCR = (STG + G_PART0 + G_PART1 + 15) / 16 * 16;
     static constexpr uint32_t SCR_G = F64 ? 2 * kChunks * MB * 4 + 2 * MB * 8 : 0;   // + scan state
-    static constexpr uint32_t ACC = (SCR + 2 * SCR_G + 7) / 8 * 8;   // [2 slots][NACC] doubles
-    static constexpr uint32_t CNT = ACC + 2 * NACC * 8;              // tiles done [2 slots]
+    // lag sums per [table slot][group][warp][NACC] doubles: one writer per slot, so every
+    // partial sum runs in a fixed order
+    static constexpr uint32_t ACC = (SCR + 2 * SCR_G + 7) / 8 * 8;
+    static constexpr uint32_t CNT = ACC + 16 * NACC * 8;             // tiles done [2 slots]
     static constexpr uint32_t CARRY = CNT + 16;                      // [2][MB] floats
     static constexpr uint32_t CARRY64 = (CARRY + 2 * MB * 4 + 7) / 8 * 8;   // [2][MB] doubles
     static constexpr uint32_t MISC = (CARRY64 + 2 * MB * 8 + 15) / 16 * 16;
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         *abort_flag = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < 2 * NACC; i += kBwThreads) acc_ch[i] = 0.0;
+    for (int i = tid; i < 16 * NACC; i += kBwThreads) acc_ch[i] = 0.0;
     if (tid < 2) tiles_done[tid] = 0u;
     tc_fence_before();
     __syncthreads();
@@ -1291,7 +1293,9 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                     if (lane == k) mine = v;
                 }
-                if (lane < NACC) atomicAdd(&acc_ch[pv.tab * NACC + lane], (double)mine);
+                // this warp's own slot (no other thread adds to it): the channel's tiles of
+                // this group are summed in processing order
+                if (lane < NACC) acc_ch[((pv.tab * 2 + eg) * 4 + (et >> 5)) * NACC + lane] += (double)mine;
             }
             named_sync(bar_id, 128);
             if (et == 0) mbar_arrive(&tmem_free[tb]);
@@ -1360,8 +1364,17 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (!epi_ok[3]) break;
                 const Channel c = channel_of(bt, pv.ch);
                 for (int k = et; k < NACC; k += 128) {
-                    const double v = acc_ch[pv.tab * NACC + k];
-                    acc_ch[pv.tab * NACC + k] = 0.0;
+                    // fixed order: warp by warp, the two groups' sums (a commutative pair: the
+                    // group a tile lands on depends on the CTA's earlier channels)
+                    double v = 0.0;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        double *s0 = acc_ch + ((pv.tab * 2 + 0) * 4 + w) * NACC + k;
+                        double *s1 = acc_ch + ((pv.tab * 2 + 1) * 4 + w) * NACC + k;
+                        v += *s0 + *s1;
+                        *s0 = 0.0;
+                        *s1 = 0.0;
+                    }
                     if (k <= MB) {
                         if (gb && k <= c.N) gb[pv.ch * bt.Nstride + k] = (float)v;
                     } else {

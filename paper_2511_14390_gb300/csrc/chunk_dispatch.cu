@@ -2,10 +2,22 @@
 // workspace sizes, and the setup + main kernel launches per bucket.
 #include <cudaTypedefs.h>
 #include <mutex>
+#include <type_traits>
 
 #include "chunk.cuh"
+#include "hi.cuh"
 
 namespace dfilt {
+
+#define DFILT_HI_BUCKETS(X) X(16) X(32) X(64)
+#define DFILT_HI_EXTERN(V)                                                                        \
+    extern template cudaError_t hi_plan<V>(const HiArgs &, const Batch &, cudaStream_t);          \
+    extern template cudaError_t hi_jump<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
+    extern template cudaError_t hi_scan<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
+    extern template cudaError_t hi_tc<V>(const HiArgs &, const Batch &, int, int, cudaStream_t);   \
+    extern template cudaError_t hi_reduce<V>(const HiArgs &, const Batch &, cudaStream_t);
+DFILT_HI_BUCKETS(DFILT_HI_EXTERN)
+#undef DFILT_HI_EXTERN
 
 #define DFILT_EXTERN(V)                                                                          \
     extern template cudaError_t chunk_fwd_mb<V>(const float *, const float *, float *, float *, \
@@ -101,14 +113,103 @@ static size_t list_bytes(int64_t B, bool ragged) {
     return ragged ? ((size_t)(B + 16) * sizeof(int) + 255) / 256 * 256 : 0;
 }
 
-size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged) {
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
-    return kWsHeader + (size_t)B * p.fstride + list_bytes(B, ragged);
+// ---------------------------------------------------------------------------
+// Decoupled high-order path: which buckets take it, and its workspace blocks
+// ---------------------------------------------------------------------------
+static bool hi_eligible(const ChunkLayout &l, const HiOpt &ho) {
+    return l.MB >= 16 && l.fp64_scan && ho.path != DFILT_PATH_FUSED;
 }
 
-size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged) {
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+// Blocks of the decoupled path behind the fused path's workspace (all 256-byte aligned):
+//   ctl      work counters (4 per bucket)
+//   pref     per hi bucket: tile and span prefix sums over its channel positions
+//   jump     per channel: the span transition (MB x MB double words)
+//   flags    per scan item: inclusive state published;  incl: that state
+//   (backward) sprime: the adjoint's chunk states; ybuf: y recomputed; partial: lag
+//   sums per tile
+struct HiWs {
+    size_t ctl = 0, pref = 0, jump = 0, flags = 0, incl = 0, sprime = 0, ybuf = 0, partial = 0;
+    size_t end = 0;
+    size_t ctl_bytes = 0;   // the block cleared once per call (counters)
+    int nhi = 0, mbmax = 0;
+    int64_t items_bound = 0;
+};
+static size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+static HiWs hi_ws(size_t base, const ChunkPlan &p, int64_t B, int64_t total, int Mstride,
+                  bool bwd, const HiOpt &ho) {
+    HiWs h;
+    for (int j = 0; j < p.nb; ++j)
+        if (hi_eligible(p.lay[j], ho)) {
+            ++h.nhi;
+            h.mbmax = p.lay[j].MB > h.mbmax ? p.lay[j].MB : h.mbmax;
+        }
+    h.end = base;
+    if (!h.nhi) return h;
+    // every span holds at least one tile and every channel ends at most one partial
+    // tile: items and tiles per bucket are at most total / 8192 + B + 1
+    h.items_bound = total / kTileSamples + B + 1;
+    size_t o = al256(base);
+    h.ctl = o;
+    h.ctl_bytes = 256;
+    o += 256;
+    h.pref = o;
+    o += al256((size_t)h.nhi * 2 * (B + 1) * sizeof(int64_t));
+    h.jump = o;
+    o += al256((size_t)B * h.mbmax * h.mbmax * 8);
+    h.flags = o;
+    o += al256((size_t)h.items_bound * 4);
+    h.incl = o;
+    o += al256((size_t)h.items_bound * h.mbmax * 8);
+    if (bwd) {
+        h.sprime = o;
+        o += chunk_saved_state_bytes(B, total, Mstride);
+        h.ybuf = o;
+        o += al256((size_t)total * 4);
+        h.partial = o;
+        o += al256((size_t)h.items_bound * (2 * h.mbmax + 1) * 4);
+    }
+    h.end = o;
+    return h;
+}
+
+static size_t fused_fwd_ws(int64_t B, const ChunkPlan &p, bool ragged) {
+    return kWsHeader + (size_t)B * p.fstride + list_bytes(B, ragged);
+}
+static size_t fused_bwd_ws(int64_t B, const ChunkPlan &p, bool ragged) {
     return kWsHeader + (size_t)B * p.bstride + list_bytes(B, ragged);
+}
+
+size_t chunk_fwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                          const HiOpt &ho) {
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    return hi_ws(fused_fwd_ws(B, p, ragged), p, B, total, Mmax, false, ho).end;
+}
+
+size_t chunk_bwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                          const HiOpt &ho) {
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    return hi_ws(fused_bwd_ws(B, p, ragged), p, B, total, Mmax, true, ho).end;
+}
+
+// Span length of the decoupled scan (tiles, a power of two): the caller's choice, else
+// enough spans that the chains fill every SM several times over.
+int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, const HiOpt &ho) {
+    if (ho.span_tiles > 0) return ho.span_tiles;
+    const int64_t chains = (int64_t)num_sms * 4;
+    int64_t want;
+    if (!ragged) {
+        const int64_t T = B > 0 ? total / B : 0;
+        const int64_t nt = (T + kTileSamples - 1) / kTileSamples;
+        const int64_t per = B >= chains ? 1 : (chains + B - 1) / B;   // spans per channel
+        want = (nt + per - 1) / per;
+    } else {
+        want = (total / kTileSamples) / chains;
+    }
+    (void)MB;
+    int st = 1;
+    while (st < want && st < 4096) st <<= 1;
+    return st;
 }
 
 size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged) {
@@ -152,9 +253,41 @@ __global__ void __launch_bounds__(1024) bucket_channels_kernel(const int *__rest
 
 }  // namespace
 
+// The decoupled path for bucket j of a call (forward or backward), launched on `st`.
+struct HiCall {
+    HiArgs a;
+    Batch bt;
+    int MB;
+};
+
+template <class F>
+static cudaError_t hi_switch(int MB, F f) {
+    switch (MB) {
+        case 16: return f(std::integral_constant<int, 16>{});
+        case 32: return f(std::integral_constant<int, 32>{});
+        case 64: return f(std::integral_constant<int, 64>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Fill the plan pointers of bucket `hj` (its rank among the call's hi buckets).
+static void hi_plan_ptrs(HiArgs &a, char *w, const HiWs &hw, int hj, int64_t B, int span_tiles) {
+    int64_t *pref = reinterpret_cast<int64_t *>(w + hw.pref) + (size_t)hj * 2 * (B + 1);
+    a.plan.tile_pref = pref;
+    a.plan.span_pref = pref + (B + 1);
+    a.plan.span_tiles = span_tiles;
+    int lg = 0;
+    while ((1 << lg) < span_tiles) ++lg;
+    a.plan.log2_span = lg;
+    a.jump = reinterpret_cast<float2 *>(w + hw.jump);
+    a.flags = reinterpret_cast<unsigned *>(w + hw.flags);
+    a.incl = reinterpret_cast<float2 *>(w + hw.incl);
+}
+
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
-                             int fp64_opt, int precision, int num_sms, cudaStream_t st) {
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st,
+                             const HiOpt &ho) {
     const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
     const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
     char *w = static_cast<char *>(ws);
@@ -162,11 +295,23 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
     // with a saved buffer, the same setup launch also writes the backward's tables into it
     char *btabs = saved ? reinterpret_cast<char *>(saved) + chunk_saved_state_bytes(bt.B, bt.total, Mmax)
                         : nullptr;
+    const HiWs hw = hi_ws(fused_fwd_ws(bt.B, p, ragged), p, bt.B, bt.total, Mmax, false, ho);
     Batch bb[8];
     int *list = reinterpret_cast<int *>(w + kWsHeader + (size_t)bt.B * p.fstride);
     if (ragged) {
         bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, list, list + bt.B);
         cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // the decoupled path needs `saved` for its chunk states
+    bool use_hi[8] = {};
+    bool any_hi = false;
+    for (int j = 0; j < p.nb; ++j) {
+        use_hi[j] = saved != nullptr && hw.nhi > 0 && hi_eligible(p.lay[j], ho);
+        any_hi |= use_hi[j];
+    }
+    if (any_hi) {
+        const cudaError_t e = cudaMemsetAsync(w + hw.ctl, 0, hw.ctl_bytes, st);
         if (e != cudaSuccess) return e;
     }
     for (int j = 0; j < p.nb; ++j) {
@@ -184,7 +329,48 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
     cudaError_t e = cudaSuccess;
     timing_mark(0, 0, st);
+    int hj = 0;
     for (int j = 0; j < p.nb && e == cudaSuccess; ++j) {
+        if (use_hi[j]) {
+            const int MB = p.lay[j].MB;
+            HiArgs h{};
+            h.sig = x;
+            h.zi = zi;
+            h.out = y;
+            h.states = saved;
+            h.states2 = saved;
+            h.tabs = w + kWsHeader;
+            h.tab_stride = ragged ? (int64_t)p.fstride : (int64_t)p.lay[j].fwd_tab;
+            h.three = three;
+            h.plan.list = bb[j].list;
+            h.plan.list_range = bb[j].list_range;
+            const int stl = hi_span_tiles(MB, bt.B, bt.total, ragged, num_sms, ho);
+            hi_plan_ptrs(h, w, hw, hj, bt.B, stl);
+            auto *ctl = reinterpret_cast<unsigned long long *>(w + hw.ctl) + 4 * hj;
+            ++hj;
+            e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
+                constexpr int V = decltype(mbc)::value;
+                using Tab = ChunkTab<V>;
+                HiArgs q = h;
+                cudaError_t r = hi_plan<V>(q, bb[j], st);
+                if (r != cudaSuccess) return r;
+                q.counter = ctl + 0;
+                r = hi_tc<V>(q, bb[j], hi::kEFwd, num_sms, st);   // E_c into the slots
+                if (r != cudaSuccess) return r;
+                r = hi_jump<V>(q, bb[j], false, num_sms, st);
+                if (r != cudaSuccess) return r;
+                r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
+                if (r != cudaSuccess) return r;
+                q.counter = ctl + 1;
+                r = hi_scan<V>(q, bb[j], false, num_sms, st);   // S_c over the slots
+                if (r != cudaSuccess) return r;
+                q.counter = ctl + 2;
+                q.tab_g = (int)Tab::F_G;
+                q.tab_ol = (int)Tab::F_OL;
+                return hi_tc<V>(q, bb[j], hi::kY, num_sms, st);   // y
+            });
+            continue;
+        }
         switch (p.lay[j].MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
@@ -203,7 +389,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
 cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
                              const float *a, const float *saved, float *gx, float *gb, float *ga,
                              float *gzi, void *ws, const Batch &bt, int Mmax, int fp64_opt,
-                             int precision, int num_sms, cudaStream_t st) {
+                             int precision, int num_sms, cudaStream_t st, const HiOpt &ho) {
     const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
     const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
     const bool read_y = saved == nullptr;   // y is recomputed whenever the chunk states exist
@@ -214,6 +400,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     const char *tabs = saved ? reinterpret_cast<const char *>(saved) +
                                    chunk_saved_state_bytes(bt.B, bt.total, Mmax)
                              : wsc + kWsHeader;
+    const HiWs hw = hi_ws(fused_bwd_ws(bt.B, p, ragged), p, bt.B, bt.total, Mmax, true, ho);
     Batch bb[8];
     int *list = reinterpret_cast<int *>(wsc + kWsHeader + (size_t)bt.B * p.bstride);
     cudaError_t e = cudaSuccess;
@@ -222,7 +409,15 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    bool use_hi[8] = {};
+    bool any_hi = false;
+    for (int j = 0; j < p.nb; ++j) {
+        use_hi[j] = saved != nullptr && hw.nhi > 0 && hi_eligible(p.lay[j], ho);
+        any_hi |= use_hi[j];
+    }
     if (saved) e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * p.nb, st);
+    if (e != cudaSuccess) return e;
+    if (any_hi) e = cudaMemsetAsync(wsc + hw.ctl, 0, hw.ctl_bytes, st);
     if (e != cudaSuccess) return e;
     for (int j = 0; j < p.nb; ++j) {
         bb[j] = bt;
@@ -240,7 +435,70 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     }
     const int three = precision == DFILT_PREC_TF32X3 ? 1 : 0;
     timing_mark(1, 0, st);
+    int hj = 0;
     for (int j = 0; j < p.nb && e == cudaSuccess; ++j) {
+        if (use_hi[j]) {
+            const int MB = p.lay[j].MB;
+            HiArgs h{};
+            h.tabs = tabs;
+            h.tab_stride = ragged ? (int64_t)p.bstride : (int64_t)p.lay[j].bwd_tab;
+            h.three = three;
+            h.plan.list = bb[j].list;
+            h.plan.list_range = bb[j].list_range;
+            const int stl = hi_span_tiles(MB, bt.B, bt.total, ragged, num_sms, ho);
+            hi_plan_ptrs(h, wsc, hw, hj, bt.B, stl);
+            auto *ctl = reinterpret_cast<unsigned long long *>(wsc + hw.ctl) + 4 * hj;
+            ++hj;
+            float *sprime = reinterpret_cast<float *>(wsc + hw.sprime);
+            float *ybuf = reinterpret_cast<float *>(wsc + hw.ybuf);
+            h.partial = reinterpret_cast<float *>(wsc + hw.partial);
+            e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
+                constexpr int V = decltype(mbc)::value;
+                using Tab = ChunkTab<V>;
+                HiArgs q = h;
+                cudaError_t r = hi_plan<V>(q, bb[j], st);
+                if (r != cudaSuccess) return r;
+                // E'_c = (T_h^a G_c)[0:MB] into the adjoint's slots
+                q.sig = gy;
+                q.states = sprime;
+                q.counter = ctl + 0;
+                r = hi_tc<V>(q, bb[j], hi::kEBwd, num_sms, st);
+                if (r != cudaSuccess) return r;
+                r = hi_jump<V>(q, bb[j], true, num_sms, st);
+                if (r != cudaSuccess) return r;
+                r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
+                if (r != cudaSuccess) return r;
+                q.counter = ctl + 1;
+                q.gzi = gzi;
+                r = hi_scan<V>(q, bb[j], true, num_sms, st);   // S'_c, grad_zi
+                if (r != cudaSuccess) return r;
+                const float *yv = y;
+                if (!yv) {
+                    // y recomputed from the forward's chunk states (Y pass, backward record)
+                    HiArgs qy = q;
+                    qy.sig = x;
+                    qy.states2 = saved;
+                    qy.out = ybuf;
+                    qy.counter = ctl + 2;
+                    qy.tab_g = (int)Tab::B_G;
+                    qy.tab_ol = (int)Tab::b_ol(true);
+                    r = hi_tc<V>(qy, bb[j], hi::kY, num_sms, st);
+                    if (r != cudaSuccess) return r;
+                    yv = ybuf;
+                }
+                q.sig = gy;
+                q.x = x;
+                q.y = yv;
+                q.out = gx;
+                q.counter = ctl + 3;
+                r = hi_tc<V>(q, bb[j], hi::kU, num_sms, st);   // grad_x, lag sums per tile
+                if (r != cudaSuccess) return r;
+                q.gb = gb;
+                q.ga = ga;
+                return hi_reduce<V>(q, bb[j], st);
+            });
+            continue;
+        }
         switch (p.lay[j].MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \

@@ -312,8 +312,10 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
         double v[MB];
 #pragma unroll
         for (int k = 0; k < MB; ++k) v[k] = k == m ? 1.0 : 0.0;
+        float *OLb = reinterpret_cast<float *>(R + Tab::b_ol(f64));
         for (int i = 0; i < L; ++i) {
             sOL[i][m] = v[0];
+            OLb[i * MB + m] = (float)v[0];
             const double v0 = v[0];
 #pragma unroll
             for (int k = 0; k < MB; ++k) v[k] = (k + 1 < MB ? v[k + 1] : 0.0) - sa[k] * v0;

@@ -1,0 +1,122 @@
+// The decoupled chunked path for high-order state buckets (MB >= 16).
+//
+// The same chunk algebra as the single-kernel path (chunk.cuh, Sec. 3.2's operator at
+// chunk granularity, L = 64), split into launches so that the one serial part, the
+// chunk-state scan, no longer pins a channel's tiles to one SM:
+//
+//   forward   E pass     E_c = R_L X_c for every chunk (tensor cores, per tile,
+//                        any tile on any SM), written into the chunk-state slots
+//             scan       S_{c+1} = Abar S_c + E_c in double words; a channel is cut
+//                        into spans of whole tiles scanned by different CTAs, joined
+//                        by a bounded look-back (below); S_c overwrites E_c
+//             Y pass     Y_c = T_g X_c + O_L S_c, one tensor-core product with the
+//                        operand [X_c | S_c] (K = L + state width)
+//   backward  E' pass    E'_c = (T_h^a G_c)[0:MB]
+//             scan       S'_{c-1} = Abar' S'_c + E'_c from the end (S'_{C-1} = 0);
+//                        the last state is u[0:MB] = grad_zi
+//             (Y pass)   y recomputed from the forward's states when not given
+//             U pass     U_c = T_h^a G_c + O^u S'_c (tensor cores); then per chunk
+//                        grad_x = sum_k b_k u[n+k] and the lag sums of grad_b,
+//                        grad_a on the CUDA cores, one partial per tile
+//             reduce     per channel, the tile partials summed in tile order (FP64)
+//
+// Look-back (the paper's associative operator applied to spans).  Work items are
+// (channel, span) pairs handed out in order; span s > 0 first scans its own chunks
+// from a zero state (its aggregate A_s), then waits (bounded) for its predecessor's
+// inclusive state P_{s-1} and publishes P_s = J P_{s-1} + A_s, J = Abar^K the
+// transition over K chunks of one span, before it rescans its chunks from P_{s-1}.
+// Span 0 starts from the initial state and publishes its end state.  A predecessor
+// was always handed out earlier, so its CTA is running: no wait can deadlock.
+#pragma once
+
+#include "chunk_pipe.cuh"
+
+namespace dfilt {
+namespace hi {
+
+// Channel positions of one launch (the bucket's sub-list of a ragged batch, or the
+// whole batch) with the prefix sums of their tiles and scan spans.
+struct Plan {
+    const int *list;         // bucket list (nullptr: position = channel)
+    const int *list_range;   // [lo, hi) into list
+    int64_t *tile_pref;      // [n + 1] tiles before each position
+    int64_t *span_pref;      // [n + 1] scan spans before each position
+    int span_tiles;          // tiles per scan span (a power of two)
+    int log2_span;           // log2(span_tiles)
+};
+
+__device__ __forceinline__ int64_t plan_count(const Plan &p, const Batch &bt) {
+    return p.list ? (int64_t)(p.list_range[1] - p.list_range[0]) : bt.B;
+}
+__device__ __forceinline__ int64_t plan_channel(const Plan &p, int64_t pos) {
+    return p.list ? (int64_t)p.list[p.list_range[0] + pos] : pos;
+}
+__device__ __forceinline__ int64_t tiles_of(int64_t len) { return (len + kTileSamples - 1) / kTileSamples; }
+
+// Position whose half-open range [pref[pos], pref[pos+1]) holds item w (w < pref[n]).
+__device__ __forceinline__ int64_t find_pos(const int64_t *pref, int64_t n, int64_t w) {
+    int64_t lo = 0, hi = n;   // invariant: pref[lo] <= w < pref[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pref[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Loads without the (incoherent) L1: data another SM published in this launch.
+__device__ __forceinline__ float2 ld_cg2(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Tile-pass modes
+enum Mode { kEFwd = 0, kEBwd = 1, kY = 2, kU = 3 };
+
+// Number of lag sums per channel: grad_b[0..MB] then grad_a[1..MB]
+template <int MB>
+__host__ __device__ constexpr int nacc() { return 2 * MB + 1; }
+
+}  // namespace hi
+
+// ---- launchers (hi_tc.cu, hi_scan.cu; one translation unit per bucket) ----
+// Table records: the forward record (fwd_tabs, ChunkTab<MB> layout) and the backward
+// record (bwd_tabs) at the strides in bt; states: chunk slots (Mstride floats each).
+struct HiArgs {
+    const float *sig;       // x (forward passes, Y pass) or gy (E', U passes)
+    const float *x;         // U pass: the forward's input
+    const float *y;         // U pass: the forward's output
+    const float *zi;        // forward scan: initial state (nullable)
+    float *out;             // Y pass: y; U pass: grad_x (nullable)
+    float *states;          // chunk slots: E then S (forward), E' then S' (backward)
+    const float *states2;   // U pass reads S' from `states`; Y pass reads S from here
+    float *gzi;             // backward scan: grad_zi (nullable)
+    float *partial;         // U pass: per-tile lag sums; reduce: input
+    float *gb, *ga;         // reduce outputs (nullable)
+    const char *tabs;       // records used by the pass
+    int64_t tab_stride;
+    int tab_g, tab_ol;      // Y pass: byte offsets of g and O_L in a record
+    float2 *jump;           // scan: per channel Abar^K (double words, column-major)
+    unsigned *flags;        // scan: per item, inclusive state published
+    float2 *incl;           // scan: per item inclusive state (MB double words)
+    unsigned long long *counter;
+    hi::Plan plan;
+    int three;
+};
+template <int MB>
+cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st);
+template <int MB>
+cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st);
+template <int MB>
+cudaError_t hi_scan(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st);
+template <int MB>
+cudaError_t hi_tc(const HiArgs &h, const Batch &bt, int mode, int num_sms, cudaStream_t st);
+template <int MB>
+cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st);
+
+}  // namespace dfilt

@@ -1,0 +1,479 @@
+// Decoupled high-order path, CUDA-core kernels: launch plan, span transitions, the
+// chunk-state scan with its look-back, and the fixed-order reduction of the backward's
+// per-tile lag sums.  See hi.cuh for the scheme.
+#include "hi.cuh"
+
+#ifndef DFILT_MB
+#error "compile once per state bucket with -DDFILT_MB=<16|32|64>"
+#endif
+
+namespace dfilt {
+
+namespace {
+
+using hi::Plan;
+
+// ---------------------------------------------------------------------------
+// Plan: per position of the launch's channel list, the tiles and scan spans before it
+// (exclusive prefix sums; one block).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) hi_plan_kernel(Plan p, Batch bt) {
+    __shared__ long long wt[32], ws[32];
+    __shared__ long long carry_t, carry_s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t n = hi::plan_count(p, bt);
+    if (t == 0) {
+        carry_t = 0;
+        carry_s = 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + t;
+        long long nt = 0, ns = 0;
+        if (i < n) {
+            const Channel c = channel_of(bt, hi::plan_channel(p, i));
+            nt = hi::tiles_of(c.len);
+            ns = (nt + p.span_tiles - 1) >> p.log2_span;
+        }
+        // inclusive warp scans, then across warps
+        long long it = nt, is = ns;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long a = __shfl_up_sync(0xffffffffu, it, o);
+            const long long b = __shfl_up_sync(0xffffffffu, is, o);
+            if (lane >= o) {
+                it += a;
+                is += b;
+            }
+        }
+        if (lane == 31) {
+            wt[warp] = it;
+            ws[warp] = is;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            long long a = wt[lane], b = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long a2 = __shfl_up_sync(0xffffffffu, a, o);
+                const long long b2 = __shfl_up_sync(0xffffffffu, b, o);
+                if (lane >= o) {
+                    a += a2;
+                    b += b2;
+                }
+            }
+            wt[lane] = a;   // inclusive over warps
+            ws[lane] = b;
+        }
+        __syncthreads();
+        const long long offt = carry_t + (warp > 0 ? wt[warp - 1] : 0);
+        const long long offs = carry_s + (warp > 0 ? ws[warp - 1] : 0);
+        if (i < n) {
+            p.tile_pref[i] = offt + it - nt;
+            p.span_pref[i] = offs + is - ns;
+        }
+        __syncthreads();
+        if (t == 0) {
+            carry_t += wt[31];
+            carry_s += ws[31];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        p.tile_pref[n] = carry_t;
+        p.span_pref[n] = carry_s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Span transition J = Abar^K, K = 128 * span_tiles chunks, for every channel with more
+// than one span: repeated squaring in double words (column-major, as the scan block).
+// ---------------------------------------------------------------------------
+template <int MB>
+__global__ void __launch_bounds__(256) hi_jump_kernel(HiArgs h, Batch bt, int bwd) {
+    using Tab = ChunkTab<MB>;
+    extern __shared__ float2 sP[];   // [2][MB*MB]
+    const int64_t pos = blockIdx.x;
+    if (pos >= hi::plan_count(h.plan, bt)) return;
+    const int64_t ch = hi::plan_channel(h.plan, pos);
+    const Channel c = channel_of(bt, ch);
+    if (hi::tiles_of(c.len) <= h.plan.span_tiles) return;   // one span: no jump needed
+    const float2 *At = reinterpret_cast<const float2 *>(h.tabs + (size_t)ch * h.tab_stride +
+                                                        (bwd ? Tab::B_SCAN : Tab::F_SCAN));
+    constexpr int E = MB * MB;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) sP[e] = At[e];
+    __syncthreads();
+    const int nsq = 7 + h.plan.log2_span;   // 2^7 chunks per tile
+    int cur = 0;
+    for (int s = 0; s < nsq; ++s) {
+        const float2 *P = sP + cur * E;
+        float2 *Q = sP + (cur ^ 1) * E;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            const int i = e % MB, j = e / MB;   // Q[i][j], column-major at j*MB + i
+            float hh = 0.f, ll = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < MB; ++k) {
+                const float2 pk = P[j * MB + k];   // P[k][j]
+                pipe::dw_acc(hh, ll, P[k * MB + i], pk.x, pk.y);   // P[i][k] * P[k][j]
+            }
+            const dw v = fast_two_sum(hh, ll);
+            Q[e] = make_float2(v.hi, v.lo);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    float2 *J = h.jump + (size_t)ch * E;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) J[e] = sP[cur * E + e];
+}
+
+// ---------------------------------------------------------------------------
+// Chunk-state scan.  One chain per CTA of NT = MB * TPR threads: thread (r, p) owns
+// row r of the transition, columns p*JPT .. p*JPT+JPT-1 in registers (double words);
+// the state vector alternates between two shared-memory buffers, one CTA barrier per
+// chunk.  E rows of a tile are staged in shared memory (double-buffered, cp.async)
+// and overwritten in global memory by the states of the output pass.
+// ---------------------------------------------------------------------------
+template <int MB, int TPR, bool REV>
+__global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, int e_al16) {
+    using Tab = ChunkTab<MB>;
+    constexpr int NT = MB * TPR, JPT = MB / TPR;
+    constexpr int NA = JPT >= 8 ? 4 : (JPT >= 2 ? 2 : 1);   // independent accumulators
+    extern __shared__ float4 smem4[];
+    float *ebuf = reinterpret_cast<float *>(smem4);                  // [2][kChunks][MB]
+    float2 *st = reinterpret_cast<float2 *>(ebuf + 2 * kChunks * MB);   // [2][MB]
+    long long *info = reinterpret_cast<long long *>(st + 2 * MB);    // [4]
+    const int t = threadIdx.x, r = t / TPR, p = t % TPR;
+    auto sync = [] {
+        if constexpr (NT == 32) __syncwarp();
+        else __syncthreads();
+    };
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t total = h.plan.span_pref[n];
+    const int ST = h.plan.span_tiles;
+    const int Ms = bt.Mstride;
+    float2 a[JPT];
+    int64_t cur_ch = -1;
+    bool first_item = true;
+
+    for (;;) {
+        if (t == 0) info[0] = (long long)atomicAdd(h.counter, 1ull);
+        sync();
+        const int64_t w = info[0];
+        sync();   // info[] is rewritten below
+        if (w >= total) break;
+        const int64_t pos = hi::find_pos(h.plan.span_pref, n, w);
+        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const Channel c = channel_of(bt, ch);
+        const int64_t s = w - h.plan.span_pref[pos];
+        const int64_t nsp = h.plan.span_pref[pos + 1] - h.plan.span_pref[pos];
+        const int64_t ntiles = hi::tiles_of(c.len);
+        const int64_t sp = REV ? nsp - 1 - s : s;   // the span's index in time
+        const int64_t t0 = sp * ST, t1 = (t0 + ST < ntiles) ? t0 + ST : ntiles;
+        const int64_t cbase = c.off / kL + ch;       // the channel's first chunk slot
+        if (ch != cur_ch) {
+            const float2 *At = reinterpret_cast<const float2 *>(h.tabs + (size_t)ch * h.tab_stride +
+                                                                (REV ? Tab::B_SCAN : Tab::F_SCAN));
+#pragma unroll
+            for (int q = 0; q < JPT; ++q) a[q] = __ldg(At + (p * JPT + q) * MB + r);
+            cur_ch = ch;
+        }
+
+        // E rows of tile `tile` into staging buffer `b` (rows beyond the tile's chunks
+        // are not read; entries beyond the channel's order read as zero)
+        auto stage = [&](int64_t tile, int b) {
+            const int64_t tl = c.len - tile * kTileSamples;
+            const int nch = (int)(((tl < kTileSamples ? tl : kTileSamples) + kL - 1) / kL);
+            const float *src = h.states + (size_t)(cbase + tile * kChunks) * Ms;
+            float *dst = ebuf + b * kChunks * MB;
+            const uint32_t d0 = smem_u32(dst);
+            if (e_al16) {
+                for (int i = t; i < nch * (MB / 4); i += NT) {
+                    const int row = i / (MB / 4), m4 = (i % (MB / 4)) * 4;
+                    const int nv = c.M - m4 < 0 ? 0 : (c.M - m4 > 4 ? 4 : c.M - m4);
+                    cp_async16(d0 + (uint32_t)(row * MB + m4) * 4,
+                               nv ? (const void *)(src + (size_t)row * Ms + m4) : (const void *)src,
+                               nv * 4);
+                }
+            } else {
+                for (int i = t; i < nch * MB; i += NT) {
+                    const int row = i / MB, m = i % MB;
+                    const bool v = m < c.M;
+                    cp_async4(d0 + (uint32_t)(row * MB + m) * 4,
+                              v ? (const void *)(src + (size_t)row * Ms + m) : (const void *)src, v ? 4 : 0);
+                }
+            }
+            cp_async_commit();
+        };
+
+        // One chunk step: the state in st[buf] enters chunk cc of the staged tile eb;
+        // the next state goes to st[buf ^ 1].  With `out`, the entering state is
+        // written to the chunk's slot.
+        auto step = [&](const float *e, int cc, int buf, float *slot_row) {
+            const float2 *cur = st + buf * MB;
+            float2 *nxt = st + (buf ^ 1) * MB;
+            float hh[NA], ll[NA];
+#pragma unroll
+            for (int i = 0; i < NA; ++i) {
+                hh[i] = 0.f;
+                ll[i] = 0.f;
+            }
+            if (p == 0) hh[0] = e[cc * MB + r];
+#pragma unroll
+            for (int q = 0; q < JPT; ++q) {
+                const float2 sj = cur[p * JPT + q];
+                pipe::dw_acc(hh[q % NA], ll[q % NA], a[q], sj.x, sj.y);
+            }
+            float hs = hh[0], ls = ll[0];
+#pragma unroll
+            for (int i = 1; i < NA; ++i) {
+                const dw s2 = two_sum(hs, hh[i]);
+                hs = s2.hi;
+                ls += ll[i] + s2.lo;
+            }
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hs, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, ls, o);
+                const dw s2 = two_sum(hs, oh);
+                hs = s2.hi;
+                ls += ol + s2.lo;
+            }
+            if (p == 0) {
+                if (slot_row && r < c.M) slot_row[r] = cur[r].x + cur[r].y;
+                const dw v = fast_two_sum(hs, ls);
+                nxt[r] = make_float2(v.hi, v.lo);
+            }
+            sync();
+        };
+
+        // Scan tiles [t0, t1) in processing order from the state in st[buf0]; returns the
+        // buffer holding the final state.  `out` writes the states to the slots.
+        auto run = [&](int buf0, bool out) -> int {
+            int buf = buf0;
+            const int64_t ntl = t1 - t0;
+            stage(REV ? t1 - 1 : t0, 0);
+            for (int64_t ti = 0; ti < ntl; ++ti) {
+                const int64_t tile = REV ? t1 - 1 - ti : t0 + ti;
+                if (ti + 1 < ntl) {
+                    stage(REV ? tile - 1 : tile + 1, (int)((ti + 1) & 1));
+                    cp_async_wait_1();
+                } else {
+                    cp_async_wait_all();
+                }
+                sync();
+                const float *e = ebuf + (ti & 1) * kChunks * MB;
+                const int64_t tl = c.len - tile * kTileSamples;
+                const int nch = (int)(((tl < kTileSamples ? tl : kTileSamples) + kL - 1) / kL);
+                float *slots = h.states + (size_t)(cbase + tile * kChunks) * Ms;
+                for (int k = 0; k < nch; ++k) {
+                    const int cc = REV ? nch - 1 - k : k;
+                    step(e, cc, buf, out ? slots + (size_t)cc * Ms : nullptr);
+                    buf ^= 1;
+                }
+                sync();   // staging buffer (ti & 1) is refilled two tiles on
+            }
+            return buf;
+        };
+
+        // timeout drill: the first item also waits on a flag nothing sets
+        if (first_item && bt.stall_drill) {
+            bool ok = false;
+            if (t == 0) {
+                volatile long long *dead = info + 3;
+                *dead = 0;
+                for (long long it = 0; it < bt.wait_limit; ++it) {
+                    if (*dead) {
+                        ok = true;
+                        break;
+                    }
+                    if (it > 64) __nanosleep(32);
+                }
+                if (!ok) set_status(bt.status, DFILT_ERR_TIMEOUT);
+                info[1] = ok ? 1 : 0;
+            }
+            sync();
+            if (!info[1]) break;
+        }
+        first_item = false;
+
+        int fin;
+        if (s == 0) {
+            // the channel's initial state: zi (forward) or zero (adjoint, App. A)
+            if (t < MB) {
+                const float z = (!REV && h.zi && t < c.M) ? h.zi[ch * Ms + t] : 0.f;
+                st[t] = make_float2(z, 0.f);
+            }
+            sync();
+            fin = run(0, true);
+            if (nsp > 1) {
+                if (t < MB) h.incl[(size_t)w * MB + t] = st[fin * MB + t];
+                sync();
+                if (t == 0) {
+                    __threadfence();
+                    hi::st_release(h.flags + w, 1u);
+                }
+            }
+        } else {
+            // aggregate: the span from a zero state
+            if (t < MB) st[t] = make_float2(0.f, 0.f);
+            sync();
+            const int ag = run(0, false);
+            const int pb = ag ^ 1;   // the predecessor's inclusive state goes here
+            if (t == 0) {
+                bool ok = false;
+                for (long long it = 0; it < bt.wait_limit; ++it) {
+                    if (hi::ld_acquire(h.flags + (w - 1)) != 0u) {
+                        ok = true;
+                        break;
+                    }
+                    if (it > 64) __nanosleep(64);
+                }
+                if (!ok) set_status(bt.status, DFILT_ERR_TIMEOUT);
+                __threadfence();
+                info[1] = ok ? 1 : 0;
+            }
+            sync();
+            if (!info[1]) break;
+            if (t < MB) st[pb * MB + t] = hi::ld_cg2(h.incl + (size_t)(w - 1) * MB + t);
+            sync();
+            if (s + 1 < nsp) {
+                // P_s = J P_{s-1} + A_s, published for the next span
+                const float2 *J = h.jump + (size_t)ch * MB * MB;
+                float hh = 0.f, ll = 0.f;
+                if (p == 0) {
+                    hh = st[ag * MB + r].x;
+                    ll = st[ag * MB + r].y;
+                }
+#pragma unroll 4
+                for (int q = 0; q < JPT; ++q) {
+                    const float2 pj = st[pb * MB + p * JPT + q];
+                    pipe::dw_acc(hh, ll, __ldg(J + (p * JPT + q) * MB + r), pj.x, pj.y);
+                }
+#pragma unroll
+                for (int o = TPR / 2; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, hh, o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, ll, o);
+                    const dw s2 = two_sum(hh, oh);
+                    hh = s2.hi;
+                    ll += ol + s2.lo;
+                }
+                if (p == 0) {
+                    const dw v = fast_two_sum(hh, ll);
+                    h.incl[(size_t)w * MB + r] = make_float2(v.hi, v.lo);
+                }
+                sync();
+                if (t == 0) {
+                    __threadfence();
+                    hi::st_release(h.flags + w, 1u);
+                }
+            }
+            fin = run(pb, true);
+        }
+        // the adjoint's last state is u[0 : MB) = grad_zi (the span holding chunk 0)
+        if (REV && sp == 0 && h.gzi && t < c.M) {
+            h.gzi[ch * Ms + t] = st[fin * MB + t].x + st[fin * MB + t].y;
+        }
+        sync();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Coefficient gradients: per channel, the tiles' lag sums in tile order (FP64).
+// One warp per channel position.
+// ---------------------------------------------------------------------------
+template <int MB>
+__global__ void __launch_bounds__(128) hi_reduce_kernel(HiArgs h, Batch bt) {
+    constexpr int NACC = hi::nacc<MB>();
+    const int lane = threadIdx.x & 31;
+    const int64_t pos = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (pos >= hi::plan_count(h.plan, bt)) return;
+    const int64_t ch = hi::plan_channel(h.plan, pos);
+    const Channel c = channel_of(bt, ch);
+    const int64_t tb = h.plan.tile_pref[pos], nt = h.plan.tile_pref[pos + 1] - tb;
+    for (int k = lane; k < NACC; k += 32) {
+        double v = 0.0;
+        for (int64_t i = 0; i < nt; ++i) v += (double)h.partial[(size_t)(tb + i) * NACC + k];
+        if (k <= MB) {
+            if (h.gb && k <= c.N) h.gb[ch * bt.Nstride + k] = (float)v;
+        } else {
+            const int m = k - MB - 1;
+            if (h.ga && m < c.M) h.ga[ch * bt.Mstride + m] = (float)(-v);
+        }
+    }
+    // an empty channel has no adjoint: its state gradient is zero
+    if (c.len == 0 && h.gzi && lane < c.M) h.gzi[ch * bt.Mstride + lane] = 0.f;
+    if (c.len == 0 && h.gzi && lane + 32 < c.M) h.gzi[ch * bt.Mstride + lane + 32] = 0.f;
+}
+
+// threads per state row of the scan (the CTA holds MB * TPR threads)
+constexpr int scan_tpr(int mb) { return mb <= 16 ? 2 : 2; }
+
+template <int MB, bool REV>
+cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st) {
+    constexpr int TPR = scan_tpr(MB);
+    constexpr int NT = MB * TPR;
+    auto kern = hi_scan_kernel<MB, TPR, REV>;
+    const size_t smem = (size_t)2 * kChunks * MB * 4 + 2 * MB * 8 + 64;
+    static int occ[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
+        if (e != cudaSuccess) return e;
+        occ[dev] = o < 1 ? 1 : o;
+    }
+    const int e_al16 = (bt.Mstride % 4 == 0 && (reinterpret_cast<uintptr_t>(h.states) & 15) == 0) ? 1 : 0;
+    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt, e_al16);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <int MB>
+cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st) {
+    hi_plan_kernel<<<1, 1024, 0, st>>>(h.plan, bt);
+    return cudaGetLastError();
+}
+
+template <int MB>
+cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st) {
+    (void)num_sms;
+    const size_t smem = (size_t)2 * MB * MB * 8;
+    auto kern = hi_jump_kernel<MB>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem > 48 * 1024 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    // one block per channel position (at most B; blocks past the launch's list exit)
+    if (bt.B <= 0) return cudaSuccess;
+    kern<<<(unsigned)bt.B, 256, smem, st>>>(h, bt, bwd ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int MB>
+cudaError_t hi_scan(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st) {
+    return bwd ? launch_scan<MB, true>(h, bt, num_sms, st) : launch_scan<MB, false>(h, bt, num_sms, st);
+}
+
+template <int MB>
+cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st) {
+    if (bt.B <= 0) return cudaSuccess;
+    hi_reduce_kernel<MB><<<(unsigned)((bt.B + 3) / 4), 128, 0, st>>>(h, bt);
+    return cudaGetLastError();
+}
+
+template cudaError_t hi_plan<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
+template cudaError_t hi_jump<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
+template cudaError_t hi_scan<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
+template cudaError_t hi_reduce<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
+
+}  // namespace dfilt

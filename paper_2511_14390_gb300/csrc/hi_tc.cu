@@ -1,0 +1,493 @@
+// Decoupled high-order path, tensor-core tile passes (sm_103a).  Every tile (128 chunks
+// x 64 samples of one channel) is independent here, since the chunk states come from
+// the scan kernel: a persistent CTA takes tiles from a counter, in channel order, and
+// rebuilds its B operand only when the channel changes.
+//
+//   E pass (forward)   D = X R_L^T           N = MB      -> E_c into the chunk slots
+//   E' pass (backward) D = G (T_h^a)^T[:MB]  N = MB      -> E'_c into the chunk slots
+//   Y pass             D = [X | S] [T_g | O_L]^T         N = 64 -> y
+//   U pass             D = [G | S'] [T_h^a | O^u]^T      N = 64 -> u; then, per chunk
+//                      row on the CUDA cores, grad_x = sum_k b_k u[n+k] and the lag
+//                      sums of grad_b, grad_a; one partial per tile (fixed order)
+//
+// Operands: K-major, 128-byte swizzle, TF32 split in three products (hi*hi + hi*lo +
+// lo*hi, FP32-class) or one; the raw FP32 words serve as the A hi part (the tensor
+// cores read a TF32 operand's upper 19 bits, which is the hi part of the split).
+#include <cstring>
+
+#include "hi.cuh"
+
+#ifndef DFILT_MB
+#error "compile once per state bucket with -DDFILT_MB=<16|32|64>"
+#endif
+
+namespace dfilt {
+
+namespace {
+
+using hi::Plan;
+constexpr int kThreads = 128;
+constexpr uint32_t kKBlock = kChunks * 128;   // one 32-wide K block of the A operand
+
+template <int MB, int MODE>
+struct TcSmem {
+    using Tab = ChunkTab<MB>;
+    static constexpr bool OUT = MODE >= hi::kY;                   // [signal | state] operand
+    static constexpr int KS = OUT ? (MB <= 32 ? 32 : 64) : 0;     // state K width
+    static constexpr int N = OUT ? kL : Tab::MPAD;                // MMA N
+    static constexpr int KTOT = kL + KS;
+    static constexpr int KB = KTOT / 32;                          // K blocks
+    static constexpr uint32_t BBLK = (uint32_t)N * 128;           // bytes of one B K block
+    static constexpr uint32_t BHI = 0;
+    static constexpr uint32_t BLO = KB * BBLK;
+    static constexpr uint32_t A0 = (2 * KB * BBLK + 1023) / 1024 * 1024;
+    static constexpr uint32_t AHI = A0;
+    static constexpr uint32_t ALO = A0 + KB * kKBlock;
+    static constexpr uint32_t AEND = A0 + 2 * KB * kKBlock;
+    // U pass epilogue (over the A operand once the product is done): u_ext rows of UW
+    // floats (u[0..64), S'[0..MB), zeros), then the x and y tiles, 256-byte rows
+    static constexpr int UW = (kL + MB + 31) / 32 * 32;
+    static constexpr uint32_t UEXT = A0;
+    static constexpr uint32_t XT = UEXT + (uint32_t)kChunks * UW * 4;
+    static constexpr uint32_t YT = XT + (uint32_t)kChunks * kL * 4;
+    static constexpr uint32_t EPEND = MODE == hi::kU ? YT + (uint32_t)kChunks * kL * 4 : 0;
+    static constexpr int KBLK = (MB + 1 + 15) / 16;               // lag blocks of 16
+    static constexpr uint32_t RED = (AEND > EPEND ? AEND : EPEND);
+    static constexpr uint32_t COEF = RED + (MODE == hi::kU ? 4u * KBLK * 32 * 4 : 0u);
+    static constexpr uint32_t MISC = COEF + (MODE == hi::kU ? (uint32_t)KBLK * 16 * 4 : 0u);
+    // misc: mbarrier (8) | drill mbarrier (8) | tmem base (4) | ok flag (4) | work item (8)
+    static constexpr uint32_t BYTES = MISC + 32;
+    static constexpr uint32_t ALLOC = BYTES + 1024;
+    static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+};
+
+// byte offset of 16-byte piece j of row r in a 256-byte-row staging tile
+__device__ __forceinline__ uint32_t rowp(int r, int j) { return (uint32_t)(r * 256 + ((j ^ (r & 15)) << 4)); }
+
+template <int MB, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    hi_tc_kernel(HiArgs h, Batch bt, int sig_al, int out_al, int xy_al) {
+    using Tab = ChunkTab<MB>;
+    using SM = TcSmem<MB, MODE>;
+    constexpr int N = SM::N, KTOT = SM::KTOT, KB = SM::KB;
+    extern __shared__ char smem_raw[];
+    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + SM::MISC);
+    uint64_t *mbar_dead = mbar + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::MISC + 16);
+    volatile int *ok_slot = reinterpret_cast<volatile int *>(smem + SM::MISC + 20);
+    long long *item = reinterpret_cast<long long *>(smem + SM::MISC + 24);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, SM::TMEM_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_init(mbar_dead, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = idesc_tf32_m128(N);
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t total = h.plan.tile_pref[n];
+    const int Ms = bt.Mstride;
+    uint32_t phase = 0;
+    int64_t cur_ch = -1;
+
+    for (;;) {
+        if (tid == 0) *item = (long long)atomicAdd(h.counter, 1ull);
+        __syncthreads();
+        const int64_t w = *item;
+        if (w >= total) break;
+        const int64_t pos = hi::find_pos(h.plan.tile_pref, n, w);
+        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const Channel c = channel_of(bt, ch);
+        const int64_t tile = w - h.plan.tile_pref[pos];
+        const int64_t tstart = c.off + tile * kTileSamples;
+        const int64_t tl64 = c.len - tile * kTileSamples;
+        const int tlen = (int)(tl64 < kTileSamples ? tl64 : kTileSamples);
+        const int nch = (tlen + kL - 1) / kL;
+        const int64_t slot0 = c.off / kL + ch + tile * kChunks;   // the tile's first chunk slot
+        const char *R = h.tabs + (size_t)ch * h.tab_stride;
+
+        // ---- B operand (the channel's tables), split into TF32 hi | lo ----
+        if (ch != cur_ch) {
+            for (int idx = tid; idx < N * KTOT; idx += kThreads) {
+                const int nn = idx / KTOT, k = idx % KTOT;
+                float v = 0.f;
+                if constexpr (MODE == hi::kEFwd) {
+                    if (nn < MB) v = reinterpret_cast<const float *>(R + Tab::F_RL)[nn * kL + k];
+                } else if constexpr (MODE == hi::kEBwd) {
+                    if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
+                } else if constexpr (MODE == hi::kY) {
+                    if (k < kL) {
+                        if (k <= nn) v = reinterpret_cast<const float *>(R + h.tab_g)[nn - k];
+                    } else if (k - kL < MB) {
+                        v = reinterpret_cast<const float *>(R + h.tab_ol)[nn * MB + (k - kL)];
+                    }
+                } else {
+                    if (k < kL) {
+                        if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
+                    } else if (k - kL < MB) {
+                        v = reinterpret_cast<const float *>(R + Tab::B_OU)[nn * MB + (k - kL)];
+                    }
+                }
+                float hv, lv;
+                split_tf32(v, hv, lv);
+                const uint32_t o = (uint32_t)(k >> 5) * SM::BBLK + sw128_off(nn, k & 31);
+                *reinterpret_cast<float *>(smem + SM::BHI + o) = hv;
+                *reinterpret_cast<float *>(smem + SM::BLO + o) = lv;
+            }
+            if constexpr (MODE == hi::kU) {
+                // b_0..b_MB from the record's coefficient block (zero past the order)
+                const float *cf = reinterpret_cast<const float *>(R + Tab::b_coef(true));
+                float *sb = reinterpret_cast<float *>(smem + SM::COEF);
+                for (int k = tid; k < SM::KBLK * 16; k += kThreads) sb[k] = k <= MB ? cf[MB + k] : 0.f;
+            }
+            cur_ch = ch;
+        }
+
+        // ---- A operand: the signal tile, then (Y, U) the chunk states ----
+        pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, tstart, tlen,
+                                        sig_al && ((tstart & 3) == 0), tid);
+        if constexpr (SM::OUT) {
+            const float *sv = MODE == hi::kY ? h.states2 : h.states;
+            const float *src = sv + (size_t)slot0 * Ms;
+            constexpr int P4 = SM::KS / 4;   // 16-byte pieces per row
+            for (int id = tid; id < kChunks * P4; id += kThreads) {
+                const int row = id / P4, m4 = (id % P4) * 4;
+                const uint32_t d = sbase + SM::AHI + (uint32_t)(2 + (m4 >> 5)) * kKBlock + sw128_off(row, m4 & 31);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int m = m4 + e;
+                    const bool v = row < nch && m < c.M;
+                    cp_async4(d + 4 * e, v ? (const void *)(src + (size_t)row * Ms + m) : (const void *)sv,
+                              v ? 4 : 0);
+                }
+            }
+            cp_async_commit();
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (h.three) {
+            for (int id = tid; id < KB * kChunks * 8; id += kThreads) {
+                const int kb = id / (kChunks * 8), rem = id % (kChunks * 8);
+                const int r = rem >> 3, j = rem & 7;
+                const uint32_t o = (uint32_t)kb * kKBlock + (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4));
+                const float4 v = *reinterpret_cast<const float4 *>(smem + SM::AHI + o);
+                float4 hv, lv;
+                split_tf32(v.x, hv.x, lv.x);
+                split_tf32(v.y, hv.y, lv.y);
+                split_tf32(v.z, hv.z, lv.z);
+                split_tf32(v.w, hv.w, lv.w);
+                *reinterpret_cast<float4 *>(smem + SM::ALO + o) = lv;
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        // ---- tensor cores ----
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < KTOT / 8; ++kk) {
+                const uint32_t ka = (uint32_t)(kk >> 2) * kKBlock + (kk & 3) * 32;
+                const uint32_t kbo = (uint32_t)(kk >> 2) * SM::BBLK + (kk & 3) * 32;
+                const uint64_t ahi = sdesc_sw128(sbase + SM::AHI + ka);
+                const uint64_t bhi = sdesc_sw128(sbase + SM::BHI + kbo);
+                mma_tf32(tmem, ahi, bhi, idesc, kk > 0 ? 1u : 0u);
+                if (h.three) {
+                    mma_tf32(tmem, ahi, sdesc_sw128(sbase + SM::BLO + kbo), idesc, 1u);
+                    mma_tf32(tmem, sdesc_sw128(sbase + SM::ALO + ka), bhi, idesc, 1u);
+                }
+            }
+            mma_commit(mbar);
+            bool ok = mbar_wait_bounded(mbar, phase, bt.wait_limit);
+            if (ok && bt.stall_drill) ok = mbar_wait_bounded(mbar_dead, 0, bt.wait_limit);
+            if (!ok) {
+                set_status(bt.status, DFILT_ERR_TIMEOUT);
+                mbar_wait_bounded(mbar, phase, kDefaultWaitLimit);   // drain before leaving
+            }
+            *ok_slot = ok ? 1 : 0;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        tc_fence_after();
+        if (!*ok_slot) break;
+
+        // ---- epilogues (thread = chunk row = TMEM lane) ----
+        const int cr = tid;
+        if constexpr (MODE == hi::kEFwd || MODE == hi::kEBwd) {
+            float *dst = h.states + (size_t)(slot0 + cr) * Ms;
+#pragma unroll
+            for (int cb = 0; cb < N / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
+                if (cr < nch) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (cb * 16 + i < c.M) dst[cb * 16 + i] = v[i];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+        } else if constexpr (MODE == hi::kY) {
+            char *stag = smem + SM::AHI;   // the operand is consumed
+#pragma unroll
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int p4 = 0; p4 < 4; ++p4)
+                    *reinterpret_cast<float4 *>(stag + rowp(cr, cb * 4 + p4)) =
+                        make_float4(v[4 * p4], v[4 * p4 + 1], v[4 * p4 + 2], v[4 * p4 + 3]);
+            }
+            tc_fence_before();
+            __syncthreads();
+            const bool al = out_al && ((tstart & 3) == 0);
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+                const int id = tid + kThreads * q;
+                const int r = id >> 4, j = id & 15;
+                const float4 v = *reinterpret_cast<const float4 *>(stag + rowp(r, j));
+                const int s = r * kL + j * 4;
+                const int nv = min(max(tlen - s, 0), 4);
+                float *g = h.out + tstart + s;
+                if (nv == 4 && al) {
+                    *reinterpret_cast<float4 *>(g) = v;
+                } else {
+                    if (nv > 0) g[0] = v.x;
+                    if (nv > 1) g[1] = v.y;
+                    if (nv > 2) g[2] = v.z;
+                    if (nv > 3) g[3] = v.w;
+                }
+            }
+            __syncthreads();
+        } else {
+            constexpr int UW = SM::UW, KBLK = SM::KBLK, NACC = hi::nacc<MB>();
+            // (1) S'_c of this row (raw words of the operand's state blocks)
+            float sp[MB];
+#pragma unroll
+            for (int m = 0; m < MB; ++m)
+                sp[m] = *reinterpret_cast<const float *>(smem + SM::AHI + (uint32_t)(2 + (m >> 5)) * kKBlock +
+                                                         sw128_off(cr, m & 31));
+            __syncthreads();   // the operand region is rewritten from here on
+            // (2) x and y tiles (rows of 256 bytes), u_ext rows
+            {
+                const bool al = xy_al && ((tstart & 3) == 0);
+                for (int q = 0; q < 16; ++q) {
+                    const int id = tid + kThreads * q;
+                    const int r = id >> 4, j = id & 15;
+                    const int s = r * kL + j * 4;
+                    const int nv = min(max(tlen - s, 0), 4);
+                    const uint32_t dx = sbase + SM::XT + rowp(r, j), dy = sbase + SM::YT + rowp(r, j);
+                    const float *gx_ = h.x + tstart + s, *gy_ = h.y + tstart + s;
+                    if (al) {
+                        cp_async16(dx, nv ? (const void *)gx_ : (const void *)h.x, nv * 4);
+                        cp_async16(dy, nv ? (const void *)gy_ : (const void *)h.y, nv * 4);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            cp_async4(dx + 4 * e, e < nv ? (const void *)(gx_ + e) : (const void *)h.x, e < nv ? 4 : 0);
+                            cp_async4(dy + 4 * e, e < nv ? (const void *)(gy_ + e) : (const void *)h.y, e < nv ? 4 : 0);
+                        }
+                    }
+                }
+                cp_async_commit();
+            }
+            char *urow = smem + SM::UEXT + (uint32_t)cr * UW * 4;
+            auto upiece = [&](int j) { return urow + (((j ^ (cr & 7))) << 4); };
+#pragma unroll
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int p4 = 0; p4 < 4; ++p4)
+                    *reinterpret_cast<float4 *>(upiece(cb * 4 + p4)) =
+                        make_float4(v[4 * p4], v[4 * p4 + 1], v[4 * p4 + 2], v[4 * p4 + 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < (UW - kL) / 4; ++j) {
+                float q4[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) q4[e] = (4 * j + e < MB) ? sp[4 * j + e] : 0.f;
+                *reinterpret_cast<float4 *>(upiece(kL / 4 + j)) = make_float4(q4[0], q4[1], q4[2], q4[3]);
+            }
+            tc_fence_before();
+            cp_async_wait_all();
+            __syncthreads();
+            const char *xrow = smem + SM::XT, *yrow = smem + SM::YT;
+            auto ld16 = [&](const char *base, int j0, float (&v)[16]) {   // samples 4*j0 .. 4*j0+15
+#pragma unroll
+                for (int p4 = 0; p4 < 4; ++p4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(base + rowp(cr, j0 + p4));
+                    v[4 * p4] = q.x; v[4 * p4 + 1] = q.y; v[4 * p4 + 2] = q.z; v[4 * p4 + 3] = q.w;
+                }
+            };
+            auto ldwin = [&](int f0, float (&win)[32]) {   // u_ext[f0 .. f0+32), zero past the row
+#pragma unroll
+                for (int p4 = 0; p4 < 8; ++p4) {
+                    const int j = f0 / 4 + p4;
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (j < UW / 4) q = *reinterpret_cast<const float4 *>(upiece(j));
+                    win[4 * p4] = q.x; win[4 * p4 + 1] = q.y; win[4 * p4 + 2] = q.z; win[4 * p4 + 3] = q.w;
+                }
+            };
+            // (3) lag sums: b-lag k: sum_n u[n+k] x[n] (k = 0..MB), a-lag k: sum_n u[n+1+k] y[n]
+            float *red = reinterpret_cast<float *>(smem + SM::RED);
+#pragma unroll 1
+            for (int kb = 0; kb < KBLK; ++kb) {
+                float acc[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+#pragma unroll 1
+                for (int nb = 0; nb < kL / 16; ++nb) {
+                    float xv[16], yv[16], win[32];
+                    ld16(xrow, nb * 4, xv);
+                    ld16(yrow, nb * 4, yv);
+                    ldwin(16 * (nb + kb), win);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            acc[j] = fmaf(win[q + j], xv[q], acc[j]);
+                            acc[16 + j] = fmaf(win[q + 1 + j], yv[q], acc[16 + j]);
+                        }
+                    }
+                }
+                // warp total of all 32 sums: halving butterfly, lane L ends with sum L
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < o; ++i) {
+                        const bool up = (lane & o) != 0;
+                        const float send = up ? acc[i] : acc[i + o];
+                        const float keep = up ? acc[i + o] : acc[i];
+                        acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+                red[(warp * KBLK + kb) * 32 + lane] = acc[0];
+            }
+            // (4) grad_x = sum_k b_k u[n+k], written over this row of the x tile
+            const float *sb = reinterpret_cast<const float *>(smem + SM::COEF);
+            const int nkb = (c.N + 16) / 16;
+#pragma unroll 1
+            for (int nb = 0; nb < kL / 16; ++nb) {
+                float g[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) g[q] = 0.f;
+#pragma unroll 1
+                for (int kb = 0; kb < nkb; ++kb) {
+                    float win[32], bv[16];
+                    ldwin(16 * (nb + kb), win);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) bv[j] = sb[16 * kb + j];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) g[q] = fmaf(bv[j], win[q + j], g[q]);
+                }
+#pragma unroll
+                for (int p4 = 0; p4 < 4; ++p4)
+                    *reinterpret_cast<float4 *>(smem + SM::XT + rowp(cr, nb * 4 + p4)) =
+                        make_float4(g[4 * p4], g[4 * p4 + 1], g[4 * p4 + 2], g[4 * p4 + 3]);
+            }
+            __syncthreads();
+            // the tile's lag sums in a fixed order (warps 0..3)
+            for (int i = tid; i < KBLK * 32; i += kThreads) {
+                const int kb = i / 32, j = i % 32;
+                const float v = red[(0 * KBLK + kb) * 32 + j] + red[(1 * KBLK + kb) * 32 + j] +
+                                red[(2 * KBLK + kb) * 32 + j] + red[(3 * KBLK + kb) * 32 + j];
+                const int k = 16 * kb + (j & 15);
+                if (j < 16) {
+                    if (k <= MB) h.partial[(size_t)w * NACC + k] = v;
+                } else if (k < MB) {
+                    h.partial[(size_t)w * NACC + MB + 1 + k] = v;
+                }
+            }
+            if (h.out) {
+                const bool al = out_al && ((tstart & 3) == 0);
+#pragma unroll 4
+                for (int q = 0; q < 16; ++q) {
+                    const int id = tid + kThreads * q;
+                    const int r = id >> 4, j = id & 15;
+                    const float4 v = *reinterpret_cast<const float4 *>(smem + SM::XT + rowp(r, j));
+                    const int s = r * kL + j * 4;
+                    const int nv = min(max(tlen - s, 0), 4);
+                    float *g = h.out + tstart + s;
+                    if (nv == 4 && al) {
+                        *reinterpret_cast<float4 *>(g) = v;
+                    } else {
+                        if (nv > 0) g[0] = v.x;
+                        if (nv > 1) g[1] = v.y;
+                        if (nv > 2) g[2] = v.z;
+                        if (nv > 3) g[3] = v.w;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, SM::TMEM_COLS);
+    }
+}
+
+template <int MB, int MODE>
+cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st) {
+    using SM = TcSmem<MB, MODE>;
+    static_assert(SM::ALLOC <= pipe::kSmemMax, "shared memory budget");
+    auto kern = hi_tc_kernel<MB, MODE>;
+    static int occ[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, SM::ALLOC);
+        if (e != cudaSuccess) return e;
+        const int tmem_cap = 512 / (int)SM::TMEM_COLS;
+        o = o < 1 ? 1 : o;
+        occ[dev] = o < tmem_cap ? o : tmem_cap;
+    }
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? 1 : 0; };
+    const int xy_al = (h.x && h.y) ? (al(h.x) & al(h.y)) : 0;
+    kern<<<(unsigned)(num_sms * occ[dev]), kThreads, SM::ALLOC, st>>>(h, bt, al(h.sig),
+                                                                      h.out ? al(h.out) : 0, xy_al);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <int MB>
+cudaError_t hi_tc(const HiArgs &h, const Batch &bt, int mode, int num_sms, cudaStream_t st) {
+    switch (mode) {
+        case hi::kEFwd: return launch_tc<MB, hi::kEFwd>(h, bt, num_sms, st);
+        case hi::kEBwd: return launch_tc<MB, hi::kEBwd>(h, bt, num_sms, st);
+        case hi::kY: return launch_tc<MB, hi::kY>(h, bt, num_sms, st);
+        case hi::kU: return launch_tc<MB, hi::kU>(h, bt, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t hi_tc<DFILT_MB>(const HiArgs &, const Batch &, int, int, cudaStream_t);
+
+}  // namespace dfilt

@@ -73,16 +73,30 @@ constexpr int kMaxF32ScanBucket = 16;
 // (direction 0 forward, 1 backward).  A no-op while timing is off.
 void timing_mark(int direction, int phase, cudaStream_t st);
 
+// High-order path choice of a call (dfilt_opts.path, .span_tiles).
+struct HiOpt {
+    int path = 0;         // dfilt_path
+    int span_tiles = 0;   // 0 automatic
+};
+
 // fp64_opt: the caller's scan option (-1 automatic per bucket, 0 off, 1 on)
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
                              float *y, float *saved, void *ws, const Batch &bt, int Mmax,
-                             int fp64_opt, int precision, int num_sms, cudaStream_t st);
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st,
+                             const HiOpt &ho);
 cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, const float *b,
                              const float *a, const float *saved, float *gx, float *gb,
                              float *ga, float *gzi, void *ws, const Batch &bt, int Mmax,
-                             int fp64_opt, int precision, int num_sms, cudaStream_t st);
-size_t chunk_fwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged);
-size_t chunk_bwd_ws_bytes(int64_t B, int Mmax, int fp64_opt, bool ragged);
+                             int fp64_opt, int precision, int num_sms, cudaStream_t st,
+                             const HiOpt &ho);
+// Workspace bytes; `total` = samples of the batch (the decoupled path's per-span and
+// per-tile records grow with it).
+size_t chunk_fwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                          const HiOpt &ho);
+size_t chunk_bwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                          const HiOpt &ho);
+// Span length (tiles) the decoupled path uses for a bucket of a call.
+int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, const HiOpt &ho);
 
 // Tensor map of a signal viewed as rows of one chunk (L floats), 3-D so that one box
 // {32 floats, 1 half, 128 rows} is one 128-byte-swizzled K block of a tensor-core

@@ -70,7 +70,11 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     if (o.precision != DFILT_PREC_TF32 && o.precision != DFILT_PREC_TF32X3)
         return DFILT_ERR_UNSUPPORTED;
     // Capacity check before touching the device: the tables for B channels must fit.
-    if (chunk_fwd_ws_bytes(B, M, o.fp64_scan, false) > kNoallocScratchBytes) return DFILT_ERR_WORKSPACE;
+    // (the single-kernel chunked path: its scratch is the per-channel tables alone)
+    HiOpt ho;
+    ho.path = DFILT_PATH_FUSED;
+    if (chunk_fwd_ws_bytes(B, B * T, M, o.fp64_scan, false, ho) > kNoallocScratchBytes)
+        return DFILT_ERR_WORKSPACE;
     if (B == 0 || T == 0) return DFILT_OK;
     int *status = nullptr, num_sms = 0, drill = 0;
     long long wait_limit = 0;
@@ -96,7 +100,7 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     bt.fwd_stride = 0;
     bt.bwd_stride = 0;
     const cudaError_t e = launch_chunk_fwd(x, b, a, zi, y, nullptr, scratch, bt, M, o.fp64_scan,
-                                           o.precision, num_sms, static_cast<cudaStream_t>(stream));
+                                           o.precision, num_sms, static_cast<cudaStream_t>(stream), ho);
     if (e == cudaSuccess) return api_check_output(y, B * T, static_cast<cudaStream_t>(stream));
     return e == cudaErrorNotSupported ? DFILT_ERR_UNSUPPORTED : DFILT_ERR_CUDA;
 }

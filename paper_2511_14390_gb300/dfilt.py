@@ -40,19 +40,27 @@ class DfiltError(RuntimeError):
         self.code = code
 
 
+PATHS = {"auto": 0, "fused": 1, "decoupled": 2}
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("precision", ctypes.c_int),
-                ("chunk_len", ctypes.c_int), ("fp64_scan", ctypes.c_int)]
+                ("chunk_len", ctypes.c_int), ("fp64_scan", ctypes.c_int),
+                ("path", ctypes.c_int), ("span_tiles", ctypes.c_int)]
 
 
-def make_opts(algo="auto", precision="tf32x3", fp64_scan=-1, chunk_len=0) -> Opts:
+def make_opts(algo="auto", precision="tf32x3", fp64_scan=-1, chunk_len=0, path="auto",
+              span_tiles=0) -> Opts:
     if isinstance(algo, str):
         algo = ALGOS[algo]
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
+    if isinstance(path, str):
+        path = PATHS[path]
     if algo == ALGOS["sequential"]:
         precision = PRECISIONS["fp32"]
-    return Opts(int(algo), int(precision), int(chunk_len), int(fp64_scan))
+    return Opts(int(algo), int(precision), int(chunk_len), int(fp64_scan), int(path),
+                int(span_tiles))
 
 
 _lib = None

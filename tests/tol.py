@@ -98,5 +98,7 @@ def log_errors(name: str, **vals):
         v = np.asarray(v, dtype=np.float64)
         rec[k] = {"max": float(v.max()) if v.size else 0.0,
                   "median": float(np.median(v)) if v.size else 0.0}
+        if 1 < v.size <= 64:
+            rec[k]["values"] = [float(t) for t in v.ravel()]
     with open(path, "a") as f:
         f.write(json.dumps(rec) + "\n")
