@@ -336,6 +336,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
             HiArgs h{};
             h.sig = x;
             h.zi = zi;
+            h.acoef = a;
             h.out = y;
             h.states = saved;
             h.states2 = saved;
@@ -440,6 +441,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
         if (use_hi[j]) {
             const int MB = p.lay[j].MB;
             HiArgs h{};
+            h.acoef = a;
             h.tabs = tabs;
             h.tab_stride = ragged ? (int64_t)p.bstride : (int64_t)p.lay[j].bwd_tab;
             h.three = three;

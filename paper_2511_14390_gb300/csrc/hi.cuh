@@ -27,6 +27,17 @@
 // transition over K chunks of one span, before it rescans its chunks from P_{s-1}.
 // Span 0 starts from the initial state and publishes its end state.  A predecessor
 // was always handed out earlier, so its CTA is running: no wait can deadlock.
+//
+// J is not formed by repeated squaring: companion-matrix powers grow transiently by
+// orders of magnitude before they decay, and squaring them loses every digit (it
+// diverges even in FP64 on some order-32 filters).  Instead J follows from the impulse
+// response h of 1/A near n = 64K, written out in closed form (the same identities as
+// the per-chunk tables, with the chunk length 64 replaced by 64K):
+//     forward   J[k][m]  = -sum_{l=k+1..M} a_l h[64K + k - l - m]
+//     adjoint   J'[k][m] = -sum_{j=0..M-1-m} a_{j+1+m} h[64K - 1 - k - j]
+// and h near 64K comes from the impulse's state evolved over K chunks by the chunk
+// transition, in double words: errors stay relative to the decayed values, as in the
+// scan itself.
 #pragma once
 
 #include "chunk_pipe.cuh"
@@ -92,6 +103,7 @@ struct HiArgs {
     const float *x;         // U pass: the forward's input
     const float *y;         // U pass: the forward's output
     const float *zi;        // forward scan: initial state (nullable)
+    const float *acoef;     // span transitions: denominators a[B, Mstride]
     float *out;             // Y pass: y; U pass: grad_x (nullable)
     float *states;          // chunk slots: E then S (forward), E' then S' (backward)
     const float *states2;   // U pass reads S' from `states`; Y pass reads S from here

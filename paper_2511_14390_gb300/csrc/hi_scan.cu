@@ -13,6 +13,9 @@ namespace {
 
 using hi::Plan;
 
+// threads per state row of the scan (the CTA holds MB * TPR threads)
+constexpr int scan_tpr(int mb) { return mb <= 16 ? 2 : 2; }
+
 // ---------------------------------------------------------------------------
 // Plan: per position of the launch's channel list, the tiles and scan spans before it
 // (exclusive prefix sums; one block).
@@ -86,44 +89,146 @@ __global__ void __launch_bounds__(1024) hi_plan_kernel(Plan p, Batch bt) {
 }
 
 // ---------------------------------------------------------------------------
-// Span transition J = Abar^K, K = 128 * span_tiles chunks, for every channel with more
-// than one span: repeated squaring in double words (column-major, as the scan block).
+// Span transition J = Abar^K (K = 128 * span_tiles chunks) of every channel with more
+// than one span, forward (J) or adjoint (J'), from the impulse response of 1/A near
+// n = 64K (hi.cuh).  One CTA per channel, the scan's thread layout; double words:
+//   1. h[0 .. 64 + MB) by the all-pole difference equation (warp 0; the lanes share
+//      each step's dot product)
+//   2. Abar[k][m] = -sum_{l>k} a_l h[64 + k - l - m] and the impulse's state after the
+//      first chunk S_1[k] = -sum_{l>k} a_l h[64 + k - l]
+//   3. S_{c+1} = Abar S_c up to S_{K-1} (the one serial part: K - 2 chunk steps)
+//   4. h[64(K-2) .. 64K) = the free responses of S_{K-2}, S_{K-1}:
+//      h[64c + j] = sum_m h[j - m] S_c[m]
+//   5. J or J' by the closed forms, column-major like the scan block
 // ---------------------------------------------------------------------------
-template <int MB>
-__global__ void __launch_bounds__(256) hi_jump_kernel(HiArgs h, Batch bt, int bwd) {
-    using Tab = ChunkTab<MB>;
-    extern __shared__ float2 sP[];   // [2][MB*MB]
+template <int MB, int TPR>
+__global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, int bwd) {
+    constexpr int NT = MB * TPR, JPT = MB / TPR;
+    constexpr int NA = JPT >= 8 ? 4 : (JPT >= 2 ? 2 : 1);
+    constexpr int H = kL + MB;   // h[0 .. H)
+    extern __shared__ float4 smem4[];
+    float2 *sA = reinterpret_cast<float2 *>(smem4);   // Abar, column-major [MB*MB]
+    float2 *sh = sA + MB * MB;                        // h[0 .. H)
+    float2 *st = sh + H;                              // [2][MB] states
+    float2 *hw = st + 2 * MB;                         // h[64(K-2) .. 64K)  [128]
+    float *sa = reinterpret_cast<float *>(hw + 2 * kL);   // a_1 .. a_MB
+    const int t = threadIdx.x, r = t / TPR, p = t % TPR, lane = t & 31;
+    auto sync = [] {
+        if constexpr (NT == 32) __syncwarp();
+        else __syncthreads();
+    };
     const int64_t pos = blockIdx.x;
     if (pos >= hi::plan_count(h.plan, bt)) return;
     const int64_t ch = hi::plan_channel(h.plan, pos);
     const Channel c = channel_of(bt, ch);
     if (hi::tiles_of(c.len) <= h.plan.span_tiles) return;   // one span: no jump needed
-    const float2 *At = reinterpret_cast<const float2 *>(h.tabs + (size_t)ch * h.tab_stride +
-                                                        (bwd ? Tab::B_SCAN : Tab::F_SCAN));
-    constexpr int E = MB * MB;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) sP[e] = At[e];
-    __syncthreads();
-    const int nsq = 7 + h.plan.log2_span;   // 2^7 chunks per tile
-    int cur = 0;
-    for (int s = 0; s < nsq; ++s) {
-        const float2 *P = sP + cur * E;
-        float2 *Q = sP + (cur ^ 1) * E;
-        for (int e = threadIdx.x; e < E; e += blockDim.x) {
-            const int i = e % MB, j = e / MB;   // Q[i][j], column-major at j*MB + i
+    const int64_t K = (int64_t)kChunks << h.plan.log2_span;
+    for (int k = t; k < MB; k += NT) sa[k] = k < c.M ? h.acoef[ch * bt.Mstride + k] : 0.f;
+    sync();
+    // 1. h by the difference equation h[n] = -sum_{j=1..MB} a_j h[n-j]
+    if (t < 32) {
+        if (t == 0) sh[0] = make_float2(1.f, 0.f);
+        __syncwarp();
+        for (int n = 1; n < H; ++n) {
             float hh = 0.f, ll = 0.f;
-#pragma unroll 8
-            for (int k = 0; k < MB; ++k) {
-                const float2 pk = P[j * MB + k];   // P[k][j]
-                pipe::dw_acc(hh, ll, P[k * MB + i], pk.x, pk.y);   // P[i][k] * P[k][j]
+            for (int j = lane + 1; j <= MB; j += 32)
+                if (j <= n) pipe::dw_acc(hh, ll, sh[n - j], -sa[j - 1], 0.f);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hh, o);
+                const float ol = __shfl_xor_sync(0xffffffffu, ll, o);
+                const dw s2 = two_sum(hh, oh);
+                hh = s2.hi;
+                ll += ol + s2.lo;
             }
-            const dw v = fast_two_sum(hh, ll);
-            Q[e] = make_float2(v.hi, v.lo);
+            if (lane == 0) {
+                const dw v = fast_two_sum(hh, ll);
+                sh[n] = make_float2(v.hi, v.lo);
+            }
+            __syncwarp();
         }
-        __syncthreads();
-        cur ^= 1;
     }
-    float2 *J = h.jump + (size_t)ch * E;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) J[e] = sP[cur * E + e];
+    sync();
+    auto H_ = [&](int n) { return n >= 0 ? sh[n] : make_float2(0.f, 0.f); };
+    // 2. the chunk transition and the impulse's state after one chunk
+    for (int e = t; e < MB * MB; e += NT) {
+        const int k = e % MB, m = e / MB;   // element (k, m) at m*MB + k
+        float hh = 0.f, ll = 0.f;
+        for (int l = k + 1; l <= MB; ++l) pipe::dw_acc(hh, ll, H_(kL + k - l - m), -sa[l - 1], 0.f);
+        const dw v = fast_two_sum(hh, ll);
+        sA[e] = make_float2(v.hi, v.lo);
+    }
+    for (int k = t; k < MB; k += NT) {
+        float hh = 0.f, ll = 0.f;
+        for (int l = k + 1; l <= MB; ++l) pipe::dw_acc(hh, ll, H_(kL + k - l), -sa[l - 1], 0.f);
+        const dw v = fast_two_sum(hh, ll);
+        st[k] = make_float2(v.hi, v.lo);
+    }
+    sync();
+    // 3. S_{c+1} = Abar S_c, c = 1 .. K-2 (S_1 in st[0]); then S_{K-2} and S_{K-1}
+    float2 a[JPT];
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) a[q] = sA[(p * JPT + q) * MB + r];
+    int buf = 0;
+    for (int64_t cc = 1; cc < K - 1; ++cc) {
+        const float2 *cur = st + buf * MB;
+        float hh[NA], ll[NA];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            hh[i] = 0.f;
+            ll[i] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < JPT; ++q) {
+            const float2 sj = cur[p * JPT + q];
+            pipe::dw_acc(hh[q % NA], ll[q % NA], a[q], sj.x, sj.y);
+        }
+        float hs = hh[0], ls = ll[0];
+#pragma unroll
+        for (int i = 1; i < NA; ++i) {
+            const dw s2 = two_sum(hs, hh[i]);
+            hs = s2.hi;
+            ls += ll[i] + s2.lo;
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hs, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, ls, o);
+            const dw s2 = two_sum(hs, oh);
+            hs = s2.hi;
+            ls += ol + s2.lo;
+        }
+        if (p == 0) {
+            const dw v = fast_two_sum(hs, ls);
+            st[(buf ^ 1) * MB + r] = make_float2(v.hi, v.lo);
+        }
+        sync();
+        buf ^= 1;
+    }
+    // st[buf] = S_{K-1}, st[buf ^ 1] = S_{K-2}
+    // 4. h[64(K-2) + i], i < 128, from the free responses of the two states
+    for (int i = t; i < 2 * kL; i += NT) {
+        const float2 *S = st + (i < kL ? (buf ^ 1) : buf) * MB;
+        const int j = i % kL;
+        float hh = 0.f, ll = 0.f;
+        for (int m = 0; m < MB && m <= j; ++m) pipe::dw_acc(hh, ll, sh[j - m], S[m].x, S[m].y);
+        const dw v = fast_two_sum(hh, ll);
+        hw[i] = make_float2(v.hi, v.lo);
+    }
+    sync();
+    // 5. the closed forms (hw index i <-> h[64(K-2) + i], so h[64K - d] = hw[128 - d])
+    float2 *J = h.jump + (size_t)ch * MB * MB;
+    for (int e = t; e < MB * MB; e += NT) {
+        const int k = e % MB, m = e / MB;
+        float hh = 0.f, ll = 0.f;
+        if (!bwd) {
+            for (int l = k + 1; l <= MB; ++l) pipe::dw_acc(hh, ll, hw[2 * kL + k - l - m], -sa[l - 1], 0.f);
+        } else {
+            for (int j = 0; j + m < MB; ++j) pipe::dw_acc(hh, ll, hw[2 * kL - 1 - k - j], -sa[j + m], 0.f);
+        }
+        const dw v = fast_two_sum(hh, ll);
+        J[e] = make_float2(v.hi, v.lo);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -405,8 +510,6 @@ __global__ void __launch_bounds__(128) hi_reduce_kernel(HiArgs h, Batch bt) {
     if (c.len == 0 && h.gzi && lane + 32 < c.M) h.gzi[ch * bt.Mstride + lane + 32] = 0.f;
 }
 
-// threads per state row of the scan (the CTA holds MB * TPR threads)
-constexpr int scan_tpr(int mb) { return mb <= 16 ? 2 : 2; }
 
 template <int MB, bool REV>
 cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st) {
@@ -442,8 +545,9 @@ cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st) {
 template <int MB>
 cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st) {
     (void)num_sms;
-    const size_t smem = (size_t)2 * MB * MB * 8;
-    auto kern = hi_jump_kernel<MB>;
+    constexpr int TPR = scan_tpr(MB);
+    const size_t smem = (size_t)(MB * MB + kL + MB + 2 * MB + 2 * kL) * 8 + MB * 4 + 64;
+    auto kern = hi_jump_kernel<MB, TPR>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -455,7 +559,7 @@ cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cud
     }
     // one block per channel position (at most B; blocks past the launch's list exit)
     if (bt.B <= 0) return cudaSuccess;
-    kern<<<(unsigned)bt.B, 256, smem, st>>>(h, bt, bwd ? 1 : 0);
+    kern<<<(unsigned)bt.B, MB * TPR, smem, st>>>(h, bt, bwd ? 1 : 0);
     return cudaGetLastError();
 }
 

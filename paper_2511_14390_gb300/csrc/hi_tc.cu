@@ -3,16 +3,20 @@
 // the scan kernel: a persistent CTA takes tiles from a counter, in channel order, and
 // rebuilds its B operand only when the channel changes.
 //
-//   E pass (forward)   D = X R_L^T           N = MB      -> E_c into the chunk slots
-//   E' pass (backward) D = G (T_h^a)^T[:MB]  N = MB      -> E'_c into the chunk slots
-//   Y pass             D = [X | S] [T_g | O_L]^T         N = 64 -> y
-//   U pass             D = [G | S'] [T_h^a | O^u]^T      N = 64 -> u; then, per chunk
-//                      row on the CUDA cores, grad_x = sum_k b_k u[n+k] and the lag
-//                      sums of grad_b, grad_a; one partial per tile (fixed order)
+//   E pass (forward)   D = X R_L^T           N = MB   -> E_c into the chunk slots
+//   E' pass (backward) D = G (T_h^a)^T[:MB]  N = MB   -> E'_c into the chunk slots
+//   Y pass             D = X T_g^T           N = 64   -> y = D + O_L S_c
+//   U pass             D = G (T_h^a)^T       N = 64   -> u = D + O^u S'_c; then grad_x =
+//                      sum_k b_k u[n+k] and the lag sums of grad_b, grad_a; one partial
+//                      per tile (fixed order)
+// The free responses O_L S_c and O^u S'_c are added on the CUDA cores in FP32, per chunk
+// row: the chunk states of high-order filters are large numbers whose combination
+// cancels, and the split-TF32 product (about 21 bits per operand) would cost digits
+// there that FP32 FMAs keep (the single-kernel path does the same).
 //
 // Operands: K-major, 128-byte swizzle, TF32 split in three products (hi*hi + hi*lo +
-// lo*hi, FP32-class) or one; the raw FP32 words serve as the A hi part (the tensor
-// cores read a TF32 operand's upper 19 bits, which is the hi part of the split).
+// lo*hi) or one; the raw FP32 words serve as the A hi part (the tensor cores read a
+// TF32 operand's upper 19 bits, which is the hi part of the split).
 #include <cstring>
 
 #include "hi.cuh"
@@ -32,15 +36,15 @@ constexpr uint32_t kKBlock = kChunks * 128;   // one 32-wide K block of the A op
 template <int MB, int MODE>
 struct TcSmem {
     using Tab = ChunkTab<MB>;
-    static constexpr bool OUT = MODE >= hi::kY;                   // [signal | state] operand
-    static constexpr int KS = OUT ? (MB <= 32 ? 32 : 64) : 0;     // state K width
+    static constexpr bool OUT = MODE >= hi::kY;                   // y or u rows
     static constexpr int N = OUT ? kL : Tab::MPAD;                // MMA N
-    static constexpr int KTOT = kL + KS;
-    static constexpr int KB = KTOT / 32;                          // K blocks
+    static constexpr int KTOT = kL;
+    static constexpr int KB = 2;                                  // K blocks of 32
     static constexpr uint32_t BBLK = (uint32_t)N * 128;           // bytes of one B K block
     static constexpr uint32_t BHI = 0;
     static constexpr uint32_t BLO = KB * BBLK;
-    static constexpr uint32_t A0 = (2 * KB * BBLK + 1023) / 1024 * 1024;
+    static constexpr uint32_t OT = 2 * KB * BBLK;                 // O_L or O^u [L][MB] f32
+    static constexpr uint32_t A0 = (OT + (OUT ? kL * MB * 4 : 0) + 1023) / 1024 * 1024;
     static constexpr uint32_t AHI = A0;
     static constexpr uint32_t ALO = A0 + KB * kKBlock;
     static constexpr uint32_t AEND = A0 + 2 * KB * kKBlock;
@@ -127,23 +131,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if constexpr (MODE == hi::kEBwd) {
                     if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
                 } else if constexpr (MODE == hi::kY) {
-                    if (k < kL) {
-                        if (k <= nn) v = reinterpret_cast<const float *>(R + h.tab_g)[nn - k];
-                    } else if (k - kL < MB) {
-                        v = reinterpret_cast<const float *>(R + h.tab_ol)[nn * MB + (k - kL)];
-                    }
+                    if (k <= nn) v = reinterpret_cast<const float *>(R + h.tab_g)[nn - k];
                 } else {
-                    if (k < kL) {
-                        if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
-                    } else if (k - kL < MB) {
-                        v = reinterpret_cast<const float *>(R + Tab::B_OU)[nn * MB + (k - kL)];
-                    }
+                    if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
                 }
                 float hv, lv;
                 split_tf32(v, hv, lv);
                 const uint32_t o = (uint32_t)(k >> 5) * SM::BBLK + sw128_off(nn, k & 31);
                 *reinterpret_cast<float *>(smem + SM::BHI + o) = hv;
                 *reinterpret_cast<float *>(smem + SM::BLO + o) = lv;
+            }
+            if constexpr (SM::OUT) {
+                // the free-response table O_L (Y pass) or O^u (U pass), [L][MB] FP32
+                const float *src = reinterpret_cast<const float *>(
+                    R + (MODE == hi::kY ? (size_t)h.tab_ol : (size_t)Tab::B_OU));
+                float *ot = reinterpret_cast<float *>(smem + SM::OT);
+                for (int i = tid; i < kL * MB; i += kThreads) ot[i] = src[i];
             }
             if constexpr (MODE == hi::kU) {
                 // b_0..b_MB from the record's coefficient block (zero past the order)
@@ -157,22 +160,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- A operand: the signal tile, then (Y, U) the chunk states ----
         pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, tstart, tlen,
                                         sig_al && ((tstart & 3) == 0), tid);
+        // (Y, U) this row's chunk state, FP32, for the free response in the epilogue
+        float S[SM::OUT ? MB : 1];
         if constexpr (SM::OUT) {
-            const float *sv = MODE == hi::kY ? h.states2 : h.states;
-            const float *src = sv + (size_t)slot0 * Ms;
-            constexpr int P4 = SM::KS / 4;   // 16-byte pieces per row
-            for (int id = tid; id < kChunks * P4; id += kThreads) {
-                const int row = id / P4, m4 = (id % P4) * 4;
-                const uint32_t d = sbase + SM::AHI + (uint32_t)(2 + (m4 >> 5)) * kKBlock + sw128_off(row, m4 & 31);
+            const float *sv = (MODE == hi::kY ? h.states2 : h.states) + (size_t)(slot0 + tid) * Ms;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int m = m4 + e;
-                    const bool v = row < nch && m < c.M;
-                    cp_async4(d + 4 * e, v ? (const void *)(src + (size_t)row * Ms + m) : (const void *)sv,
-                              v ? 4 : 0);
-                }
-            }
-            cp_async_commit();
+            for (int m = 0; m < MB; ++m) S[m] = (tid < nch && m < c.M) ? __ldg(sv + m) : 0.f;
         }
         cp_async_wait_all();
         __syncthreads();
@@ -241,11 +234,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
         } else if constexpr (MODE == hi::kY) {
             char *stag = smem + SM::AHI;   // the operand is consumed
-#pragma unroll
+            const float *ot = reinterpret_cast<const float *>(smem + SM::OT);
+#pragma unroll 1
             for (int cb = 0; cb < kL / 16; ++cb) {
                 float v[16];
                 tmem_ld16(taddr + cb * 16, v);
                 tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float *ol = ot + (cb * 16 + i) * MB;
+                    float acc = v[i];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) acc = fmaf(ol[m], S[m], acc);
+                    v[i] = acc;
+                }
 #pragma unroll
                 for (int p4 = 0; p4 < 4; ++p4)
                     *reinterpret_cast<float4 *>(stag + rowp(cr, cb * 4 + p4)) =
@@ -274,13 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
         } else {
             constexpr int UW = SM::UW, KBLK = SM::KBLK, NACC = hi::nacc<MB>();
-            // (1) S'_c of this row (raw words of the operand's state blocks)
-            float sp[MB];
-#pragma unroll
-            for (int m = 0; m < MB; ++m)
-                sp[m] = *reinterpret_cast<const float *>(smem + SM::AHI + (uint32_t)(2 + (m >> 5)) * kKBlock +
-                                                         sw128_off(cr, m & 31));
-            __syncthreads();   // the operand region is rewritten from here on
+            // (1) S'_c of this row is in S[]; the operand region is rewritten from here on
+            const float *ot = reinterpret_cast<const float *>(smem + SM::OT);
             // (2) x and y tiles (rows of 256 bytes), u_ext rows
             {
                 const bool al = xy_al && ((tstart & 3) == 0);
@@ -306,11 +303,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             char *urow = smem + SM::UEXT + (uint32_t)cr * UW * 4;
             auto upiece = [&](int j) { return urow + (((j ^ (cr & 7))) << 4); };
-#pragma unroll
+#pragma unroll 1
             for (int cb = 0; cb < kL / 16; ++cb) {
                 float v[16];
                 tmem_ld16(taddr + cb * 16, v);
                 tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {   // u = zero-state part + O^u S'
+                    const float *ou = ot + (cb * 16 + i) * MB;
+                    float acc = v[i];
+#pragma unroll
+                    for (int m = 0; m < MB; ++m) acc = fmaf(ou[m], S[m], acc);
+                    v[i] = acc;
+                }
 #pragma unroll
                 for (int p4 = 0; p4 < 4; ++p4)
                     *reinterpret_cast<float4 *>(upiece(cb * 4 + p4)) =
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < (UW - kL) / 4; ++j) {
                 float q4[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) q4[e] = (4 * j + e < MB) ? sp[4 * j + e] : 0.f;
+                for (int e = 0; e < 4; ++e) q4[e] = (4 * j + e < MB) ? S[4 * j + e] : 0.f;
                 *reinterpret_cast<float4 *>(upiece(kL / 4 + j)) = make_float4(q4[0], q4[1], q4[2], q4[3]);
             }
             tc_fence_before();
