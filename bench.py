@@ -219,7 +219,7 @@ def kernel_name(direction, M):
     """Main kernel of the chunked path for a state bucket (the warp-specialised kernels
     serve the buckets whose layouts fit; see the dispatch in csrc/chunk_*.cu)."""
     mb = next(v for v in (2, 4, 8, 16, 32, 64) if M <= v)
-    f64 = 1 if M > 4 else 0
+    f64 = 1 if M > 2 else 0
     if direction == "forward":
         if mb >= 32:
             return f"chunk_fwd_kernel<{mb}, {f64}>"

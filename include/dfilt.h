@@ -75,7 +75,7 @@ typedef struct {
     int chunk_len;   /* chunk length L of the chunked algorithm; 0 = default (64) */
     int fp64_scan;   /* high-precision chunk-state scan (a serial scan in double-word
                         FP32 arithmetic, about 44 bits: FP64-class accuracy without
-                        GB300's narrow FP64 pipe): -1 auto (orders above 4),
+                        GB300's narrow FP64 pipe): -1 auto (orders above 2),
                         0 off (FP32 two-level scan, orders <= 16), 1 on */
     int path;        /* chunked algorithm, orders above 8 (state buckets 16..64) with the
                         high-precision scan: DFILT_PATH_AUTO, DFILT_PATH_FUSED or

@@ -65,11 +65,13 @@ int chunk_bucket(int M) {
 ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt) {
     ChunkLayout l;
     l.MB = chunk_bucket(Mmax);
-    // FP32 powers of the chunk transition stay stable for low orders; above order 4 the
-    // transient growth of companion-matrix powers makes an FP32 scan diverge on some
-    // filters, so the automatic choice there is the serial scan in double words
-    // (FP64-class accuracy; the only one above the FP32 table bucket limit).
-    l.fp64_scan = fp64_scan_opt < 0 ? (Mmax > 4) : (fp64_scan_opt != 0);
+    // FP32 powers of the chunk transition stay accurate for orders <= 2 up to pole radius
+    // 0.9995; from order 3 on, the transient growth of companion-matrix powers costs an
+    // FP32 scan accuracy (measured 21x the double-word scan's error at order 4, radius
+    // 0.99-0.9995) and diverges on some high-order filters, so the automatic choice
+    // there is the serial scan in double words (FP64-class accuracy; the only one above
+    // the FP32 table bucket limit).
+    l.fp64_scan = fp64_scan_opt < 0 ? (Mmax > 2) : (fp64_scan_opt != 0);
     if (l.MB > kMaxF32ScanBucket) l.fp64_scan = true;
     size_t f = 0, b = 0;
     switch (l.MB) {

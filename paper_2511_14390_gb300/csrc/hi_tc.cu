@@ -6,13 +6,16 @@
 //   E pass (forward)   D = X R_L^T           N = MB   -> E_c into the chunk slots
 //   E' pass (backward) D = G (T_h^a)^T[:MB]  N = MB   -> E'_c into the chunk slots
 //   Y pass             D = X T_g^T           N = 64   -> y = D + O_L S_c
-//   U pass             D = G (T_h^a)^T       N = 64   -> u = D + O^u S'_c; then grad_x =
-//                      sum_k b_k u[n+k] and the lag sums of grad_b, grad_a; one partial
-//                      per tile (fixed order)
-// The free responses O_L S_c and O^u S'_c are added on the CUDA cores in FP32, per chunk
-// row: the chunk states of high-order filters are large numbers whose combination
-// cancels, and the split-TF32 product (about 21 bits per operand) would cost digits
-// there that FP32 FMAs keep (the single-kernel path does the same).
+//   U pass             D = G [T_g^a ; T_h^a]^T  N = 128 -> grad_x = D[:, 0:64) +
+//                      O^gx S'_c and u = D[:, 64:128) + O^u S'_c; then the lag sums of
+//                      grad_b, grad_a from u (kept in tensor memory with its tail
+//                      u[64..64+MB) = S'_c); one partial per tile (fixed order)
+// The free responses O_L S_c, O^u S'_c and O^gx S'_c are added on the CUDA cores in FP32,
+// per chunk row: the chunk states of high-order filters are large numbers whose
+// combination cancels, and the split-TF32 product (about 21 bits per operand) would cost
+// digits there that FP32 FMAs keep.  For the same reason grad_x comes from the impulse
+// response of B/A directly, not as B applied to the all-pole adjoint u (which can be far
+// larger than grad_x when zeros of B sit near poles of A).
 //
 // Operands: K-major, 128-byte swizzle, TF32 split in three products (hi*hi + hi*lo +
 // lo*hi) or one; the raw FP32 words serve as the A hi part (the tensor cores read a
@@ -37,32 +40,35 @@ template <int MB, int MODE>
 struct TcSmem {
     using Tab = ChunkTab<MB>;
     static constexpr bool OUT = MODE >= hi::kY;                   // y or u rows
-    static constexpr int N = OUT ? kL : Tab::MPAD;                // MMA N
+    static constexpr int N = MODE == hi::kU ? 2 * kL : (OUT ? kL : Tab::MPAD);   // MMA N
     static constexpr int KTOT = kL;
     static constexpr int KB = 2;                                  // K blocks of 32
     static constexpr uint32_t BBLK = (uint32_t)N * 128;           // bytes of one B K block
     static constexpr uint32_t BHI = 0;
     static constexpr uint32_t BLO = KB * BBLK;
-    static constexpr uint32_t OT = 2 * KB * BBLK;                 // O_L or O^u [L][MB] f32
-    static constexpr uint32_t A0 = (OT + (OUT ? kL * MB * 4 : 0) + 1023) / 1024 * 1024;
+    // free-response tables [L][MB] f32: O_L (Y pass), or O^u then O^gx (U pass)
+    static constexpr int NOT = MODE == hi::kU ? 2 : (OUT ? 1 : 0);
+    static constexpr uint32_t OT = 2 * KB * BBLK;
+    static constexpr uint32_t A0 = (OT + NOT * kL * MB * 4 + 1023) / 1024 * 1024;
     static constexpr uint32_t AHI = A0;
     static constexpr uint32_t ALO = A0 + KB * kKBlock;
     static constexpr uint32_t AEND = A0 + 2 * KB * kKBlock;
-    // U pass epilogue (over the A operand once the product is done): u_ext rows of UW
-    // floats (u[0..64), S'[0..MB), zeros), then the x and y tiles, 256-byte rows
-    static constexpr int UW = (kL + MB + 31) / 32 * 32;
-    static constexpr uint32_t UEXT = A0;
-    static constexpr uint32_t XT = UEXT + (uint32_t)kChunks * UW * 4;
+    // U pass epilogue, over the A operand once the product is done: the x and y tiles
+    // (256-byte rows)
+    static constexpr uint32_t XT = A0;
     static constexpr uint32_t YT = XT + (uint32_t)kChunks * kL * 4;
-    static constexpr uint32_t EPEND = MODE == hi::kU ? YT + (uint32_t)kChunks * kL * 4 : 0;
     static constexpr int KBLK = (MB + 1 + 15) / 16;               // lag blocks of 16
-    static constexpr uint32_t RED = (AEND > EPEND ? AEND : EPEND);
-    static constexpr uint32_t COEF = RED + (MODE == hi::kU ? 4u * KBLK * 32 * 4 : 0u);
-    static constexpr uint32_t MISC = COEF + (MODE == hi::kU ? (uint32_t)KBLK * 16 * 4 : 0u);
+    static constexpr uint32_t RED = AEND;
+    static constexpr uint32_t MISC = RED + (MODE == hi::kU ? 4u * KBLK * 32 * 4 : 0u);
     // misc: mbarrier (8) | drill mbarrier (8) | tmem base (4) | ok flag (4) | work item (8)
     static constexpr uint32_t BYTES = MISC + 32;
     static constexpr uint32_t ALLOC = BYTES + 1024;
-    static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+    // U pass tensor memory: grad_x [0, 64), then the adjoint window u_ext from column 64:
+    // u[0..64), S'[0..MB), zeros (the lag windows read columns below
+    // 64 + 16 (KBLK + 2) + 32)
+    static constexpr int UEND = kL + 16 * (KBLK + 2) + 32;
+    static constexpr uint32_t TMEM_COLS = MODE == hi::kU ? 256 : (N < 32 ? 32 : N);
+    static_assert(MODE != hi::kU || UEND <= 256, "tensor-memory window");
 };
 
 // byte offset of 16-byte piece j of row r in a 256-byte-row staging tile
@@ -133,7 +139,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if constexpr (MODE == hi::kY) {
                     if (k <= nn) v = reinterpret_cast<const float *>(R + h.tab_g)[nn - k];
                 } else {
-                    if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
+                    const int n2 = nn & (kL - 1);
+                    if (k >= n2)
+                        v = reinterpret_cast<const float *>(R + (nn < kL ? Tab::B_G : Tab::B_H))[k - n2];
                 }
                 float hv, lv;
                 split_tf32(v, hv, lv);
@@ -142,17 +150,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 *reinterpret_cast<float *>(smem + SM::BLO + o) = lv;
             }
             if constexpr (SM::OUT) {
-                // the free-response table O_L (Y pass) or O^u (U pass), [L][MB] FP32
+                // the free-response tables: O_L (Y pass), or O^u and O^gx (U pass)
+                float *ot = reinterpret_cast<float *>(smem + SM::OT);
                 const float *src = reinterpret_cast<const float *>(
                     R + (MODE == hi::kY ? (size_t)h.tab_ol : (size_t)Tab::B_OU));
-                float *ot = reinterpret_cast<float *>(smem + SM::OT);
                 for (int i = tid; i < kL * MB; i += kThreads) ot[i] = src[i];
-            }
-            if constexpr (MODE == hi::kU) {
-                // b_0..b_MB from the record's coefficient block (zero past the order)
-                const float *cf = reinterpret_cast<const float *>(R + Tab::b_coef(true));
-                float *sb = reinterpret_cast<float *>(smem + SM::COEF);
-                for (int k = tid; k < SM::KBLK * 16; k += kThreads) sb[k] = k <= MB ? cf[MB + k] : 0.f;
+                if constexpr (MODE == hi::kU) {
+                    const float *src2 = reinterpret_cast<const float *>(R + Tab::B_OGX);
+                    for (int i = tid; i < kL * MB; i += kThreads) ot[kL * MB + i] = src2[i];
+                }
             }
             cur_ch = ch;
         }
@@ -275,19 +281,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncthreads();
         } else {
-            constexpr int UW = SM::UW, KBLK = SM::KBLK, NACC = hi::nacc<MB>();
-            // (1) S'_c of this row is in S[]; the operand region is rewritten from here on
-            const float *ot = reinterpret_cast<const float *>(smem + SM::OT);
-            // (2) x and y tiles (rows of 256 bytes), u_ext rows
+            constexpr int KBLK = SM::KBLK, NACC = hi::nacc<MB>();
+            const float *ou = reinterpret_cast<const float *>(smem + SM::OT);
+            const float *ogx = ou + kL * MB;
+            // (1) x and y tiles (rows of 256 bytes) over the consumed operand
             {
                 const bool al = xy_al && ((tstart & 3) == 0);
                 for (int q = 0; q < 16; ++q) {
                     const int id = tid + kThreads * q;
                     const int r = id >> 4, j = id & 15;
-                    const int s = r * kL + j * 4;
-                    const int nv = min(max(tlen - s, 0), 4);
+                    const int s0 = r * kL + j * 4;
+                    const int nv = min(max(tlen - s0, 0), 4);
                     const uint32_t dx = sbase + SM::XT + rowp(r, j), dy = sbase + SM::YT + rowp(r, j);
-                    const float *gx_ = h.x + tstart + s, *gy_ = h.y + tstart + s;
+                    const float *gx_ = h.x + tstart + s0, *gy_ = h.y + tstart + s0;
                     if (al) {
                         cp_async16(dx, nv ? (const void *)gx_ : (const void *)h.x, nv * 4);
                         cp_async16(dy, nv ? (const void *)gy_ : (const void *)h.y, nv * 4);
@@ -301,34 +307,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 cp_async_commit();
             }
-            char *urow = smem + SM::UEXT + (uint32_t)cr * UW * 4;
-            auto upiece = [&](int j) { return urow + (((j ^ (cr & 7))) << 4); };
+            // (2) the adjoint window in tensor memory: u = D + O^u S' over columns
+            // 64 .. 128, then S' and zeros
 #pragma unroll 1
             for (int cb = 0; cb < kL / 16; ++cb) {
                 float v[16];
-                tmem_ld16(taddr + cb * 16, v);
+                tmem_ld16(taddr + kL + cb * 16, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {   // u = zero-state part + O^u S'
-                    const float *ou = ot + (cb * 16 + i) * MB;
+                for (int i = 0; i < 16; ++i) {
+                    const float *o = ou + (cb * 16 + i) * MB;
                     float acc = v[i];
 #pragma unroll
-                    for (int m = 0; m < MB; ++m) acc = fmaf(ou[m], S[m], acc);
+                    for (int m = 0; m < MB; ++m) acc = fmaf(o[m], S[m], acc);
                     v[i] = acc;
                 }
-#pragma unroll
-                for (int p4 = 0; p4 < 4; ++p4)
-                    *reinterpret_cast<float4 *>(upiece(cb * 4 + p4)) =
-                        make_float4(v[4 * p4], v[4 * p4 + 1], v[4 * p4 + 2], v[4 * p4 + 3]);
+                tmem_st16(taddr + kL + cb * 16, v);
             }
 #pragma unroll
-            for (int j = 0; j < (UW - kL) / 4; ++j) {
-                float q4[4];
+            for (int cb = 0; cb < (SM::UEND - 2 * kL + 15) / 16; ++cb) {
+                float v[16];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) q4[e] = (4 * j + e < MB) ? S[4 * j + e] : 0.f;
-                *reinterpret_cast<float4 *>(upiece(kL / 4 + j)) = make_float4(q4[0], q4[1], q4[2], q4[3]);
+                for (int i = 0; i < 16; ++i) v[i] = (cb * 16 + i < MB) ? S[cb * 16 + i] : 0.f;
+                tmem_st16(taddr + 2 * kL + cb * 16, v);
             }
-            tc_fence_before();
+            tmem_wait_st();
             cp_async_wait_all();
             __syncthreads();
             const char *xrow = smem + SM::XT, *yrow = smem + SM::YT;
@@ -337,15 +340,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int p4 = 0; p4 < 4; ++p4) {
                     const float4 q = *reinterpret_cast<const float4 *>(base + rowp(cr, j0 + p4));
                     v[4 * p4] = q.x; v[4 * p4 + 1] = q.y; v[4 * p4 + 2] = q.z; v[4 * p4 + 3] = q.w;
-                }
-            };
-            auto ldwin = [&](int f0, float (&win)[32]) {   // u_ext[f0 .. f0+32), zero past the row
-#pragma unroll
-                for (int p4 = 0; p4 < 8; ++p4) {
-                    const int j = f0 / 4 + p4;
-                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (j < UW / 4) q = *reinterpret_cast<const float4 *>(upiece(j));
-                    win[4 * p4] = q.x; win[4 * p4 + 1] = q.y; win[4 * p4 + 2] = q.z; win[4 * p4 + 3] = q.w;
                 }
             };
             // (3) lag sums: b-lag k: sum_n u[n+k] x[n] (k = 0..MB), a-lag k: sum_n u[n+1+k] y[n]
@@ -357,18 +351,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 #pragma unroll 1
                 for (int nb = 0; nb < kL / 16; ++nb) {
-                    float xv[16], yv[16], win[32];
+                    float xv[16], yv[16], w0[16], w1[16];
                     ld16(xrow, nb * 4, xv);
                     ld16(yrow, nb * 4, yv);
-                    ldwin(16 * (nb + kb), win);
+                    const uint32_t f0 = taddr + kL + 16 * (nb + kb);   // u_ext[16(nb+kb) ..]
+                    tmem_ld16(f0, w0);
+                    tmem_ld16(f0 + 16, w1);
+                    tmem_wait_ld();
+#define DFILT_WIN(i) ((i) < 16 ? w0[(i)] : w1[(i) - 16])
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            acc[j] = fmaf(win[q + j], xv[q], acc[j]);
-                            acc[16 + j] = fmaf(win[q + 1 + j], yv[q], acc[16 + j]);
+                            acc[j] = fmaf(DFILT_WIN(q + j), xv[q], acc[j]);
+                            acc[16 + j] = fmaf(DFILT_WIN(q + 1 + j), yv[q], acc[16 + j]);
                         }
                     }
+#undef DFILT_WIN
                 }
                 // warp total of all 32 sums: halving butterfly, lane L ends with sum L
 #pragma unroll
@@ -383,30 +382,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 red[(warp * KBLK + kb) * 32 + lane] = acc[0];
             }
-            // (4) grad_x = sum_k b_k u[n+k], written over this row of the x tile
-            const float *sb = reinterpret_cast<const float *>(smem + SM::COEF);
-            const int nkb = (c.N + 16) / 16;
+            // (4) grad_x = D[:, 0:64) + O^gx S', written over this row of the x tile
 #pragma unroll 1
-            for (int nb = 0; nb < kL / 16; ++nb) {
-                float g[16];
+            for (int cb = 0; cb < kL / 16; ++cb) {
+                float v[16];
+                tmem_ld16(taddr + cb * 16, v);
+                tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 16; ++q) g[q] = 0.f;
-#pragma unroll 1
-                for (int kb = 0; kb < nkb; ++kb) {
-                    float win[32], bv[16];
-                    ldwin(16 * (nb + kb), win);
+                for (int i = 0; i < 16; ++i) {
+                    const float *o = ogx + (cb * 16 + i) * MB;
+                    float acc = v[i];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) bv[j] = sb[16 * kb + j];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) g[q] = fmaf(bv[j], win[q + j], g[q]);
+                    for (int m = 0; m < MB; ++m) acc = fmaf(o[m], S[m], acc);
+                    v[i] = acc;
                 }
 #pragma unroll
                 for (int p4 = 0; p4 < 4; ++p4)
-                    *reinterpret_cast<float4 *>(smem + SM::XT + rowp(cr, nb * 4 + p4)) =
-                        make_float4(g[4 * p4], g[4 * p4 + 1], g[4 * p4 + 2], g[4 * p4 + 3]);
+                    *reinterpret_cast<float4 *>(smem + SM::XT + rowp(cr, cb * 4 + p4)) =
+                        make_float4(v[4 * p4], v[4 * p4 + 1], v[4 * p4 + 2], v[4 * p4 + 3]);
             }
+            tc_fence_before();
             __syncthreads();
             // the tile's lag sums in a fixed order (warps 0..3)
             for (int i = tid; i < KBLK * 32; i += kThreads) {

@@ -92,17 +92,41 @@ def test_decoupled_high_radius(M):
         assert (e[nm] < bound).all(), (M, nm, e[nm], bound)
 
 
-def test_span_split_agrees():
-    """The same order-32 channels scanned in one span per channel and in 1-tile spans:
-    only the look-back's span transitions differ, so the outputs agree to far below
-    the FP32 rounding of the inputs."""
-    w = inputs.make("biquad_1024x48000", B=4, T=8 * 8192 + 5, M=32, N=8, seed=801)
-    redraw(w, 0.8, 0.99, 802)
+def long_memory_filters(B, M, N, seed, r_long=0.999):
+    """Denominators with one conjugate pole pair at radius r_long (a state that still
+    carries ~0.8% of itself across a 8192-sample span) and the rest well damped
+    (radius 0.3-0.6), so the look-back's span transition matters and the recursion stays
+    well conditioned."""
+    rng = np.random.default_rng(seed)
+    a = np.zeros((B, M), dtype=np.float32)
+    b = np.zeros((B, N + 1), dtype=np.float32)
+    for i in range(B):
+        th = rng.uniform(0.1, 3.0)
+        poles = np.concatenate([[r_long * np.exp(1j * th), r_long * np.exp(-1j * th)],
+                                inputs._draw_roots(rng, M - 2, 0.3, 0.6)])
+        a[i] = np.real(np.poly(poles))[1:].astype(np.float32)
+        assert np.abs(np.roots(np.concatenate([[1.0], a[i].astype(np.float64)]))).max() < 0.9995
+        b[i] = inputs.draw_numerator(rng, N, True)
+    return a, b
+
+
+@pytest.mark.parametrize("M", [16, 32, 64])
+def test_span_split_agrees(M):
+    """Channels scanned in one span and in 1-tile spans (eight CTAs per channel joined by
+    the look-back): only the span transitions and entry states differ, so the outputs
+    agree to the level of FP32 rounding, and both meet the oracle."""
+    w = inputs.make("biquad_1024x48000", B=4, T=8 * 8192 + 5, M=M, N=8, seed=801 + M)
+    w.a, w.b = long_memory_filters(w.B, M, 8, 802 + M)
     y1, g1 = run_fixed(w, algo="chunked", path="decoupled", span_tiles=16)
     y2, g2 = run_fixed(w, algo="chunked", path="decoupled", span_tiles=1)
-    assert rel_rows(y2, y1).max() < 1e-6
-    for a, b in zip(g1, g2):
-        assert rel_rows(b, a).max() < 1e-5
+    yr, gr = oracle_fixed(w)
+    e1, e2 = errors(w, y1, g1, yr, gr), errors(w, y2, g2, yr, gr)
+    log_errors(f"span_split_M{M}/one_span", **e1)
+    log_errors(f"span_split_M{M}/tile_spans", **e2)
+    assert rel_rows(y2, y1).max() < 1e-5
+    assert rel_rows(g2[0], g1[0]).max() < 1e-5
+    for nm in ("y", "gx", "gb", "ga", "gzi"):
+        assert (e2[nm] < 1e-5).all(), (M, nm, e2[nm])
 
 
 def test_decoupled_matches_fused():
@@ -241,10 +265,8 @@ def test_order16_full_size_sampled():
     w = inputs.make("allpole16_256x262144")
     y, g = run_fixed(w, algo="chunked")
     idx = np.array([0, 100, 200, 255])
-    sub = inputs.Workload(x=w.x[idx], b=w.b[idx], a=w.a[idx], zi=w.zi[idx], gy=w.gy[idx],
+    sub = inputs.Workload(x=w.x[idx], b=w.b[idx], a=w.a[idx], zi=None, gy=w.gy[idx],
                           M=w.M, N=w.N, radius=w.radius[idx])
-    if sub.zi is None:
-        sub.zi = np.zeros((len(idx), w.M), dtype=np.float32)
     yr, gr = oracle_fixed(sub)
     gx, gb, ga, gz = [t[idx] for t in g]
     e = errors(sub, y[idx], [gx, gb, ga, gz], yr, gr)
@@ -295,13 +317,15 @@ def test_ragged4096_full_size_sampled():
             assert v < tol, (i, M, e - s, nm, v, tol)
 
 
-@pytest.mark.parametrize("M", [1, 2, 4])
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
 def test_low_order_near_unit_circle(M):
-    """Orders <= 4 with poles at radius 0.99-0.9995 over 16 tiles, where the
-    automatic choice runs the FP32 two-level chunk-state scan: it must meet the same
-    per-channel bound as the double-word scan and stay within 4x of the sequential
-    FP32 kernel's error."""
-    w = inputs.make("biquad_1024x48000", B=6, T=16 * 8192 + 3, M=M, N=M, seed=900 + M)
+    """Orders <= 4 with poles at radius 0.99-0.9995 over 16 tiles.  The automatic scan
+    choice (FP32 two-level scan for orders <= 2, double words above) must meet the same
+    per-channel bound as the forced double-word scan and stay within 4x of the
+    sequential FP32 kernel's error.  (At order 4 an FP32 scan measured 21x the
+    double-word scan's error on one such channel, which is why orders 3 and 4 take the
+    double-word scan.)"""
+    w = inputs.make("biquad_1024x48000", B=16, T=16 * 8192 + 3, M=M, N=M, seed=900 + M)
     redraw(w, 0.99, 0.9995, 910 + M)
     yr, gr = oracle_fixed(w)
     res = {"auto": run_fixed(w, algo="chunked"),
