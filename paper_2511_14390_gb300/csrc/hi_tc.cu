@@ -53,12 +53,15 @@ struct TcSmem {
     static constexpr uint32_t AHI = A0;
     static constexpr uint32_t ALO = A0 + KB * kKBlock;
     static constexpr uint32_t AEND = A0 + 2 * KB * kKBlock;
-    // U pass epilogue, over the A operand once the product is done: the x and y tiles
-    // (256-byte rows)
-    static constexpr uint32_t XT = A0;
-    static constexpr uint32_t YT = XT + (uint32_t)kChunks * kL * 4;
+    // U pass: the x and y tiles (256-byte rows), loaded with the gy tile into their own
+    // buffers where shared memory allows, else over the A operand once it is consumed
     static constexpr int KBLK = (MB + 1 + 15) / 16;               // lag blocks of 16
-    static constexpr uint32_t RED = AEND;
+    static constexpr uint32_t XY_BYTES = 2u * kChunks * kL * 4;
+    static constexpr bool SEPXY =
+        MODE == hi::kU && AEND + XY_BYTES + 4u * KBLK * 32 * 4 + 32 + 1024 <= pipe::kSmemMax;
+    static constexpr uint32_t XT = SEPXY ? AEND : A0;
+    static constexpr uint32_t YT = XT + (uint32_t)kChunks * kL * 4;
+    static constexpr uint32_t RED = SEPXY ? AEND + XY_BYTES : AEND;
     static constexpr uint32_t MISC = RED + (MODE == hi::kU ? 4u * KBLK * 32 * 4 : 0u);
     // misc: mbarrier (8) | drill mbarrier (8) | tmem base (4) | ok flag (4) | work item (8)
     static constexpr uint32_t BYTES = MISC + 32;
@@ -76,7 +79,7 @@ __device__ __forceinline__ uint32_t rowp(int r, int j) { return (uint32_t)(r * 2
 
 template <int MB, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    hi_tc_kernel(HiArgs h, Batch bt, int sig_al, int out_al, int xy_al) {
+    hi_tc_kernel(HiArgs h, Batch bt, int sig_al, int out_al, int xy_al, int st_al) {
     using Tab = ChunkTab<MB>;
     using SM = TcSmem<MB, MODE>;
     constexpr int N = SM::N, KTOT = SM::KTOT, KB = SM::KB;
@@ -111,12 +114,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     int64_t cur_ch = -1;
 
+    // U pass: the tile's x and y rows into XT / YT (zero past tlen)
+    auto load_xy = [&](int64_t tstart, int tlen) {
+        const bool al = xy_al && ((tstart & 3) == 0);
+        for (int q = 0; q < 16; ++q) {
+            const int id = tid + kThreads * q;
+            const int r = id >> 4, j = id & 15;
+            const int s0 = r * kL + j * 4;
+            const int nv = min(max(tlen - s0, 0), 4);
+            const uint32_t dx = sbase + SM::XT + rowp(r, j), dy = sbase + SM::YT + rowp(r, j);
+            const float *gx_ = h.x + tstart + s0, *gy_ = h.y + tstart + s0;
+            if (al) {
+                cp_async16(dx, nv ? (const void *)gx_ : (const void *)h.x, nv * 4);
+                cp_async16(dy, nv ? (const void *)gy_ : (const void *)h.y, nv * 4);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    cp_async4(dx + 4 * e, e < nv ? (const void *)(gx_ + e) : (const void *)h.x, e < nv ? 4 : 0);
+                    cp_async4(dy + 4 * e, e < nv ? (const void *)(gy_ + e) : (const void *)h.y, e < nv ? 4 : 0);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // tiles are taken in runs of kRun consecutive ones (mostly one channel: the tables
+    // are rebuilt only when the channel changes)
+    constexpr int kRun = 4;
+    int64_t w = 0, wend = 0, pos = 0;
     for (;;) {
-        if (tid == 0) *item = (long long)atomicAdd(h.counter, 1ull);
-        __syncthreads();
-        const int64_t w = *item;
-        if (w >= total) break;
-        const int64_t pos = hi::find_pos(h.plan.tile_pref, n, w);
+        if (w >= wend) {
+            if (tid == 0) *item = (long long)atomicAdd(h.counter, 1ull);
+            __syncthreads();
+            w = *item * kRun;
+            __syncthreads();   // *item is rewritten at the next run
+            if (w >= total) break;
+            wend = w + kRun < total ? w + kRun : total;
+            pos = hi::find_pos(h.plan.tile_pref, n, w);
+        } else {
+            while (h.plan.tile_pref[pos + 1] <= w) ++pos;   // the next channel with tiles
+        }
         const int64_t ch = hi::plan_channel(h.plan, pos);
         const Channel c = channel_of(bt, ch);
         const int64_t tile = w - h.plan.tile_pref[pos];
@@ -166,12 +202,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- A operand: the signal tile, then (Y, U) the chunk states ----
         pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, tstart, tlen,
                                         sig_al && ((tstart & 3) == 0), tid);
+        if constexpr (SM::SEPXY) load_xy(tstart, tlen);
         // (Y, U) this row's chunk state, FP32, for the free response in the epilogue
         float S[SM::OUT ? MB : 1];
         if constexpr (SM::OUT) {
             const float *sv = (MODE == hi::kY ? h.states2 : h.states) + (size_t)(slot0 + tid) * Ms;
+            const bool v = tid < nch;
+            if (st_al) {   // rows of Mstride floats, 16-byte aligned
 #pragma unroll
-            for (int m = 0; m < MB; ++m) S[m] = (tid < nch && m < c.M) ? __ldg(sv + m) : 0.f;
+                for (int m4 = 0; m4 < MB; m4 += 4) {
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (v && m4 < c.M) q = __ldg(reinterpret_cast<const float4 *>(sv + m4));
+                    S[m4] = q.x;
+                    S[m4 + 1] = m4 + 1 < c.M ? q.y : 0.f;
+                    S[m4 + 2] = m4 + 2 < c.M ? q.z : 0.f;
+                    S[m4 + 3] = m4 + 3 < c.M ? q.w : 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MB; ++m) S[m] = (v && m < c.M) ? __ldg(sv + m) : 0.f;
+            }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -251,7 +301,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float *ol = ot + (cb * 16 + i) * MB;
                     float acc = v[i];
 #pragma unroll
-                    for (int m = 0; m < MB; ++m) acc = fmaf(ol[m], S[m], acc);
+                    for (int m4 = 0; m4 < MB; m4 += 4) {   // O_L rows are 16-byte aligned
+                        const float4 q = *reinterpret_cast<const float4 *>(ol + m4);
+                        acc = fmaf(q.x, S[m4], acc);
+                        acc = fmaf(q.y, S[m4 + 1], acc);
+                        acc = fmaf(q.z, S[m4 + 2], acc);
+                        acc = fmaf(q.w, S[m4 + 3], acc);
+                    }
                     v[i] = acc;
                 }
 #pragma unroll
@@ -284,29 +340,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             constexpr int KBLK = SM::KBLK, NACC = hi::nacc<MB>();
             const float *ou = reinterpret_cast<const float *>(smem + SM::OT);
             const float *ogx = ou + kL * MB;
-            // (1) x and y tiles (rows of 256 bytes) over the consumed operand
-            {
-                const bool al = xy_al && ((tstart & 3) == 0);
-                for (int q = 0; q < 16; ++q) {
-                    const int id = tid + kThreads * q;
-                    const int r = id >> 4, j = id & 15;
-                    const int s0 = r * kL + j * 4;
-                    const int nv = min(max(tlen - s0, 0), 4);
-                    const uint32_t dx = sbase + SM::XT + rowp(r, j), dy = sbase + SM::YT + rowp(r, j);
-                    const float *gx_ = h.x + tstart + s0, *gy_ = h.y + tstart + s0;
-                    if (al) {
-                        cp_async16(dx, nv ? (const void *)gx_ : (const void *)h.x, nv * 4);
-                        cp_async16(dy, nv ? (const void *)gy_ : (const void *)h.y, nv * 4);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            cp_async4(dx + 4 * e, e < nv ? (const void *)(gx_ + e) : (const void *)h.x, e < nv ? 4 : 0);
-                            cp_async4(dy + 4 * e, e < nv ? (const void *)(gy_ + e) : (const void *)h.y, e < nv ? 4 : 0);
-                        }
-                    }
-                }
-                cp_async_commit();
-            }
+            // (1) x and y tiles (rows of 256 bytes) over the consumed operand, unless they
+            // were loaded with the signal tile
+            if constexpr (!SM::SEPXY) load_xy(tstart, tlen);
             // (2) the adjoint window in tensor memory: u = D + O^u S' over columns
             // 64 .. 128, then S' and zeros
 #pragma unroll 1
@@ -319,7 +355,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float *o = ou + (cb * 16 + i) * MB;
                     float acc = v[i];
 #pragma unroll
-                    for (int m = 0; m < MB; ++m) acc = fmaf(o[m], S[m], acc);
+                    for (int m4 = 0; m4 < MB; m4 += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(o + m4);
+                        acc = fmaf(q.x, S[m4], acc);
+                        acc = fmaf(q.y, S[m4 + 1], acc);
+                        acc = fmaf(q.z, S[m4 + 2], acc);
+                        acc = fmaf(q.w, S[m4 + 3], acc);
+                    }
                     v[i] = acc;
                 }
                 tmem_st16(taddr + kL + cb * 16, v);
@@ -393,7 +435,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float *o = ogx + (cb * 16 + i) * MB;
                     float acc = v[i];
 #pragma unroll
-                    for (int m = 0; m < MB; ++m) acc = fmaf(o[m], S[m], acc);
+                    for (int m4 = 0; m4 < MB; m4 += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(o + m4);
+                        acc = fmaf(q.x, S[m4], acc);
+                        acc = fmaf(q.y, S[m4 + 1], acc);
+                        acc = fmaf(q.z, S[m4 + 2], acc);
+                        acc = fmaf(q.w, S[m4 + 3], acc);
+                    }
                     v[i] = acc;
                 }
 #pragma unroll
@@ -437,6 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             __syncthreads();
         }
+        ++w;
     }
     tc_fence_before();
     __syncthreads();
@@ -461,17 +510,29 @@ cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, SM::ALLOC);
+        // CTAs per SM: shared memory, registers and tensor memory (the persistent CTAs
+        // never wait on one another, so a grid larger than what is resident is harmless)
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
+        int smem_sm = 0, smem_blk = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_blk, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        int o = smem_sm / (int)(SM::ALLOC + smem_blk + fa.sharedSizeBytes);
+        const int regs = (fa.numRegs + 7) / 8 * 8;
+        const int oreg = regs > 0 ? 65536 / (regs * kThreads) : o;
+        o = o < oreg ? o : oreg;
         const int tmem_cap = 512 / (int)SM::TMEM_COLS;
-        o = o < 1 ? 1 : o;
-        occ[dev] = o < tmem_cap ? o : tmem_cap;
+        o = o < tmem_cap ? o : tmem_cap;
+        occ[dev] = o < 1 ? 1 : (o > 4 ? 4 : o);
     }
     auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? 1 : 0; };
     const int xy_al = (h.x && h.y) ? (al(h.x) & al(h.y)) : 0;
+    const float *sv = MODE == hi::kY ? h.states2 : h.states;
+    const int st_al = (sv && al(sv) && bt.Mstride % 4 == 0) ? 1 : 0;
     kern<<<(unsigned)(num_sms * occ[dev]), kThreads, SM::ALLOC, st>>>(h, bt, al(h.sig),
-                                                                      h.out ? al(h.out) : 0, xy_al);
+                                                                      h.out ? al(h.out) : 0, xy_al,
+                                                                      st_al);
     return cudaGetLastError();
 }
 
