@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfilt.so")
 BUCKETS = [2, 4, 8, 16, 32, 64]
-HI_BUCKETS = [16, 32, 64]   # the decoupled high-order path
+HI_BUCKETS = [8, 16, 32, 64]   # the decoupled high-order path
 # (object name, source, extra defines): the chunked kernels compile once per state bucket
 UNITS = ([("api", "api.cu", []), ("seq", "seq.cu", []), ("chunk_setup", "chunk_setup.cu", []),
           ("chunk_dispatch", "chunk_dispatch.cu", []), ("noalloc", "noalloc.cu", []),

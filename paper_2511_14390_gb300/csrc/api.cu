@@ -133,7 +133,7 @@ void sizes(const Resolved &r, int64_t B, int64_t total, int Mmax, bool ragged, s
     size_t f = 0, s = 0, w = 0;
     if (r.algo == DFILT_ALGO_CHUNKED) {
         f = chunk_fwd_ws_bytes(B, total, Mmax, r.fp64_opt, ragged, r.hi);
-        s = chunk_saved_bytes(B, total, Mmax, r.fp64_opt, ragged);
+        s = chunk_saved_bytes(B, total, Mmax, r.fp64_opt, ragged, r.hi);
         w = chunk_bwd_ws_bytes(B, total, Mmax, r.fp64_opt, ragged, r.hi);
     }
     if (fwd) *fwd = f;

@@ -9,7 +9,7 @@
 
 namespace dfilt {
 
-#define DFILT_HI_BUCKETS(X) X(16) X(32) X(64)
+#define DFILT_HI_BUCKETS(X) X(8) X(16) X(32) X(64)
 #define DFILT_HI_EXTERN(V)                                                                        \
     extern template cudaError_t hi_plan<V>(const HiArgs &, const Batch &, cudaStream_t);          \
     extern template cudaError_t hi_jump<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
@@ -88,20 +88,34 @@ ChunkLayout chunk_layout(int Mmax, int fp64_scan_opt) {
     return l;
 }
 
+// the decoupled path's state buckets (8 holds orders 3..8 when the path may be taken)
+static bool hi_path_allowed(const HiOpt &ho) { return ho.path != DFILT_PATH_FUSED; }
+
 // Per-bucket plan: a fixed-shape batch is one bucket; a ragged batch runs every state
 // bucket up to its largest order as its own launch pair (setup + main kernel) over the
-// channels of that bucket, with records at a common stride.
-ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged) {
+// channels of that bucket, with records at a common stride.  Where the decoupled path may
+// run, the double-word-scan orders 3 and 4 join bucket 8.
+ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged, const HiOpt &ho) {
     ChunkPlan p{};
     p.ragged = ragged;
+    auto lay_of = [&](int m) {
+        ChunkLayout l = chunk_layout(m, fp64_opt);
+        if (l.MB == 4 && l.fp64_scan && hi_path_allowed(ho)) l = chunk_layout(8, fp64_opt);
+        return l;
+    };
     if (!ragged) {
         p.nb = 1;
-        p.lay[0] = chunk_layout(Mmax, fp64_opt);
+        p.lay[0] = lay_of(Mmax);
     } else {
         const int top = chunk_bucket(Mmax);
         p.nb = 0;
-        for (int mb : {2, 4, 8, 16, 32, 64})
-            if (mb <= top) p.lay[p.nb++] = chunk_layout(mb, fp64_opt);
+        for (int mb : {2, 4, 8, 16, 32, 64}) {
+            if (mb > top) break;
+            const ChunkLayout l = lay_of(mb);
+            if (p.nb > 0 && p.lay[p.nb - 1].MB == l.MB) continue;   // merged into the next
+            p.lay[p.nb++] = l;
+        }
+        if (p.nb > 0 && p.lay[p.nb - 1].MB < top) p.lay[p.nb++] = lay_of(top);
     }
     for (int j = 0; j < p.nb; ++j) {
         p.fstride = p.lay[j].fwd_tab > p.fstride ? p.lay[j].fwd_tab : p.fstride;
@@ -119,7 +133,7 @@ static size_t list_bytes(int64_t B, bool ragged) {
 // Decoupled high-order path: which buckets take it, and its workspace blocks
 // ---------------------------------------------------------------------------
 static bool hi_eligible(const ChunkLayout &l, const HiOpt &ho) {
-    return l.MB >= 16 && l.fp64_scan && ho.path != DFILT_PATH_FUSED;
+    return l.MB >= 8 && l.fp64_scan && ho.path != DFILT_PATH_FUSED;
 }
 
 // Blocks of the decoupled path behind the fused path's workspace (all 256-byte aligned):
@@ -184,13 +198,13 @@ static size_t fused_bwd_ws(int64_t B, const ChunkPlan &p, bool ragged) {
 
 size_t chunk_fwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
                           const HiOpt &ho) {
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
     return hi_ws(fused_fwd_ws(B, p, ragged), p, B, total, Mmax, false, ho).end;
 }
 
 size_t chunk_bwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
                           const HiOpt &ho) {
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
     return hi_ws(fused_bwd_ws(B, p, ragged), p, B, total, Mmax, true, ho).end;
 }
 
@@ -214,17 +228,23 @@ int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, co
     return st;
 }
 
-size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged) {
-    return chunk_saved_state_bytes(B, total, Mmax) + (size_t)B * chunk_plan(Mmax, fp64_opt, ragged).bstride;
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                         const HiOpt &ho) {
+    return chunk_saved_state_bytes(B, total, Mmax) +
+           (size_t)B * chunk_plan(Mmax, fp64_opt, ragged, ho).bstride;
 }
 
 namespace {
 
 // Sort the channels of a ragged batch by state bucket (one block; order within a bucket
 // is arbitrary, which no result depends on): list[starts[j] .. starts[j+1]) are the
-// channels of bucket j (orders up to 2 << j; the last bucket takes the rest).
+// channels of bucket j (orders up to be.mb[j]; the last bucket takes the rest).
+struct BucketEdges {
+    int mb[8];   // bucket j takes the orders above mb[j-1] up to mb[j]
+};
+
 __global__ void __launch_bounds__(1024) bucket_channels_kernel(const int *__restrict__ Ms, int64_t B,
-                                                               int Mstride, int nb,
+                                                               int Mstride, int nb, BucketEdges be,
                                                                int *__restrict__ list,
                                                                int *__restrict__ starts) {
     __shared__ int cnt[8], pos[8];
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(1024) bucket_channels_kernel(const int *__rest
         int m = Ms[i];
         m = m < 1 ? 1 : (m > Mstride ? Mstride : m);
         int j = 0;
-        while (j < nb - 1 && m > (2 << j)) ++j;
+        while (j < nb - 1 && m > be.mb[j]) ++j;
         return j;
     };
     for (int64_t i = threadIdx.x; i < B; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1);
@@ -253,6 +273,12 @@ __global__ void __launch_bounds__(1024) bucket_channels_kernel(const int *__rest
     for (int64_t i = threadIdx.x; i < B; i += blockDim.x) list[atomicAdd(&pos[bucket(i)], 1)] = (int)i;
 }
 
+BucketEdges edges(const ChunkPlan &p) {
+    BucketEdges be{};
+    for (int j = 0; j < p.nb; ++j) be.mb[j] = p.lay[j].MB;
+    return be;
+}
+
 }  // namespace
 
 // The decoupled path for bucket j of a call (forward or backward), launched on `st`.
@@ -265,6 +291,7 @@ struct HiCall {
 template <class F>
 static cudaError_t hi_switch(int MB, F f) {
     switch (MB) {
+        case 8: return f(std::integral_constant<int, 8>{});
         case 16: return f(std::integral_constant<int, 16>{});
         case 32: return f(std::integral_constant<int, 32>{});
         case 64: return f(std::integral_constant<int, 64>{});
@@ -291,7 +318,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                              int fp64_opt, int precision, int num_sms, cudaStream_t st,
                              const HiOpt &ho) {
     const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
     char *w = static_cast<char *>(ws);
     auto *counters = reinterpret_cast<unsigned long long *>(w);   // one per bucket
     // with a saved buffer, the same setup launch also writes the backward's tables into it
@@ -301,7 +328,8 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
     Batch bb[8];
     int *list = reinterpret_cast<int *>(w + kWsHeader + (size_t)bt.B * p.fstride);
     if (ragged) {
-        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, list, list + bt.B);
+        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, edges(p), list,
+                                                   list + bt.B);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -394,7 +422,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                              float *gzi, void *ws, const Batch &bt, int Mmax, int fp64_opt,
                              int precision, int num_sms, cudaStream_t st, const HiOpt &ho) {
     const bool ragged = bt.offsets != nullptr && bt.Ms != nullptr;
-    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged);
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
     const bool read_y = saved == nullptr;   // y is recomputed whenever the chunk states exist
     if (read_y && (!y || chunk_bucket(Mmax) > 32)) return cudaErrorNotSupported;
     char *wsc = static_cast<char *>(ws);
@@ -408,7 +436,8 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     int *list = reinterpret_cast<int *>(wsc + kWsHeader + (size_t)bt.B * p.bstride);
     cudaError_t e = cudaSuccess;
     if (ragged) {
-        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, list, list + bt.B);
+        bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, edges(p), list,
+                                                   list + bt.B);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

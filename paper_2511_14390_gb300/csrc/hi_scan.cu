@@ -4,7 +4,7 @@
 #include "hi.cuh"
 
 #ifndef DFILT_MB
-#error "compile once per state bucket with -DDFILT_MB=<16|32|64>"
+#error "compile once per state bucket with -DDFILT_MB=<8|16|32|64>"
 #endif
 
 namespace dfilt {
@@ -14,7 +14,9 @@ namespace {
 using hi::Plan;
 
 // threads per state row of the scan (the CTA holds MB * TPR threads)
-constexpr int scan_tpr(int mb) { return mb <= 16 ? 2 : 2; }
+// (one thread per row at order 32: no shuffles, and the columns past the channel's own
+// order are skipped warp-uniformly)
+constexpr int scan_tpr(int mb) { return mb <= 8 ? 4 : (mb == 32 ? 1 : 2); }
 
 // ---------------------------------------------------------------------------
 // Plan: per position of the launch's channel list, the tiles and scan spans before it
@@ -323,10 +325,24 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, in
                 ll[i] = 0.f;
             }
             if (p == 0) hh[0] = e[cc * MB + r];
+            if constexpr (TPR == 1) {
+                // columns in blocks of 4, up to the channel's order (zero beyond)
 #pragma unroll
-            for (int q = 0; q < JPT; ++q) {
-                const float2 sj = cur[p * JPT + q];
-                pipe::dw_acc(hh[q % NA], ll[q % NA], a[q], sj.x, sj.y);
+                for (int q4 = 0; q4 < JPT; q4 += 4) {
+                    if (q4 < c.M) {
+#pragma unroll
+                        for (int q = q4; q < q4 + 4; ++q) {
+                            const float2 sj = cur[q];
+                            pipe::dw_acc(hh[q % NA], ll[q % NA], a[q], sj.x, sj.y);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < JPT; ++q) {
+                    const float2 sj = cur[p * JPT + q];
+                    pipe::dw_acc(hh[q % NA], ll[q % NA], a[q], sj.x, sj.y);
+                }
             }
             float hs = hh[0], ls = ll[0];
 #pragma unroll

@@ -25,7 +25,7 @@
 #include "hi.cuh"
 
 #ifndef DFILT_MB
-#error "compile once per state bucket with -DDFILT_MB=<16|32|64>"
+#error "compile once per state bucket with -DDFILT_MB=<8|16|32|64>"
 #endif
 
 namespace dfilt {

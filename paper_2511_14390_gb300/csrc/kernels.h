@@ -26,6 +26,12 @@ constexpr int kTileSamples = kL * kChunks;
 // State-dimension bucket of the chunked kernels (M padded with zero coefficients).
 int chunk_bucket(int M);
 
+// High-order path choice of a call (dfilt_opts.path, .span_tiles).
+struct HiOpt {
+    int path = 0;         // dfilt_path
+    int span_tiles = 0;   // 0 automatic
+};
+
 // Per-channel table sizes (floats / doubles) written by the setup kernels.
 struct ChunkLayout {
     int MB;             // state bucket
@@ -42,7 +48,9 @@ struct ChunkPlan {
     size_t fstride, bstride;
     bool ragged;
 };
-ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged);
+// Orders 3 and 4 run in the order-8 bucket where the decoupled path may take them (it
+// starts at bucket 8), so that forward, backward and the workspace sizes agree.
+ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged, const HiOpt &ho);
 
 // Forward-to-backward buffer (`saved`): the chunk states (channel i's chunks start at
 // chunk index offsets[i] / L + i; each chunk stores Mstride floats), then, 256-byte
@@ -51,7 +59,8 @@ ChunkPlan chunk_plan(int Mmax, int fp64_opt, bool ragged);
 inline size_t chunk_saved_state_bytes(int64_t B, int64_t total, int Mstride) {
     return ((size_t)(total / kL + B + 1) * (size_t)Mstride * sizeof(float) + 255) / 256 * 256;
 }
-size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged);
+size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
+                         const HiOpt &ho);
 
 // Per-bucket launchers (one translation unit per bucket, compiled with -DDFILT_MB=<MB>).
 template <int MB>
@@ -72,12 +81,6 @@ constexpr int kMaxF32ScanBucket = 16;
 // launchers call it with phase 0 just before and phase 1 just after the main kernel
 // (direction 0 forward, 1 backward).  A no-op while timing is off.
 void timing_mark(int direction, int phase, cudaStream_t st);
-
-// High-order path choice of a call (dfilt_opts.path, .span_tiles).
-struct HiOpt {
-    int path = 0;         // dfilt_path
-    int span_tiles = 0;   // 0 automatic
-};
 
 // fp64_opt: the caller's scan option (-1 automatic per bucket, 0 off, 1 on)
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,
