@@ -150,9 +150,10 @@ dfilt_status dfilt_forward(const float *x, const float *b, const float *a, const
  *                  wanted)
  *   ws, ws_bytes   workspace of at least `bwd_ws` bytes
  * With `saved`, b and a must be the forward's (the tables in `saved` were formed
- * from them) and opts must select the same algorithm, chunk length and scan
- * precision as the forward that filled `saved`.  The call may be repeated with the
- * same `saved`.
+ * from them) and opts must select the same algorithm, chunk length, scan precision,
+ * path and span length as the forward that filled `saved`.  The call may be repeated
+ * with the same `saved`.  Passing y together with `saved` saves the decoupled path a
+ * recomputation of y (the single-kernel path recomputes it either way).
  */
 dfilt_status dfilt_backward(const float *gy, const float *x, const float *y,
                             const float *b, const float *a, const float *zi, const void *saved,

@@ -228,10 +228,18 @@ int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, co
     return st;
 }
 
+// `saved` = chunk states | backward records | (decoupled path) the adjoint's span
+// transitions J' per channel, formed by the forward together with its own
+static size_t saved_jump_off(int64_t B, int64_t total, int Mmax, const ChunkPlan &p) {
+    return al256(chunk_saved_state_bytes(B, total, Mmax) + (size_t)B * p.bstride);
+}
+
 size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
                          const HiOpt &ho) {
-    return chunk_saved_state_bytes(B, total, Mmax) +
-           (size_t)B * chunk_plan(Mmax, fp64_opt, ragged, ho).bstride;
+    const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
+    const HiWs hw = hi_ws(0, p, B, total, Mmax, false, ho);
+    return saved_jump_off(B, total, Mmax, p) +
+           (hw.nhi ? al256((size_t)B * hw.mbmax * hw.mbmax * 8) : 0);
 }
 
 namespace {
@@ -388,7 +396,9 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                 q.counter = ctl + 0;
                 r = hi_tc<V>(q, bb[j], hi::kEFwd, num_sms, st);   // E_c into the slots
                 if (r != cudaSuccess) return r;
-                r = hi_jump<V>(q, bb[j], false, num_sms, st);
+                q.jump2 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(saved) +
+                                                     saved_jump_off(bt.B, bt.total, Mmax, p));
+                r = hi_jump<V>(q, bb[j], false, num_sms, st);   // J, and J' for the backward
                 if (r != cudaSuccess) return r;
                 r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
                 if (r != cudaSuccess) return r;
@@ -497,8 +507,9 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.counter = ctl + 0;
                 r = hi_tc<V>(q, bb[j], hi::kEBwd, num_sms, st);
                 if (r != cudaSuccess) return r;
-                r = hi_jump<V>(q, bb[j], true, num_sms, st);
-                if (r != cudaSuccess) return r;
+                // the adjoint's span transitions, formed by the forward
+                q.jump = reinterpret_cast<float2 *>(const_cast<char *>(reinterpret_cast<const char *>(saved)) +
+                                                    saved_jump_off(bt.B, bt.total, Mmax, p));
                 r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 1;

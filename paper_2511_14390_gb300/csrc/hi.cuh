@@ -114,6 +114,7 @@ struct HiArgs {
     int64_t tab_stride;
     int tab_g, tab_ol;      // Y pass: byte offsets of g and O_L in a record
     float2 *jump;           // scan: per channel Abar^K (double words, column-major)
+    float2 *jump2;          // forward's span transitions: also the adjoint's J' (nullable)
     unsigned *flags;        // scan: per item, inclusive state published
     float2 *incl;           // scan: per item inclusive state (MB double words)
     unsigned long long *counter;

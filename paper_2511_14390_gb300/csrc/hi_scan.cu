@@ -218,18 +218,22 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
         hw[i] = make_float2(v.hi, v.lo);
     }
     sync();
-    // 5. the closed forms (hw index i <-> h[64(K-2) + i], so h[64K - d] = hw[128 - d])
-    float2 *J = h.jump + (size_t)ch * MB * MB;
+    // 5. the closed forms (hw index i <-> h[64(K-2) + i], so h[64K - d] = hw[128 - d]):
+    // J into h.jump, and (forward call) J' into h.jump2 for the backward
     for (int e = t; e < MB * MB; e += NT) {
         const int k = e % MB, m = e / MB;
-        float hh = 0.f, ll = 0.f;
         if (!bwd) {
+            float hh = 0.f, ll = 0.f;
             for (int l = k + 1; l <= MB; ++l) pipe::dw_acc(hh, ll, hw[2 * kL + k - l - m], -sa[l - 1], 0.f);
-        } else {
-            for (int j = 0; j + m < MB; ++j) pipe::dw_acc(hh, ll, hw[2 * kL - 1 - k - j], -sa[j + m], 0.f);
+            const dw v = fast_two_sum(hh, ll);
+            h.jump[(size_t)ch * MB * MB + e] = make_float2(v.hi, v.lo);
         }
-        const dw v = fast_two_sum(hh, ll);
-        J[e] = make_float2(v.hi, v.lo);
+        if (bwd || h.jump2) {
+            float hh = 0.f, ll = 0.f;
+            for (int j = 0; j + m < MB; ++j) pipe::dw_acc(hh, ll, hw[2 * kL - 1 - k - j], -sa[j + m], 0.f);
+            const dw v = fast_two_sum(hh, ll);
+            (bwd ? h.jump : h.jump2)[(size_t)ch * MB * MB + e] = make_float2(v.hi, v.lo);
+        }
     }
 }
 
@@ -237,17 +241,19 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
 // Chunk-state scan.  One chain per CTA of NT = MB * TPR threads: thread (r, p) owns
 // row r of the transition, columns p*JPT .. p*JPT+JPT-1 in registers (double words);
 // the state vector alternates between two shared-memory buffers, one CTA barrier per
-// chunk.  E rows of a tile are staged in shared memory (double-buffered, cp.async)
-// and overwritten in global memory by the states of the output pass.
+// chunk.  Part 0 of each row prefetches its entry of E kPre chunks ahead into registers
+// (the chunk slots are read straight from global memory, so a CTA needs almost no
+// shared memory and many chains share an SM); the output pass overwrites each slot's E
+// with the chunk's state after its E was read.
 // ---------------------------------------------------------------------------
 template <int MB, int TPR, bool REV>
-__global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, int e_al16) {
+__global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
     using Tab = ChunkTab<MB>;
     constexpr int NT = MB * TPR, JPT = MB / TPR;
     constexpr int NA = JPT >= 8 ? 4 : (JPT >= 2 ? 2 : 1);   // independent accumulators
+    constexpr int kPre = 8;                                   // E prefetch distance (chunks)
     extern __shared__ float4 smem4[];
-    float *ebuf = reinterpret_cast<float *>(smem4);                  // [2][kChunks][MB]
-    float2 *st = reinterpret_cast<float2 *>(ebuf + 2 * kChunks * MB);   // [2][MB]
+    float2 *st = reinterpret_cast<float2 *>(smem4);                  // [2][MB]
     long long *info = reinterpret_cast<long long *>(st + 2 * MB);    // [4]
     const int t = threadIdx.x, r = t / TPR, p = t % TPR;
     auto sync = [] {
@@ -273,9 +279,10 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, in
         const Channel c = channel_of(bt, ch);
         const int64_t s = w - h.plan.span_pref[pos];
         const int64_t nsp = h.plan.span_pref[pos + 1] - h.plan.span_pref[pos];
-        const int64_t ntiles = hi::tiles_of(c.len);
+        const int64_t nchunks = (c.len + kL - 1) / kL;
         const int64_t sp = REV ? nsp - 1 - s : s;   // the span's index in time
-        const int64_t t0 = sp * ST, t1 = (t0 + ST < ntiles) ? t0 + ST : ntiles;
+        const int64_t k0 = sp * ST * kChunks;       // the span's chunks [k0, k1)
+        const int64_t k1 = (k0 + (int64_t)ST * kChunks < nchunks) ? k0 + (int64_t)ST * kChunks : nchunks;
         const int64_t cbase = c.off / kL + ch;       // the channel's first chunk slot
         if (ch != cur_ch) {
             const float2 *At = reinterpret_cast<const float2 *>(h.tabs + (size_t)ch * h.tab_stride +
@@ -285,37 +292,10 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, in
             cur_ch = ch;
         }
 
-        // E rows of tile `tile` into staging buffer `b` (rows beyond the tile's chunks
-        // are not read; entries beyond the channel's order read as zero)
-        auto stage = [&](int64_t tile, int b) {
-            const int64_t tl = c.len - tile * kTileSamples;
-            const int nch = (int)(((tl < kTileSamples ? tl : kTileSamples) + kL - 1) / kL);
-            const float *src = h.states + (size_t)(cbase + tile * kChunks) * Ms;
-            float *dst = ebuf + b * kChunks * MB;
-            const uint32_t d0 = smem_u32(dst);
-            if (e_al16) {
-                for (int i = t; i < nch * (MB / 4); i += NT) {
-                    const int row = i / (MB / 4), m4 = (i % (MB / 4)) * 4;
-                    const int nv = c.M - m4 < 0 ? 0 : (c.M - m4 > 4 ? 4 : c.M - m4);
-                    cp_async16(d0 + (uint32_t)(row * MB + m4) * 4,
-                               nv ? (const void *)(src + (size_t)row * Ms + m4) : (const void *)src,
-                               nv * 4);
-                }
-            } else {
-                for (int i = t; i < nch * MB; i += NT) {
-                    const int row = i / MB, m = i % MB;
-                    const bool v = m < c.M;
-                    cp_async4(d0 + (uint32_t)(row * MB + m) * 4,
-                              v ? (const void *)(src + (size_t)row * Ms + m) : (const void *)src, v ? 4 : 0);
-                }
-            }
-            cp_async_commit();
-        };
-
-        // One chunk step: the state in st[buf] enters chunk cc of the staged tile eb;
-        // the next state goes to st[buf ^ 1].  With `out`, the entering state is
-        // written to the chunk's slot.
-        auto step = [&](const float *e, int cc, int buf, float *slot_row) {
+        // One chunk step: the state in st[buf] enters the chunk whose input is e (this
+        // row's entry, part 0 only); the next state goes to st[buf ^ 1].  With a slot, the
+        // entering state is written to it.
+        auto step = [&](float e, int buf, float *slot_row) {
             const float2 *cur = st + buf * MB;
             float2 *nxt = st + (buf ^ 1) * MB;
             float hh[NA], ll[NA];
@@ -324,7 +304,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, in
                 hh[i] = 0.f;
                 ll[i] = 0.f;
             }
-            if (p == 0) hh[0] = e[cc * MB + r];
+            if (p == 0) hh[0] = e;
             if constexpr (TPR == 1) {
                 // columns in blocks of 4, up to the channel's order (zero beyond)
 #pragma unroll
@@ -367,31 +347,30 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt, in
             sync();
         };
 
-        // Scan tiles [t0, t1) in processing order from the state in st[buf0]; returns the
-        // buffer holding the final state.  `out` writes the states to the slots.
+        // Scan the span's chunks in processing order from the state in st[buf0]; returns
+        // the buffer holding the final state.  `out` writes the states to the slots.
         auto run = [&](int buf0, bool out) -> int {
             int buf = buf0;
-            const int64_t ntl = t1 - t0;
-            stage(REV ? t1 - 1 : t0, 0);
-            for (int64_t ti = 0; ti < ntl; ++ti) {
-                const int64_t tile = REV ? t1 - 1 - ti : t0 + ti;
-                if (ti + 1 < ntl) {
-                    stage(REV ? tile - 1 : tile + 1, (int)((ti + 1) & 1));
-                    cp_async_wait_1();
-                } else {
-                    cp_async_wait_all();
+            const int64_t cnt = k1 - k0;
+            const bool ld = (p == 0) && (r < c.M);
+            auto slot = [&](int64_t i) {   // the i-th chunk in processing order
+                return h.states + (size_t)(cbase + (REV ? k1 - 1 - i : k0 + i)) * Ms;
+            };
+            auto eload = [&](int64_t i) -> float { return (ld && i < cnt) ? __ldcg(slot(i) + r) : 0.f; };
+            float ring[kPre];
+#pragma unroll
+            for (int u = 0; u < kPre; ++u) ring[u] = eload(u);
+            for (int64_t i0 = 0; i0 < cnt; i0 += kPre) {
+#pragma unroll
+                for (int u = 0; u < kPre; ++u) {
+                    const int64_t i = i0 + u;
+                    if (i < cnt) {
+                        const float e = ring[u];
+                        ring[u] = eload(i + kPre);
+                        step(e, buf, out ? slot(i) : nullptr);
+                        buf ^= 1;
+                    }
                 }
-                sync();
-                const float *e = ebuf + (ti & 1) * kChunks * MB;
-                const int64_t tl = c.len - tile * kTileSamples;
-                const int nch = (int)(((tl < kTileSamples ? tl : kTileSamples) + kL - 1) / kL);
-                float *slots = h.states + (size_t)(cbase + tile * kChunks) * Ms;
-                for (int k = 0; k < nch; ++k) {
-                    const int cc = REV ? nch - 1 - k : k;
-                    step(e, cc, buf, out ? slots + (size_t)cc * Ms : nullptr);
-                    buf ^= 1;
-                }
-                sync();   // staging buffer (ti & 1) is refilled two tiles on
             }
             return buf;
         };
@@ -532,21 +511,18 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
     constexpr int TPR = scan_tpr(MB);
     constexpr int NT = MB * TPR;
     auto kern = hi_scan_kernel<MB, TPR, REV>;
-    const size_t smem = (size_t)2 * kChunks * MB * 4 + 2 * MB * 8 + 64;
+    const size_t smem = (size_t)2 * MB * 8 + 64;
     static int occ[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!occ[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
         if (e != cudaSuccess) return e;
         occ[dev] = o < 1 ? 1 : o;
     }
-    const int e_al16 = (bt.Mstride % 4 == 0 && (reinterpret_cast<uintptr_t>(h.states) & 15) == 0) ? 1 : 0;
-    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt, e_al16);
+    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt);
     return cudaGetLastError();
 }
 

@@ -382,12 +382,13 @@ class DFilt(torch.autograd.Function):
     def forward(ctx, x, b, a, zi=None, opts: Opts | None = None):
         opts = opts or make_opts()
         y, saved = dfilt_forward(x, b, a, zi, opts=opts)
-        keep_y = saved is None   # without chunk states the backward re-reads y
+        # y is kept for the backward (it is the output, so this costs no memory): the
+        # decoupled high-order path reads it instead of recomputing it from the chunk
+        # states, and the single-kernel path re-reads it when there are no chunk states
         ctx.opts = opts
         ctx.has_zi = zi is not None
         ctx.save_for_backward(x, b, a, zi if zi is not None else x.new_empty(0),
-                              saved if saved is not None else x.new_empty(0),
-                              y if keep_y else x.new_empty(0))
+                              saved if saved is not None else x.new_empty(0), y)
         return y
 
     @staticmethod
@@ -452,12 +453,11 @@ class DFiltRagged(torch.autograd.Function):
     def forward(ctx, x, offsets, Ms, Ns, b, a, zi=None, opts: Opts | None = None):
         opts = opts or make_opts()
         y, saved = dfilt_forward_ragged(x, offsets, Ms, Ns, b, a, zi, opts=opts)
-        keep_y = saved is None   # without chunk states the backward re-reads y
-        ctx.opts = opts
+        ctx.opts = opts   # y is kept for the backward, as in DFilt
         ctx.has_zi = zi is not None
         empty = x.new_empty(0)
         ctx.save_for_backward(x, offsets, Ms, Ns, b, a, zi if zi is not None else empty,
-                              saved if saved is not None else empty, y if keep_y else empty)
+                              saved if saved is not None else empty, y)
         return y
 
     @staticmethod
