@@ -17,6 +17,9 @@ using hi::Plan;
 // (one thread per row at order 32: no shuffles, and the columns past the channel's own
 // order are skipped warp-uniformly)
 constexpr int scan_tpr(int mb) { return mb <= 8 ? 4 : (mb == 32 ? 1 : 2); }
+// Chains (CTAs) per SM: enough warps to keep the FP32 pipes issuing, few enough that a
+// long channel's chain is not slowed by many others sharing its SM
+constexpr int scan_chains_per_sm(int mb) { return mb <= 16 ? 16 : (mb == 32 ? 8 : 4); }
 
 // ---------------------------------------------------------------------------
 // Plan: per position of the launch's channel list, the tiles and scan spans before it
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
     extern __shared__ float4 smem4[];
     float2 *st = reinterpret_cast<float2 *>(smem4);                  // [2][MB]
     long long *info = reinterpret_cast<long long *>(st + 2 * MB);    // [4]
+    float *ering = reinterpret_cast<float *>(info + 4);              // [kPre][MB] E prefetch
     const int t = threadIdx.x, r = t / TPR, p = t % TPR;
     auto sync = [] {
         if constexpr (NT == 32) __syncwarp();
@@ -348,7 +352,9 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
         };
 
         // Scan the span's chunks in processing order from the state in st[buf0]; returns
-        // the buffer holding the final state.  `out` writes the states to the slots.
+        // the buffer holding the final state.  `out` writes the states to the slots.  The
+        // E entry of chunk i + kPre is copied (cp.async) into this lane's ring slot while
+        // chunk i is scanned; each lane reads and refills only its own slots.
         auto run = [&](int buf0, bool out) -> int {
             int buf = buf0;
             const int64_t cnt = k1 - k0;
@@ -356,22 +362,25 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
             auto slot = [&](int64_t i) {   // the i-th chunk in processing order
                 return h.states + (size_t)(cbase + (REV ? k1 - 1 - i : k0 + i)) * Ms;
             };
-            auto eload = [&](int64_t i) -> float { return (ld && i < cnt) ? __ldcg(slot(i) + r) : 0.f; };
-            float ring[kPre];
-#pragma unroll
-            for (int u = 0; u < kPre; ++u) ring[u] = eload(u);
-            for (int64_t i0 = 0; i0 < cnt; i0 += kPre) {
-#pragma unroll
-                for (int u = 0; u < kPre; ++u) {
-                    const int64_t i = i0 + u;
-                    if (i < cnt) {
-                        const float e = ring[u];
-                        ring[u] = eload(i + kPre);
-                        step(e, buf, out ? slot(i) : nullptr);
-                        buf ^= 1;
-                    }
+            auto issue = [&](int64_t i) {
+                if (p == 0) {
+                    const bool v = ld && i < cnt;
+                    cp_async4(smem_u32(ering + (i % kPre) * MB + r), v ? (const void *)(slot(i) + r)
+                                                                      : (const void *)h.states,
+                              v ? 4 : 0);
                 }
+                cp_async_commit();
+            };
+            for (int u = 0; u < kPre; ++u) issue(u);
+#pragma unroll 1
+            for (int64_t i = 0; i < cnt; ++i) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(kPre - 1) : "memory");
+                const float e = p == 0 ? ering[(i % kPre) * MB + r] : 0.f;
+                issue(i + kPre);
+                step(e, buf, out ? slot(i) : nullptr);
+                buf ^= 1;
             }
+            cp_async_wait_all();
             return buf;
         };
 
@@ -511,7 +520,7 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
     constexpr int TPR = scan_tpr(MB);
     constexpr int NT = MB * TPR;
     auto kern = hi_scan_kernel<MB, TPR, REV>;
-    const size_t smem = (size_t)2 * MB * 8 + 64;
+    const size_t smem = (size_t)2 * MB * 8 + 32 + (size_t)8 * MB * 4;
     static int occ[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -520,6 +529,7 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
         int o = 0;
         const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
         if (e != cudaSuccess) return e;
+        o = o < scan_chains_per_sm(MB) ? o : scan_chains_per_sm(MB);
         occ[dev] = o < 1 ? 1 : o;
     }
     kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt);
