@@ -210,6 +210,18 @@ dfilt_status dfilt_sync_status(void *stream);
 dfilt_status dfilt_kernel_timing(int enable);
 dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
                                       int *bwd_calls);
+/*
+ * The same records split by class (each array of 8 entries, not NULL; read and discarded
+ * like dfilt_kernel_timing_read): 0 the forward calls and 1 the backward calls as above;
+ * within them, for the chunked algorithm, 2 the chunk-state scans, 3 the E passes
+ * (zero-state chunk end states), 4 the output passes (y), 5 the adjoint output passes
+ * (grad_x and the coefficient-gradient sums), 6 the span transitions, 7 the
+ * single-kernel path's main kernels.  A class records one pair per state bucket and call.
+ */
+dfilt_status dfilt_kernel_timing_read_classes(double *ms, int *calls);
+
+/* Number of kernels the library has launched in this process (a measurement aid). */
+dfilt_status dfilt_launch_count(int64_t *n);
 
 /*
  * Optional output check (off by default).  With enable != 0, every later forward /

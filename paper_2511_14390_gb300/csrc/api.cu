@@ -3,6 +3,7 @@
 // or frees device memory.
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include <nvtx3/nvToolsExt.h>
@@ -56,6 +57,7 @@ cudaError_t check_finite(const float *p, int64_t n, int *status, int num_sms, cu
     const int64_t want = (n / 4 + 255) / 256;
     const int grid = (int)(want < 4LL * num_sms ? (want > 0 ? want : 1) : 4LL * num_sms);
     check_finite_kernel<<<grid, 256, 0, st>>>(p, n, status);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -234,12 +236,17 @@ struct TimingSlot {
 std::mutex g_tmu;
 bool g_timing_on = false;
 TimingSlot g_slots[kTimingSlots];
-thread_local int t_pending[2] = {-1, -1};
+constexpr int kTimingClasses = 8;
+thread_local int t_pending[kTimingClasses] = {-1, -1, -1, -1, -1, -1, -1, -1};
+std::atomic<long long> g_launches{0};
 
 }  // namespace
 
 namespace dfilt {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 void timing_mark(int dir, int phase, cudaStream_t st) {
+    if (dir < 0 || dir >= kTimingClasses) return;
     std::lock_guard<std::mutex> lk(g_tmu);
     if (!g_timing_on) return;
     int dev = 0;
@@ -463,12 +470,14 @@ dfilt_status dfilt_kernel_timing(int enable) {
     return DFILT_OK;
 }
 
-dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
-                                      int *bwd_calls) {
+// sums of the recorded pairs per class (then discarded)
+static dfilt_status timing_collect(double *ms, int *n) {
     std::lock_guard<std::mutex> lk(g_tmu);
-    double ms[2] = {0.0, 0.0};
-    int n[2] = {0, 0};
     dfilt_status st = DFILT_OK;
+    for (int k = 0; k < kTimingClasses; ++k) {
+        ms[k] = 0.0;
+        n[k] = 0;
+    }
     for (TimingSlot &sl : g_slots) {
         if (sl.state != 2) {
             sl.state = 0;
@@ -484,11 +493,30 @@ dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bw
         }
         sl.state = 0;
     }
+    return st;
+}
+
+dfilt_status dfilt_kernel_timing_read(double *fwd_ms, int *fwd_calls, double *bwd_ms,
+                                      int *bwd_calls) {
+    double ms[kTimingClasses];
+    int n[kTimingClasses];
+    const dfilt_status st = timing_collect(ms, n);
     if (fwd_ms) *fwd_ms = ms[0];
     if (fwd_calls) *fwd_calls = n[0];
     if (bwd_ms) *bwd_ms = ms[1];
     if (bwd_calls) *bwd_calls = n[1];
     return st;
+}
+
+dfilt_status dfilt_kernel_timing_read_classes(double *ms, int *calls) {
+    if (!ms || !calls) return DFILT_ERR_INVALID_ARG;
+    return timing_collect(ms, calls);
+}
+
+dfilt_status dfilt_launch_count(int64_t *n) {
+    if (!n) return DFILT_ERR_INVALID_ARG;
+    *n = (int64_t)g_launches.load(std::memory_order_relaxed);
+    return DFILT_OK;
 }
 
 dfilt_status dfilt_set_numeric_check(int enable) {

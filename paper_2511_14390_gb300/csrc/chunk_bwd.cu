@@ -537,7 +537,7 @@ cudaError_t launch_bwd_t(const float *gy, const float *x, const float *y, const 
     auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     const int mask = (al(gy) ? 1 : 0) | (al(x) ? 2 : 0) | ((y && al(y)) ? 4 : 0) | ((gx && al(gx)) ? 8 : 0);
     kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(gy, x, y, b, a, saved, gx, gb, ga, gzi, tabs,
-                                                      counter, bt, three, mask);
+                                                      counter, bt, three, mask); note_launch();
     return cudaGetLastError();
 }
 
@@ -1436,7 +1436,7 @@ cudaError_t launch_bwd_ws(const float *gy, const float *x, const float *b,
         if (gx && make_chunk_tmap(&tmgx, gx, bt.total)) tma |= 4;
     }
     kern<<<(unsigned)grid, kBwThreads, SM::ALLOC, st>>>(gy, x, b, a, saved, gx, gb, ga, gzi, tabs, counter,
-                                                       bt, three, mask, tma, tmg, tmx, tmgx);
+                                                       bt, three, mask, tma, tmg, tmx, tmgx); note_launch();
     return cudaGetLastError();
 }
 

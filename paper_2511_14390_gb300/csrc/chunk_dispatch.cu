@@ -337,7 +337,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
     int *list = reinterpret_cast<int *>(w + kWsHeader + (size_t)bt.B * p.fstride);
     if (ragged) {
         bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, edges(p), list,
-                                                   list + bt.B);
+                                                   list + bt.B); note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -394,24 +394,34 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                 cudaError_t r = hi_plan<V>(q, bb[j], st);
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 0;
+                timing_mark(kTimeEPass, 0, st);
                 r = hi_tc<V>(q, bb[j], hi::kEFwd, num_sms, st);   // E_c into the slots
+                timing_mark(kTimeEPass, 1, st);
                 if (r != cudaSuccess) return r;
                 q.jump2 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(saved) +
                                                      saved_jump_off(bt.B, bt.total, Mmax, p));
+                timing_mark(kTimeJump, 0, st);
                 r = hi_jump<V>(q, bb[j], false, num_sms, st);   // J, and J' for the backward
+                timing_mark(kTimeJump, 1, st);
                 if (r != cudaSuccess) return r;
                 r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 1;
+                timing_mark(kTimeScan, 0, st);
                 r = hi_scan<V>(q, bb[j], false, num_sms, st);   // S_c over the slots
+                timing_mark(kTimeScan, 1, st);
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 2;
                 q.tab_g = (int)Tab::F_G;
                 q.tab_ol = (int)Tab::F_OL;
-                return hi_tc<V>(q, bb[j], hi::kY, num_sms, st);   // y
+                timing_mark(kTimeYPass, 0, st);
+                r = hi_tc<V>(q, bb[j], hi::kY, num_sms, st);   // y
+                timing_mark(kTimeYPass, 1, st);
+                return r;
             });
             continue;
         }
+        timing_mark(kTimeFused, 0, st);
         switch (p.lay[j].MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
@@ -422,6 +432,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
 #undef X
             default: e = cudaErrorInvalidValue;
         }
+        timing_mark(kTimeFused, 1, st);
     }
     timing_mark(0, 1, st);
     return e;
@@ -447,7 +458,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
     cudaError_t e = cudaSuccess;
     if (ragged) {
         bucket_channels_kernel<<<1, 1024, 0, st>>>(bt.Ms, bt.B, bt.Mstride, p.nb, edges(p), list,
-                                                   list + bt.B);
+                                                   list + bt.B); note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -505,7 +516,9 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.sig = gy;
                 q.states = sprime;
                 q.counter = ctl + 0;
+                timing_mark(kTimeEPass, 0, st);
                 r = hi_tc<V>(q, bb[j], hi::kEBwd, num_sms, st);
+                timing_mark(kTimeEPass, 1, st);
                 if (r != cudaSuccess) return r;
                 // the adjoint's span transitions, formed by the forward
                 q.jump = reinterpret_cast<float2 *>(const_cast<char *>(reinterpret_cast<const char *>(saved)) +
@@ -514,7 +527,9 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 1;
                 q.gzi = gzi;
+                timing_mark(kTimeScan, 0, st);
                 r = hi_scan<V>(q, bb[j], true, num_sms, st);   // S'_c, grad_zi
+                timing_mark(kTimeScan, 1, st);
                 if (r != cudaSuccess) return r;
                 const float *yv = y;
                 if (!yv) {
@@ -526,7 +541,9 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                     qy.counter = ctl + 2;
                     qy.tab_g = (int)Tab::B_G;
                     qy.tab_ol = (int)Tab::b_ol(true);
+                    timing_mark(kTimeYPass, 0, st);
                     r = hi_tc<V>(qy, bb[j], hi::kY, num_sms, st);
+                    timing_mark(kTimeYPass, 1, st);
                     if (r != cudaSuccess) return r;
                     yv = ybuf;
                 }
@@ -535,14 +552,18 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.y = yv;
                 q.out = gx;
                 q.counter = ctl + 3;
+                timing_mark(kTimeUPass, 0, st);
                 r = hi_tc<V>(q, bb[j], hi::kU, num_sms, st);   // grad_x, lag sums per tile
                 if (r != cudaSuccess) return r;
                 q.gb = gb;
                 q.ga = ga;
-                return hi_reduce<V>(q, bb[j], st);
+                r = hi_reduce<V>(q, bb[j], st);
+                timing_mark(kTimeUPass, 1, st);
+                return r;
             });
             continue;
         }
+        timing_mark(kTimeFused, 0, st);
         switch (p.lay[j].MB) {
 #define X(V)                                                                                   \
     case V:                                                                                    \
@@ -553,6 +574,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
 #undef X
             default: e = cudaErrorInvalidValue;
         }
+        timing_mark(kTimeFused, 1, st);
     }
     timing_mark(1, 1, st);
     return e;

@@ -424,7 +424,7 @@ cudaError_t launch_fwd_t(const float *x, const float *zi, float *y, float *saved
     const int64_t grid = bt.B < slots ? bt.B : slots;
     const int x_al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
     const int y_al = (reinterpret_cast<uintptr_t>(y) & 15) == 0;
-    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(x, zi, y, saved, tabs, counter, bt, three, x_al, y_al);
+    kern<<<(unsigned)grid, kThreads, SM::ALLOC, st>>>(x, zi, y, saved, tabs, counter, bt, three, x_al, y_al); note_launch();
     return cudaGetLastError();
 }
 
@@ -1090,7 +1090,7 @@ cudaError_t launch_fwd_ws(const float *x, const float *zi, float *y, float *save
         make_chunk_tmap(&tmy, y, bt.total))
         use_tma = 1;
     kern<<<(unsigned)grid, kFwdThreads, SM::ALLOC, st>>>(x, zi, y, saved, tabs, counter, bt, three, x_al,
-                                                       y_al, use_tma, tmx, tmy);
+                                                       y_al, use_tma, tmx, tmy); note_launch();
     return cudaGetLastError();
 }
 

@@ -411,7 +411,7 @@ cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, c
     const dim3 small_grid((unsigned)((bt.B + kSmallWarps - 1) / kSmallWarps), 1);   // both records per warp
     const dim3 large_grid((unsigned)bt.B, gy);
     auto small = [&](auto kern) -> cudaError_t {
-        kern<<<small_grid, 32 * kSmallWarps, 0, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan);
+        kern<<<small_grid, 32 * kSmallWarps, 0, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan); note_launch();
         return cudaGetLastError();
     };
     auto large = [&](auto kern, int mb, size_t smem) -> cudaError_t {
@@ -420,7 +420,7 @@ cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, c
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<large_grid, mb, smem, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan);
+        kern<<<large_grid, mb, smem, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan); note_launch();
         return cudaGetLastError();
     };
     switch (MB) {

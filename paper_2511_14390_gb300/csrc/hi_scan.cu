@@ -532,7 +532,7 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
         o = o < scan_chains_per_sm(MB) ? o : scan_chains_per_sm(MB);
         occ[dev] = o < 1 ? 1 : o;
     }
-    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt);
+    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt); note_launch();
     return cudaGetLastError();
 }
 
@@ -540,7 +540,7 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
 
 template <int MB>
 cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st) {
-    hi_plan_kernel<<<1, 1024, 0, st>>>(h.plan, bt);
+    hi_plan_kernel<<<1, 1024, 0, st>>>(h.plan, bt); note_launch();
     return cudaGetLastError();
 }
 
@@ -561,7 +561,7 @@ cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cud
     }
     // one block per channel position (at most B; blocks past the launch's list exit)
     if (bt.B <= 0) return cudaSuccess;
-    kern<<<(unsigned)bt.B, MB * TPR, smem, st>>>(h, bt, bwd ? 1 : 0);
+    kern<<<(unsigned)bt.B, MB * TPR, smem, st>>>(h, bt, bwd ? 1 : 0); note_launch();
     return cudaGetLastError();
 }
 
@@ -573,7 +573,7 @@ cudaError_t hi_scan(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cud
 template <int MB>
 cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st) {
     if (bt.B <= 0) return cudaSuccess;
-    hi_reduce_kernel<MB><<<(unsigned)((bt.B + 3) / 4), 128, 0, st>>>(h, bt);
+    hi_reduce_kernel<MB><<<(unsigned)((bt.B + 3) / 4), 128, 0, st>>>(h, bt); note_launch();
     return cudaGetLastError();
 }
 

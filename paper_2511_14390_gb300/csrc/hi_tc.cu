@@ -532,7 +532,7 @@ cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_
     const int st_al = (sv && al(sv) && bt.Mstride % 4 == 0) ? 1 : 0;
     kern<<<(unsigned)(num_sms * occ[dev]), kThreads, SM::ALLOC, st>>>(h, bt, al(h.sig),
                                                                       h.out ? al(h.out) : 0, xy_al,
-                                                                      st_al);
+                                                                      st_al); note_launch();
     return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ extern "C" dfilt_status dfilt_ic_df1(const float *b, const float *a, const float
     if (!zi || (xpast && N > 0 && !b) || (ypast && !a)) return DFILT_ERR_INVALID_ARG;
     const int64_t n = B * M;
     ic_df1_kernel<<<(unsigned)((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        b, a, N > 0 ? xpast : nullptr, ypast, zi, B, N, M);
+        b, a, N > 0 ? xpast : nullptr, ypast, zi, B, N, M); note_launch();
     return cudaGetLastError() == cudaSuccess ? DFILT_OK : DFILT_ERR_CUDA;
 }
 
@@ -93,6 +93,6 @@ extern "C" dfilt_status dfilt_ic_df1_backward(const float *b, const float *a, co
     if (B > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
     ic_df1_bwd_kernel<<<(unsigned)B, 64, 0, static_cast<cudaStream_t>(stream)>>>(
         b, a, N > 0 ? xpast : nullptr, ypast, gzi, N > 0 ? gxpast : nullptr, gypast, gb, ga, N,
-        M);
+        M); note_launch();
     return cudaGetLastError() == cudaSuccess ? DFILT_OK : DFILT_ERR_CUDA;
 }

@@ -240,13 +240,13 @@ extern "C" dfilt_status dfilt_jvp(const float *x, const float *y, const float *b
         kern<<<grid, kJvpThreads, 0, st>>>(
             reinterpret_cast<const float4 *>(x), reinterpret_cast<const float4 *>(dx),
             reinterpret_cast<const float4 *>(y), b, db, da, reinterpret_cast<float4 *>(v), ones,
-            B, T, N, M);
+            B, T, N, M); note_launch();
     } else {
         const int64_t segs = (T + kJvpSeg - 1) / kJvpSeg;
         const int64_t blocks = B * segs;
         if (blocks > 0x7fffffffLL) return DFILT_ERR_UNSUPPORTED;
         jvp_input_kernel<<<(unsigned)blocks, kJvpThreads, 0, st>>>(x, dx, y, b, db, da, v, ones,
-                                                                    B, T, N, M, segs);
+                                                                    B, T, N, M, segs); note_launch();
     }
     if (cudaGetLastError() != cudaSuccess) return DFILT_ERR_CUDA;
     return dfilt_forward(v, ones, a, dzi, dy, nullptr, w + L.fwd, L.fwd_bytes, B, T, 0, M, opts,

@@ -81,6 +81,14 @@ constexpr int kMaxF32ScanBucket = 16;
 // launchers call it with phase 0 just before and phase 1 just after the main kernel
 // (direction 0 forward, 1 backward).  A no-op while timing is off.
 void timing_mark(int direction, int phase, cudaStream_t st);
+// Timing classes beyond the two directions (dfilt_kernel_timing_read_classes)
+enum TimingClass {
+    kTimeFwd = 0, kTimeBwd = 1, kTimeScan = 2, kTimeEPass = 3, kTimeYPass = 4, kTimeUPass = 5,
+    kTimeJump = 6, kTimeFused = 7
+};
+// Count of kernel launches issued by the library (dfilt_launch_count); every launch site
+// calls it once per launch.
+void note_launch();
 
 // fp64_opt: the caller's scan option (-1 automatic per bucket, 0 off, 1 on)
 cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, const float *zi,

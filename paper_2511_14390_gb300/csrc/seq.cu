@@ -267,7 +267,7 @@ cudaError_t launch_seq_fwd(const float *x, const float *b, const float *a, const
     const dim3 grid((unsigned)((bt.B + 31) / 32)), block(32);
     switch (mb) {
 #define X(MB) \
-    case MB: seq_fwd_kernel<MB><<<grid, block, 0, st>>>(x, b, a, zi, y, bt); break;
+    case MB: seq_fwd_kernel<MB><<<grid, block, 0, st>>>(x, b, a, zi, y, bt); note_launch(); break;
         DFILT_SEQ_CASES(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -284,7 +284,7 @@ cudaError_t launch_seq_bwd(const float *gy, const float *x, const float *y, cons
     switch (mb) {
 #define X(MB)                                                                               \
     case MB:                                                                                \
-        seq_bwd_kernel<MB><<<grid, block, 0, st>>>(gy, x, y, b, a, gx, gb, ga, gzi, bt);    \
+        seq_bwd_kernel<MB><<<grid, block, 0, st>>>(gy, x, y, b, a, gx, gb, ga, gzi, bt); note_launch();    \
         break;
         DFILT_SEQ_CASES(X)
 #undef X

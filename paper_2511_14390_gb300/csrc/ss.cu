@@ -377,7 +377,7 @@ cudaError_t ss_scan(const float *A, int trans, const float *v0, const float *z, 
     float *pw = reinterpret_cast<float *>(ws + L.pw);
     float *agg = reinterpret_cast<float *>(ws + L.agg);
     float *seg_in = reinterpret_cast<float *>(ws + L.seg_in);
-    ss_setup_kernel<M><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(A, pw, B, trans);
+    ss_setup_kernel<M><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(A, pw, B, trans); note_launch();
     if (L.G == 0) return cudaGetLastError();
     const int64_t groups = (L.G + kSsWarps - 1) / kSsWarps;
     const int64_t blocks = B * groups;
@@ -390,10 +390,10 @@ cudaError_t ss_scan(const float *A, int trans, const float *v0, const float *z, 
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ss_seg_kernel<M, REV, false><<<(unsigned)blocks, 32 * kSsWarps, smem, st>>>(
-        A, trans, pw, z, nullptr, nullptr, agg, B, T, L.G, groups);
-    ss_carry_kernel<M><<<(unsigned)((B + 3) / 4), 128, 0, st>>>(pw, v0, agg, seg_in, B, L.G);
+        A, trans, pw, z, nullptr, nullptr, agg, B, T, L.G, groups); note_launch();
+    ss_carry_kernel<M><<<(unsigned)((B + 3) / 4), 128, 0, st>>>(pw, v0, agg, seg_in, B, L.G); note_launch();
     ss_seg_kernel<M, REV, true><<<(unsigned)blocks, 32 * kSsWarps, smem, st>>>(
-        A, trans, pw, z, out, seg_in, agg, B, T, L.G, groups);
+        A, trans, pw, z, out, seg_in, agg, B, T, L.G, groups); note_launch();
     return cudaGetLastError();
 }
 
@@ -414,12 +414,12 @@ cudaError_t ss_backward_m(const float *A, const float *v0, const float *v, const
         const int64_t blocks = B * L.G;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         if (blocks > 0)
-            ss_grada_kernel<M><<<(unsigned)blocks, 256, 0, st>>>(gz, v, v0, part, B, T, L.G);
+            ss_grada_kernel<M><<<(unsigned)blocks, 256, 0, st>>>(gz, v, v0, part, B, T, L.G); note_launch();
     }
     if (gA || gv0) {
         const int64_t n = B * M * M;
         ss_grada_final_kernel<M><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, A, gz, gA,
-                                                                           gv0, B, T, L.G);
+                                                                           gv0, B, T, L.G); note_launch();
     }
     return cudaGetLastError();
 }

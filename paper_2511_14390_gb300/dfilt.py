@@ -31,7 +31,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_set_wait_limit", "dfilt_forward_noalloc", "dfilt_kernel_timing",
            "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
            "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward",
-           "dfilt_ic_df1", "dfilt_ic_df1_backward"]
+           "dfilt_ic_df1", "dfilt_ic_df1_backward", "dfilt_kernel_timing_read_classes",
+           "dfilt_launch_count"]
 
 
 class DfiltError(RuntimeError):
@@ -106,6 +107,8 @@ def lib():
             L.dfilt_ic_df1_backward.argtypes = [P, P, P, P, P, P, P, P, P, i64, i32, i32, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
             L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
+            L.dfilt_kernel_timing_read_classes.argtypes = [PD, PI]
+            L.dfilt_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i32
             L.dfilt_status_string.restype = ctypes.c_char_p
@@ -368,6 +371,25 @@ def dfilt_kernel_timing_read():
     _check(lib().dfilt_kernel_timing_read(ctypes.byref(fm), ctypes.byref(fn), ctypes.byref(bm),
                                           ctypes.byref(bn)), "dfilt_kernel_timing_read")
     return (fm.value, fn.value), (bm.value, bn.value)
+
+
+TIMING_CLASSES = ["forward", "backward", "scan", "e_pass", "y_pass", "u_pass", "span_transition",
+                  "fused"]
+
+
+def dfilt_kernel_timing_read_classes():
+    """{class: (ms_total, records)} of the recorded event pairs (then discarded)."""
+    ms = (ctypes.c_double * 8)()
+    n = (ctypes.c_int * 8)()
+    _check(lib().dfilt_kernel_timing_read_classes(ms, n), "dfilt_kernel_timing_read_classes")
+    return {k: (ms[i], n[i]) for i, k in enumerate(TIMING_CLASSES)}
+
+
+def dfilt_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    v = ctypes.c_int64()
+    _check(lib().dfilt_launch_count(ctypes.byref(v)), "dfilt_launch_count")
+    return v.value
 
 
 # ---------------------------------------------------------------------------

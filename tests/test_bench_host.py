@@ -17,16 +17,30 @@ def test_radius_bins():
     assert out["other"]["channels"] == 2 and out["[0.5, 0.9)"]["channels"] == 3
 
 
-def test_kernel_name_follows_the_dispatch():
-    """Main-kernel names per state bucket: warp-specialised kernels where their layouts
-    fit (forward to MB = 16 with two signal stages at 16, backward to MB = 8), the
-    first-generation kernels above; double-word scan above order 4."""
-    assert bench.kernel_name("forward", 2) == "chunk_fwd_ws_kernel<2, 0, 3>"
-    assert bench.kernel_name("forward", 5) == "chunk_fwd_ws_kernel<8, 1, 3>"
-    assert bench.kernel_name("forward", 16) == "chunk_fwd_ws_kernel<16, 1, 2>"
-    assert bench.kernel_name("forward", 33) == "chunk_fwd_kernel<64, 1>"
-    assert bench.kernel_name("backward", 4) == "chunk_bwd_ws_kernel<4, 0>"
-    assert bench.kernel_name("backward", 12) == "chunk_bwd_kernel<16, 1, 0>"
+def test_class_work_and_roofline():
+    """Algorithmic work per kernel class (orders >= 3 on the decoupled path, <= 2 on the
+    single-kernel one) and the roofline table built from per-class event times."""
+    lens = np.array([64 * 10, 64 * 10])
+    Ms = np.array([2, 32])
+    w = bench.class_work(lens, Ms)
+    assert w["fused"]["bytes"] == 20 * 640 + 2 * 4 * 10 * 2
+    assert w["u_pass"]["bytes"] == 16 * 640 + 4 * 10 * 32
+    assert w["scan"]["ops"] == 2 * 10 * 32 * 32 * bench.DW_MAC_OPS
+    cls = {"scan": (3.0, 6), "u_pass": (1.5, 3), "fused": (0.0, 0)}
+    dom, table = bench.roofline_from_classes(cls, w, 3, 6000.0, "measured")
+    assert dom == "scan" and set(table) == {"scan", "u_pass"}
+    assert table["scan"]["bound"] == "alu" and table["u_pass"]["bound"] == "hbm"
+    assert abs(table["u_pass"]["achieved"] - w["u_pass"]["bytes"] / 0.5e-3 / 1e9) < 1e-9
+    assert abs(table["scan"]["frac"] - table["scan"]["achieved"] / bench.FP32_OPS_PEAK_T) < 1e-12
+
+
+def test_oracle_sample_is_bounded():
+    """The CPU legs time a deterministic, bounded sample of the workload's channels."""
+    from paper_2511_14390_gb300 import inputs
+    w = inputs.make_ragged(B=64, T_range=(100, 5000), M_range=(1, 4), seed=3)
+    kind, idx, n = bench.oracle_sample(w, 20000)
+    assert kind == "ragged" and n <= 20000 and len(idx) >= 1
+    assert n == int(np.diff(w.offsets)[idx].sum())
 
 
 def test_profiled_traffic_reads_marker_and_detects_stale_sources(tmp_path, monkeypatch):
