@@ -612,6 +612,32 @@ def ragged_outputs(r, w, pick):
     return ys, grads
 
 
+def hi_buckets(Ms):
+    """State buckets of the decoupled path present in a batch (orders 3..8 run in 8)."""
+    out = set()
+    for m in np.unique(np.asarray(Ms)):
+        if m >= 3:
+            out.add(next(v for v in (8, 16, 32, 64) if m <= v))
+    return sorted(out)
+
+
+def autotune(step, Ms, torch, dfilt, stream):
+    """The measured launch shape of the decoupled scan for this batch (span length and
+    chains per SM of every state bucket present), installed for the runs that follow;
+    reported per bucket with the best step time."""
+    from paper_2511_14390_gb300 import tune
+    tune.reset()
+    buckets = hi_buckets(Ms)
+    if not buckets:
+        return None
+    t0 = time.perf_counter()
+    table, seen = tune.tune(step, buckets, lambda fn: time_loop(torch, stream, fn, 2, 1))
+    return {"seconds": time.perf_counter() - t0,
+            "chosen": {str(mb): {"span_tiles": sp, "chains_per_sm": c, "ms_per_step": ms}
+                       for mb, (sp, c, ms) in table.items()},
+            "candidates": {str(mb): len(v) for mb, v in seen.items()}}
+
+
 def fixed_config(name, torch, dfilt, stream, a, hbm, src):
     """One fixed-shape workload: chunked fwd + bwd call pairs (automatic path), the
     sequential kernel, errors of both against the oracle on sampled channels, and the
@@ -619,11 +645,12 @@ def fixed_config(name, torch, dfilt, stream, a, hbm, src):
     w = make_workload(name)
     B, T = w.x.shape
     r = Runner(w, "chunked", torch, dfilt, stream)
+    tuned = autotune(r.pair, np.full(B, w.M), torch, dfilt, stream)
     steps = max(3, min(a.steps, int(2e9 // max(1, B * T))))
     ms = time_loop(torch, stream, r.pair, steps, a.warmup)
     out = {"workload": name, "B": B, "T": T, "M": int(w.M), "N": int(w.N),
            "value": B * T / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "path": "decoupled" if uses_decoupled(w.M) else "fused"}
+           "path": "decoupled" if uses_decoupled(w.M) else "fused", "autotune": tuned}
     if B * T < 1e6:   # launch-bound: the pair captured in a CUDA graph as well
         gms = graph_time(torch, stream, lambda sp: r.pair(sp), steps * 20, a.warmup)
         out["graph_replay"] = {"value": B * T / (gms / 1e3) / 1e9, "ms_per_step": gms}
@@ -689,6 +716,7 @@ def main():
         step = r.pair
         step_on = lambda sp: r.pair(sp)
     samples = int(w.x.size)
+    tuned = autotune(step, w.Ms if ragged else np.full(w.B, w.M), torch, dfilt, stream)
     clk = Clocks(Clocks.target(torch))
     n0 = dfilt.dfilt_launch_count()
     ms_eager = maxrank(time_loop(torch, stream, step, a.steps, a.warmup, barrier))
@@ -775,7 +803,8 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "precision": "tf32x3", "data": "synthetic",
             "config": dict(workload_config(w, a.workload),
-                           timed="CUDA-graph replay of the step" if use_graph else "eager step"),
+                           timed="CUDA-graph replay of the step" if use_graph else "eager step",
+                           autotune=tuned),
             "eager": {"value": whole_job_rate(samples, world, ms_eager), "ms_per_step": ms_eager},
             "graph_replay": graph, "ms_fwd_calls": fwd_ms, "ms_bwd_calls": bwd_ms,
             "rel_err_vs_fp64": rel_err, "sequential": seq, "roofline": roof, "kernels": kernels,

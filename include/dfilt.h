@@ -224,6 +224,19 @@ dfilt_status dfilt_kernel_timing_read_classes(double *ms, int *calls);
 dfilt_status dfilt_launch_count(int64_t *n);
 
 /*
+ * Tuning table of the decoupled path (the paper has no counterpart; the launch shape is
+ * this library's choice), per state bucket (2, 4, 8, 16, 32 or 64; orders up to the
+ * bucket, above the previous one): span_tiles, the 8192-sample tiles per scan span (a
+ * power of two up to 4096), and chains_per_sm, the chunk-state scan's CTAs per SM (at
+ * most 32); 0 restores the built-in rule.  Calls whose opts give span_tiles use that
+ * instead.  Process-wide; a call made while another thread changes the table sees
+ * either setting.  The package's tuner (paper_2511_14390_gb300.tune) measures candidates
+ * and installs the best.
+ */
+dfilt_status dfilt_tuning_set(int state_bucket, int span_tiles, int chains_per_sm);
+dfilt_status dfilt_tuning_get(int state_bucket, int *span_tiles, int *chains_per_sm);
+
+/*
  * Optional output check (off by default).  With enable != 0, every later forward /
  * backward call (dfilt_forward*, dfilt_backward*) also scans its outputs on `stream`
  * for non-finite values and records DFILT_ERR_NUMERIC in the device status word

@@ -513,6 +513,17 @@ dfilt_status dfilt_kernel_timing_read_classes(double *ms, int *calls) {
     return timing_collect(ms, calls);
 }
 
+dfilt_status dfilt_tuning_set(int state_bucket, int span_tiles, int chains_per_sm) {
+    return dfilt::hi_tuning_set(state_bucket, span_tiles, chains_per_sm) ? DFILT_OK
+                                                                         : DFILT_ERR_INVALID_ARG;
+}
+
+dfilt_status dfilt_tuning_get(int state_bucket, int *span_tiles, int *chains_per_sm) {
+    if (chunk_bucket(state_bucket) != state_bucket) return DFILT_ERR_INVALID_ARG;
+    dfilt::hi_tuning_get(state_bucket, span_tiles, chains_per_sm);
+    return DFILT_OK;
+}
+
 dfilt_status dfilt_launch_count(int64_t *n) {
     if (!n) return DFILT_ERR_INVALID_ARG;
     *n = (int64_t)g_launches.load(std::memory_order_relaxed);

@@ -208,23 +208,58 @@ size_t chunk_bwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool
     return hi_ws(fused_bwd_ws(B, p, ragged), p, B, total, Mmax, true, ho).end;
 }
 
+// ---------------------------------------------------------------------------
+// Tuning table of the decoupled scan, per state bucket: span length (tiles) and chains
+// per SM; 0 = the rule below.  Set by dfilt_tuning_set (the package's tuner measures
+// candidates and installs the best).
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+int g_tune_span[7] = {};     // index log2(MB) - 1 (MB = 2..64)
+int g_tune_chains[7] = {};
+int tune_index(int MB) {
+    int i = 0;
+    while ((2 << i) < MB && i < 6) ++i;
+    return i;
+}
+}  // namespace
+
+bool hi_tuning_set(int MB, int span_tiles, int chains_per_sm) {
+    if (chunk_bucket(MB) != MB || span_tiles < 0 || span_tiles > 4096 ||
+        (span_tiles & (span_tiles - 1)) != 0 || chains_per_sm < 0 || chains_per_sm > 32)
+        return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_span[tune_index(MB)] = span_tiles;
+    g_tune_chains[tune_index(MB)] = chains_per_sm;
+    return true;
+}
+void hi_tuning_get(int MB, int *span_tiles, int *chains_per_sm) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (span_tiles) *span_tiles = g_tune_span[tune_index(MB)];
+    if (chains_per_sm) *chains_per_sm = g_tune_chains[tune_index(MB)];
+}
+
 // Span length of the decoupled scan (tiles, a power of two): the caller's choice, else
-// enough spans that the chains fill every SM several times over.
+// the tuning table's, else about half of the tiles per chain (rounded down to a power of
+// two), measured best on the order-16, orders-64 and ragged workloads: shorter spans
+// add rescans (every span after a channel's first scans twice), longer ones lengthen the
+// longest chain.
 int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, const HiOpt &ho) {
     if (ho.span_tiles > 0) return ho.span_tiles;
-    const int64_t chains = (int64_t)num_sms * 4;
-    int64_t want;
+    int st_tab = 0, ch_tab = 0;
+    hi_tuning_get(MB, &st_tab, &ch_tab);
+    if (st_tab > 0) return st_tab;
+    const int64_t chains = (int64_t)num_sms * (ch_tab > 0 ? ch_tab : hi_scan_chains_default(MB));
+    int64_t tiles;
     if (!ragged) {
         const int64_t T = B > 0 ? total / B : 0;
-        const int64_t nt = (T + kTileSamples - 1) / kTileSamples;
-        const int64_t per = B >= chains ? 1 : (chains + B - 1) / B;   // spans per channel
-        want = (nt + per - 1) / per;
+        tiles = B * ((T + kTileSamples - 1) / kTileSamples);
     } else {
-        want = (total / kTileSamples) / chains;
+        tiles = total / kTileSamples + B;
     }
-    (void)MB;
+    const int64_t want = tiles / (2 * chains);
     int st = 1;
-    while (st < want && st < 4096) st <<= 1;
+    while (2 * st <= want && st < 4096) st <<= 1;
     return st;
 }
 

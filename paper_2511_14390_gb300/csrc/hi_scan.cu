@@ -18,8 +18,8 @@ using hi::Plan;
 // order are skipped warp-uniformly)
 constexpr int scan_tpr(int mb) { return mb <= 8 ? 4 : (mb == 32 ? 1 : 2); }
 // Chains (CTAs) per SM: enough warps to keep the FP32 pipes issuing, few enough that a
-// long channel's chain is not slowed by many others sharing its SM
-constexpr int scan_chains_per_sm(int mb) { return mb <= 16 ? 16 : (mb == 32 ? 8 : 4); }
+// long channel's chain is not slowed by many others sharing its SM (the tuning table's
+// value where one is set, hi_scan_chains_default otherwise)
 
 // ---------------------------------------------------------------------------
 // Plan: per position of the launch's channel list, the tiles and scan spans before it
@@ -529,10 +529,13 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
         int o = 0;
         const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, NT, smem);
         if (e != cudaSuccess) return e;
-        o = o < scan_chains_per_sm(MB) ? o : scan_chains_per_sm(MB);
-        occ[dev] = o < 1 ? 1 : o;
+        occ[dev] = o < 1 ? 1 : o;   // resident CTAs per SM
     }
-    kern<<<(unsigned)(num_sms * occ[dev]), NT, smem, st>>>(h, bt); note_launch();
+    int want = 0;
+    hi_tuning_get(MB, nullptr, &want);
+    if (want <= 0) want = hi_scan_chains_default(MB);
+    const int per_sm = want < occ[dev] ? want : occ[dev];
+    kern<<<(unsigned)(num_sms * per_sm), NT, smem, st>>>(h, bt); note_launch();
     return cudaGetLastError();
 }
 

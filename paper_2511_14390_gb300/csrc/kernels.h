@@ -108,6 +108,11 @@ size_t chunk_bwd_ws_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool
                           const HiOpt &ho);
 // Span length (tiles) the decoupled path uses for a bucket of a call.
 int hi_span_tiles(int MB, int64_t B, int64_t total, bool ragged, int num_sms, const HiOpt &ho);
+// Tuning table of the decoupled scan per state bucket (0 = automatic); the scan's
+// default chains (CTAs) per SM.
+bool hi_tuning_set(int MB, int span_tiles, int chains_per_sm);
+void hi_tuning_get(int MB, int *span_tiles, int *chains_per_sm);
+constexpr int hi_scan_chains_default(int MB) { return MB <= 16 ? 16 : (MB == 32 ? 8 : 4); }
 
 // Tensor map of a signal viewed as rows of one chunk (L floats), 3-D so that one box
 // {32 floats, 1 half, 128 rows} is one 128-byte-swizzled K block of a tensor-core

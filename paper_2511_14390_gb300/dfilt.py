@@ -32,7 +32,7 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
            "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward",
            "dfilt_ic_df1", "dfilt_ic_df1_backward", "dfilt_kernel_timing_read_classes",
-           "dfilt_launch_count"]
+           "dfilt_launch_count", "dfilt_tuning_set", "dfilt_tuning_get"]
 
 
 class DfiltError(RuntimeError):
@@ -109,6 +109,8 @@ def lib():
             L.dfilt_kernel_timing_read.argtypes = [PD, PI, PD, PI]
             L.dfilt_kernel_timing_read_classes.argtypes = [PD, PI]
             L.dfilt_launch_count.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+            L.dfilt_tuning_set.argtypes = [i32, i32, i32]
+            L.dfilt_tuning_get.argtypes = [i32, PI, PI]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i32
             L.dfilt_status_string.restype = ctypes.c_char_p
@@ -383,6 +385,20 @@ def dfilt_kernel_timing_read_classes():
     n = (ctypes.c_int * 8)()
     _check(lib().dfilt_kernel_timing_read_classes(ms, n), "dfilt_kernel_timing_read_classes")
     return {k: (ms[i], n[i]) for i, k in enumerate(TIMING_CLASSES)}
+
+
+def dfilt_tuning_set(state_bucket: int, span_tiles: int = 0, chains_per_sm: int = 0):
+    """Install a decoupled-path launch shape for a state bucket (0 = automatic)."""
+    _check(lib().dfilt_tuning_set(int(state_bucket), int(span_tiles), int(chains_per_sm)),
+           "dfilt_tuning_set")
+
+
+def dfilt_tuning_get(state_bucket: int):
+    """(span_tiles, chains_per_sm) installed for a state bucket (0 = automatic)."""
+    s, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().dfilt_tuning_get(int(state_bucket), ctypes.byref(s), ctypes.byref(c)),
+           "dfilt_tuning_get")
+    return s.value, c.value
 
 
 def dfilt_launch_count() -> int:

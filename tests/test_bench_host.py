@@ -59,3 +59,37 @@ def test_profiled_traffic_reads_marker_and_detects_stale_sources(tmp_path, monke
     assert bench.profiled_traffic("my_kernel<2, 0>", "other") is None
     src.write_bytes(b"kernel v2")
     assert bench.profiled_traffic("my_kernel<2, 0>", "wl") is None
+
+
+def test_tuner_choice_is_deterministic():
+    """The tuner's pick depends only on the measurements: the fastest pair, ties broken
+    toward the shorter span and then fewer chains, whatever the order of the candidates."""
+    from paper_2511_14390_gb300 import tune
+    t = {(4, 8): 2.0, (2, 16): 1.5, (8, 4): 1.5, (1, 8): 3.0, (2, 8): 1.5}
+    assert tune.choose(t) == (2, 8)
+    shuffled = dict(reversed(list(t.items())))
+    assert tune.choose(shuffled) == (2, 8)
+    assert tune.shape_key("GB300", 32, 4096, 593554462) == tune.shape_key("GB300", 32, 4500,
+                                                                        650000000)
+    assert tune.shape_key("GB300", 32, 4096, 593554462) != tune.shape_key("GB300", 16, 4096,
+                                                                        593554462)
+
+
+def test_tuner_cache_roundtrip(tmp_path, monkeypatch):
+    """Cached pairs are merged into the file and installed by lookup (through a fake
+    library setter: no GPU)."""
+    from paper_2511_14390_gb300 import tune
+    calls = []
+    monkeypatch.setattr(tune.dfilt, "dfilt_tuning_set", lambda mb, s, c: calls.append((mb, s, c)))
+    path = str(tmp_path / "cache.json")
+    tune.save({"k32": {"span_tiles": 16, "chains_per_sm": 8, "ms": 1.0}}, path)
+    tune.save({"k16": {"span_tiles": 2, "chains_per_sm": 16, "ms": 2.0}}, path)
+    hits = tune.lookup({32: "k32", 16: "k16", 64: "missing"}, path)
+    assert set(hits) == {32, 16} and sorted(calls) == [(16, 2, 16), (32, 16, 8)]
+    # the descent installs the best candidate of each bucket in turn
+    calls.clear()
+    times = iter([3.0, 1.0, 2.0, 5.0])
+    table, seen = tune.tune(None, [32, 64], lambda step: next(times), spans=(1, 2),
+                            chains={32: (8,), 64: (4,)})
+    assert table[32][:2] == (2, 8) and table[64][:2] == (1, 4)
+    assert calls[-1] == (64, 1, 4) and (32, 2, 8) in calls
