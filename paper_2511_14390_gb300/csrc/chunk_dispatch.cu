@@ -139,12 +139,13 @@ static bool hi_eligible(const ChunkLayout &l, const HiOpt &ho) {
 // Blocks of the decoupled path behind the fused path's workspace (all 256-byte aligned):
 //   ctl      work counters (4 per bucket)
 //   pref     per hi bucket: tile and span prefix sums over its channel positions
+//   pos      per hi bucket: the channel position of every tile and every scan span
 //   jump     per channel: the span transition (MB x MB double words)
 //   flags    per scan item: inclusive state published;  incl: that state
 //   (backward) sprime: the adjoint's chunk states; ybuf: y recomputed; partial: lag
 //   sums per tile
 struct HiWs {
-    size_t ctl = 0, pref = 0, jump = 0, flags = 0, incl = 0, sprime = 0, ybuf = 0, partial = 0;
+    size_t ctl = 0, pref = 0, pos = 0, jump = 0, flags = 0, incl = 0, sprime = 0, ybuf = 0, partial = 0;
     size_t end = 0;
     size_t ctl_bytes = 0;   // the block cleared once per call (counters)
     int nhi = 0, mbmax = 0;
@@ -171,6 +172,8 @@ static HiWs hi_ws(size_t base, const ChunkPlan &p, int64_t B, int64_t total, int
     o += 256;
     h.pref = o;
     o += al256((size_t)h.nhi * 2 * (B + 1) * sizeof(int64_t));
+    h.pos = o;
+    o += al256((size_t)h.nhi * 2 * h.items_bound * sizeof(int));
     h.jump = o;
     o += al256((size_t)B * h.mbmax * h.mbmax * 8);
     h.flags = o;
@@ -347,6 +350,9 @@ static void hi_plan_ptrs(HiArgs &a, char *w, const HiWs &hw, int hj, int64_t B, 
     int64_t *pref = reinterpret_cast<int64_t *>(w + hw.pref) + (size_t)hj * 2 * (B + 1);
     a.plan.tile_pref = pref;
     a.plan.span_pref = pref + (B + 1);
+    int *pos = reinterpret_cast<int *>(w + hw.pos) + (size_t)hj * 2 * hw.items_bound;
+    a.plan.tile_pos = pos;
+    a.plan.span_pos = pos + hw.items_bound;
     a.plan.span_tiles = span_tiles;
     int lg = 0;
     while ((1 << lg) < span_tiles) ++lg;

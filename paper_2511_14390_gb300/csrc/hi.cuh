@@ -52,6 +52,8 @@ struct Plan {
     const int *list_range;   // [lo, hi) into list
     int64_t *tile_pref;      // [n + 1] tiles before each position
     int64_t *span_pref;      // [n + 1] scan spans before each position
+    int *tile_pos;           // [tiles] the position of each tile
+    int *span_pos;           // [spans] the position of each scan span
     int span_tiles;          // tiles per scan span (a power of two)
     int log2_span;           // log2(span_tiles)
 };
@@ -63,17 +65,6 @@ __device__ __forceinline__ int64_t plan_channel(const Plan &p, int64_t pos) {
     return p.list ? (int64_t)p.list[p.list_range[0] + pos] : pos;
 }
 __device__ __forceinline__ int64_t tiles_of(int64_t len) { return (len + kTileSamples - 1) / kTileSamples; }
-
-// Position whose half-open range [pref[pos], pref[pos+1]) holds item w (w < pref[n]).
-__device__ __forceinline__ int64_t find_pos(const int64_t *pref, int64_t n, int64_t w) {
-    int64_t lo = 0, hi = n;   // invariant: pref[lo] <= w < pref[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (pref[mid] <= w) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
 // Loads without the (incoherent) L1: data another SM published in this launch.
 __device__ __forceinline__ float2 ld_cg2(const float2 *p) { return __ldcg(p); }

@@ -93,6 +93,19 @@ __global__ void __launch_bounds__(1024) hi_plan_kernel(Plan p, Batch bt) {
     }
 }
 
+// Per tile and per scan span of the launch, its channel position (one warp per
+// position), so that work items find their channel with one load.
+__global__ void __launch_bounds__(256) hi_pos_kernel(Plan p, Batch bt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = hi::plan_count(p, bt);
+    for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * 8) {
+        const int64_t t0 = p.tile_pref[i], t1 = p.tile_pref[i + 1];
+        for (int64_t t = t0 + lane; t < t1; t += 32) p.tile_pos[t] = (int)i;
+        const int64_t s0 = p.span_pref[i], s1 = p.span_pref[i + 1];
+        for (int64_t q = s0 + lane; q < s1; q += 32) p.span_pos[q] = (int)i;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Span transition J = Abar^K (K = 128 * span_tiles chunks) of every channel with more
 // than one span, forward (J) or adjoint (J'), from the impulse response of 1/A near
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
         const int64_t w = info[0];
         sync();   // info[] is rewritten below
         if (w >= total) break;
-        const int64_t pos = hi::find_pos(h.plan.span_pref, n, w);
+        const int64_t pos = h.plan.span_pos[w];
         const int64_t ch = hi::plan_channel(h.plan, pos);
         const Channel c = channel_of(bt, ch);
         const int64_t s = w - h.plan.span_pref[pos];
@@ -544,6 +557,9 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
 template <int MB>
 cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st) {
     hi_plan_kernel<<<1, 1024, 0, st>>>(h.plan, bt); note_launch();
+    if (bt.B <= 0) return cudaGetLastError();
+    const int64_t blocks = (bt.B + 7) / 8;
+    hi_pos_kernel<<<(unsigned)(blocks < 2048 ? blocks : 2048), 256, 0, st>>>(h.plan, bt); note_launch();
     return cudaGetLastError();
 }
 

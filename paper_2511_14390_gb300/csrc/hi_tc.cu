@@ -33,7 +33,10 @@ namespace dfilt {
 namespace {
 
 using hi::Plan;
-constexpr int kThreads = 128;
+// threads per CTA: one per chunk row, two in the U pass (each takes half of a row's
+// columns and lag products, so that eight warps hide the latencies of its longer epilogue)
+template <int MODE>
+__host__ __device__ constexpr int threads_of() { return MODE == hi::kU ? 256 : 128; }
 constexpr uint32_t kKBlock = kChunks * 128;   // one 32-wide K block of the A operand
 
 template <int MB, int MODE>
@@ -57,12 +60,13 @@ struct TcSmem {
     // buffers where shared memory allows, else over the A operand once it is consumed
     static constexpr int KBLK = (MB + 1 + 15) / 16;               // lag blocks of 16
     static constexpr uint32_t XY_BYTES = 2u * kChunks * kL * 4;
+    static constexpr uint32_t RED_BYTES = MODE == hi::kU ? 8u * KBLK * 32 * 4 : 0u;   // 8 warps
     static constexpr bool SEPXY =
-        MODE == hi::kU && AEND + XY_BYTES + 4u * KBLK * 32 * 4 + 32 + 1024 <= pipe::kSmemMax;
+        MODE == hi::kU && AEND + XY_BYTES + RED_BYTES + 32 + 1024 <= pipe::kSmemMax;
     static constexpr uint32_t XT = SEPXY ? AEND : A0;
     static constexpr uint32_t YT = XT + (uint32_t)kChunks * kL * 4;
     static constexpr uint32_t RED = SEPXY ? AEND + XY_BYTES : AEND;
-    static constexpr uint32_t MISC = RED + (MODE == hi::kU ? 4u * KBLK * 32 * 4 : 0u);
+    static constexpr uint32_t MISC = RED + RED_BYTES;
     // misc: mbarrier (8) | drill mbarrier (8) | tmem base (4) | ok flag (4) | work item (8)
     static constexpr uint32_t BYTES = MISC + 32;
     static constexpr uint32_t ALLOC = BYTES + 1024;
@@ -78,10 +82,12 @@ struct TcSmem {
 __device__ __forceinline__ uint32_t rowp(int r, int j) { return (uint32_t)(r * 256 + ((j ^ (r & 15)) << 4)); }
 
 template <int MB, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<MODE>(), 1)
     hi_tc_kernel(HiArgs h, Batch bt, int sig_al, int out_al, int xy_al, int st_al) {
     using Tab = ChunkTab<MB>;
     using SM = TcSmem<MB, MODE>;
+    constexpr int kThreads = threads_of<MODE>();
+    constexpr int kPieces = kChunks * 16 / kThreads;   // 16-byte pieces of a tile per thread
     constexpr int N = SM::N, KTOT = SM::KTOT, KB = SM::KB;
     extern __shared__ char smem_raw[];
     char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -92,6 +98,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int *ok_slot = reinterpret_cast<volatile int *>(smem + SM::MISC + 20);
     long long *item = reinterpret_cast<long long *>(smem + SM::MISC + 24);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // chunk row = tensor-memory lane of this thread, and (U pass) which half of the row
+    const int cr = tid & (kChunks - 1), half = tid / kChunks;
 
     if (warp == 0) {
         tmem_alloc(tmem_slot, SM::TMEM_COLS);
@@ -106,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     constexpr uint32_t idesc = idesc_tf32_m128(N);
     const int64_t n = hi::plan_count(h.plan, bt);
     const int64_t total = h.plan.tile_pref[n];
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // U pass: the tile's x and y rows into XT / YT (zero past tlen)
     auto load_xy = [&](int64_t tstart, int tlen) {
         const bool al = xy_al && ((tstart & 3) == 0);
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < kPieces; ++q) {
             const int id = tid + kThreads * q;
             const int r = id >> 4, j = id & 15;
             const int s0 = r * kL + j * 4;
@@ -137,10 +145,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         cp_async_commit();
     };
-    // tiles are taken in runs of kRun consecutive ones (mostly one channel: the tables
-    // are rebuilt only when the channel changes)
-    constexpr int kRun = 4;
-    int64_t w = 0, wend = 0, pos = 0;
+    // Tiles are taken in runs of kRun consecutive ones (mostly one channel: the tables
+    // are rebuilt only when the channel changes), each tile's channel found with one
+    // lookup.  Within a run the next tile's signal tile is copied into the operand while
+    // this tile's epilogue runs (also its x and y tiles in the U pass, once this tile's
+    // are consumed); not where the U pass's x and y sit over the operand.
+    constexpr int kRun = 8;
+    constexpr bool kPrefetch = MODE != hi::kU || SM::SEPXY;
+    int64_t w = 0, wend = 0;
+    bool pre = false;   // this tile's signal (and U: x, y) tiles already copied
     for (;;) {
         if (w >= wend) {
             if (tid == 0) *item = (long long)atomicAdd(h.counter, 1ull);
@@ -149,10 +162,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();   // *item is rewritten at the next run
             if (w >= total) break;
             wend = w + kRun < total ? w + kRun : total;
-            pos = hi::find_pos(h.plan.tile_pref, n, w);
-        } else {
-            while (h.plan.tile_pref[pos + 1] <= w) ++pos;   // the next channel with tiles
         }
+        const int64_t pos = h.plan.tile_pos[w];
         const int64_t ch = hi::plan_channel(h.plan, pos);
         const Channel c = channel_of(bt, ch);
         const int64_t tile = w - h.plan.tile_pref[pos];
@@ -162,9 +173,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nch = (tlen + kL - 1) / kL;
         const int64_t slot0 = c.off / kL + ch + tile * kChunks;   // the tile's first chunk slot
         const char *R = h.tabs + (size_t)ch * h.tab_stride;
+        // the next tile of the run, whose inputs are copied during this tile's epilogue
+        const bool has_next = kPrefetch && w + 1 < wend;
+        int64_t ntstart = 0;
+        int ntlen = 0;
+        if (has_next) {
+            const int64_t npos = h.plan.tile_pos[w + 1];
+            const Channel nc = channel_of(bt, hi::plan_channel(h.plan, npos));
+            const int64_t ntile = w + 1 - h.plan.tile_pref[npos];
+            ntstart = nc.off + ntile * kTileSamples;
+            const int64_t ntl64 = nc.len - ntile * kTileSamples;
+            ntlen = (int)(ntl64 < kTileSamples ? ntl64 : kTileSamples);
+        }
 
         // ---- B operand (the channel's tables), split into TF32 hi | lo ----
         if (ch != cur_ch) {
+#pragma unroll 8
             for (int idx = tid; idx < N * KTOT; idx += kThreads) {
                 const int nn = idx / KTOT, k = idx % KTOT;
                 float v = 0.f;
@@ -190,24 +214,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float *ot = reinterpret_cast<float *>(smem + SM::OT);
                 const float *src = reinterpret_cast<const float *>(
                     R + (MODE == hi::kY ? (size_t)h.tab_ol : (size_t)Tab::B_OU));
-                for (int i = tid; i < kL * MB; i += kThreads) ot[i] = src[i];
+#pragma unroll 4
+                for (int i = tid; i < kL * MB / 4; i += kThreads)
+                    reinterpret_cast<float4 *>(ot)[i] = __ldg(reinterpret_cast<const float4 *>(src) + i);
                 if constexpr (MODE == hi::kU) {
                     const float *src2 = reinterpret_cast<const float *>(R + Tab::B_OGX);
-                    for (int i = tid; i < kL * MB; i += kThreads) ot[kL * MB + i] = src2[i];
+#pragma unroll 4
+                    for (int i = tid; i < kL * MB / 4; i += kThreads)
+                        reinterpret_cast<float4 *>(ot + kL * MB)[i] =
+                            __ldg(reinterpret_cast<const float4 *>(src2) + i);
                 }
             }
             cur_ch = ch;
         }
 
         // ---- A operand: the signal tile, then (Y, U) the chunk states ----
-        pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, tstart, tlen,
-                                        sig_al && ((tstart & 3) == 0), tid);
-        if constexpr (SM::SEPXY) load_xy(tstart, tlen);
+        if (!pre) {
+            pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, tstart, tlen,
+                                            sig_al && ((tstart & 3) == 0), tid);
+            if constexpr (SM::SEPXY) load_xy(tstart, tlen);
+        }
         // (Y, U) this row's chunk state, FP32, for the free response in the epilogue
         float S[SM::OUT ? MB : 1];
         if constexpr (SM::OUT) {
-            const float *sv = (MODE == hi::kY ? h.states2 : h.states) + (size_t)(slot0 + tid) * Ms;
-            const bool v = tid < nch;
+            const float *sv = (MODE == hi::kY ? h.states2 : h.states) + (size_t)(slot0 + cr) * Ms;
+            const bool v = cr < nch;
             if (st_al) {   // rows of Mstride floats, 16-byte aligned
 #pragma unroll
                 for (int m4 = 0; m4 < MB; m4 += 4) {
@@ -270,9 +301,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         tc_fence_after();
         if (!*ok_slot) break;
+        // the operand is consumed: the next tile's signal goes there now
+        if (has_next)
+            pipe::load_tile_async<kThreads>(sbase + SM::AHI, h.sig, ntstart, ntlen,
+                                            sig_al && ((ntstart & 3) == 0), tid);
 
         // ---- epilogues (thread = chunk row = TMEM lane) ----
-        const int cr = tid;
         if constexpr (MODE == hi::kEFwd || MODE == hi::kEBwd) {
             float *dst = h.states + (size_t)(slot0 + cr) * Ms;
 #pragma unroll
@@ -289,7 +323,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncthreads();
         } else if constexpr (MODE == hi::kY) {
-            char *stag = smem + SM::AHI;   // the operand is consumed
+            char *stag = smem + SM::ALO;   // the operand's low part is consumed (the high part
+                                           // receives the next tile)
             const float *ot = reinterpret_cast<const float *>(smem + SM::OT);
 #pragma unroll 1
             for (int cb = 0; cb < kL / 16; ++cb) {
@@ -319,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
             const bool al = out_al && ((tstart & 3) == 0);
 #pragma unroll 4
-            for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < kPieces; ++q) {
                 const int id = tid + kThreads * q;
                 const int r = id >> 4, j = id & 15;
                 const float4 v = *reinterpret_cast<const float4 *>(stag + rowp(r, j));
@@ -344,9 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             // were loaded with the signal tile
             if constexpr (!SM::SEPXY) load_xy(tstart, tlen);
             // (2) the adjoint window in tensor memory: u = D + O^u S' over columns
-            // 64 .. 128, then S' and zeros
+            // 64 .. 128, then S' and zeros (each half of the CTA takes half the columns)
 #pragma unroll 1
-            for (int cb = 0; cb < kL / 16; ++cb) {
+            for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
                 float v[16];
                 tmem_ld16(taddr + kL + cb * 16, v);
                 tmem_wait_ld();
@@ -368,13 +403,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int cb = 0; cb < (SM::UEND - 2 * kL + 15) / 16; ++cb) {
+                if ((cb & 1) != half) continue;   // static indices into S[]
                 float v[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = (cb * 16 + i < MB) ? S[cb * 16 + i] : 0.f;
                 tmem_st16(taddr + 2 * kL + cb * 16, v);
             }
             tmem_wait_st();
-            cp_async_wait_all();
+            if constexpr (!SM::SEPXY) cp_async_wait_all();   // x, y over the operand
             __syncthreads();
             const char *xrow = smem + SM::XT, *yrow = smem + SM::YT;
             auto ld16 = [&](const char *base, int j0, float (&v)[16]) {   // samples 4*j0 .. 4*j0+15
@@ -392,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 #pragma unroll 1
-                for (int nb = 0; nb < kL / 16; ++nb) {
+                for (int nb = 2 * half; nb < 2 * half + 2; ++nb) {   // this half's samples
                     float xv[16], yv[16], w0[16], w1[16];
                     ld16(xrow, nb * 4, xv);
                     ld16(yrow, nb * 4, yv);
@@ -422,11 +458,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
-                red[(warp * KBLK + kb) * 32 + lane] = acc[0];
+                red[(warp * KBLK + kb) * 32 + lane] = acc[0];   // warp = 4 half + quadrant
             }
             // (4) grad_x = D[:, 0:64) + O^gx S', written over this row of the x tile
 #pragma unroll 1
-            for (int cb = 0; cb < kL / 16; ++cb) {
+            for (int cb = 2 * half; cb < 2 * half + 2; ++cb) {
                 float v[16];
                 tmem_ld16(taddr + cb * 16, v);
                 tmem_wait_ld();
@@ -451,11 +487,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             __syncthreads();
-            // the tile's lag sums in a fixed order (warps 0..3)
+            // the tile's lag sums in a fixed order (warps 0..7)
             for (int i = tid; i < KBLK * 32; i += kThreads) {
                 const int kb = i / 32, j = i % 32;
-                const float v = red[(0 * KBLK + kb) * 32 + j] + red[(1 * KBLK + kb) * 32 + j] +
-                                red[(2 * KBLK + kb) * 32 + j] + red[(3 * KBLK + kb) * 32 + j];
+                float v = 0.f;
+#pragma unroll
+                for (int e = 0; e < kThreads / 32; ++e) v += red[(e * KBLK + kb) * 32 + j];
                 const int k = 16 * kb + (j & 15);
                 if (j < 16) {
                     if (k <= MB) h.partial[(size_t)w * NACC + k] = v;
@@ -466,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (h.out) {
                 const bool al = out_al && ((tstart & 3) == 0);
 #pragma unroll 4
-                for (int q = 0; q < 16; ++q) {
+                for (int q = 0; q < kPieces; ++q) {
                     const int id = tid + kThreads * q;
                     const int r = id >> 4, j = id & 15;
                     const float4 v = *reinterpret_cast<const float4 *>(smem + SM::XT + rowp(r, j));
@@ -484,8 +521,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             __syncthreads();
+            // x and y of the next tile, now that this tile's are consumed
+            if constexpr (SM::SEPXY) {
+                if (has_next) load_xy(ntstart, ntlen);
+            }
         }
         ++w;
+        pre = has_next;
     }
     tc_fence_before();
     __syncthreads();
@@ -520,7 +562,7 @@ cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_
         cudaDeviceGetAttribute(&smem_blk, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         int o = smem_sm / (int)(SM::ALLOC + smem_blk + fa.sharedSizeBytes);
         const int regs = (fa.numRegs + 7) / 8 * 8;
-        const int oreg = regs > 0 ? 65536 / (regs * kThreads) : o;
+        const int oreg = regs > 0 ? 65536 / (regs * threads_of<MODE>()) : o;
         o = o < oreg ? o : oreg;
         const int tmem_cap = 512 / (int)SM::TMEM_COLS;
         o = o < tmem_cap ? o : tmem_cap;
@@ -530,7 +572,7 @@ cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_
     const int xy_al = (h.x && h.y) ? (al(h.x) & al(h.y)) : 0;
     const float *sv = MODE == hi::kY ? h.states2 : h.states;
     const int st_al = (sv && al(sv) && bt.Mstride % 4 == 0) ? 1 : 0;
-    kern<<<(unsigned)(num_sms * occ[dev]), kThreads, SM::ALLOC, st>>>(h, bt, al(h.sig),
+    kern<<<(unsigned)(num_sms * occ[dev]), threads_of<MODE>(), SM::ALLOC, st>>>(h, bt, al(h.sig),
                                                                       h.out ? al(h.out) : 0, xy_al,
                                                                       st_al); note_launch();
     return cudaGetLastError();
