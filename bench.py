@@ -61,6 +61,9 @@ def args_():
     p.add_argument("--no-jvp", action="store_true", help="skip the forward-mode (JVP) leg")
     p.add_argument("--no-ss", action="store_true",
                    help="skip the dense state-space recurrence leg (M = 2, 64 x 2^20 steps)")
+    p.add_argument("--tuning", default="",
+                   help="install the decoupled scan's launch shape instead of measuring it: "
+                        "'MB:span:chains,...' (e.g. 8:2:32,16:2:32,32:4:16)")
     p.add_argument("--channels", type=int, default=0,
                    help="override the workload's channel count (smaller profiling cases)")
     return p.parse_args()
@@ -621,15 +624,31 @@ def hi_buckets(Ms):
     return sorted(out)
 
 
-def autotune(step, Ms, torch, dfilt, stream):
+def parse_tuning(spec: str) -> dict:
+    """'MB:span:chains,...' -> {MB: (span, chains)}."""
+    out = {}
+    for item in filter(None, (t.strip() for t in spec.split(","))):
+        mb, sp, ch = (int(v) for v in item.split(":"))
+        out[mb] = (sp, ch)
+    return out
+
+
+def autotune(step, Ms, torch, dfilt, stream, given: str = ""):
     """The measured launch shape of the decoupled scan for this batch (span length and
     chains per SM of every state bucket present), installed for the runs that follow;
-    reported per bucket with the best step time."""
+    reported per bucket with the best step time.  With `given` ('MB:span:chains,...')
+    that shape is installed instead and nothing is measured."""
     from paper_2511_14390_gb300 import tune
     tune.reset()
     buckets = hi_buckets(Ms)
     if not buckets:
         return None
+    if given:
+        table = parse_tuning(given)
+        for mb, (sp, ch) in table.items():
+            dfilt.dfilt_tuning_set(mb, sp, ch)
+        return {"given": {str(mb): {"span_tiles": sp, "chains_per_sm": ch}
+                          for mb, (sp, ch) in table.items()}}
     t0 = time.perf_counter()
     table, seen = tune.tune(step, buckets, lambda fn: time_loop(torch, stream, fn, 2, 1))
     return {"seconds": time.perf_counter() - t0,
@@ -716,7 +735,7 @@ def main():
         step = r.pair
         step_on = lambda sp: r.pair(sp)
     samples = int(w.x.size)
-    tuned = autotune(step, w.Ms if ragged else np.full(w.B, w.M), torch, dfilt, stream)
+    tuned = autotune(step, w.Ms if ragged else np.full(w.B, w.M), torch, dfilt, stream, a.tuning)
     clk = Clocks(Clocks.target(torch))
     n0 = dfilt.dfilt_launch_count()
     ms_eager = maxrank(time_loop(torch, stream, step, a.steps, a.warmup, barrier))
