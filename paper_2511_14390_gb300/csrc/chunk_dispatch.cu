@@ -15,7 +15,8 @@ namespace dfilt {
     extern template cudaError_t hi_jump<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
     extern template cudaError_t hi_scan<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
     extern template cudaError_t hi_tc<V>(const HiArgs &, const Batch &, int, int, cudaStream_t);   \
-    extern template cudaError_t hi_reduce<V>(const HiArgs &, const Batch &, cudaStream_t);
+    extern template cudaError_t hi_reduce<V>(const HiArgs &, const Batch &, cudaStream_t);        \
+    extern template cudaError_t hi_epass<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 DFILT_HI_BUCKETS(DFILT_HI_EXTERN)
 #undef DFILT_HI_EXTERN
 
@@ -436,7 +437,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 0;
                 timing_mark(kTimeEPass, 0, st);
-                r = hi_tc<V>(q, bb[j], hi::kEFwd, num_sms, st);   // E_c into the slots
+                r = hi_epass<V>(q, bb[j], false, num_sms, st);   // E_c into the slots
                 timing_mark(kTimeEPass, 1, st);
                 if (r != cudaSuccess) return r;
                 q.jump2 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(saved) +
@@ -558,7 +559,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.states = sprime;
                 q.counter = ctl + 0;
                 timing_mark(kTimeEPass, 0, st);
-                r = hi_tc<V>(q, bb[j], hi::kEBwd, num_sms, st);
+                r = hi_epass<V>(q, bb[j], true, num_sms, st);
                 timing_mark(kTimeEPass, 1, st);
                 if (r != cudaSuccess) return r;
                 // the adjoint's span transitions, formed by the forward

@@ -1,17 +1,17 @@
-// The decoupled chunked path for high-order state buckets (MB >= 16).
+// The decoupled chunked path for orders above 2 (state buckets 8..64, double-word scan).
 //
 // The same chunk algebra as the single-kernel path (chunk.cuh, Sec. 3.2's operator at
 // chunk granularity, L = 64), split into launches so that the one serial part, the
 // chunk-state scan, no longer pins a channel's tiles to one SM:
 //
-//   forward   E pass     E_c = R_L X_c for every chunk (tensor cores, per tile,
-//                        any tile on any SM), written into the chunk-state slots
+//   forward   E pass     E_c = R_L X_c for every chunk (FP32 FMAs on the CUDA cores,
+//                        per tile, any tile on any SM), written into the chunk slots
 //             scan       S_{c+1} = Abar S_c + E_c in double words; a channel is cut
 //                        into spans of whole tiles scanned by different CTAs, joined
 //                        by a bounded look-back (below); S_c overwrites E_c
-//             Y pass     Y_c = T_g X_c + O_L S_c, one tensor-core product with the
-//                        operand [X_c | S_c] (K = L + state width)
-//   backward  E' pass    E'_c = (T_h^a G_c)[0:MB]
+//             Y pass     Y_c = T_g X_c + O_L S_c: T_g X_c on the tensor cores, the
+//                        free response O_L S_c in FP32 on the CUDA cores
+//   backward  E' pass    E'_c = (T_h^a G_c)[0:MB] (CUDA cores, like the E pass)
 //             scan       S'_{c-1} = Abar' S'_c + E'_c from the end (S'_{C-1} = 0);
 //                        the last state is u[0:MB] = grad_zi
 //             (Y pass)   y recomputed from the forward's states when not given
@@ -77,8 +77,8 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
-// Tile-pass modes
-enum Mode { kEFwd = 0, kEBwd = 1, kY = 2, kU = 3 };
+// Tensor-core tile-pass modes (the E passes run on the CUDA cores, hi_epass)
+enum Mode { kY = 2, kU = 3 };
 
 // Number of lag sums per channel: grad_b[0..MB] then grad_a[1..MB]
 template <int MB>
@@ -122,5 +122,7 @@ template <int MB>
 cudaError_t hi_tc(const HiArgs &h, const Batch &bt, int mode, int num_sms, cudaStream_t st);
 template <int MB>
 cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st);
+template <int MB>
+cudaError_t hi_epass(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st);
 
 }  // namespace dfilt

@@ -500,6 +500,145 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
 }
 
 // ---------------------------------------------------------------------------
+// E pass on the CUDA cores: for every chunk of the launch's tiles, E_c = R_L x_c
+// (forward: the zero-state end state of the chunk) or E'_c = (T_h^a G_c)[0:MB] (adjoint:
+// the reversed Toeplitz product's first MB rows, h the impulse response of 1/A), into
+// the chunk slots.  64 x M FMAs per chunk in FP32 (more accurate than a split-TF32
+// product, and far below the FP32 rate for M <= 64): the pass streams the signal once.
+// Thread = chunk row; tiles are taken from a counter in runs of eight (mostly one
+// channel: the table R^T[j][m] is rebuilt in shared memory only when the channel
+// changes) and staged by cp.async in two shared-memory stages, the next tile's copy in
+// flight while this one is summed.  Samples past a channel's end are zero.
+// ---------------------------------------------------------------------------
+template <int MB>
+struct ESmem {
+    static constexpr uint32_t STAGE = pipe::kTileBytes;           // one 128 x 64 signal tile
+    static constexpr uint32_t TAB = 2 * STAGE;                    // R^T [kL][MB] floats
+    static constexpr uint32_t ITEM = TAB + (uint32_t)kL * MB * 4; // work item (8 bytes)
+    static constexpr uint32_t BYTES = ITEM + 16;
+};
+
+template <int MB, bool BWD>
+__global__ void __launch_bounds__(kChunks) hi_e_kernel(HiArgs h, Batch bt, int sig_al, int st_al) {
+    using Tab = ChunkTab<MB>;
+    using SM = ESmem<MB>;
+    constexpr int kThreads = kChunks;
+    extern __shared__ float4 smem4[];
+    char *smem = reinterpret_cast<char *>(smem4);
+    const uint32_t sbase = smem_u32(smem);
+    float *tab = reinterpret_cast<float *>(smem + SM::TAB);
+    long long *item = reinterpret_cast<long long *>(smem + SM::ITEM);
+    const int tid = threadIdx.x;
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t total = h.plan.tile_pref[n];
+    const int Ms = bt.Mstride;
+    constexpr int kRun = 8;
+    int64_t w = 0, wend = 0, cur_ch = -1;
+    int stage = 0;
+    bool pre = false;   // this tile already in flight (copied during the previous one)
+    auto tile_of = [&](int64_t wi, int64_t &ch, Channel &c, int64_t &tstart, int &tlen) {
+        const int64_t pos = h.plan.tile_pos[wi];
+        ch = hi::plan_channel(h.plan, pos);
+        c = channel_of(bt, ch);
+        const int64_t tile = wi - h.plan.tile_pref[pos];
+        tstart = c.off + tile * kTileSamples;
+        const int64_t tl = c.len - tile * kTileSamples;
+        tlen = (int)(tl < kTileSamples ? tl : kTileSamples);
+    };
+    for (;;) {
+        if (w >= wend) {
+            if (tid == 0) *item = (long long)atomicAdd(h.counter, 1ull);
+            __syncthreads();
+            w = *item * kRun;
+            __syncthreads();   // *item is rewritten at the next run
+            if (w >= total) break;
+            wend = w + kRun < total ? w + kRun : total;
+        }
+        int64_t ch, tstart;
+        Channel c;
+        int tlen;
+        tile_of(w, ch, c, tstart, tlen);
+        const int nch = (tlen + kL - 1) / kL;
+        const int64_t slot0 = c.off / kL + ch + (tstart - c.off) / kL;   // the tile's first chunk slot
+        if (!pre)
+            pipe::load_tile_async<kThreads>(sbase + stage * SM::STAGE, h.sig, tstart, tlen,
+                                            sig_al && ((tstart & 3) == 0), tid);
+        const bool has_next = w + 1 < wend;
+        if (has_next) {
+            int64_t nch_, ntstart;
+            Channel nc;
+            int ntlen;
+            tile_of(w + 1, nch_, nc, ntstart, ntlen);
+            pipe::load_tile_async<kThreads>(sbase + (stage ^ 1) * SM::STAGE, h.sig, ntstart, ntlen,
+                                            sig_al && ((ntstart & 3) == 0), tid);
+        }
+        if (ch != cur_ch) {
+            // R^T[j][m]: forward R_L[m][j]; adjoint h[j - m] for j >= m (else 0)
+            const char *R = h.tabs + (size_t)ch * h.tab_stride;
+            for (int idx = tid; idx < kL * MB; idx += kThreads) {
+                const int j = idx / MB, m = idx % MB;
+                float v;
+                if constexpr (BWD) v = j >= m ? reinterpret_cast<const float *>(R + Tab::B_H)[j - m] : 0.f;
+                else v = reinterpret_cast<const float *>(R + Tab::F_RL)[m * kL + j];
+                tab[idx] = v;
+            }
+            cur_ch = ch;
+        }
+        if (has_next) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        else cp_async_wait_all();
+        __syncthreads();
+        if (tid < nch) {
+            const char *xs = smem + stage * SM::STAGE;
+            float acc[MB];
+#pragma unroll
+            for (int m = 0; m < MB; ++m) acc[m] = 0.f;
+#pragma unroll 1
+            for (int j16 = 0; j16 < 16; ++j16) {
+                const float4 xv = *reinterpret_cast<const float4 *>(xs + pipe::op_piece(tid, j16));
+                const float xq[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float *tr = tab + (j16 * 4 + q) * MB;
+#pragma unroll
+                    for (int m4 = 0; m4 < MB; m4 += 4) {
+                        if (m4 < c.M) {   // rows past the channel's order are not needed
+                            const float4 t4 = *reinterpret_cast<const float4 *>(tr + m4);
+                            acc[m4] = fmaf(t4.x, xq[q], acc[m4]);
+                            acc[m4 + 1] = fmaf(t4.y, xq[q], acc[m4 + 1]);
+                            acc[m4 + 2] = fmaf(t4.z, xq[q], acc[m4 + 2]);
+                            acc[m4 + 3] = fmaf(t4.w, xq[q], acc[m4 + 3]);
+                        }
+                    }
+                }
+            }
+            float *dst = h.states + (size_t)(slot0 + tid) * Ms;
+            if (st_al) {
+#pragma unroll
+                for (int m4 = 0; m4 < MB; m4 += 4) {
+                    if (m4 + 4 <= c.M) {
+                        *reinterpret_cast<float4 *>(dst + m4) =
+                            make_float4(acc[m4], acc[m4 + 1], acc[m4 + 2], acc[m4 + 3]);
+                    } else if (m4 < c.M) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (m4 + i < c.M) dst[m4 + i] = acc[m4 + i];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MB; ++m)
+                    if (m < c.M) dst[m] = acc[m];
+            }
+        }
+        __syncthreads();   // this stage and the table are free again
+        stage ^= 1;
+        ++w;
+        pre = has_next;
+    }
+    cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
 // Coefficient gradients: per channel, the tiles' lag sums in tile order (FP64).
 // One warp per channel position.
 // ---------------------------------------------------------------------------
@@ -552,6 +691,28 @@ cudaError_t launch_scan(const HiArgs &h, const Batch &bt, int num_sms, cudaStrea
     return cudaGetLastError();
 }
 
+template <int MB, bool BWD>
+cudaError_t launch_e(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st) {
+    using SM = ESmem<MB>;
+    auto kern = hi_e_kernel<MB, BWD>;
+    static int occ[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kChunks, SM::BYTES);
+        if (e != cudaSuccess) return e;
+        occ[dev] = o < 1 ? 1 : o;
+    }
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? 1 : 0; };
+    const int st_al = (al(h.states) && bt.Mstride % 4 == 0) ? 1 : 0;
+    kern<<<(unsigned)(num_sms * occ[dev]), kChunks, SM::BYTES, st>>>(h, bt, al(h.sig), st_al); note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <int MB>
@@ -596,9 +757,15 @@ cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int MB>
+cudaError_t hi_epass(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st) {
+    return bwd ? launch_e<MB, true>(h, bt, num_sms, st) : launch_e<MB, false>(h, bt, num_sms, st);
+}
+
 template cudaError_t hi_plan<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_jump<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_scan<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_reduce<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
+template cudaError_t hi_epass<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 
 }  // namespace dfilt

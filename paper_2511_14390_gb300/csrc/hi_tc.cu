@@ -3,8 +3,6 @@
 // the scan kernel: a persistent CTA takes tiles from a counter, in channel order, and
 // rebuilds its B operand only when the channel changes.
 //
-//   E pass (forward)   D = X R_L^T           N = MB   -> E_c into the chunk slots
-//   E' pass (backward) D = G (T_h^a)^T[:MB]  N = MB   -> E'_c into the chunk slots
 //   Y pass             D = X T_g^T           N = 64   -> y = D + O_L S_c
 //   U pass             D = G [T_g^a ; T_h^a]^T  N = 128 -> grad_x = D[:, 0:64) +
 //                      O^gx S'_c and u = D[:, 64:128) + O^u S'_c; then the lag sums of
@@ -42,8 +40,9 @@ constexpr uint32_t kKBlock = kChunks * 128;   // one 32-wide K block of the A op
 template <int MB, int MODE>
 struct TcSmem {
     using Tab = ChunkTab<MB>;
-    static constexpr bool OUT = MODE >= hi::kY;                   // y or u rows
-    static constexpr int N = MODE == hi::kU ? 2 * kL : (OUT ? kL : Tab::MPAD);   // MMA N
+    static_assert(MODE == hi::kY || MODE == hi::kU, "tile passes: Y and U");
+    static constexpr bool OUT = true;                             // y or u rows
+    static constexpr int N = MODE == hi::kU ? 2 * kL : kL;        // MMA N
     static constexpr int KTOT = kL;
     static constexpr int KB = 2;                                  // K blocks of 32
     static constexpr uint32_t BBLK = (uint32_t)N * 128;           // bytes of one B K block
@@ -192,11 +191,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             for (int idx = tid; idx < N * KTOT; idx += kThreads) {
                 const int nn = idx / KTOT, k = idx % KTOT;
                 float v = 0.f;
-                if constexpr (MODE == hi::kEFwd) {
-                    if (nn < MB) v = reinterpret_cast<const float *>(R + Tab::F_RL)[nn * kL + k];
-                } else if constexpr (MODE == hi::kEBwd) {
-                    if (k >= nn) v = reinterpret_cast<const float *>(R + Tab::B_H)[k - nn];
-                } else if constexpr (MODE == hi::kY) {
+                if constexpr (MODE == hi::kY) {
                     if (k <= nn) v = reinterpret_cast<const float *>(R + h.tab_g)[nn - k];
                 } else {
                     const int n2 = nn & (kL - 1);
@@ -307,22 +302,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                                             sig_al && ((ntstart & 3) == 0), tid);
 
         // ---- epilogues (thread = chunk row = TMEM lane) ----
-        if constexpr (MODE == hi::kEFwd || MODE == hi::kEBwd) {
-            float *dst = h.states + (size_t)(slot0 + cr) * Ms;
-#pragma unroll
-            for (int cb = 0; cb < N / 16; ++cb) {
-                float v[16];
-                tmem_ld16(taddr + cb * 16, v);
-                tmem_wait_ld();
-                if (cr < nch) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (cb * 16 + i < c.M) dst[cb * 16 + i] = v[i];
-                }
-            }
-            tc_fence_before();
-            __syncthreads();
-        } else if constexpr (MODE == hi::kY) {
+        if constexpr (MODE == hi::kY) {
             char *stag = smem + SM::ALO;   // the operand's low part is consumed (the high part
                                            // receives the next tile)
             const float *ot = reinterpret_cast<const float *>(smem + SM::OT);
@@ -337,11 +317,13 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     float acc = v[i];
 #pragma unroll
                     for (int m4 = 0; m4 < MB; m4 += 4) {   // O_L rows are 16-byte aligned
-                        const float4 q = *reinterpret_cast<const float4 *>(ol + m4);
-                        acc = fmaf(q.x, S[m4], acc);
-                        acc = fmaf(q.y, S[m4 + 1], acc);
-                        acc = fmaf(q.z, S[m4 + 2], acc);
-                        acc = fmaf(q.w, S[m4 + 3], acc);
+                        if (m4 < c.M) {   // the state is zero past the channel's order
+                            const float4 q = *reinterpret_cast<const float4 *>(ol + m4);
+                            acc = fmaf(q.x, S[m4], acc);
+                            acc = fmaf(q.y, S[m4 + 1], acc);
+                            acc = fmaf(q.z, S[m4 + 2], acc);
+                            acc = fmaf(q.w, S[m4 + 3], acc);
+                        }
                     }
                     v[i] = acc;
                 }
@@ -391,11 +373,13 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     float acc = v[i];
 #pragma unroll
                     for (int m4 = 0; m4 < MB; m4 += 4) {
-                        const float4 q = *reinterpret_cast<const float4 *>(o + m4);
-                        acc = fmaf(q.x, S[m4], acc);
-                        acc = fmaf(q.y, S[m4 + 1], acc);
-                        acc = fmaf(q.z, S[m4 + 2], acc);
-                        acc = fmaf(q.w, S[m4 + 3], acc);
+                        if (m4 < c.M) {
+                            const float4 q = *reinterpret_cast<const float4 *>(o + m4);
+                            acc = fmaf(q.x, S[m4], acc);
+                            acc = fmaf(q.y, S[m4 + 1], acc);
+                            acc = fmaf(q.z, S[m4 + 2], acc);
+                            acc = fmaf(q.w, S[m4 + 3], acc);
+                        }
                     }
                     v[i] = acc;
                 }
@@ -424,25 +408,37 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             float *red = reinterpret_cast<float *>(smem + SM::RED);
 #pragma unroll 1
             for (int kb = 0; kb < KBLK; ++kb) {
+                // lag blocks past the channel's orders are skipped (uniform over the CTA):
+                // b-lags 16 kb .. need 16 kb <= N, a-lags 16 kb + 1 .. need 16 kb < M
+                const bool need_x = 16 * kb <= c.N, need_y = 16 * kb < c.M;
                 float acc[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 #pragma unroll 1
-                for (int nb = 2 * half; nb < 2 * half + 2; ++nb) {   // this half's samples
+                for (int nb = 2 * half; nb < 2 * half + 2 && (need_x || need_y); ++nb) {
                     float xv[16], yv[16], w0[16], w1[16];
-                    ld16(xrow, nb * 4, xv);
                     ld16(yrow, nb * 4, yv);
                     const uint32_t f0 = taddr + kL + 16 * (nb + kb);   // u_ext[16(nb+kb) ..]
                     tmem_ld16(f0, w0);
                     tmem_ld16(f0 + 16, w1);
                     tmem_wait_ld();
 #define DFILT_WIN(i) ((i) < 16 ? w0[(i)] : w1[(i) - 16])
+                    if (need_x) {
+                        ld16(xrow, nb * 4, xv);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
+                        for (int q = 0; q < 16; ++q) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            acc[j] = fmaf(DFILT_WIN(q + j), xv[q], acc[j]);
-                            acc[16 + j] = fmaf(DFILT_WIN(q + 1 + j), yv[q], acc[16 + j]);
+                            for (int j = 0; j < 16; ++j) {
+                                acc[j] = fmaf(DFILT_WIN(q + j), xv[q], acc[j]);
+                                acc[16 + j] = fmaf(DFILT_WIN(q + 1 + j), yv[q], acc[16 + j]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                acc[16 + j] = fmaf(DFILT_WIN(q + 1 + j), yv[q], acc[16 + j]);
                         }
                     }
 #undef DFILT_WIN
@@ -472,11 +468,13 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     float acc = v[i];
 #pragma unroll
                     for (int m4 = 0; m4 < MB; m4 += 4) {
-                        const float4 q = *reinterpret_cast<const float4 *>(o + m4);
-                        acc = fmaf(q.x, S[m4], acc);
-                        acc = fmaf(q.y, S[m4 + 1], acc);
-                        acc = fmaf(q.z, S[m4 + 2], acc);
-                        acc = fmaf(q.w, S[m4 + 3], acc);
+                        if (m4 < c.M) {
+                            const float4 q = *reinterpret_cast<const float4 *>(o + m4);
+                            acc = fmaf(q.x, S[m4], acc);
+                            acc = fmaf(q.y, S[m4 + 1], acc);
+                            acc = fmaf(q.z, S[m4 + 2], acc);
+                            acc = fmaf(q.w, S[m4 + 3], acc);
+                        }
                     }
                     v[i] = acc;
                 }
@@ -583,8 +581,6 @@ cudaError_t launch_tc(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_
 template <int MB>
 cudaError_t hi_tc(const HiArgs &h, const Batch &bt, int mode, int num_sms, cudaStream_t st) {
     switch (mode) {
-        case hi::kEFwd: return launch_tc<MB, hi::kEFwd>(h, bt, num_sms, st);
-        case hi::kEBwd: return launch_tc<MB, hi::kEBwd>(h, bt, num_sms, st);
         case hi::kY: return launch_tc<MB, hi::kY>(h, bt, num_sms, st);
         case hi::kU: return launch_tc<MB, hi::kU>(h, bt, num_sms, st);
         default: return cudaErrorInvalidValue;

@@ -57,30 +57,45 @@ def grad_errors(w, y, yr, grads, gref, needs=(True, True, True, True)):
     return errs
 
 
-def check(name, mode, w, needs=(True, True, True, True), tol=None, gtol=None):
+def check(name, mode, w, needs=(True, True, True, True), tol=None, gtol=None, norm_tol=None):
+    """Every output against the oracle (y, grad_x normwise; coefficient gradients against
+    their terms' scale, tests/tol.py).  With norm_tol, the coefficient and state
+    gradients must also meet the plain normwise bound max_k |got - ref| / max_k |ref|
+    per channel."""
     tol = TOL[mode] if tol is None else tol
     gtol = GTOL[mode] if gtol is None else gtol
     y, grads = run_fixed(w, mode, needs)
     yr, gref = oracle_fixed(w)
     errs = grad_errors(w, y, yr, grads, gref, needs)
-    log_errors(f"{name}/{mode}", **errs)
+    norms = {nm + "_norm": rel_rows(g, r) for nm, g, r, nd in
+             zip(["gx", "gb", "ga", "gzi"], grads, gref, needs) if nd and nm != "gx"}
+    log_errors(f"{name}/{mode}", **errs, **norms)
     tol, gtol = np.broadcast_to(tol, errs["y"].shape), np.broadcast_to(gtol, errs["y"].shape)
     assert (errs["y"] < tol).all(), (name, mode, "y", errs["y"], tol)
     for nm in ["gx", "gb", "ga", "gzi"]:
         if nm in errs:
             assert (errs[nm] < gtol).all(), (name, mode, nm, errs[nm], gtol)
+    if norm_tol is not None:
+        for nm, v in norms.items():
+            assert (v < norm_tol).all(), (name, mode, nm, v, norm_tol)
+
+
+# The plain normwise bound on grad_b, grad_a, grad_zi where the workloads' conditioning
+# allows it (order 2, poles up to radius 0.95 / 0.99): the stated 1e-5 of the FP32
+# paths, in the survey's metric.
+NORM = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": None, "chunk3d": 1e-5}
 
 
 @pytest.mark.parametrize("mode", ["seq", "chunk3", "chunk1", "chunk3d"])
 def test_allpole2(mode):
     w = inputs.make("allpole2_4x4096", B=8, T=3 * 8192 + 501)
-    check("allpole2", mode, w, needs=(True, False, True, False))
+    check("allpole2", mode, w, needs=(True, False, True, False), norm_tol=NORM[mode])
 
 
 @pytest.mark.parametrize("mode", ["seq", "chunk3", "chunk1", "chunk3d"])
 def test_biquad(mode):
     w = inputs.make("biquad_1024x48000", B=40, T=2 * 8192 + 4321)
-    check("biquad", mode, w)
+    check("biquad", mode, w, norm_tol=NORM[mode])
 
 
 @pytest.mark.parametrize("mode", ["seq", "chunk3"])
