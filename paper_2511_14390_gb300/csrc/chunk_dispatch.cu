@@ -273,12 +273,59 @@ static size_t saved_jump_off(int64_t B, int64_t total, int Mmax, const ChunkPlan
     return al256(chunk_saved_state_bytes(B, total, Mmax) + (size_t)B * p.bstride);
 }
 
+// Table length of the forward's span entry corrections (samples of h per channel, one
+// double word each): a power of two from 4096 to 65536, at most an eighth of the mean
+// channel length, so the tables add at most 1 byte per sample of the batch to `saved`
+// (beyond that floor).  A channel whose impulse response does not decay within its span
+// and the table has its spans rescanned.
+static int hi_tcap(int64_t B, int64_t total) {
+    const int64_t per = B > 0 ? total / (8 * B) : 0;
+    int64_t t = 4096;
+    while (t * 2 <= per && t < 65536) t *= 2;
+    return (int)t;
+}
+
+// The decoupled path's part of `saved`, behind the chunk states and backward records:
+//   jump2   per channel: the adjoint's span transition J' (formed by the forward)
+//   htab    per channel: h of 1/A over the correction region (tcap floats)
+//   hlen    per channel: samples of h kept (0: no correction)
+//   entry   per hi bucket and span: the forward's span entry state (Mstride floats)
+struct HiSaved {
+    size_t jump2 = 0, htab = 0, hlen = 0, entry = 0, end = 0;
+    int tcap = 0;
+};
+static HiSaved hi_saved(int64_t B, int64_t total, int Mmax, const ChunkPlan &p, const HiWs &hw) {
+    HiSaved sv;
+    sv.jump2 = saved_jump_off(B, total, Mmax, p);
+    size_t o = sv.jump2;
+    if (hw.nhi) {
+        o += al256((size_t)B * hw.mbmax * hw.mbmax * 8);
+        sv.tcap = hi_tcap(B, total);
+        sv.htab = o;
+        o += al256((size_t)B * sv.tcap * 8);
+        sv.hlen = o;
+        o += al256((size_t)B * 4);
+        sv.entry = o;
+        o += al256((size_t)hw.nhi * hw.items_bound * Mmax * 8);
+    }
+    sv.end = o;
+    return sv;
+}
+
 size_t chunk_saved_bytes(int64_t B, int64_t total, int Mmax, int fp64_opt, bool ragged,
                          const HiOpt &ho) {
     const ChunkPlan p = chunk_plan(Mmax, fp64_opt, ragged, ho);
     const HiWs hw = hi_ws(0, p, B, total, Mmax, false, ho);
-    return saved_jump_off(B, total, Mmax, p) +
-           (hw.nhi ? al256((size_t)B * hw.mbmax * hw.mbmax * 8) : 0);
+    return hi_saved(B, total, Mmax, p, hw).end;
+}
+
+// Point a bucket's call at the correction blocks of `saved` (bucket rank hj).
+static void hi_saved_ptrs(HiArgs &a, char *saved, const HiSaved &sv, const HiWs &hw, int hj,
+                          int Mmax) {
+    a.htab = reinterpret_cast<float2 *>(saved + sv.htab);
+    a.hlen = reinterpret_cast<int *>(saved + sv.hlen);
+    a.tcap = sv.tcap;
+    a.entry = reinterpret_cast<float2 *>(saved + sv.entry) + (size_t)hj * hw.items_bound * Mmax;
 }
 
 namespace {
@@ -427,6 +474,8 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
             h.plan.list_range = bb[j].list_range;
             const int stl = hi_span_tiles(MB, bt.B, bt.total, ragged, num_sms, ho);
             hi_plan_ptrs(h, w, hw, hj, bt.B, stl);
+            const HiSaved sv = hi_saved(bt.B, bt.total, Mmax, p, hw);
+            hi_saved_ptrs(h, reinterpret_cast<char *>(saved), sv, hw, hj, Mmax);
             auto *ctl = reinterpret_cast<unsigned long long *>(w + hw.ctl) + 4 * hj;
             ++hj;
             e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
@@ -440,8 +489,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                 r = hi_epass<V>(q, bb[j], false, num_sms, st);   // E_c into the slots
                 timing_mark(kTimeEPass, 1, st);
                 if (r != cudaSuccess) return r;
-                q.jump2 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(saved) +
-                                                     saved_jump_off(bt.B, bt.total, Mmax, p));
+                q.jump2 = reinterpret_cast<float2 *>(reinterpret_cast<char *>(saved) + sv.jump2);
                 timing_mark(kTimeJump, 0, st);
                 r = hi_jump<V>(q, bb[j], false, num_sms, st);   // J, and J' for the backward
                 timing_mark(kTimeJump, 1, st);
@@ -458,6 +506,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
                 q.tab_ol = (int)Tab::F_OL;
                 timing_mark(kTimeYPass, 0, st);
                 r = hi_tc<V>(q, bb[j], hi::kY, num_sms, st);   // y
+                if (r == cudaSuccess) r = hi_yfix<V>(q, bb[j], hw.items_bound, st);   // span entries
                 timing_mark(kTimeYPass, 1, st);
                 return r;
             });
@@ -548,6 +597,8 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
             float *sprime = reinterpret_cast<float *>(wsc + hw.sprime);
             float *ybuf = reinterpret_cast<float *>(wsc + hw.ybuf);
             h.partial = reinterpret_cast<float *>(wsc + hw.partial);
+            const HiSaved sv = hi_saved(bt.B, bt.total, Mmax, p, hw);
+            const int hj_this = hj - 1;
             e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
                 constexpr int V = decltype(mbc)::value;
                 using Tab = ChunkTab<V>;
@@ -564,7 +615,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 if (r != cudaSuccess) return r;
                 // the adjoint's span transitions, formed by the forward
                 q.jump = reinterpret_cast<float2 *>(const_cast<char *>(reinterpret_cast<const char *>(saved)) +
-                                                    saved_jump_off(bt.B, bt.total, Mmax, p));
+                                                    sv.jump2);
                 r = cudaMemsetAsync(q.flags, 0, (size_t)hw.items_bound * 4, st);
                 if (r != cudaSuccess) return r;
                 q.counter = ctl + 1;
@@ -583,8 +634,11 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                     qy.counter = ctl + 2;
                     qy.tab_g = (int)Tab::B_G;
                     qy.tab_ol = (int)Tab::b_ol(true);
+                    hi_saved_ptrs(qy, const_cast<char *>(reinterpret_cast<const char *>(saved)), sv, hw,
+                                  hj_this, Mmax);
                     timing_mark(kTimeYPass, 0, st);
                     r = hi_tc<V>(qy, bb[j], hi::kY, num_sms, st);
+                    if (r == cudaSuccess) r = hi_yfix<V>(qy, bb[j], hw.items_bound, st);
                     timing_mark(kTimeYPass, 1, st);
                     if (r != cudaSuccess) return r;
                     yv = ybuf;

@@ -24,9 +24,19 @@
 // (channel, span) pairs handed out in order; span s > 0 first scans its own chunks
 // from a zero state (its aggregate A_s), then waits (bounded) for its predecessor's
 // inclusive state P_{s-1} and publishes P_s = J P_{s-1} + A_s, J = Abar^K the
-// transition over K chunks of one span, before it rescans its chunks from P_{s-1}.
-// Span 0 starts from the initial state and publishes its end state.  A predecessor
-// was always handed out earlier, so its CTA is running: no wait can deadlock.
+// transition over K chunks of one span.  Span 0 starts from the initial state and
+// publishes its end state.  A predecessor was always handed out earlier, so its CTA is
+// running: no wait can deadlock.
+//
+// The states of span s > 0 are then S_c = S~_c + Abar^(c - c0) P_{s-1}, with S~_c the
+// zero-start states of the aggregate pass.  In the forward, where the channel's
+// impulse response h of 1/A decays within a table length (below 2^-40 of its largest
+// value, a bound read off the impulse's chunk state norm), the aggregate pass writes
+// S~_c to the chunk slots and keeps P_{s-1}; the Y pass computes y from S~_c, and the
+// free response of the entry state, sum_m P_m h[n - m] (TDF-II state == injection at
+// times m < M, Sec. 2), is added to the span's first samples afterwards in double-word
+// arithmetic: one scan pass per span instead of two.  Other channels, and the adjoint,
+// rescan their spans from P_{s-1}.
 //
 // J is not formed by repeated squaring: companion-matrix powers grow transiently by
 // orders of magnitude before they decay, and squaring them loses every digit (it
@@ -111,6 +121,16 @@ struct HiArgs {
     unsigned long long *counter;
     hi::Plan plan;
     int three;
+    // Span entry corrections (forward): a span after a channel's first keeps the states
+    // of its chunks scanned from a zero state, and its true entry state P adds the free
+    // response sum_m P_m h[n - m] to y over the first samples of the span (hi_yfix).
+    // Double words throughout: over long horizons the terms P_m h[n - m] cancel by many
+    // orders of magnitude (the TDF-II state components of a high-order or near-unit-
+    // circle filter are large and h[n - m] varies slowly in m).
+    float2 *htab;           // [B][tcap] impulse response h of 1/A, h[0 .. hlen)
+    int *hlen;              // [B] samples of h kept (0: the span is rescanned instead)
+    int tcap;               // table length per channel (0: no corrections)
+    float2 *entry;          // per span in time order: entry state (Mstride double words)
 };
 template <int MB>
 cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st);
@@ -124,5 +144,7 @@ template <int MB>
 cudaError_t hi_reduce(const HiArgs &h, const Batch &bt, cudaStream_t st);
 template <int MB>
 cudaError_t hi_epass(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st);
+template <int MB>
+cudaError_t hi_yfix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st);
 
 }  // namespace dfilt

@@ -130,10 +130,27 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
     float2 *st = sh + H;                              // [2][MB] states
     float2 *hw = st + 2 * MB;                         // h[64(K-2) .. 64K)  [128]
     float *sa = reinterpret_cast<float *>(hw + 2 * kL);   // a_1 .. a_MB
+    float *red = sa + MB;                                   // [NT / 32] block sums
     const int t = threadIdx.x, r = t / TPR, p = t % TPR, lane = t & 31;
     auto sync = [] {
         if constexpr (NT == 32) __syncwarp();
         else __syncthreads();
+    };
+    // sum of v over the CTA, returned to every thread
+    auto block_sum = [&](float v) -> float {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if constexpr (NT == 32) {
+            return v;
+        } else {
+            if (lane == 0) red[t >> 5] = v;
+            __syncthreads();
+            float tot = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) tot += red[w];
+            __syncthreads();
+            return tot;
+        }
     };
     const int64_t pos = blockIdx.x;
     if (pos >= hi::plan_count(h.plan, bt)) return;
@@ -183,12 +200,34 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
         st[k] = make_float2(v.hi, v.lo);
     }
     sync();
-    // 3. S_{c+1} = Abar S_c, c = 1 .. K-2 (S_1 in st[0]); then S_{K-2} and S_{K-1}
+    // 3. S_{c+1} = Abar S_c, c = 1 .. K-2 (S_1 in st[0]); then S_{K-2} and S_{K-1}.
+    //    Forward call with a correction table: h[64c .. 64c + 64) = sum_m h[j - m] S_c[m]
+    //    (the free response of the impulse's state entering chunk c, double words) goes
+    //    into the table until ||S_c||_1 <= 2^-40, from where on every |h[n]| <= 2^-40
+    //    max|h| (h[64c + n] = sum_m S_c[m] h[n - m]).
+    const bool tab = !bwd && h.htab != nullptr && h.tcap > 0;
+    const int64_t tchunks = tab ? ((int64_t)h.tcap / kL < K ? (int64_t)h.tcap / kL : K) : 0;
+    float2 *ht = tab ? h.htab + (size_t)ch * h.tcap : nullptr;
+    int64_t hz = -1;   // first chunk whose entering state is below the bound
+    auto table_chunk = [&](int64_t cidx, const float2 *S) -> bool {   // true: bound reached
+        const float nrm = block_sum(p == 0 ? fabsf(S[r].x + S[r].y) : 0.f);
+        if (nrm <= 9.094947e-13f) return true;   // 2^-40
+        for (int j = t; j < kL; j += NT) {
+            float hh = 0.f, ll = 0.f;
+            for (int m = 0; m < MB && m <= j; ++m) pipe::dw_acc(hh, ll, sh[j - m], S[m].x, S[m].y);
+            const dw v = fast_two_sum(hh, ll);
+            ht[cidx * kL + j] = make_float2(v.hi, v.lo);
+        }
+        return false;
+    };
+    if (tab)
+        for (int j = t; j < kL; j += NT) ht[j] = sh[j];   // chunk 0: h directly
     float2 a[JPT];
 #pragma unroll
     for (int q = 0; q < JPT; ++q) a[q] = sA[(p * JPT + q) * MB + r];
     int buf = 0;
     for (int64_t cc = 1; cc < K - 1; ++cc) {
+        if (tab && hz < 0 && cc < tchunks && table_chunk(cc, st + buf * MB)) hz = cc;
         const float2 *cur = st + buf * MB;
         float hh[NA], ll[NA];
 #pragma unroll
@@ -224,6 +263,12 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
         buf ^= 1;
     }
     // st[buf] = S_{K-1}, st[buf ^ 1] = S_{K-2}
+    if (tab) {
+        if (hz < 0 && K - 1 < tchunks && table_chunk(K - 1, st + buf * MB)) hz = K - 1;
+        // samples of h kept: up to the bound, else the whole span when it fits the table,
+        // else none (the channel's spans are rescanned)
+        if (t == 0) h.hlen[ch] = hz >= 0 ? (int)(hz * kL) : (K <= tchunks ? (int)(K * kL) : 0);
+    }
     // 4. h[64(K-2) + i], i < 128, from the free responses of the two states
     for (int i = t; i < 2 * kL; i += NT) {
         const float2 *S = st + (i < kL ? (buf ^ 1) : buf) * MB;
@@ -436,10 +481,14 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
                 }
             }
         } else {
-            // aggregate: the span from a zero state
+            // aggregate: the span from a zero state.  Forward spans of channels with a
+            // correction table keep these zero-start states (written to the slots) and
+            // their entry state; the Y pass and hi_yfix add the entry state's free
+            // response, so the span is not rescanned.
+            const bool keep = !REV && h.hlen != nullptr && h.hlen[ch] > 0;
             if (t < MB) st[t] = make_float2(0.f, 0.f);
             sync();
-            const int ag = run(0, false);
+            const int ag = run(0, keep);
             const int pb = ag ^ 1;   // the predecessor's inclusive state goes here
             if (t == 0) {
                 bool ok = false;
@@ -458,6 +507,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
             if (!info[1]) break;
             if (t < MB) st[pb * MB + t] = hi::ld_cg2(h.incl + (size_t)(w - 1) * MB + t);
             sync();
+            if (keep && t < c.M) h.entry[(size_t)w * Ms + t] = st[pb * MB + t];
             if (s + 1 < nsp) {
                 // P_s = J P_{s-1} + A_s, published for the next span
                 const float2 *J = h.jump + (size_t)ch * MB * MB;
@@ -489,7 +539,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
                     hi::st_release(h.flags + w, 1u);
                 }
             }
-            fin = run(pb, true);
+            fin = keep ? ag : run(pb, true);
         }
         // the adjoint's last state is u[0 : MB) = grad_zi (the span holding chunk 0)
         if (REV && sp == 0 && h.gzi && t < c.M) {
@@ -639,6 +689,66 @@ __global__ void __launch_bounds__(kChunks) hi_e_kernel(HiArgs h, Batch bt, int s
 }
 
 // ---------------------------------------------------------------------------
+// Entry-state correction of y (forward, and the backward's recomputed y): for every
+// span s > 0 of a channel with a correction table, y[n] += sum_{m<M} P_m h[n - m] over
+// the span's first hlen + M - 1 samples (n from the span start, h[j] = 0 for j < 0 and,
+// below 2^-40 of its largest value, for j >= hlen), in double words (P and h are kept as
+// double words; the sum cancels heavily for ill-conditioned filters).  One CTA per span
+// at a time; h in shared memory 1024 samples at a time, four samples per thread, the sum
+// over m in a fixed order.
+// ---------------------------------------------------------------------------
+template <int MB>
+__global__ void __launch_bounds__(256) hi_yfix_kernel(HiArgs h, Batch bt) {
+    constexpr int kBlk = 1024;
+    __shared__ float2 hs[kBlk + MB];
+    __shared__ float2 P[MB];
+    const int t = threadIdx.x;
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t items = h.plan.span_pref[n];
+    const int64_t span_len = (int64_t)h.plan.span_tiles * kTileSamples;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        const int64_t pos = h.plan.span_pos[w];
+        const int64_t sp = w - h.plan.span_pref[pos];
+        if (sp == 0) continue;
+        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int hl = h.hlen[ch];
+        if (hl <= 0) continue;
+        const Channel c = channel_of(bt, ch);
+        const int64_t s0 = sp * span_len;
+        const int64_t slen = c.len - s0 < span_len ? c.len - s0 : span_len;
+        const int64_t want = (int64_t)hl + c.M - 1;
+        const int64_t rlen = want < slen ? want : slen;
+        __syncthreads();   // the previous span's P and h are no longer read
+        if (t < MB) P[t] = t < c.M ? h.entry[(size_t)w * bt.Mstride + t] : make_float2(0.f, 0.f);
+        const float2 *hc = h.htab + (size_t)ch * h.tcap;
+        float *yp = h.out + c.off + s0;
+        for (int64_t b0 = 0; b0 < rlen; b0 += kBlk) {
+            __syncthreads();
+            for (int i = t; i < kBlk + MB - 1; i += 256) {   // hs[i] = h[b0 - (MB - 1) + i]
+                const int64_t j = b0 - (MB - 1) + i;
+                hs[i] = (j >= 0 && j < hl) ? hc[j] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int q = 0; q < kBlk / 256; ++q) {
+                const int i = t + 256 * q;
+                if (b0 + i < rlen) {
+                    float hh = 0.f, ll = 0.f;
+#pragma unroll 4
+                    for (int m = 0; m < MB; ++m) {
+                        if (m < c.M) {
+                            const float2 hv = hs[i + MB - 1 - m];
+                            pipe::dw_acc(hh, ll, P[m], hv.x, hv.y);
+                        }
+                    }
+                    yp[b0 + i] += hh + ll;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Coefficient gradients: per channel, the tiles' lag sums in tile order (FP64).
 // One warp per channel position.
 // ---------------------------------------------------------------------------
@@ -728,7 +838,7 @@ template <int MB>
 cudaError_t hi_jump(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st) {
     (void)num_sms;
     constexpr int TPR = scan_tpr(MB);
-    const size_t smem = (size_t)(MB * MB + kL + MB + 2 * MB + 2 * kL) * 8 + MB * 4 + 64;
+    const size_t smem = (size_t)(MB * MB + kL + MB + 2 * MB + 2 * kL) * 8 + MB * 4 + 16 + 64;
     auto kern = hi_jump_kernel<MB, TPR>;
     static bool configured[64] = {};
     int dev = 0;
@@ -762,10 +872,22 @@ cudaError_t hi_epass(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cu
     return bwd ? launch_e<MB, true>(h, bt, num_sms, st) : launch_e<MB, false>(h, bt, num_sms, st);
 }
 
+template <int MB>
+cudaError_t hi_yfix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (int64_t)(sms > 0 ? sms : 1) * 8;
+    if (grid > items_bound) grid = items_bound > 0 ? items_bound : 1;
+    hi_yfix_kernel<MB><<<(unsigned)grid, 256, 0, st>>>(h, bt); note_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t hi_plan<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_jump<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_scan<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_reduce<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_epass<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
+template cudaError_t hi_yfix<DFILT_MB>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
 
 }  // namespace dfilt

@@ -19,12 +19,14 @@ from tol import U32, coef_err, coef_scales, kappa, log_errors, rel_rows
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
-# "Equal accuracy" of the chunked path against the sequential FP32 kernel, per channel.
-# The split-TF32 tensor-core product (hi*hi + hi*lo + lo*hi of 11-bit pieces) rounds
-# each product to about 2^-20 where an FP32 FMA rounds to 2^-24, so on ill-conditioned
-# channels, where both errors are that rounding amplified by the same condition number,
-# the chunked error can be up to ~16x the sequential one; measured at most 7.4x.
-EQ = 8.0
+# "Equal accuracy" of the chunked path against the sequential FP32 kernel, per channel:
+# chunked error <= max(EQ x sequential error, 1e-5).  Both errors are FP32 rounding in
+# the recursion amplified by the same condition number; the chunked path adds the
+# split-TF32 Toeplitz products (11-bit operand pieces, the lo x lo product dropped), so
+# its error may sit a small factor above the sequential kernel's on some channels.
+# Measured in these tests: at most 1.8x (order 2 at radius 0.99-0.9995, grad_x); ratios
+# up to 4.5x occur only on channels whose errors are both below the 1e-5 floor.
+EQ = 3.0
 
 
 def dev(a):
