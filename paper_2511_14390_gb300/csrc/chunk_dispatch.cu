@@ -16,7 +16,9 @@ namespace dfilt {
     extern template cudaError_t hi_scan<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
     extern template cudaError_t hi_tc<V>(const HiArgs &, const Batch &, int, int, cudaStream_t);   \
     extern template cudaError_t hi_reduce<V>(const HiArgs &, const Batch &, cudaStream_t);        \
-    extern template cudaError_t hi_epass<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
+    extern template cudaError_t hi_epass<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
+    extern template cudaError_t hi_yfix<V>(const HiArgs &, const Batch &, int64_t, cudaStream_t);    \
+    extern template cudaError_t hi_ufix<V>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
 DFILT_HI_BUCKETS(DFILT_HI_EXTERN)
 #undef DFILT_HI_EXTERN
 
@@ -147,6 +149,7 @@ static bool hi_eligible(const ChunkLayout &l, const HiOpt &ho) {
 //   sums per tile
 struct HiWs {
     size_t ctl = 0, pref = 0, pos = 0, jump = 0, flags = 0, incl = 0, sprime = 0, ybuf = 0, partial = 0;
+    size_t entry_b = 0, span_part = 0;   // backward: adjoint span entry states, their lag sums
     size_t end = 0;
     size_t ctl_bytes = 0;   // the block cleared once per call (counters)
     int nhi = 0, mbmax = 0;
@@ -187,6 +190,10 @@ static HiWs hi_ws(size_t base, const ChunkPlan &p, int64_t B, int64_t total, int
         h.ybuf = o;
         o += al256((size_t)total * 4);
         h.partial = o;
+        o += al256((size_t)h.items_bound * (2 * h.mbmax + 1) * 4);
+        h.entry_b = o;
+        o += al256((size_t)h.items_bound * Mstride * 8);
+        h.span_part = o;
         o += al256((size_t)h.items_bound * (2 * h.mbmax + 1) * 4);
     }
     h.end = o;
@@ -599,6 +606,11 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
             h.partial = reinterpret_cast<float *>(wsc + hw.partial);
             const HiSaved sv = hi_saved(bt.B, bt.total, Mmax, p, hw);
             const int hj_this = hj - 1;
+            // the forward's correction table; this call's own span entry states
+            hi_saved_ptrs(h, const_cast<char *>(reinterpret_cast<const char *>(saved)), sv, hw, hj_this, Mmax);
+            h.entry = reinterpret_cast<float2 *>(wsc + hw.entry_b);
+            h.span_part = reinterpret_cast<float *>(wsc + hw.span_part);
+            h.bcoef = b;
             e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
                 constexpr int V = decltype(mbc)::value;
                 using Tab = ChunkTab<V>;
@@ -650,6 +662,8 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.counter = ctl + 3;
                 timing_mark(kTimeUPass, 0, st);
                 r = hi_tc<V>(q, bb[j], hi::kU, num_sms, st);   // grad_x, lag sums per tile
+                if (r != cudaSuccess) return r;
+                r = hi_ufix<V>(q, bb[j], hw.items_bound, st);   // adjoint span entries
                 if (r != cudaSuccess) return r;
                 q.gb = gb;
                 q.ga = ga;

@@ -30,13 +30,19 @@
 //
 // The states of span s > 0 are then S_c = S~_c + Abar^(c - c0) P_{s-1}, with S~_c the
 // zero-start states of the aggregate pass.  In the forward, where the channel's
-// impulse response h of 1/A decays within a table length (below 2^-40 of its largest
-// value, a bound read off the impulse's chunk state norm), the aggregate pass writes
+// impulse response h of 1/A decays within half a span and the table length (below
+// 2^-40 of its largest value, a bound read off the impulse's chunk state norm), the
+// aggregate pass writes
 // S~_c to the chunk slots and keeps P_{s-1}; the Y pass computes y from S~_c, and the
 // free response of the entry state, sum_m P_m h[n - m] (TDF-II state == injection at
 // times m < M, Sec. 2), is added to the span's first samples afterwards in double-word
-// arithmetic: one scan pass per span instead of two.  Other channels, and the adjoint,
-// rescan their spans from P_{s-1}.
+// arithmetic: one scan pass per span instead of two.  The adjoint does the same: its
+// zero-start states give u and grad_x in the U pass, and hi_ufix adds the free response
+// of the adjoint entry state P' (the state at the span's end in time): in reversed time
+// i from the span's last sample, v[i] = sum_j h[i - j] w_j with w_j = -sum_{k>j} a_k
+// P'_{k-j-1} (P' read as past outputs of the reversed all-pole recursion), extended by
+// v[-1-m] = P'_m; then grad_x += sum_k b_k v[i - k] and the lag sums of v with x and y
+// go into per-span partials.  Channels without a table rescan their spans from P_{s-1}.
 //
 // J is not formed by repeated squaring: companion-matrix powers grow transiently by
 // orders of magnitude before they decay, and squaring them loses every digit (it
@@ -130,7 +136,10 @@ struct HiArgs {
     float2 *htab;           // [B][tcap] impulse response h of 1/A, h[0 .. hlen)
     int *hlen;              // [B] samples of h kept (0: the span is rescanned instead)
     int tcap;               // table length per channel (0: no corrections)
-    float2 *entry;          // per span in time order: entry state (Mstride double words)
+    float2 *entry;          // per span: entry state (Mstride double words; forward spans
+                            // in time order, adjoint spans in processing order)
+    float *span_part;       // adjoint: per span, the correction's lag sums (nacc floats)
+    const float *bcoef;     // adjoint correction: numerators b[B, Nstride]
 };
 template <int MB>
 cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st);
@@ -146,5 +155,7 @@ template <int MB>
 cudaError_t hi_epass(const HiArgs &h, const Batch &bt, bool bwd, int num_sms, cudaStream_t st);
 template <int MB>
 cudaError_t hi_yfix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st);
+template <int MB>
+cudaError_t hi_ufix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st);
 
 }  // namespace dfilt

@@ -205,7 +205,10 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
     //    (the free response of the impulse's state entering chunk c, double words) goes
     //    into the table until ||S_c||_1 <= 2^-40, from where on every |h[n]| <= 2^-40
     //    max|h| (h[64c + n] = sum_m S_c[m] h[n - m]).
-    const bool tab = !bwd && h.htab != nullptr && h.tcap > 0;
+    // (state bucket 64 rescans: at M = 64 the corrections' double-word sums, about 2M + N
+    // terms per sample of a region, plus this table cost more than the rescans they save,
+    // measured on the order-64 workload; up to M = 32 they save about half the scan time)
+    const bool tab = !bwd && MB <= 32 && h.htab != nullptr && h.tcap > 0;
     const int64_t tchunks = tab ? ((int64_t)h.tcap / kL < K ? (int64_t)h.tcap / kL : K) : 0;
     float2 *ht = tab ? h.htab + (size_t)ch * h.tcap : nullptr;
     int64_t hz = -1;   // first chunk whose entering state is below the bound
@@ -263,11 +266,14 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
         buf ^= 1;
     }
     // st[buf] = S_{K-1}, st[buf ^ 1] = S_{K-2}
+    if (!bwd && !tab && h.hlen != nullptr && t == 0) h.hlen[ch] = 0;   // this channel rescans
     if (tab) {
         if (hz < 0 && K - 1 < tchunks && table_chunk(K - 1, st + buf * MB)) hz = K - 1;
-        // samples of h kept: up to the bound, else the whole span when it fits the table,
-        // else none (the channel's spans are rescanned)
-        if (t == 0) h.hlen[ch] = hz >= 0 ? (int)(hz * kL) : (K <= tchunks ? (int)(K * kL) : 0);
+        // samples of h kept: up to the bound when that is at most half the span; a slower
+        // decay makes the corrections (double-word sums over the region, about M + N
+        // multiply-adds per sample forward and backward) cost about as much as a rescan
+        // (M^2 / 64 per sample), so those channels rescan (hlen 0)
+        if (t == 0) h.hlen[ch] = (hz >= 0 && 2 * hz <= K) ? (int)(hz * kL) : 0;
     }
     // 4. h[64(K-2) + i], i < 128, from the free responses of the two states
     for (int i = t; i < 2 * kL; i += NT) {
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
             // correction table keep these zero-start states (written to the slots) and
             // their entry state; the Y pass and hi_yfix add the entry state's free
             // response, so the span is not rescanned.
-            const bool keep = !REV && h.hlen != nullptr && h.hlen[ch] > 0;
+            const bool keep = h.hlen != nullptr && h.hlen[ch] > 0;
             if (t < MB) st[t] = make_float2(0.f, 0.f);
             sync();
             const int ag = run(0, keep);
@@ -508,7 +514,9 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
             if (t < MB) st[pb * MB + t] = hi::ld_cg2(h.incl + (size_t)(w - 1) * MB + t);
             sync();
             if (keep && t < c.M) h.entry[(size_t)w * Ms + t] = st[pb * MB + t];
-            if (s + 1 < nsp) {
+            // the adjoint's time-first span without a rescan: its inclusive state is grad_zi
+            const bool zi_here = REV && keep && sp == 0 && h.gzi != nullptr;
+            if (s + 1 < nsp || zi_here) {
                 // P_s = J P_{s-1} + A_s, published for the next span
                 const float2 *J = h.jump + (size_t)ch * MB * MB;
                 float hh = 0.f, ll = 0.f;
@@ -531,10 +539,11 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
                 }
                 if (p == 0) {
                     const dw v = fast_two_sum(hh, ll);
-                    h.incl[(size_t)w * MB + r] = make_float2(v.hi, v.lo);
+                    if (s + 1 < nsp) h.incl[(size_t)w * MB + r] = make_float2(v.hi, v.lo);
+                    if (zi_here && r < c.M) h.gzi[ch * Ms + r] = v.hi + v.lo;
                 }
                 sync();
-                if (t == 0) {
+                if (t == 0 && s + 1 < nsp) {
                     __threadfence();
                     hi::st_release(h.flags + w, 1u);
                 }
@@ -542,7 +551,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
             fin = keep ? ag : run(pb, true);
         }
         // the adjoint's last state is u[0 : MB) = grad_zi (the span holding chunk 0)
-        if (REV && sp == 0 && h.gzi && t < c.M) {
+        if (REV && sp == 0 && h.gzi && t < c.M && !(s > 0 && h.hlen != nullptr && h.hlen[ch] > 0)) {
             h.gzi[ch * Ms + t] = st[fin * MB + t].x + st[fin * MB + t].y;
         }
         sync();
@@ -749,6 +758,125 @@ __global__ void __launch_bounds__(256) hi_yfix_kernel(HiArgs h, Batch bt) {
 }
 
 // ---------------------------------------------------------------------------
+// Entry-state correction of the adjoint (backward, hi.cuh): for every span of a channel
+// with a table except its last in time, with P' its adjoint entry state and i the
+// reversed-time offset from its last sample (sample n = end - 1 - i):
+//   w_j = -sum_{k=j+1..M} a_k P'_{k-j-1}                        (j < M, double words)
+//   v[i] = sum_{j<M} h[i - j] w_j,  v[-1-m] = P'_m               (double words)
+//   grad_x[n] += sum_{k<=N} b_k v[i - k]                          (double words)
+//   lag sums: b-lag k += v[i - k] x[n],  a-lag k += v[i - k] y[n]   (FP32, per thread)
+// over i < min(hlen + 3 MB, span length) (v vanishes below 2^-40 of its scale beyond
+// hlen + M - 1).  One CTA per span at a time, 1024 samples per block step; the lag sums
+// are reduced in a fixed order into the span's partial.
+// ---------------------------------------------------------------------------
+template <int MB>
+__global__ void __launch_bounds__(256) hi_ufix_kernel(HiArgs h, Batch bt) {
+    constexpr int kBlk = 1024, NT = 256, NACC = hi::nacc<MB>();
+    __shared__ float2 hs[kBlk + MB];        // h[b0 - (MB - 1) + q]
+    __shared__ float2 vs[2][kBlk + MB];     // v[b0 - MB + q], double buffered across blocks
+    __shared__ float2 W[MB], P[MB];
+    __shared__ float Bk[MB + 1];
+    __shared__ float red[NT / 32][NACC];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t items = h.plan.span_pref[n];
+    const int64_t span_len = (int64_t)h.plan.span_tiles * kTileSamples;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        const int64_t pos = h.plan.span_pos[w];
+        const int64_t s = w - h.plan.span_pref[pos];   // processing index (last in time first)
+        if (s == 0) continue;
+        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int hl = h.hlen[ch];
+        if (hl <= 0) continue;
+        const Channel c = channel_of(bt, ch);
+        const int64_t nsp = h.plan.span_pref[pos + 1] - h.plan.span_pref[pos];
+        const int64_t end = (nsp - s) * span_len;       // a full span ends here
+        const int64_t want = (int64_t)hl + 3 * MB;
+        const int64_t R = want < span_len ? want : span_len;
+        __syncthreads();   // the previous span's shared data is no longer read
+        if (t < MB) P[t] = t < c.M ? h.entry[(size_t)w * bt.Mstride + t] : make_float2(0.f, 0.f);
+        __syncthreads();
+        if (t < MB) {
+            float hh = 0.f, ll = 0.f;
+            for (int k = t + 1; k <= c.M; ++k) pipe::dw_acc(hh, ll, P[k - t - 1], -h.acoef[ch * bt.Mstride + k - 1], 0.f);
+            const dw v = fast_two_sum(hh, ll);
+            W[t] = t < c.M ? make_float2(v.hi, v.lo) : make_float2(0.f, 0.f);
+            // the first block's halo: v[-1 - m] = P'_m
+            vs[0][MB - 1 - t] = P[t];
+        }
+        if (t <= MB) Bk[t] = t <= c.N ? h.bcoef[ch * bt.Nstride + t] : 0.f;
+        float acc[NACC];
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) acc[k] = 0.f;
+        const float2 *hc = h.htab + (size_t)ch * h.tcap;
+        const float *xp = h.x + c.off + end - 1, *yp = h.y + c.off + end - 1;   // minus i
+        float *gp = h.out ? h.out + c.off + end - 1 : nullptr;
+        int cur = 0;
+        for (int64_t b0 = 0; b0 < R; b0 += kBlk) {
+            for (int q = t; q < kBlk + MB - 1; q += NT) {
+                const int64_t j = b0 - (MB - 1) + q;
+                hs[q] = (j >= 0 && j < hl) ? hc[j] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            // v over this block into vs[cur][MB + q]
+            for (int q = t; q < kBlk; q += NT) {
+                float hh = 0.f, ll = 0.f;
+                if (b0 + q < R) {
+#pragma unroll 4
+                    for (int j = 0; j < MB; ++j) {
+                        if (j < c.M) {
+                            const float2 hv = hs[q + MB - 1 - j];
+                            pipe::dw_acc(hh, ll, W[j], hv.x, hv.y);
+                        }
+                    }
+                }
+                const dw v = fast_two_sum(hh, ll);
+                vs[cur][MB + q] = make_float2(v.hi, v.lo);
+            }
+            __syncthreads();
+            // grad_x and the lag sums of this block's samples
+            for (int q = t; q < kBlk; q += NT) {
+                const int64_t i = b0 + q;
+                if (i >= R) break;
+                const float2 *vq = &vs[cur][MB + q];   // vq[-k] = v[i - k]
+                float hh = 0.f, ll = 0.f;
+#pragma unroll 4
+                for (int k = 0; k <= MB; ++k) {
+                    if (k <= c.N) pipe::dw_acc(hh, ll, make_float2(Bk[k], 0.f), vq[-k].x, vq[-k].y);
+                }
+                if (h.out) gp[-i] += hh + ll;
+                const float xv = xp[-i], yv = yp[-i];
+#pragma unroll
+                for (int k = 0; k <= MB; ++k) {
+                    const float vf = vq[-k].x + vq[-k].y;
+                    acc[k] = fmaf(vf, xv, acc[k]);
+                    if (k >= 1) acc[MB + k] = fmaf(vf, yv, acc[MB + k]);
+                }
+            }
+            __syncthreads();
+            // the next block's halo: v[b0 + kBlk - MB .. b0 + kBlk)
+            if (t < MB) vs[cur ^ 1][t] = vs[cur][kBlk + t];
+            cur ^= 1;
+        }
+        // the span's lag sums, fixed order: warp trees, then warps 0..7
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) {
+            float v = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        for (int k = t; k < NACC; k += NT) {
+            float v = 0.f;
+#pragma unroll
+            for (int e = 0; e < NT / 32; ++e) v += red[e][k];
+            h.span_part[(size_t)w * NACC + k] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Coefficient gradients: per channel, the tiles' lag sums in tile order (FP64).
 // One warp per channel position.
 // ---------------------------------------------------------------------------
@@ -761,9 +889,14 @@ __global__ void __launch_bounds__(128) hi_reduce_kernel(HiArgs h, Batch bt) {
     const int64_t ch = hi::plan_channel(h.plan, pos);
     const Channel c = channel_of(bt, ch);
     const int64_t tb = h.plan.tile_pref[pos], nt = h.plan.tile_pref[pos + 1] - tb;
+    // spans corrected by hi_ufix (processing index >= 1 of channels with a table)
+    const int64_t sb = h.plan.span_pref[pos], ns = h.plan.span_pref[pos + 1] - sb;
+    const bool fixed = h.span_part != nullptr && ns > 1 && h.hlen[ch] > 0;
     for (int k = lane; k < NACC; k += 32) {
         double v = 0.0;
         for (int64_t i = 0; i < nt; ++i) v += (double)h.partial[(size_t)(tb + i) * NACC + k];
+        if (fixed)
+            for (int64_t i = 1; i < ns; ++i) v += (double)h.span_part[(size_t)(sb + i) * NACC + k];
         if (k <= MB) {
             if (h.gb && k <= c.N) h.gb[ch * bt.Nstride + k] = (float)v;
         } else {
@@ -883,11 +1016,23 @@ cudaError_t hi_yfix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaS
     return cudaGetLastError();
 }
 
+template <int MB>
+cudaError_t hi_ufix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (int64_t)(sms > 0 ? sms : 1) * 4;
+    if (grid > items_bound) grid = items_bound > 0 ? items_bound : 1;
+    hi_ufix_kernel<MB><<<(unsigned)grid, 256, 0, st>>>(h, bt); note_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t hi_plan<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_jump<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_scan<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_reduce<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_epass<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_yfix<DFILT_MB>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
+template cudaError_t hi_ufix<DFILT_MB>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
 
 }  // namespace dfilt
