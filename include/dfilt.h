@@ -268,9 +268,11 @@ dfilt_status dfilt_set_wait_limit(int64_t iters);
  *   same y with the chunked algorithm (opts->algo must be AUTO or CHUNKED).
  *   Scratch: a fixed 4 MiB device array inside this library (per GPU that loads it,
  *   held until the process exits) instead of a caller workspace.  A batch whose
- *   per-channel tables need more (dfilt_workspace_size's fwd_ws > 4 MiB, e.g. more
- *   than 2730 channels at M <= 2, 63 channels at M = 64) is rejected with
- *   DFILT_ERR_WORKSPACE before anything is launched.
+ *   per-channel tables need more -- dfilt_workspace_size's fwd_ws for the same batch
+ *   and opts with path = DFILT_PATH_FUSED above 4 MiB -- is rejected with
+ *   DFILT_ERR_WORKSPACE before anything is launched.  With the automatic scan
+ *   precision that is more than 2730 channels at M <= 2 (the same with fp64_scan = 1),
+ *   334 at M = 16, 168 at M = 32, 63 at M = 64.
  *   The first call on each device looks up the array's address (one-time set-up);
  *   make that first call before any stream capture.  All calls share the array:
  *   calls whose work overlaps on the GPU (other streams or threads) race and must be
