@@ -46,6 +46,42 @@ def recurrence_backward(A, v0, v, grad_v):
     return grad_A, grad_v0, grad_z
 
 
+def diag_forward(lam, V, Vinv, v0, z):
+    """The App. B operator with A diagonalised, A = V diag(lam) V^-1 (Diag-EXT, Sec. 3.2
+    and Sec. 4): in the eigenbasis the state q = V^-1 v evolves element by element,
+    q(n+1) = lam * q(n) + V^-1 z(n), q(0) = V^-1 v0, and v(n) = Re(V q(n)) (real for
+    a real A whose complex eigenvectors come in conjugate pairs).
+    lam: (M,) complex; V, Vinv: (M, M) complex; v0: (M,); z: (T, M) -> v(1..T): (T, M)."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    V = np.asarray(V, dtype=np.complex128)
+    Vinv = np.asarray(Vinv, dtype=np.complex128)
+    z = np.asarray(z, dtype=np.float64)
+    q = Vinv @ np.asarray(v0, dtype=np.float64)
+    out = np.empty(z.shape)
+    for n in range(z.shape[0]):
+        q = lam * q + Vinv @ z[n]
+        out[n] = (V @ q).real
+    return out
+
+
+def diag_backward(lam, V, Vinv, v0, v, grad_v):
+    """Backward of the diagonalised operator: App. A's dL/dz is the operator for A^T run
+    on the time-reversed upstream gradient from a zero state, and
+    A^T = Vinv^T diag(lam) V^T is diagonalised by the transposed pair; then
+    dL/dv(0) = A^T dL/dz(0) and dL/dA = sum_n dL/dz(n) v(n)^T with v(n) the state
+    before step n.  Returns (grad_A, grad_v0, grad_z), all real."""
+    lam = np.asarray(lam, dtype=np.complex128)
+    V = np.asarray(V, dtype=np.complex128)
+    Vinv = np.asarray(Vinv, dtype=np.complex128)
+    g = np.asarray(grad_v, dtype=np.float64)
+    M = lam.shape[0]
+    grad_z = diag_forward(lam, Vinv.T, V.T, np.zeros(M), g[::-1])[::-1]
+    grad_v0 = (Vinv.T @ (lam * (V.T @ grad_z[0]))).real
+    before = np.vstack([np.asarray(v0, dtype=np.float64)[None, :], v[:-1]])   # v(0..T-1)
+    grad_A = grad_z.T @ before
+    return grad_A, grad_v0, grad_z
+
+
 def companion(a):
     """Companion matrix of 1 + a_1 z^-1 + ... + a_M z^-M (Sec. 2): first row -a,
     ones on the subdiagonal."""

@@ -379,11 +379,66 @@ def pin_df1_initial_conditions(lib=None):
                 assert _rel(got, fd) < 1e-7, ("df1 fd", nm, M, N)
 
 
+def pin_recurrence_diagonalised(lib=None, ss=None):
+    """The diagonalised App. B operator (Diag-EXT): with A's eigendecomposition from
+    numpy's eig (a library routine) it equals the dense operator (itself pinned by
+    closed forms and central differences above) for random real A with distinct
+    eigenvalues, real and complex; a diagonal A gives geometric sums and a scaled
+    rotation r R(theta) gives r^n R(n theta) v0 in closed form; its backward
+    (grad_A, grad_v0, grad_z) equals FP64 central differences of <g, v>, grad_A taken
+    through the eigendecomposition of the perturbed A.  (`ss` may replace the
+    oracle module, for planted-mistake checks.)"""
+    if ss is None:
+        from oracle import statespace as ss
+    rng = np.random.default_rng(31)
+    eig = lambda A: (lambda w, V: (w, V, np.linalg.inv(V)))(*np.linalg.eig(A))
+    for M, T in [(1, 30), (2, 40), (3, 25), (4, 33)]:
+        A = 0.6 * rng.standard_normal((M, M)) / np.sqrt(M)
+        v0 = rng.standard_normal(M); z = rng.standard_normal((T, M))
+        lam, V, Vi = eig(A)
+        assert _rel(ss.diag_forward(lam, V, Vi, v0, z), ss.recurrence_forward(A, v0, z)) < 1e-12, \
+            ("diag == dense", M)
+    lam = np.array([0.9, -0.6, 0.3])
+    v0 = rng.standard_normal(3); z = rng.standard_normal((25, 3))
+    v = ss.diag_forward(lam, np.eye(3), np.eye(3), v0, z)
+    for i in range(3):
+        ref = [lam[i] ** (n + 1) * v0[i] + sum(lam[i] ** (n - k) * z[k, i] for k in range(n + 1))
+               for n in range(25)]
+        assert _rel(v[:, i], ref) < 1e-13, "diag geometric"
+    r, th = 0.97, 0.4
+    Rm = r * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    w0 = np.array([1.0, -0.5])
+    lam, V, Vi = eig(Rm)
+    v = ss.diag_forward(lam, V, Vi, w0, np.zeros((30, 2)))
+    for n in range(30):
+        c, s_ = np.cos((n + 1) * th), np.sin((n + 1) * th)
+        assert _rel(v[n], r ** (n + 1) * np.array([[c, -s_], [s_, c]]) @ w0) < 1e-12, "diag rotation"
+    for M, T in [(2, 30), (3, 17), (4, 12)]:
+        A = 0.6 * rng.standard_normal((M, M)) / np.sqrt(M)
+        v0 = rng.standard_normal(M); z = rng.standard_normal((T, M)); g = rng.standard_normal((T, M))
+        lam, V, Vi = eig(A)
+        v = ss.diag_forward(lam, V, Vi, v0, z)
+        gA, gv0, gz = ss.diag_backward(lam, V, Vi, v0, v, g)
+        L = lambda AA, vv, zz: float((g * ss.diag_forward(*eig(AA), vv, zz)).sum())
+        h = 1e-6
+        def fd(arr, which):
+            out = np.zeros_like(arr)
+            for idx in np.ndindex(arr.shape):
+                ap, am = arr.copy(), arr.copy(); ap[idx] += h; am[idx] -= h
+                kp = dict(AA=A, vv=v0, zz=z); km = dict(AA=A, vv=v0, zz=z)
+                kp[which] = ap; km[which] = am
+                out[idx] = (L(**kp) - L(**km)) / (2 * h)
+            return out
+        assert _rel(gA, fd(A, "AA")) < 1e-6, ("diag fd A", M)
+        assert _rel(gv0, fd(v0, "vv")) < 1e-6, ("diag fd v0", M)
+        assert _rel(gz, fd(z, "zz")) < 1e-6, ("diag fd z", M)
+
+
 ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfilter,
             pin_injection_form, pin_linearity_shift, pin_exact_forward,
             pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace,
             pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint,
-            pin_recurrence_dense, pin_df1_initial_conditions]
+            pin_recurrence_dense, pin_df1_initial_conditions, pin_recurrence_diagonalised]
 
 
 def run_all(lib=None):

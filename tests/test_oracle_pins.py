@@ -129,3 +129,31 @@ def test_oracle_threads_deterministic():
     y1 = oracle.forward(w.x, w.b, w.a, w.zi, nthreads=1)
     y4 = oracle.forward(w.x, w.b, w.a, w.zi, nthreads=4)
     assert np.array_equal(y1, y4)
+
+
+# Planted mistakes in the diagonalised state-space operator (oracle/statespace.py):
+# each must fail pin_recurrence_diagonalised.
+DIAG_MUTATIONS = [
+    ("diag input projection", "q = lam * q + Vinv @ z[n]", "q = lam * q + V @ z[n]"),
+    ("diag output takes the imaginary part", "out[n] = (V @ q).real", "out[n] = (V @ q).imag"),
+    ("diag initial state not projected", "q = Vinv @ np.asarray(v0, dtype=np.float64)",
+     "q = np.asarray(v0, dtype=np.complex128)"),
+    ("diag adjoint basis not transposed", "diag_forward(lam, Vinv.T, V.T, np.zeros(M), g[::-1])",
+     "diag_forward(lam, V, Vinv, np.zeros(M), g[::-1])"),
+    ("diag grad_v0 drops lam", "grad_v0 = (Vinv.T @ (lam * (V.T @ grad_z[0]))).real",
+     "grad_v0 = (Vinv.T @ (V.T @ grad_z[0])).real"),
+    ("diag grad_A pairs v(n+1)", "before = np.vstack([np.asarray(v0, dtype=np.float64)[None, :], v[:-1]])",
+     "before = v"),
+]
+
+
+@pytest.mark.parametrize("desc,orig,mut", DIAG_MUTATIONS, ids=[m[0] for m in DIAG_MUTATIONS])
+def test_planted_mistake_in_diag_operator_is_caught(desc, orig, mut):
+    import types
+    from oracle import statespace
+    src = open(statespace.__file__).read()
+    assert src.count(orig) == 1, f"mutation site not unique: {orig}"
+    mod = types.ModuleType("statespace_mutant")
+    exec(compile(src.replace(orig, mut), "statespace_mutant.py", "exec"), mod.__dict__)
+    with pytest.raises(AssertionError):
+        pins.pin_recurrence_diagonalised(ss=mod)
