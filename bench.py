@@ -1027,7 +1027,42 @@ def run_ss(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src):
     ref = ossm.recurrence_forward(As[0].astype(np.float32).astype(np.float64),
                                   v0d[0].double().cpu().numpy(), zd[0, :4096].double().cpu().numpy())
     out["rel_err_vs_fp64_first_4096_steps"] = float(np.abs(hv - ref).max() / np.abs(ref).max())
-    del zd, gvd, vd, gzd, sw1, sw2
+
+    # the same operator diagonalised (Diag-EXT): the eigendecomposition of each A (numpy's
+    # eig on the host, once, like the parameters), the scan in the eigenbasis
+    A32 = As.astype(np.float32).astype(np.float64)
+    lam = np.zeros((Bs, Ms), np.complex64)
+    Vm = np.zeros((Bs, Ms, Ms), np.complex64)
+    Vi = np.zeros((Bs, Ms, Ms), np.complex64)
+    for i in range(Bs):
+        w_, vec = np.linalg.eig(A32[i])
+        lam[i], Vm[i], Vi[i] = w_, vec, np.linalg.inv(vec)
+    ld, Vd, Vid = dev(lam), dev(Vm), dev(Vi)
+    dfw, dbw = dfilt.dfilt_diag_workspace_size(Bs, Ts, Ms)
+    dw1 = torch.empty(max(dfw, 16), dtype=torch.uint8, device="cuda")
+    dw2 = torch.empty(max(dbw, 16), dtype=torch.uint8, device="cuda")
+
+    def diag_step():
+        dfilt._check(L.dfilt_diag_forward(P(ld), P(Vd), P(Vid), P(v0d), P(zd), P(vd), P(dw1), dfw,
+                                          Bs, Ts, Ms, sptr), "dfilt_diag_forward")
+        dfilt._check(L.dfilt_diag_backward(P(ld), P(Vd), P(Vid), P(v0d), P(vd), P(gvd), P(gAd),
+                                           P(gv0d), P(gzd), P(dw2), dbw, Bs, Ts, Ms, sptr),
+                     "dfilt_diag_backward")
+
+    dms = maxrank(time_loop(torch, stream, diag_step, ns, 3, barrier))
+    status = dfilt.dfilt_sync_status()
+    if status != 0:
+        raise RuntimeError(f"device status {dfilt.STATUS[status]}")
+    hv = vd[0, :4096].double().cpu().numpy()
+    dref = ossm.diag_forward(lam[0].astype(np.complex128), Vm[0].astype(np.complex128),
+                             Vi[0].astype(np.complex128), v0d[0].double().cpu().numpy(),
+                             zd[0, :4096].double().cpu().numpy())
+    out["diagonalised"] = {
+        "workload": f"A = V diag(lam) V^-1 (M = {Ms}), the same {Bs} x {Ts} problem, fwd + bwd",
+        "value": Bs * Ts * world / (dms / 1e3) / 1e9, "unit": "Gsteps/s", "ms_per_step": dms,
+        "calls": ns, "roofline_frac": 40.0 * Bs * Ts / (dms / 1e3) / 1e9 / hbm,
+        "rel_err_vs_fp64_first_4096_steps": float(np.abs(hv - dref).max() / np.abs(dref).max())}
+    del zd, gvd, vd, gzd, sw1, sw2, dw1, dw2
     return out
 
 

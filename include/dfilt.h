@@ -337,6 +337,38 @@ dfilt_status dfilt_ss_backward(const float *A, const float *v0, const float *v, 
                                int64_t B, int64_t T, int M, void *stream);
 
 /*
+ * The same recurrence with A given by its eigendecomposition, A = V diag(lam) V^-1 (the
+ * paper's Diag-EXT, Sec. 3.2 and Sec. 4; applicable when A is diagonalisable): the
+ * state in the eigenbasis q = V^-1 v evolves element by element,
+ *     q(n+1) = lam * q(n) + V^-1 z(n),  q(0) = V^-1 v0,  v(n) = Re(V q(n)),
+ * and the backward is the same operator for A^T = V^-T diag(lam) V^T on the
+ * time-reversed dL/dv from a zero state (App. A, Eq. dLdz), then
+ * dL/dv0 = A^T dL/dz(0) and dL/dA = sum_n dL/dz(n) v(n)^T (Eq. dLdvBA), with v(n) the
+ * state before step n: the gradients are those of the dense operator above, so dL/dA
+ * needs no derivative of the eigendecomposition.
+ *   lam   [B,M]     eigenvalues, complex as interleaved (re, im) floats (8-byte aligned)
+ *   V     [B,M,M]   eigenvectors as columns, row-major, complex (8-byte aligned)
+ *   Vinv  [B,M,M]   the inverse of V, row-major, complex (8-byte aligned)
+ *   v0 [B,M], z [B,T,M], v [B,T,M], gv [B,T,M], gz [B,T,M], gA [B,M,M], gv0 [B,M]:
+ *                   real, as for dfilt_ss_forward / dfilt_ss_backward (v0 NULL = zero;
+ *                   gA, gv0 NULL = not wanted; v may be NULL when gA is NULL)
+ *   ws, ws_bytes    workspace of at least fwd_ws / bwd_ws bytes, 16-byte aligned
+ * A real A's complex eigenpairs must come in conjugate pairs (as numpy's or torch's
+ * eig returns them) for V q to be real; its imaginary part is dropped.  Supported
+ * 1 <= M <= 4 (DFILT_ERR_UNSUPPORTED above).  Complex FP32 arithmetic; the powers of
+ * lam the chunked scan uses come from FP64 squaring; dL/dA sums in a fixed order.
+ */
+dfilt_status dfilt_diag_workspace_size(int64_t B, int64_t T, int M, size_t *fwd_ws,
+                                       size_t *bwd_ws);
+dfilt_status dfilt_diag_forward(const float *lam, const float *V, const float *Vinv,
+                                const float *v0, const float *z, float *v, void *ws,
+                                size_t ws_bytes, int64_t B, int64_t T, int M, void *stream);
+dfilt_status dfilt_diag_backward(const float *lam, const float *V, const float *Vinv,
+                                 const float *v0, const float *v, const float *gv, float *gA,
+                                 float *gv0, float *gz, void *ws, size_t ws_bytes, int64_t B,
+                                 int64_t T, int M, void *stream);
+
+/*
  * Direct-form initial conditions: past inputs xpast[B,N] = (x[-1], ..., x[-N]) and past
  * outputs ypast[B,M] = (y[-1], ..., y[-M]) (the convention of SciPy's lfiltic and
  * MATLAB's filtic) mapped to the TDF-II state zi[B,M] that dfilt_forward takes (Sec. 2

@@ -32,7 +32,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_kernel_timing_read", "dfilt_set_numeric_check", "dfilt_jvp_workspace_size",
            "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward",
            "dfilt_ic_df1", "dfilt_ic_df1_backward", "dfilt_kernel_timing_read_classes",
-           "dfilt_launch_count", "dfilt_tuning_set", "dfilt_tuning_get"]
+           "dfilt_launch_count", "dfilt_tuning_set", "dfilt_tuning_get",
+           "dfilt_diag_workspace_size", "dfilt_diag_forward", "dfilt_diag_backward"]
 
 
 class DfiltError(RuntimeError):
@@ -103,6 +104,9 @@ def lib():
             L.dfilt_ss_workspace_size.argtypes = [i64, i64, i32, Psz, Psz]
             L.dfilt_ss_forward.argtypes = [P, P, P, P, P, sz, i64, i64, i32, P]
             L.dfilt_ss_backward.argtypes = [P, P, P, P, P, P, P, P, sz, i64, i64, i32, P]
+            L.dfilt_diag_workspace_size.argtypes = [i64, i64, i32, Psz, Psz]
+            L.dfilt_diag_forward.argtypes = [P, P, P, P, P, P, P, sz, i64, i64, i32, P]
+            L.dfilt_diag_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32, P]
             L.dfilt_ic_df1.argtypes = [P, P, P, P, P, i64, i32, i32, P]
             L.dfilt_ic_df1_backward.argtypes = [P, P, P, P, P, P, P, P, P, i64, i32, i32, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
@@ -317,6 +321,53 @@ def dfilt_ss_backward(A, v0, v, gv, *, needs=(True, True), ws=None, stream=None)
     _check(lib().dfilt_ss_backward(_ptr(A), _ptr(v0), _ptr(v), _ptr(gv), _ptr(gA), _ptr(gv0),
                                    _ptr(gz), _ptr(ws), ws.numel(), B, T, M, _stream(stream)),
            "dfilt_ss_backward")
+    return gA, gv0, gz
+
+
+def _c64(t, name):
+    """A contiguous complex64 CUDA tensor (complex arrays cross the C ABI as interleaved
+    (re, im) float pairs)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex64 or not t.is_cuda:
+        raise TypeError(f"{name}: expected a complex64 CUDA tensor")
+    return t.contiguous()
+
+
+def dfilt_diag_workspace_size(B, T, M):
+    f, w = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().dfilt_diag_workspace_size(B, T, M, ctypes.byref(f), ctypes.byref(w)),
+           "dfilt_diag_workspace_size")
+    return f.value, w.value
+
+
+def dfilt_diag_forward(lam, V, Vinv, v0, z, *, v=None, ws=None, stream=None):
+    """v(1..T) [B,T,M] of v(n+1) = A v(n) + z(n) with A = V diag(lam) V^-1 given by its
+    eigendecomposition (lam [B,M], V and Vinv [B,M,M], complex64), run in the eigenbasis."""
+    lam, V, Vinv = _c64(lam, "lam"), _c64(V, "V"), _c64(Vinv, "Vinv")
+    v0, z = _f32(v0, "v0"), _f32(z, "z")
+    B, T, M = z.shape
+    fws, _ = dfilt_diag_workspace_size(B, T, M)
+    v = torch.empty_like(z) if v is None else v
+    ws = _buf(fws, z.device) if ws is None else ws
+    _check(lib().dfilt_diag_forward(_ptr(lam), _ptr(V), _ptr(Vinv), _ptr(v0), _ptr(z), _ptr(v),
+                                    _ptr(ws), ws.numel(), B, T, M, _stream(stream)),
+           "dfilt_diag_forward")
+    return v
+
+
+def dfilt_diag_backward(lam, V, Vinv, v0, v, gv, *, needs=(True, True), ws=None, stream=None):
+    """(grad_A, grad_v0, grad_z) of the diagonalised recurrence (the same gradients as the
+    dense operator's); entries of `needs` select grad_A and grad_v0."""
+    lam, V, Vinv = _c64(lam, "lam"), _c64(V, "V"), _c64(Vinv, "Vinv")
+    v0, v, gv = _f32(v0, "v0"), _f32(v, "v"), _f32(gv, "gv")
+    B, T, M = gv.shape
+    _, bws = dfilt_diag_workspace_size(B, T, M)
+    gA = torch.empty((B, M, M), dtype=torch.float32, device=gv.device) if needs[0] else None
+    gv0 = torch.empty((B, M), dtype=torch.float32, device=gv.device) if needs[1] else None
+    gz = torch.empty_like(gv)
+    ws = _buf(bws, gv.device) if ws is None else ws
+    _check(lib().dfilt_diag_backward(_ptr(lam), _ptr(V), _ptr(Vinv), _ptr(v0), _ptr(v), _ptr(gv),
+                                     _ptr(gA), _ptr(gv0), _ptr(gz), _ptr(ws), ws.numel(), B, T, M,
+                                     _stream(stream)), "dfilt_diag_backward")
     return gA, gv0, gz
 
 

@@ -123,6 +123,24 @@ def test_ss_host_checks(L):
     assert L.dfilt_ss_forward(fake, None, fake, fake, fake, 16, 4, 10, 2, None) == 6
 
 
+def test_diag_host_checks(L):
+    """Diagonalised state-space operator: workspace sizes and argument errors decided on
+    the host (no launch)."""
+    f, w = dfilt.dfilt_diag_workspace_size(64, 1 << 20, 2)
+    assert f > 0 and w > f
+    sz = ctypes.c_size_t()
+    assert L.dfilt_diag_workspace_size(4, 10, 5, ctypes.byref(sz), None) == 2    # M > 4
+    assert L.dfilt_diag_workspace_size(4, 10, 0, ctypes.byref(sz), None) == 1
+    assert L.dfilt_diag_forward(None, None, None, None, None, None, None, 0, 4, 10, 2, None) == 1
+    assert L.dfilt_diag_forward(None, None, None, None, None, None, None, 0, 0, 10, 2, None) == 0
+    assert L.dfilt_diag_backward(None, None, None, None, None, None, None, None, None, None, 0,
+                                 4, 10, 2, None) == 1
+    fake, odd = ctypes.c_void_p(4096), ctypes.c_void_p(4100)
+    assert L.dfilt_diag_forward(fake, fake, fake, None, fake, fake, fake, 16, 4, 10, 2, None) == 6
+    assert L.dfilt_diag_forward(odd, fake, fake, None, fake, fake, fake, 1 << 20, 4, 10, 2,
+                                None) == 1    # complex arrays must be 8-byte aligned
+
+
 def test_ic_df1_host_checks(L):
     """Direct-form initial conditions: argument errors and the empty batch on the host."""
     assert L.dfilt_ic_df1(None, None, None, None, None, 4, 2, 65, None) == 2
