@@ -8,8 +8,13 @@
 //   * low orders (MB <= 4): one warp per channel in double-word arithmetic
 //     (dword.cuh) on the full-rate FP32 pipes; one serial recurrence for the
 //     all-pole impulse response, then every table entry as a short sum over it;
-//   * higher orders: FP64, one block per channel, thread m evolves column m of F^i
-//     (i = 0..L) and every table is read off those columns in parallel:
+//   * higher orders with the double-word scan (the automatic choice above order 2):
+//     one block per channel, the same closed forms in FP64, the impulse response's
+//     recurrence shared by a warp and every entry summed in parallel (setup_hi_kernel,
+//     below);
+//   * higher orders with the forced FP32 scan (FP32 powers of the transition): FP64, one
+//     block per channel, thread m evolves column m of F^i (i = 0..L) and every table is
+//     read off those columns in parallel:
 //       O_L[i][m] = (F^i e_m)[0],  g[n] = sum_m Gv_m O_L[n-1][m] (n >= 1),
 //       h[n] likewise with the all-pole input vector, R_L[:, L-1-i] = F^i Gv
 //       (a reduction over the columns held in shared memory), Abar = F^L
@@ -18,6 +23,7 @@
 //     accuracy on them).  The backward's O^u columns run the anti-causal all-pole
 //     recursion from a unit future state, one column per thread.
 #include "chunk.cuh"
+#include "chunk_pipe.cuh"
 #include "dword.cuh"
 
 namespace dfilt {
@@ -401,6 +407,163 @@ __global__ void __launch_bounds__(MB) setup_large_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Higher orders (MB >= 8) with the double-word scan: both records of a channel per
+// block, every table entry a short FP64 sum over the impulse responses h (of 1/A) and
+// g (of B/A), rounded to FP32 (the scan blocks to (hi, lo) float pairs).  Closed forms
+// need O(M) multiply-adds per entry where stepping the TDF-II transition L times costs
+// O(L M) per column, so FP64 stays affordable on GB300's narrow FP64 pipe (double words
+// lose digits here: the sums cancel by orders of magnitude for high-order filters).
+// With the TDF-II state s_k[n] = sum_{l>k} (b_l x[n+k-l] - a_l y[n+k-l]) and the state
+// e_m equivalent to injecting 1 at time m (so its free response is h[n - m]):
+//   O_L[i][m] = h[i - m]                      R_L[m][j] = b_{L+m-j} - sum_{l>m} a_l g[L+m-l-j]
+//   Abar(K)[k][m] = -sum_{l>k} a_l h[K + k - l - m]        (K = L, and 4L for Abar^4)
+//   O^u(K)[n][m] = -sum_{p=0..M-1-m} a_{p+1+m} h[K - 1 - n - p]
+//       (the anti-causal free response from u[K + m] = 1; Abar' = O^u(L)[0:MB, :],
+//        Abar'^4 = O^u(4L)[0:MB, :])
+//   O^gx[n][m] = sum_k b_k U(n + k, m),  U(t, m) = O^u[t][m] (t < L), [t - L == m] (t >= L)
+// (terms past the channel's orders are zero; b_{L+m-j} only where 0 < L+m-j-m <= N).
+// Checked against the step-by-step construction, which these replace, to 1e-15.
+// ---------------------------------------------------------------------------
+template <int MB>
+struct HiSetupSmem {
+    static constexpr int H = ChunkTab<MB>::kBlockScan ? 4 * kL + MB : kL + MB;   // h[0 .. H)
+    static constexpr int G = kL + MB;                                           // g[0 .. G)
+    double h[H], g[G];
+    double ou[kL * MB];   // O^u(L)[n][m], row-major
+    double a[MB], b[MB + 1];
+};
+
+template <int MB>
+__global__ void __launch_bounds__(128) setup_hi_kernel(const float *__restrict__ b,
+                                                       const float *__restrict__ a,
+                                                       char *__restrict__ fwd_tabs,
+                                                       char *__restrict__ bwd_tabs,
+                                                       unsigned long long *__restrict__ counter,
+                                                       Batch bt) {
+    using Tab = ChunkTab<MB>;
+    using SM = HiSetupSmem<MB>;
+    constexpr int NT = 128;
+    extern __shared__ float4 smem4[];
+    SM &sm = *reinterpret_cast<SM *>(smem4);
+    const int t = threadIdx.x, lane = t & 31;
+    if (counter && blockIdx.x == 0 && t == 0) *counter = 0ull;
+    int64_t ch;
+    if (!work_channel(bt, (int64_t)blockIdx.x, &ch)) return;   // uniform across the block
+    const Channel c = channel_of(bt, ch);
+    for (int k = t; k < MB; k += NT) sm.a[k] = k < c.M ? (double)a[ch * bt.Mstride + k] : 0.0;
+    for (int k = t; k <= MB; k += NT) sm.b[k] = k <= c.N ? (double)b[ch * bt.Nstride + k] : 0.0;
+    __syncthreads();
+    const int M = c.M < MB ? c.M : MB;
+    // h by the all-pole difference equation (warp 0, the lanes share each step's sum)
+    if (t < 32) {
+        if (t == 0) sm.h[0] = 1.0;
+        __syncwarp();
+        for (int n = 1; n < SM::H; ++n) {
+            double acc = 0.0;
+            for (int j = lane + 1; j <= M; j += 32)
+                if (j <= n) acc = fma(-sm.a[j - 1], sm.h[n - j], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) sm.h[n] = acc;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    auto H = [&](int n) { return n >= 0 ? sm.h[n] : 0.0; };
+    // g = b * h
+    for (int n = t; n < SM::G; n += NT) {
+        double acc = 0.0;
+        for (int k = 0; k <= c.N && k <= n; ++k) acc = fma(sm.b[k], sm.h[n - k], acc);
+        sm.g[n] = acc;
+    }
+    // O^u(L) into shared memory
+    for (int e = t; e < kL * MB; e += NT) {
+        const int n = e / MB, m = e % MB;
+        double acc = 0.0;
+        for (int p = 0; p + 1 + m <= M; ++p) acc = fma(-sm.a[p + m], H(kL - 1 - n - p), acc);
+        sm.ou[e] = acc;
+    }
+    __syncthreads();
+    auto Gf = [&](int n) { return n >= 0 ? sm.g[n] : 0.0; };
+    auto abar = [&](int K, int k, int m) {   // Abar(K)[k][m]
+        double acc = 0.0;
+        for (int l = k + 1; l <= M; ++l) acc = fma(-sm.a[l - 1], H(K + k - l - m), acc);
+        return acc;
+    };
+    auto ou4 = [&](int n, int m) {            // O^u(4L)[n][m]
+        double acc = 0.0;
+        for (int p = 0; p + 1 + m <= M; ++p) acc = fma(-sm.a[p + m], H(4 * kL - 1 - n - p), acc);
+        return acc;
+    };
+    auto pair = [](double v) {                // (hi, lo) float pair of v
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    if (fwd_tabs) {
+        char *R = fwd_tabs + (size_t)ch * (bt.fwd_stride ? (size_t)bt.fwd_stride : Tab::fwd_rec(true));
+        float *g = reinterpret_cast<float *>(R + Tab::F_G);
+        float *RL = reinterpret_cast<float *>(R + Tab::F_RL);
+        float *OL = reinterpret_cast<float *>(R + Tab::F_OL);
+        for (int n = t; n < kL; n += NT) g[n] = (float)sm.g[n];
+        for (int e = t; e < MB * kL; e += NT) {
+            const int m = e / kL, j = e % kL;
+            const int lb = kL + m - j;   // the b term's index
+            double acc = (lb > m && lb <= c.N) ? sm.b[lb] : 0.0;
+            for (int l = m + 1; l <= M; ++l) acc = fma(-sm.a[l - 1], Gf(kL + m - l - j), acc);
+            RL[e] = (float)acc;
+        }
+        for (int e = t; e < kL * MB; e += NT) {
+            const int i = e / MB, m = e % MB;
+            OL[e] = (float)H(i - m);
+        }
+        float2 *At = reinterpret_cast<float2 *>(R + Tab::F_SCAN);   // column-major
+        for (int e = t; e < MB * MB; e += NT) {
+            const int j = e / MB, m = e % MB;   // At[j * MB + m] = Abar[m][j]
+            At[e] = pair(abar(kL, m, j));
+            if constexpr (Tab::kBlockScan) At[MB * MB + e] = pair(abar(4 * kL, m, j));
+        }
+    }
+    if (bwd_tabs) {
+        char *R = bwd_tabs + (size_t)ch * (bt.bwd_stride ? (size_t)bt.bwd_stride : Tab::bwd_rec(true));
+        float *g = reinterpret_cast<float *>(R + Tab::B_G);
+        float *hv = reinterpret_cast<float *>(R + Tab::B_H);
+        float *Ou = reinterpret_cast<float *>(R + Tab::B_OU);
+        float *Ogx = reinterpret_cast<float *>(R + Tab::B_OGX);
+        for (int n = t; n < kL; n += NT) {
+            g[n] = (float)sm.g[n];
+            hv[n] = (float)sm.h[n];
+        }
+        for (int e = t; e < kL * MB; e += NT) {
+            const int n = e / MB, m = e % MB;
+            Ou[e] = (float)sm.ou[e];
+            double acc = 0.0;
+            for (int k = 0; k <= c.N; ++k) {
+                const int tt = n + k;
+                if (tt < kL) acc = fma(sm.b[k], sm.ou[tt * MB + m], acc);
+                else if (tt - kL == m) acc += sm.b[k];
+            }
+            Ogx[e] = (float)acc;
+        }
+        float2 *At = reinterpret_cast<float2 *>(R + Tab::B_SCAN);   // column-major
+        for (int e = t; e < MB * MB; e += NT) {
+            const int j = e / MB, m = e % MB;   // At[j * MB + m] = Abar'[m][j] = O^u[m][j]
+            At[e] = pair(sm.ou[m * MB + j]);
+            if constexpr (Tab::kBlockScan) At[MB * MB + e] = pair(ou4(m, j));
+        }
+        float *C = reinterpret_cast<float *>(R + Tab::b_coef(true));
+        for (int k = t; k < MB; k += NT) C[k] = (float)sm.a[k];
+        for (int k = t; k <= MB; k += NT) C[MB + k] = (float)sm.b[k];
+        if constexpr (MB > 4) {
+            float *OLb = reinterpret_cast<float *>(R + Tab::b_ol(true));
+            for (int e = t; e < kL * MB; e += NT) {
+                const int i = e / MB, m = e % MB;
+                OLb[e] = (float)H(i - m);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, char *bwd_tabs,
@@ -423,6 +586,24 @@ cudaError_t launch_chunk_setup(const float *b, const float *a, char *fwd_tabs, c
         kern<<<large_grid, mb, smem, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt, fp64_scan); note_launch();
         return cudaGetLastError();
     };
+    auto hi = [&](auto kern, size_t smem) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<(unsigned)bt.B, 128, smem, st>>>(b, a, fwd_tabs, bwd_tabs, counter, bt); note_launch();
+        return cudaGetLastError();
+    };
+    if (fp64_scan) {
+        switch (MB) {
+            case 8: return hi(setup_hi_kernel<8>, sizeof(HiSetupSmem<8>));
+            case 16: return hi(setup_hi_kernel<16>, sizeof(HiSetupSmem<16>));
+            case 32: return hi(setup_hi_kernel<32>, sizeof(HiSetupSmem<32>));
+            case 64: return hi(setup_hi_kernel<64>, sizeof(HiSetupSmem<64>));
+            default: break;
+        }
+    }
     switch (MB) {
         case 2: return small(setup_small_kernel<2>);
         case 4: return small(setup_small_kernel<4>);
