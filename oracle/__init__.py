@@ -80,6 +80,10 @@ def _bind(lib):
     lib.oracle_backward_df1.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P, i64, i64, i32, i32,
                                         i32]
     lib.oracle_backward_df1.restype = i32
+    lib.oracle_forward_tv.argtypes = [P, P, P, P, P, i64, i64, i32, i32, i32]
+    lib.oracle_forward_tv.restype = i32
+    lib.oracle_backward_tv.argtypes = [P, P, P, P, P, P, P, P, P, P, i64, i64, i32, i32, i32]
+    lib.oracle_backward_tv.restype = i32
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = i32
     return lib
@@ -198,6 +202,36 @@ def backward_df1(gy, x, y, b, a, xpast, ypast, *, nthreads: int = 0, lib=None):
     if rc != 0:
         raise MemoryError("oracle backward_df1: allocation failed")
     return gx, gb, ga, gxp, gyp
+
+
+def forward_tv(x, b, a, ypast=None, *, nthreads: int = 0, lib=None):
+    """Parameter-varying direct form, FP64: x[B,T], b[B,T,N+1], a[B,T,M] (the
+    coefficients of each output sample), ypast[B,M] (y[-1], ..., y[-M]) or None."""
+    lib = lib or load()
+    x, b, a = _f64(x), _f64(b), _f64(a)
+    B, T = x.shape
+    N, M = b.shape[2] - 1, a.shape[2]
+    yp = None if ypast is None else _f64(ypast)
+    y = np.zeros_like(x)
+    lib.oracle_forward_tv(_ptr(x), _ptr(b), _ptr(a), _ptr(yp), _ptr(y), B, T, N, M, int(nthreads))
+    return y
+
+
+def backward_tv(gy, x, y, b, a, ypast=None, *, nthreads: int = 0, lib=None):
+    """(grad_x [B,T], grad_b [B,T,N+1], grad_a [B,T,M], grad_ypast [B,M]) in FP64 for
+    forward_tv."""
+    lib = lib or load()
+    gy, x, y, b, a = _f64(gy), _f64(x), _f64(y), _f64(b), _f64(a)
+    B, T = x.shape
+    N, M = b.shape[2] - 1, a.shape[2]
+    yp = None if ypast is None else _f64(ypast)
+    gx = np.zeros_like(x)
+    gb, ga, gyp = np.zeros((B, T, N + 1)), np.zeros((B, T, M)), np.zeros((B, M))
+    rc = lib.oracle_backward_tv(_ptr(gy), _ptr(x), _ptr(y), _ptr(b), _ptr(a), _ptr(yp), _ptr(gx),
+                                _ptr(gb), _ptr(ga), _ptr(gyp), B, T, N, M, int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle backward_tv: allocation failed")
+    return gx, gb, ga, gyp
 
 
 # ----------------------------------------------------------------------------

@@ -371,5 +371,99 @@ int oracle_backward_df1(const double *g, const double *x, const double *y, const
     return fail ? -1 : 0;
 }
 
+/*
+ * Parameter-varying direct form (Sec. 5 notes the derivation extends to it): the
+ * coefficients of output sample n are b[n][0..N], a[n][0..M-1] (a[n][k-1] = a_k at n),
+ *     y[n] = sum_{k=0..N} b[n][k] x[n-k] - sum_{k=1..M} a[n][k-1] y[n-k],
+ * x[n < 0] = 0, y[-1-j] = ypast[j] (NULL = zero).  The backward follows the same steps
+ * as the fixed-coefficient one with each coefficient taken at the output it produced:
+ *     u[n] = g[n] - sum_{k=1..M} a[n+k][k-1] u[n+k]          (u[n >= T] = 0)
+ *     grad_x[n] = sum_{k=0..N} b[n+k][k] u[n+k]
+ *     grad_b[n][k] = u[n] x[n-k],   grad_a[n][k-1] = -u[n] y[n-k]   (y past: ypast)
+ *     grad_ypast[j] = -sum_{k=j+1..M} a[k-1-j][k-1] u[k-1-j]
+ */
+static void fwd_tv(const double *x, const double *b, const double *a, const double *yp,
+                   double *y, int64_t T, int N, int M)
+{
+    for (int64_t n = 0; n < T; ++n) {
+        double acc = 0.0;
+        for (int k = 0; k <= N; ++k)
+            if (n - k >= 0) acc += b[n * (N + 1) + k] * x[n - k];
+        for (int k = 1; k <= M; ++k) {
+            const double yk = n - k >= 0 ? y[n - k] : (yp ? yp[k - n - 1] : 0.0);
+            acc -= a[n * M + k - 1] * yk;
+        }
+        y[n] = acc;
+    }
+}
+
+static void bwd_tv(const double *g, const double *x, const double *y, const double *b,
+                   const double *a, const double *yp, double *gx, double *gb, double *ga,
+                   double *gyp, int64_t T, int N, int M, double *u)
+{
+    for (int64_t n = T - 1; n >= 0; --n) {
+        double acc = g[n];
+        for (int k = 1; k <= M; ++k)
+            if (n + k < T) acc -= a[(n + k) * M + k - 1] * u[n + k];
+        u[n] = acc;
+    }
+    for (int64_t n = 0; n < T; ++n) {
+        double acc = 0.0;
+        for (int k = 0; k <= N; ++k)
+            if (n + k < T) acc += b[(n + k) * (N + 1) + k] * u[n + k];
+        gx[n] = acc;
+        for (int k = 0; k <= N; ++k) gb[n * (N + 1) + k] = n - k >= 0 ? u[n] * x[n - k] : 0.0;
+        for (int k = 1; k <= M; ++k) {
+            const double yk = n - k >= 0 ? y[n - k] : (yp ? yp[k - n - 1] : 0.0);
+            ga[n * M + k - 1] = -u[n] * yk;
+        }
+    }
+    if (gyp) {
+        for (int j = 0; j < M; ++j) {
+            double acc = 0.0;
+            for (int k = j + 1; k <= M; ++k)
+                if (k - 1 - j < T) acc += a[(k - 1 - j) * M + k - 1] * u[k - 1 - j];
+            gyp[j] = -acc;
+        }
+    }
+}
+
+/* x, y, g [B,T]; b [B,T,N+1]; a [B,T,M]; ypast [B,M] or NULL.  Returns 0 or -1. */
+int oracle_forward_tv(const double *x, const double *b, const double *a, const double *yp,
+                      double *y, int64_t B, int64_t T, int N, int M, int nthreads)
+{
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+    for (int64_t i = 0; i < B; ++i)
+        fwd_tv(x + i * T, b + i * T * (N + 1), a + i * T * M, yp ? yp + i * M : NULL, y + i * T,
+               T, N, M);
+    return 0;
+}
+
+int oracle_backward_tv(const double *g, const double *x, const double *y, const double *b,
+                       const double *a, const double *yp, double *gx, double *gb, double *ga,
+                       double *gyp, int64_t B, int64_t T, int N, int M, int nthreads)
+{
+    int fail = 0;
+    const int nt = pick_threads(nthreads);
+#pragma omp parallel num_threads(nt)
+    {
+        double *u = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+        if (!u) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < B; ++i) {
+            if (!u) continue;
+            bwd_tv(g + i * T, x + i * T, y + i * T, b + i * T * (N + 1), a + i * T * M,
+                   yp ? yp + i * M : NULL, gx + i * T, gb + i * T * (N + 1), ga + i * T * M,
+                   gyp ? gyp + i * M : NULL, T, N, M, u);
+        }
+        free(u);
+    }
+    return fail ? -1 : 0;
+}
+
 /* Threads an OpenMP region actually gets (for reporting the CPU baseline). */
 int oracle_max_threads(void) { return pick_threads(0); }

@@ -379,6 +379,52 @@ def pin_df1_initial_conditions(lib=None):
                 assert _rel(got, fd) < 1e-7, ("df1 fd", nm, M, N)
 
 
+def pin_parameter_varying(lib=None):
+    """Parameter-varying direct form (oracle.forward_tv / backward_tv): with constant
+    coefficients it equals the fixed-coefficient direct form with past outputs
+    (forward_df1, itself pinned to SciPy's lfiltic + lfilter), and its per-sample
+    coefficient gradients sum to that form's; a first-order recursion
+    y[n] = x[n] - a[n] y[n-1] has the closed form sum_k prod_{j=k+1..n} (-a[j]) x[k]
+    + prod_{j=0..n} (-a[j]) y[-1]; every gradient equals FP64 central differences."""
+    rng = np.random.default_rng(41)
+    B, T, N, M = 2, 37, 2, 3
+    x = rng.standard_normal((B, T)); yp = rng.standard_normal((B, M)); g = rng.standard_normal((B, T))
+    a0 = 0.3 * rng.standard_normal((B, M)); b0 = rng.standard_normal((B, N + 1))
+    at = np.repeat(a0[:, None, :], T, axis=1); bt = np.repeat(b0[:, None, :], T, axis=1)
+    y = oracle.forward_tv(x, bt, at, yp, lib=lib)
+    yr = oracle.forward_df1(x, b0, a0, np.zeros((B, N)), yp, lib=lib)
+    assert _rel(y, yr) < 1e-13, "tv constant == df1"
+    gx, gb, ga, gyp = oracle.backward_tv(g, x, y, bt, at, yp, lib=lib)
+    rx, rb, ra, _, ryp = oracle.backward_df1(g, x, yr, b0, a0, np.zeros((B, N)), yp, lib=lib)
+    assert _rel(gx, rx) < 1e-13 and _rel(gb.sum(1), rb) < 1e-12 and _rel(ga.sum(1), ra) < 1e-12, \
+        "tv constant gradients == df1"
+    assert _rel(gyp, ryp) < 1e-13, "tv constant grad_ypast == df1"
+    # first order, varying coefficient
+    T1 = 20
+    x1 = rng.standard_normal((1, T1)); a1 = rng.uniform(-0.9, 0.9, (1, T1, 1)); y1p = np.array([[0.7]])
+    y1 = oracle.forward_tv(x1, np.ones((1, T1, 1)), a1, y1p, lib=lib)[0]
+    for n in range(T1):
+        ref = sum(np.prod(-a1[0, k + 1:n + 1, 0]) * x1[0, k] for k in range(n + 1)) \
+            + np.prod(-a1[0, :n + 1, 0]) * 0.7
+        assert abs(y1[n] - ref) < 1e-12 * max(1.0, abs(ref)), "tv first-order closed form"
+    # central differences on a small case
+    Bs, Ts = 1, 9
+    x = rng.standard_normal((Bs, Ts)); yp = rng.standard_normal((Bs, M)); g = rng.standard_normal((Bs, Ts))
+    b = rng.standard_normal((Bs, Ts, N + 1)); a = 0.3 * rng.standard_normal((Bs, Ts, M))
+    y = oracle.forward_tv(x, b, a, yp, lib=lib)
+    gx, gb, ga, gyp = oracle.backward_tv(g, x, y, b, a, yp, lib=lib)
+    L = lambda xx, bb, aa, pp: float((g * oracle.forward_tv(xx, bb, aa, pp, lib=lib)).sum())
+    h = 1e-6
+    args = {"x": x, "b": b, "a": a, "p": yp}
+    for name, got in (("x", gx), ("b", gb), ("a", ga), ("p", gyp)):
+        fd = np.zeros_like(args[name])
+        for idx in np.ndindex(fd.shape):
+            hp = {k: v.copy() for k, v in args.items()}; hm = {k: v.copy() for k, v in args.items()}
+            hp[name][idx] += h; hm[name][idx] -= h
+            fd[idx] = (L(hp["x"], hp["b"], hp["a"], hp["p"]) - L(hm["x"], hm["b"], hm["a"], hm["p"])) / (2 * h)
+        assert _rel(got, fd) < 1e-7, ("tv fd", name)
+
+
 def pin_recurrence_diagonalised(lib=None, ss=None):
     """The diagonalised App. B operator (Diag-EXT): with A's eigendecomposition from
     numpy's eig (a library routine) it equals the dense operator (itself pinned by
@@ -438,7 +484,8 @@ ALL_PINS = [pin_single_pole, pin_biquad_allpole, pin_transfer_function, pin_lfil
             pin_injection_form, pin_linearity_shift, pin_exact_forward,
             pin_exact_gradients, pin_finite_differences, pin_duality, pin_statespace,
             pin_jvp_single_pole, pin_jvp_finite_differences, pin_jvp_adjoint,
-            pin_recurrence_dense, pin_df1_initial_conditions, pin_recurrence_diagonalised]
+            pin_recurrence_dense, pin_df1_initial_conditions, pin_recurrence_diagonalised,
+            pin_parameter_varying]
 
 
 def run_all(lib=None):

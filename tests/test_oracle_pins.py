@@ -48,6 +48,14 @@ MUTATIONS = [
     ("df1 grad_xpast coefficient index", "if (k - j < T) sum += b[k] * u[k - j];",
      "if (k - j < T) sum += b[k - 1] * u[k - j];"),
     ("df1 grad_ypast sign", "gyp[j - 1] = -sum;", "gyp[j - 1] = sum;"),
+    ("tv adjoint takes the coefficient at n", "acc -= a[(n + k) * M + k - 1] * u[n + k];",
+     "acc -= a[n * M + k - 1] * u[n + k];"),
+    ("tv grad_x takes b at n", "acc += b[(n + k) * (N + 1) + k] * u[n + k];",
+     "acc += b[n * (N + 1) + k] * u[n + k];"),
+    ("tv grad_a sign", "ga[n * M + k - 1] = -u[n] * yk;", "ga[n * M + k - 1] = u[n] * yk;"),
+    ("tv forward past-output index", "acc -= a[n * M + k - 1] * yk;", "acc -= a[n * M + k - 1] * (n - k >= 0 ? yk : 0.0);"),
+    ("tv grad_ypast coefficient time", "acc += a[(k - 1 - j) * M + k - 1] * u[k - 1 - j];",
+     "acc += a[k - 1] * u[k - 1 - j];"),
 ]
 
 
