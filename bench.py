@@ -59,6 +59,7 @@ def args_():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-jvp", action="store_true", help="skip the forward-mode (JVP) leg")
+    p.add_argument("--no-tv", action="store_true", help="skip the parameter-varying leg")
     p.add_argument("--no-ss", action="store_true",
                    help="skip the dense state-space recurrence leg (M = 2, 64 x 2^20 steps)")
     p.add_argument("--tuning", default="",
@@ -807,6 +808,7 @@ def main():
         configs = {name: fixed_config(name, torch, dfilt, stream, a, hbm, src) for name in CONFIGS}
     jvp = None if a.no_jvp else run_jvp(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src)
     ssl = None if a.no_ss else run_ss(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src)
+    tvl = None if a.no_tv else run_tv(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src)
 
     if rank == 0:
         roof = None
@@ -833,7 +835,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "gpu_launches_note": "library kernels per step (dfilt_launch_count); the loss "
                                  "gradient is one torch elementwise op",
-            "configs": configs, "jvp": jvp, "state_space": ssl,
+            "configs": configs, "jvp": jvp, "state_space": ssl, "parameter_varying": tvl,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -979,6 +981,60 @@ def run_jvp(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src):
     got = dyj.cpu().numpy()[idx].astype(np.float64)
     out["rel_err_vs_fp64"] = float((np.abs(got - dref).max(-1) / np.abs(dref).max(-1)).max())
     del jws, w1, dy1, dyj, tdx
+    return out
+
+
+def run_tv(torch, dfilt, stream, a, world, barrier, maxrank, hbm, src):
+    """Parameter-varying biquads (coefficients per output sample, poles and zeros moving
+    slowly), 1024 x 48000, forward + backward (grad_x, per-sample grad_b and grad_a,
+    grad_ypast).  Algorithmic bytes per sample: forward x, b (3), a (2) read, y written
+    (28); backward gy, x, y, b, a read, grad_x, grad_b, grad_a written (56)."""
+    B, T, N, M = 1024, 48000, 2, 2
+    rng = np.random.default_rng(21)
+    n = np.arange(T)[None, :]
+    r0, th0 = rng.uniform(0.5, 0.95, (B, 1)), rng.uniform(0.1, 3.0, (B, 1))
+    r = r0 * (1 - 0.04 * (1 + np.sin(rng.uniform(1e-3, 2e-2, (B, 1)) * n)))
+    th = th0 + 0.2 * np.sin(rng.uniform(1e-3, 2e-2, (B, 1)) * n)
+    av = np.stack([-2 * r * np.cos(th), r * r], axis=2).astype(np.float32)
+    bv = (rng.standard_normal((B, 1, N + 1)) * (1 + 0.1 * np.sin(0.003 * n))[:, :, None]).astype(np.float32)
+    dev = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+    ad, bd = dev(av), dev(bv)
+    xd = torch.randn((B, T), device="cuda", generator=torch.Generator("cuda").manual_seed(22))
+    gyd = torch.randn((B, T), device="cuda", generator=torch.Generator("cuda").manual_seed(23))
+    ypd = dev((0.1 * rng.standard_normal((B, M))).astype(np.float32))
+    nws = dfilt.dfilt_tv_workspace_size(B, T, N, M)
+    w1 = torch.empty(max(nws, 16), dtype=torch.uint8, device="cuda")
+    w2 = torch.empty(max(nws, 16), dtype=torch.uint8, device="cuda")
+    yd, gxd = torch.empty_like(xd), torch.empty_like(xd)
+    gbd, gad, gypd = torch.empty_like(bd), torch.empty_like(ad), torch.empty_like(ypd)
+    L = dfilt.lib()
+    P = dfilt._ptr
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def tv_step():
+        dfilt._check(L.dfilt_tv_forward(P(xd), P(bd), P(ad), P(ypd), P(yd), P(w1), nws, B, T, N, M,
+                                        sptr), "dfilt_tv_forward")
+        dfilt._check(L.dfilt_tv_backward(P(gyd), P(xd), P(yd), P(bd), P(ad), P(ypd), P(gxd), P(gbd),
+                                         P(gad), P(gypd), P(w2), nws, B, T, N, M, sptr),
+                     "dfilt_tv_backward")
+
+    ns = max(3, min(100, a.steps * 5))
+    ms = maxrank(time_loop(torch, stream, tv_step, ns, 3, barrier))
+    status = dfilt.dfilt_sync_status()
+    if status != 0:
+        raise RuntimeError(f"device status {dfilt.STATUS[status]}")
+    import oracle
+    k = 4096
+    hx, hy = xd[:2, :k].double().cpu().numpy(), yd[:2, :k].double().cpu().numpy()
+    ref = oracle.forward_tv(hx, bv[:2, :k].astype(np.float64), av[:2, :k].astype(np.float64),
+                            ypd[:2].double().cpu().numpy())
+    out = {"workload": f"parameter-varying biquads, {B} x {T}, fwd + bwd", "value": B * T * world / (ms / 1e3) / 1e9,
+           "unit": "Gsamples/s", "ms_per_step": ms, "calls": ns,
+           "algorithmic_bytes": 84.0 * B * T,
+           "roofline_frac": 84.0 * B * T / (ms / 1e3) / 1e9 / hbm, "peak": hbm, "peak_source": src,
+           "rel_err_vs_fp64_first_4096_samples": float((np.abs(hy - ref).max(1) / np.abs(ref).max(1)).max())}
+    del xd, gyd, yd, gxd, gbd, gad, w1, w2, ad, bd
+    torch.cuda.empty_cache()
     return out
 
 

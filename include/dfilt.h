@@ -337,6 +337,36 @@ dfilt_status dfilt_ss_backward(const float *A, const float *v0, const float *v, 
                                int64_t B, int64_t T, int M, void *stream);
 
 /*
+ * Parameter-varying direct form (Sec. 5: the derivation extends to coefficients that
+ * change over time).  Reading: each output sample n has its own coefficients, as the
+ * difference equation of Eq. rtf written per sample,
+ *     y[n] = sum_{k=0..N} b[n][k] x[n-k] - sum_{k=1..M} a[n][k-1] y[n-k],
+ * with x[n < 0] = 0 and past outputs y[-1-j] = ypast[j].  The backward takes each
+ * coefficient at the output it produced:
+ *     u[n] = gy[n] - sum_{k=1..M} a[n+k][k-1] u[n+k],   u[n >= T] = 0
+ *     grad_x[n] = sum_k b[n+k][k] u[n+k],   grad_b[n][k] = u[n] x[n-k],
+ *     grad_a[n][k-1] = -u[n] y[n-k] (ypast before n = 0),
+ *     grad_ypast[j] = -sum_{k=j+1..M} a[k-1-j][k-1] u[k-1-j].
+ *   x, y, gy, gx   [B,T]
+ *   b, gb          [B,T,N+1]   per-sample numerators (row n: b[n][0..N])
+ *   a, ga          [B,T,M]     per-sample denominators a_1..a_M (a_0 = 1)
+ *   ypast, gypast  [B,M]       y[-1], ..., y[-M]; ypast NULL = zero
+ *   gx, gb, ga, gypast may each be NULL (not wanted)
+ *   ws, ws_bytes   workspace of at least dfilt_tv_workspace_size bytes, 16-byte aligned
+ * 1 <= M <= 4 (DFILT_ERR_UNSUPPORTED above), 0 <= N <= M.  FP32 arithmetic: a chunked
+ * scan over the per-step companion matrices, the runs of steps combined by the paper's
+ * associative operator (Sec. 3.2) with a different A per step.
+ */
+dfilt_status dfilt_tv_workspace_size(int64_t B, int64_t T, int N, int M, size_t *ws_bytes);
+dfilt_status dfilt_tv_forward(const float *x, const float *b, const float *a, const float *ypast,
+                              float *y, void *ws, size_t ws_bytes, int64_t B, int64_t T, int N,
+                              int M, void *stream);
+dfilt_status dfilt_tv_backward(const float *gy, const float *x, const float *y, const float *b,
+                               const float *a, const float *ypast, float *gx, float *gb,
+                               float *ga, float *gypast, void *ws, size_t ws_bytes, int64_t B,
+                               int64_t T, int N, int M, void *stream);
+
+/*
  * The same recurrence with A given by its eigendecomposition, A = V diag(lam) V^-1 (the
  * paper's Diag-EXT, Sec. 3.2 and Sec. 4; applicable when A is diagonalisable): the
  * state in the eigenbasis q = V^-1 v evolves element by element,

@@ -21,7 +21,7 @@ HI_BUCKETS = [8, 16, 32, 64]   # the decoupled high-order path
 # (object name, source, extra defines): the chunked kernels compile once per state bucket
 UNITS = ([("api", "api.cu", []), ("seq", "seq.cu", []), ("chunk_setup", "chunk_setup.cu", []),
           ("chunk_dispatch", "chunk_dispatch.cu", []), ("noalloc", "noalloc.cu", []),
-          ("jvp", "jvp.cu", []), ("ss", "ss.cu", []), ("diag", "diag.cu", []),
+          ("jvp", "jvp.cu", []), ("ss", "ss.cu", []), ("diag", "diag.cu", []), ("tv", "tv.cu", []),
           ("ic", "ic.cu", [])]
          + [(f"chunk_fwd_{m}", "chunk_fwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS]
          + [(f"chunk_bwd_{m}", "chunk_bwd.cu", [f"-DDFILT_MB={m}"]) for m in BUCKETS]

@@ -33,7 +33,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_jvp", "dfilt_ss_workspace_size", "dfilt_ss_forward", "dfilt_ss_backward",
            "dfilt_ic_df1", "dfilt_ic_df1_backward", "dfilt_kernel_timing_read_classes",
            "dfilt_launch_count", "dfilt_tuning_set", "dfilt_tuning_get",
-           "dfilt_diag_workspace_size", "dfilt_diag_forward", "dfilt_diag_backward"]
+           "dfilt_diag_workspace_size", "dfilt_diag_forward", "dfilt_diag_backward",
+           "dfilt_tv_workspace_size", "dfilt_tv_forward", "dfilt_tv_backward"]
 
 
 class DfiltError(RuntimeError):
@@ -107,6 +108,10 @@ def lib():
             L.dfilt_diag_workspace_size.argtypes = [i64, i64, i32, Psz, Psz]
             L.dfilt_diag_forward.argtypes = [P, P, P, P, P, P, P, sz, i64, i64, i32, P]
             L.dfilt_diag_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32, P]
+            L.dfilt_tv_workspace_size.argtypes = [i64, i64, i32, i32, Psz]
+            L.dfilt_tv_forward.argtypes = [P, P, P, P, P, P, sz, i64, i64, i32, i32, P]
+            L.dfilt_tv_backward.argtypes = [P, P, P, P, P, P, P, P, P, P, P, sz, i64, i64, i32,
+                                            i32, P]
             L.dfilt_ic_df1.argtypes = [P, P, P, P, P, i64, i32, i32, P]
             L.dfilt_ic_df1_backward.argtypes = [P, P, P, P, P, P, P, P, P, i64, i32, i32, P]
             PD, PI = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
@@ -369,6 +374,46 @@ def dfilt_diag_backward(lam, V, Vinv, v0, v, gv, *, needs=(True, True), ws=None,
                                      _ptr(gA), _ptr(gv0), _ptr(gz), _ptr(ws), ws.numel(), B, T, M,
                                      _stream(stream)), "dfilt_diag_backward")
     return gA, gv0, gz
+
+
+def dfilt_tv_workspace_size(B, T, N, M):
+    w = ctypes.c_size_t()
+    _check(lib().dfilt_tv_workspace_size(B, T, N, M, ctypes.byref(w)), "dfilt_tv_workspace_size")
+    return w.value
+
+
+def dfilt_tv_forward(x, b, a, ypast=None, *, y=None, ws=None, stream=None):
+    """Parameter-varying direct form: x [B,T], b [B,T,N+1], a [B,T,M] (coefficients of each
+    output sample), ypast [B,M] (y[-1], ..., y[-M]) or None -> y [B,T]."""
+    x, b, a, ypast = _f32(x, "x"), _f32(b, "b"), _f32(a, "a"), _f32(ypast, "ypast")
+    B, T = x.shape
+    N, M = b.shape[2] - 1, a.shape[2]
+    nws = dfilt_tv_workspace_size(B, T, N, M)
+    y = torch.empty_like(x) if y is None else y
+    ws = _buf(nws, x.device) if ws is None else ws
+    _check(lib().dfilt_tv_forward(_ptr(x), _ptr(b), _ptr(a), _ptr(ypast), _ptr(y), _ptr(ws),
+                                  ws.numel(), B, T, N, M, _stream(stream)), "dfilt_tv_forward")
+    return y
+
+
+def dfilt_tv_backward(gy, x, y, b, a, ypast=None, *, needs=(True, True, True, True), ws=None,
+                      stream=None):
+    """(grad_x, grad_b, grad_a, grad_ypast) of dfilt_tv_forward; `needs` selects them
+    (None where not wanted)."""
+    gy, x, y = _f32(gy, "gy"), _f32(x, "x"), _f32(y, "y")
+    b, a, ypast = _f32(b, "b"), _f32(a, "a"), _f32(ypast, "ypast")
+    B, T = gy.shape
+    N, M = b.shape[2] - 1, a.shape[2]
+    nws = dfilt_tv_workspace_size(B, T, N, M)
+    gx = torch.empty_like(gy) if needs[0] else None
+    gb = torch.empty_like(b) if needs[1] else None
+    ga = torch.empty_like(a) if needs[2] else None
+    gyp = torch.empty((B, M), dtype=torch.float32, device=gy.device) if needs[3] else None
+    ws = _buf(nws, gy.device) if ws is None else ws
+    _check(lib().dfilt_tv_backward(_ptr(gy), _ptr(x), _ptr(y), _ptr(b), _ptr(a), _ptr(ypast),
+                                   _ptr(gx), _ptr(gb), _ptr(ga), _ptr(gyp), _ptr(ws), ws.numel(),
+                                   B, T, N, M, _stream(stream)), "dfilt_tv_backward")
+    return gx, gb, ga, gyp
 
 
 def dfilt_ic_df1(b, a, xpast, ypast, *, zi=None, stream=None):

@@ -141,6 +141,21 @@ def test_diag_host_checks(L):
                                 None) == 1    # complex arrays must be 8-byte aligned
 
 
+def test_tv_host_checks(L):
+    """Parameter-varying filter: workspace sizes and argument errors decided on the host."""
+    assert dfilt.dfilt_tv_workspace_size(8, 4096, 2, 2) > 0
+    sz = ctypes.c_size_t()
+    assert L.dfilt_tv_workspace_size(4, 10, 2, 5, ctypes.byref(sz)) == 2     # M > 4
+    assert L.dfilt_tv_workspace_size(4, 10, 3, 2, ctypes.byref(sz)) == 1     # N > M
+    assert L.dfilt_tv_workspace_size(4, 10, 0, 0, ctypes.byref(sz)) == 1
+    assert L.dfilt_tv_forward(None, None, None, None, None, None, 0, 4, 10, 2, 2, None) == 1
+    assert L.dfilt_tv_forward(None, None, None, None, None, None, 0, 0, 10, 2, 2, None) == 0
+    fake = ctypes.c_void_p(4096)
+    assert L.dfilt_tv_forward(fake, fake, fake, None, fake, fake, 16, 4, 10, 2, 2, None) == 6
+    assert L.dfilt_tv_backward(None, None, None, None, None, None, None, None, None, None, None,
+                               0, 4, 10, 2, 2, None) == 1
+
+
 def test_ic_df1_host_checks(L):
     """Direct-form initial conditions: argument errors and the empty batch on the host."""
     assert L.dfilt_ic_df1(None, None, None, None, None, 4, 2, 65, None) == 2
