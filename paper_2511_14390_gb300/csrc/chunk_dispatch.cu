@@ -18,7 +18,8 @@ namespace dfilt {
     extern template cudaError_t hi_reduce<V>(const HiArgs &, const Batch &, cudaStream_t);        \
     extern template cudaError_t hi_epass<V>(const HiArgs &, const Batch &, bool, int, cudaStream_t); \
     extern template cudaError_t hi_yfix<V>(const HiArgs &, const Batch &, int64_t, cudaStream_t);    \
-    extern template cudaError_t hi_ufix<V>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
+    extern template cudaError_t hi_ufix<V>(const HiArgs &, const Batch &, int64_t, cudaStream_t);    \
+    extern template cudaError_t hi_lag<V>(const HiArgs &, const Batch &, int, cudaStream_t);
 DFILT_HI_BUCKETS(DFILT_HI_EXTERN)
 #undef DFILT_HI_EXTERN
 
@@ -150,6 +151,7 @@ static bool hi_eligible(const ChunkLayout &l, const HiOpt &ho) {
 struct HiWs {
     size_t ctl = 0, pref = 0, pos = 0, jump = 0, flags = 0, incl = 0, sprime = 0, ybuf = 0, partial = 0;
     size_t entry_b = 0, span_part = 0;   // backward: adjoint span entry states, their lag sums
+    size_t ubuf = 0;                     // backward: the U pass's adjoint u (total floats)
     size_t end = 0;
     size_t ctl_bytes = 0;   // the block cleared once per call (counters)
     int nhi = 0, mbmax = 0;
@@ -172,8 +174,8 @@ static HiWs hi_ws(size_t base, const ChunkPlan &p, int64_t B, int64_t total, int
     h.items_bound = total / kTileSamples + B + 1;
     size_t o = al256(base);
     h.ctl = o;
-    h.ctl_bytes = 256;
-    o += 256;
+    h.ctl_bytes = al256((size_t)h.nhi * 8 * sizeof(unsigned long long));   // 8 per bucket
+    o += h.ctl_bytes;
     h.pref = o;
     o += al256((size_t)h.nhi * 2 * (B + 1) * sizeof(int64_t));
     h.pos = o;
@@ -195,6 +197,8 @@ static HiWs hi_ws(size_t base, const ChunkPlan &p, int64_t B, int64_t total, int
         o += al256((size_t)h.items_bound * Mstride * 8);
         h.span_part = o;
         o += al256((size_t)h.items_bound * (2 * h.mbmax + 1) * 4);
+        h.ubuf = o;
+        o += al256((size_t)total * 4);
     }
     h.end = o;
     return h;
@@ -483,7 +487,7 @@ cudaError_t launch_chunk_fwd(const float *x, const float *b, const float *a, con
             hi_plan_ptrs(h, w, hw, hj, bt.B, stl);
             const HiSaved sv = hi_saved(bt.B, bt.total, Mmax, p, hw);
             hi_saved_ptrs(h, reinterpret_cast<char *>(saved), sv, hw, hj, Mmax);
-            auto *ctl = reinterpret_cast<unsigned long long *>(w + hw.ctl) + 4 * hj;
+            auto *ctl = reinterpret_cast<unsigned long long *>(w + hw.ctl) + 8 * hj;
             ++hj;
             e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
                 constexpr int V = decltype(mbc)::value;
@@ -599,7 +603,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
             h.plan.list_range = bb[j].list_range;
             const int stl = hi_span_tiles(MB, bt.B, bt.total, ragged, num_sms, ho);
             hi_plan_ptrs(h, wsc, hw, hj, bt.B, stl);
-            auto *ctl = reinterpret_cast<unsigned long long *>(wsc + hw.ctl) + 4 * hj;
+            auto *ctl = reinterpret_cast<unsigned long long *>(wsc + hw.ctl) + 8 * hj;
             ++hj;
             float *sprime = reinterpret_cast<float *>(wsc + hw.sprime);
             float *ybuf = reinterpret_cast<float *>(wsc + hw.ybuf);
@@ -611,6 +615,7 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
             h.entry = reinterpret_cast<float2 *>(wsc + hw.entry_b);
             h.span_part = reinterpret_cast<float *>(wsc + hw.span_part);
             h.bcoef = b;
+            h.ubuf = reinterpret_cast<float *>(wsc + hw.ubuf);
             e = hi_switch(MB, [&](auto mbc) -> cudaError_t {
                 constexpr int V = decltype(mbc)::value;
                 using Tab = ChunkTab<V>;
@@ -661,7 +666,10 @@ cudaError_t launch_chunk_bwd(const float *gy, const float *x, const float *y, co
                 q.out = gx;
                 q.counter = ctl + 3;
                 timing_mark(kTimeUPass, 0, st);
-                r = hi_tc<V>(q, bb[j], hi::kU, num_sms, st);   // grad_x, lag sums per tile
+                r = hi_tc<V>(q, bb[j], hi::kU, num_sms, st);   // grad_x, u
+                if (r != cudaSuccess) return r;
+                q.counter = ctl + 4;
+                r = hi_lag<V>(q, bb[j], num_sms, st);   // lag sums per tile
                 if (r != cudaSuccess) return r;
                 r = hi_ufix<V>(q, bb[j], hw.items_bound, st);   // adjoint span entries
                 if (r != cudaSuccess) return r;

@@ -15,9 +15,10 @@
 //             scan       S'_{c-1} = Abar' S'_c + E'_c from the end (S'_{C-1} = 0);
 //                        the last state is u[0:MB] = grad_zi
 //             (Y pass)   y recomputed from the forward's states when not given
-//             U pass     U_c = T_h^a G_c + O^u S'_c (tensor cores); then per chunk
-//                        grad_x = sum_k b_k u[n+k] and the lag sums of grad_b,
-//                        grad_a on the CUDA cores, one partial per tile
+//             U pass     U_c = T_h^a G_c + O^u S'_c and grad_x = T_g^a G_c + O^gx S'_c
+//                        (tensor cores, free responses in FP32), u written out
+//             lag sums   grad_b / grad_a lag sums per tile from u, x, y and S' (CUDA
+//                        cores, exact lag blocks), one partial per tile
 //             reduce     per channel, the tile partials summed in tile order (FP64)
 //
 // Look-back (the paper's associative operator applied to spans).  Work items are
@@ -140,6 +141,8 @@ struct HiArgs {
                             // in time order, adjoint spans in processing order)
     float *span_part;       // adjoint: per span, the correction's lag sums (nacc floats)
     const float *bcoef;     // adjoint correction: numerators b[B, Nstride]
+    float *ubuf;            // U pass: the zero-start adjoint u it writes (like x), read by
+                            // the lag-sum kernel
 };
 template <int MB>
 cudaError_t hi_plan(const HiArgs &h, const Batch &bt, cudaStream_t st);
@@ -157,5 +160,7 @@ template <int MB>
 cudaError_t hi_yfix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st);
 template <int MB>
 cudaError_t hi_ufix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaStream_t st);
+template <int MB>
+cudaError_t hi_lag(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st);
 
 }  // namespace dfilt

@@ -698,6 +698,148 @@ __global__ void __launch_bounds__(kChunks) hi_e_kernel(HiArgs h, Batch bt, int s
 }
 
 // ---------------------------------------------------------------------------
+// Lag sums of the coefficient gradients per tile, from the U pass's zero-start adjoint u
+// (adjoint correction: hi_ufix_kernel):  b-lag k = sum_n u_ext[n + k] x[n] (k = 0..N),
+// a-lag k = sum_n u_ext[n + k] y[n] (k = 1..M), per 64-sample chunk row with the row's
+// extension u_ext[64 + m] = S'_c[m] (the adjoint chunk state: the next chunk's first
+// values from the same span).  A tile is taken in two halves of 64 rows staged in shared
+// memory (rows padded to odd strides); thread = (row, block of 16 lags) for the blocks
+// the channel's orders need, the 16 products of a sample from a sliding register window
+// over u, both halves accumulated per thread; warp trees over the 32 rows of a warp and
+// the two warps of a block in a fixed order give the tile's partial (the same layout as
+// before: b-lags at 0..MB, a-lag k at MB + k).
+// ---------------------------------------------------------------------------
+template <int MB>
+struct LagSmem {
+    static constexpr int UROW = kL + MB + 16 + 1;   // u row + tail + window slack, odd
+    static constexpr int XROW = kL + 1;
+    static constexpr int NBLK = (MB + 1 + 15) / 16 + (MB + 15) / 16;   // lag blocks, at most
+    float u[64 * UROW];
+    float x[64 * XROW];
+    float y[64 * XROW];
+    float red[NBLK][2][16];
+    long long item;
+};
+
+template <int MB>
+__global__ void __launch_bounds__(256) hi_lag_kernel(HiArgs h, Batch bt) {
+    using SM = LagSmem<MB>;
+    constexpr int NT = 256, NACC = hi::nacc<MB>();
+    constexpr int UPT = (64 * SM::NBLK + NT - 1) / NT;   // units per thread, at most
+    extern __shared__ float4 smem4[];
+    SM &sm = *reinterpret_cast<SM *>(smem4);
+    const int t = threadIdx.x, lane = t & 31;
+    const int64_t n = hi::plan_count(h.plan, bt);
+    const int64_t total = h.plan.tile_pref[n];
+    const int Ms = bt.Mstride;
+    constexpr int kRun = 1;   // no per-channel tables here: tiles one at a time balance best
+    int64_t w = 0, wend = 0;
+    for (;;) {
+        if (w >= wend) {
+            if (t == 0) sm.item = (long long)atomicAdd(h.counter, 1ull);
+            __syncthreads();
+            w = sm.item * kRun;
+            __syncthreads();
+            if (w >= total) break;
+            wend = w + kRun < total ? w + kRun : total;
+        }
+        const int64_t pos = h.plan.tile_pos[w];
+        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const Channel c = channel_of(bt, ch);
+        const int64_t tile = w - h.plan.tile_pref[pos];
+        const int64_t tstart = c.off + tile * kTileSamples;
+        const int64_t tl = c.len - tile * kTileSamples;
+        const int tlen = (int)(tl < kTileSamples ? tl : kTileSamples);
+        const int nch = (tlen + kL - 1) / kL;
+        const int64_t slot0 = c.off / kL + ch + tile * kChunks;
+        const int nbx = (c.N + 1 + 15) / 16, nby = (c.M + 15) / 16, nblk = nbx + nby;
+        const int units = 64 * nblk;
+        float acc[UPT][16];
+#pragma unroll
+        for (int q = 0; q < UPT; ++q)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[q][j] = 0.f;
+        for (int hf = 0; hf < 2 && 64 * hf < nch; ++hf) {
+            __syncthreads();   // the previous half's rows are no longer read
+            // stage rows 64 hf .. 64 hf + 63: u, x, y (zero past the tile's samples), the
+            // tail of each u row from the adjoint chunk state, zeros beyond
+            // (4-byte async copies: the rows are padded to odd strides; zero-filled)
+            const uint32_t su = smem_u32(sm.u), sx = smem_u32(sm.x), sy = smem_u32(sm.y);
+#pragma unroll 4
+            for (int e = t; e < 64 * kL; e += NT) {
+                const int r = e / kL, i = e % kL;
+                const int sidx = (64 * hf + r) * kL + i;
+                const int nb = sidx < tlen ? 4 : 0;
+                const int64_t gi = tstart + (nb ? sidx : 0);
+                cp_async4(su + 4 * (r * SM::UROW + i), h.ubuf + gi, nb);
+                cp_async4(sx + 4 * (r * SM::XROW + i), h.x + gi, nb);
+                cp_async4(sy + 4 * (r * SM::XROW + i), h.y + gi, nb);
+            }
+            for (int e = t; e < 64 * (MB + 16); e += NT) {
+                const int r = e / (MB + 16), m = e % (MB + 16);
+                const int row = 64 * hf + r;
+                const bool v = m < c.M && row < nch;
+                cp_async4(su + 4 * (r * SM::UROW + kL + m), h.states + (v ? (size_t)(slot0 + row) * Ms + m : 0),
+                          v ? 4 : 0);
+            }
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < UPT; ++q) {
+                const int uidx = t + NT * q;
+                if (uidx < units) {   // uniform over each warp (units is a multiple of 64)
+                    const int blk = uidx / 64, r = uidx % 64;
+                    const bool xb = blk < nbx;
+                    const int lag0 = xb ? 16 * blk : 16 * (blk - nbx) + 1;
+                    const float *src = (xb ? sm.x : sm.y) + r * SM::XROW;
+                    const float *ur = sm.u + r * SM::UROW + lag0;
+                    float win[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) win[j] = ur[j];
+#pragma unroll 16
+                    for (int i = 0; i < kL; ++i) {
+                        const float v = src[i];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[q][j] = fmaf(win[j], v, acc[q][j]);
+#pragma unroll
+                        for (int j = 0; j < 15; ++j) win[j] = win[j + 1];
+                        win[15] = ur[i + 16];
+                    }
+                }
+            }
+        }
+        // per block: the 32 rows of each warp in a fixed tree, then the block's two warps
+#pragma unroll
+        for (int q = 0; q < UPT; ++q) {
+            const int uidx = t + NT * q;
+            if (uidx < units) {
+                const int blk = uidx / 64, wh = (uidx % 64) >> 5;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float v = acc[q][j];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sm.red[blk][wh][j] = v;
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = t; k < NACC; k += NT) {
+            float v = 0.f;
+            if (k <= MB) {   // b-lag k
+                if (k <= c.N) v = sm.red[k / 16][0][k % 16] + sm.red[k / 16][1][k % 16];
+            } else {         // a-lag k - MB
+                const int lg = k - MB, blk = nbx + (lg - 1) / 16, j = (lg - 1) % 16;
+                if (lg <= c.M) v = sm.red[blk][0][j] + sm.red[blk][1][j];
+            }
+            h.partial[(size_t)w * NACC + k] = v;
+        }
+        ++w;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Entry-state correction of y (forward, and the backward's recomputed y): for every
 // span s > 0 of a channel with a correction table, y[n] += sum_{m<M} P_m h[n - m] over
 // the span's first hlen + M - 1 samples (n from the span start, h[j] = 0 for j < 0 and,
@@ -1027,6 +1169,26 @@ cudaError_t hi_ufix(const HiArgs &h, const Batch &bt, int64_t items_bound, cudaS
     return cudaGetLastError();
 }
 
+template <int MB>
+cudaError_t hi_lag(const HiArgs &h, const Batch &bt, int num_sms, cudaStream_t st) {
+    using SM = LagSmem<MB>;
+    auto kern = hi_lag_kernel<MB>;
+    static int occ[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 256, sizeof(SM));
+        if (e != cudaSuccess) return e;
+        occ[dev] = o < 1 ? 1 : o;
+    }
+    kern<<<(unsigned)(num_sms * occ[dev]), 256, sizeof(SM), st>>>(h, bt); note_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t hi_plan<DFILT_MB>(const HiArgs &, const Batch &, cudaStream_t);
 template cudaError_t hi_jump<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_scan<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
@@ -1034,5 +1196,6 @@ template cudaError_t hi_reduce<DFILT_MB>(const HiArgs &, const Batch &, cudaStre
 template cudaError_t hi_epass<DFILT_MB>(const HiArgs &, const Batch &, bool, int, cudaStream_t);
 template cudaError_t hi_yfix<DFILT_MB>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
 template cudaError_t hi_ufix<DFILT_MB>(const HiArgs &, const Batch &, int64_t, cudaStream_t);
+template cudaError_t hi_lag<DFILT_MB>(const HiArgs &, const Batch &, int, cudaStream_t);
 
 }  // namespace dfilt
