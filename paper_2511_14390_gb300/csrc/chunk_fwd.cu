@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using SM = FwdSmem<MB, F64>;
     constexpr int NM = SM::NM;
     extern __shared__ char smem_raw[];
-    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    char *smem = smem_align1024(smem_raw);
     const uint32_t sbase = smem_u32(smem);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + SM::MISC);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM::MISC + 8);
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     constexpr int LA = NST - 1;          // tiles loaded ahead of the one being converted
     constexpr int RING = SM::RING;
     extern __shared__ char smem_raw[];
-    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    char *smem = smem_align1024(smem_raw);
     const uint32_t sbase = smem_u32(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::M_BAR);
     uint64_t *full = bars + 0, *load_bar = bars + 6, *mma_done = bars + 9,

@@ -101,6 +101,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The dynamic shared-memory array advanced to the next 1024-byte boundary (the repeat of
+// the 128-byte swizzle).  The step is added to the array's own address rather than
+// formed by rounding an integer, so the result still derives from a shared-memory array
+// and the compiler emits shared-memory loads and stores for every access through it
+// (a pointer rebuilt from an integer is generic: each access then goes through the
+// generic path, with its longer latency, on the long scoreboard).
+__device__ __forceinline__ char *smem_align1024(char *raw) {
+    const uint32_t s = smem_u32(raw);
+    return raw + (((s + 1023u) & ~1023u) - s);
+}
+
 // 16-byte async global->shared copy; bytes beyond src_bytes (0..16) are zero-filled.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     using SM = TcSmem<MB, MODE>;
     constexpr int N = SM::N, KTOT = SM::KTOT;
     extern __shared__ char smem_raw[];
-    char *smem = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    char *smem = smem_align1024(smem_raw);
     const uint32_t sbase = smem_u32(smem);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + SM::MISC);   // [2] A operand ready (96)
     uint64_t *mma_done = full + 2;    // [2] accumulator ready, A operand consumed (commit)
