@@ -98,6 +98,10 @@ def test_decoupled_high_radius(M):
     bound = np.maximum(1e-5, 16 * U32 * kappa(w.a, w.x.shape[1]))
     for nm in ("y", "gx", "gb", "ga", "gzi"):
         assert (e[nm] < bound).all(), (M, nm, e[nm], bound)
+    # the outputs at the sequential FP32 kernel's accuracy, channel by channel, within
+    # the spread of two rounding orders over three channels (measured ratios 0.36-2.8)
+    for nm in ("y", "gx"):
+        assert (e[nm] < np.maximum(4 * es[nm], 1e-6)).all(), (M, nm, e[nm], es[nm])
 
 
 def long_memory_filters(B, M, N, seed, r_long=0.999):

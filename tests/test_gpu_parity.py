@@ -146,7 +146,10 @@ def test_high_order_scan_precision():
     bound = 16 * U32 * kappa(w.a, w.x.shape[1])
     for nm in ("y", "gx"):
         dw_err, seq_err = errs["chunk3"][nm], errs["seq"][nm]
-        assert (dw_err < np.maximum(8 * seq_err, 1e-6)).all(), (nm, dw_err, seq_err)
+        # equal accuracy, channel by channel: both paths round in FP32 in different
+        # orders, so their errors differ by chance; a factor of two allows for that and
+        # no more (measured: the chunked errors are 0.12-0.73 of the sequential ones)
+        assert (dw_err < np.maximum(2 * seq_err, 1e-6)).all(), (nm, dw_err, seq_err)
         assert (dw_err < np.maximum(bound, 1e-5)).all(), (nm, dw_err, bound)
 
 
