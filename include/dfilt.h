@@ -54,7 +54,8 @@ typedef enum {
     DFILT_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, copy) */
     DFILT_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
     DFILT_ERR_NUMERIC = 5,       /* non-finite output (dfilt_set_numeric_check) */
-    DFILT_ERR_WORKSPACE = 6      /* ws_bytes smaller than dfilt_workspace_size asks */
+    DFILT_ERR_WORKSPACE = 6,     /* ws_bytes smaller than dfilt_workspace_size asks */
+    DFILT_ERR_BOUNDS = 7         /* debug build: a device-side index check failed */
 } dfilt_status;
 
 typedef enum {
@@ -245,6 +246,25 @@ dfilt_status dfilt_tuning_get(int state_bucket, int *span_tiles, int *chains_per
  * Applies to calls made after it on any thread of the process.
  */
 dfilt_status dfilt_set_numeric_check(int enable);
+
+/*
+ * Debug build (libdfilt_debug.so, compiled with -DDFILT_DEBUG; the paper has no
+ * counterpart).  Its decoupled-path kernels (orders 3..64: E, scan, tile, lag and
+ * correction passes) check every sample range and chunk-state slot range they derive
+ * from the channel metadata and the work plan against the buffers before touching
+ * them; a range that fails is skipped (no access) and DFILT_ERR_BOUNDS is recorded in
+ * the device status word (read by dfilt_sync_status).  Nothing traps.  The release
+ * library compiles the checks out.
+ *
+ * dfilt_debug_build: 1 in the debug library, 0 in the release library.
+ * dfilt_debug_set_limit: makes the debug checks treat every signal as at most
+ *   `samples` long (<= 0: no limit, the default), so that a test can make them fail
+ *   on valid buffers: later calls skip the tiles and spans past the limit and report
+ *   DFILT_ERR_BOUNDS, and their outputs there are undefined.  Process-wide, applies to
+ *   calls made after it.  The release library returns DFILT_ERR_UNSUPPORTED.
+ */
+int dfilt_debug_build(void);
+dfilt_status dfilt_debug_set_limit(int64_t samples);
 
 /*
  * Test hook for the bounded device-side waits (no waits are unbounded).

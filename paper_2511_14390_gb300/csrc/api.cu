@@ -23,6 +23,7 @@ int *g_status_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 long long g_wait_limit = kDefaultWaitLimit;
 int g_stall_drill = 0;
+long long g_dbg_limit = 0;   // debug build: sample bound of the index checks (0: none)
 bool g_numeric_check = false;
 
 // NVTX range around an entry point (header-only NVTX: a no-op unless a profiler
@@ -165,6 +166,7 @@ Batch make_batch(const DevInfo &di, const int64_t *offsets, const int *Ms, const
         std::lock_guard<std::mutex> lk(g_mu);
         bt.wait_limit = g_wait_limit;
         bt.stall_drill = g_stall_drill;
+        bt.dbg_limit = g_dbg_limit > 0 && g_dbg_limit < total ? g_dbg_limit : total;
     }
     return bt;
 }
@@ -321,6 +323,7 @@ const char *dfilt_status_string(dfilt_status s) {
         case DFILT_ERR_TIMEOUT: return "DFILT_ERR_TIMEOUT";
         case DFILT_ERR_NUMERIC: return "DFILT_ERR_NUMERIC";
         case DFILT_ERR_WORKSPACE: return "DFILT_ERR_WORKSPACE";
+        case DFILT_ERR_BOUNDS: return "DFILT_ERR_BOUNDS";
     }
     return "DFILT_ERR_UNKNOWN";
 }
@@ -534,6 +537,25 @@ dfilt_status dfilt_set_numeric_check(int enable) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_numeric_check = enable != 0;
     return DFILT_OK;
+}
+
+int dfilt_debug_build(void) {
+#ifdef DFILT_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+dfilt_status dfilt_debug_set_limit(int64_t samples) {
+#ifdef DFILT_DEBUG
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_dbg_limit = samples > 0 ? (long long)samples : 0;
+    return DFILT_OK;
+#else
+    (void)samples;
+    return DFILT_ERR_UNSUPPORTED;
+#endif
 }
 
 dfilt_status dfilt_set_wait_limit(int64_t iters) {

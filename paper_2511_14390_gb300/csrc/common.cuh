@@ -38,6 +38,7 @@ struct Batch {
     int *status;              // device status word
     long long wait_limit;     // cap on polls of any bounded wait
     int stall_drill;          // test mode: also wait on a barrier nothing signals
+    int64_t dbg_limit;        // debug build: samples the index checks allow (<= total)
     // Optional sub-list of channels for one launch (a state-order bucket of a ragged
     // batch): work item c is channel list[list_range[0] + c], c < list_range[1] -
     // list_range[0].  nullptr: work item c is channel c < B.

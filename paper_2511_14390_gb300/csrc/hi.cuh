@@ -78,10 +78,50 @@ struct Plan {
 __device__ __forceinline__ int64_t plan_count(const Plan &p, const Batch &bt) {
     return p.list ? (int64_t)(p.list_range[1] - p.list_range[0]) : bt.B;
 }
-__device__ __forceinline__ int64_t plan_channel(const Plan &p, int64_t pos) {
-    return p.list ? (int64_t)p.list[p.list_range[0] + pos] : pos;
+__device__ __forceinline__ bool dbg_channel_ok(const Batch &bt, int64_t ch);
+// The channel at a plan position.  Debug build: an index outside the batch records
+// DFILT_ERR_BOUNDS and is replaced by channel 0, so no per-channel array is read past
+// its end (the item's results are then undefined).
+__device__ __forceinline__ int64_t plan_channel(const Plan &p, int64_t pos, const Batch &bt) {
+    const int64_t ch = p.list ? (int64_t)p.list[p.list_range[0] + pos] : pos;
+    return dbg_channel_ok(bt, ch) ? ch : 0;
 }
 __device__ __forceinline__ int64_t tiles_of(int64_t len) { return (len + kTileSamples - 1) / kTileSamples; }
+
+// Debug build (-DDFILT_DEBUG): before a work item touches memory, its channel index, its
+// sample range [start, start + len) and its chunk-state slot range [slot0, slot0 + nslot)
+// are checked against the batch (B channels), the signal (at most bt.dbg_limit samples)
+// and the slots (total / L + B + 1: one per chunk plus one spare per channel).  A failed
+// check records DFILT_ERR_BOUNDS and the caller empties the item, so nothing outside the
+// buffers is read or written.  The release build compiles both checks to `true`.
+__device__ __forceinline__ bool dbg_channel_ok(const Batch &bt, int64_t ch) {
+#ifdef DFILT_DEBUG
+    const bool ok = ch >= 0 && ch < bt.B;
+    if (!ok) set_status(bt.status, DFILT_ERR_BOUNDS);
+    return ok;
+#else
+    (void)bt;
+    (void)ch;
+    return true;
+#endif
+}
+__device__ __forceinline__ bool dbg_range_ok(const Batch &bt, int64_t start, int64_t len, int64_t slot0,
+                                             int64_t nslot) {
+#ifdef DFILT_DEBUG
+    const int64_t slots = bt.total / kL + bt.B + 1;
+    const bool ok = start >= 0 && len >= 0 && start + len <= bt.dbg_limit && slot0 >= 0 && nslot >= 0 &&
+                    slot0 + nslot <= slots;
+    if (!ok) set_status(bt.status, DFILT_ERR_BOUNDS);
+    return ok;
+#else
+    (void)bt;
+    (void)start;
+    (void)len;
+    (void)slot0;
+    (void)nslot;
+    return true;
+#endif
+}
 
 // Loads without the (incoherent) L1: data another SM published in this launch.
 __device__ __forceinline__ float2 ld_cg2(const float2 *p) { return __ldcg(p); }

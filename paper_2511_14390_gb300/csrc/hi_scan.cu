@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(1024) hi_plan_kernel(Plan p, Batch bt) {
         const int64_t i = base + t;
         long long nt = 0, ns = 0;
         if (i < n) {
-            const Channel c = channel_of(bt, hi::plan_channel(p, i));
+            const Channel c = channel_of(bt, hi::plan_channel(p, i, bt));
             nt = hi::tiles_of(c.len);
             ns = (nt + p.span_tiles - 1) >> p.log2_span;
         }
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
     };
     const int64_t pos = blockIdx.x;
     if (pos >= hi::plan_count(h.plan, bt)) return;
-    const int64_t ch = hi::plan_channel(h.plan, pos);
+    const int64_t ch = hi::plan_channel(h.plan, pos, bt);
     const Channel c = channel_of(bt, ch);
     if (hi::tiles_of(c.len) <= h.plan.span_tiles) return;   // one span: no jump needed
     const int64_t K = (int64_t)kChunks << h.plan.log2_span;
@@ -343,15 +343,19 @@ __global__ void __launch_bounds__(MB *TPR) hi_scan_kernel(HiArgs h, Batch bt) {
         sync();   // info[] is rewritten below
         if (w >= total) break;
         const int64_t pos = h.plan.span_pos[w];
-        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int64_t ch = hi::plan_channel(h.plan, pos, bt);
         const Channel c = channel_of(bt, ch);
         const int64_t s = w - h.plan.span_pref[pos];
         const int64_t nsp = h.plan.span_pref[pos + 1] - h.plan.span_pref[pos];
         const int64_t nchunks = (c.len + kL - 1) / kL;
         const int64_t sp = REV ? nsp - 1 - s : s;   // the span's index in time
         const int64_t k0 = sp * ST * kChunks;       // the span's chunks [k0, k1)
-        const int64_t k1 = (k0 + (int64_t)ST * kChunks < nchunks) ? k0 + (int64_t)ST * kChunks : nchunks;
+        int64_t k1 = (k0 + (int64_t)ST * kChunks < nchunks) ? k0 + (int64_t)ST * kChunks : nchunks;
         const int64_t cbase = c.off / kL + ch;       // the channel's first chunk slot
+        {   // debug build: a span that fails its index checks scans no chunk
+            const int64_t n0 = c.off + k0 * kL, n1 = c.off + (k1 * kL < c.len ? k1 * kL : c.len);
+            if (!hi::dbg_range_ok(bt, n0, n1 - n0, cbase + k0, k1 - k0)) k1 = k0;
+        }
         if (ch != cur_ch) {
             const float2 *At = reinterpret_cast<const float2 *>(h.tabs + (size_t)ch * h.tab_stride +
                                                                 (REV ? Tab::B_SCAN : Tab::F_SCAN));
@@ -597,12 +601,15 @@ __global__ void __launch_bounds__(kChunks) hi_e_kernel(HiArgs h, Batch bt, int s
     bool pre = false;   // this tile already in flight (copied during the previous one)
     auto tile_of = [&](int64_t wi, int64_t &ch, Channel &c, int64_t &tstart, int &tlen) {
         const int64_t pos = h.plan.tile_pos[wi];
-        ch = hi::plan_channel(h.plan, pos);
+        ch = hi::plan_channel(h.plan, pos, bt);
         c = channel_of(bt, ch);
         const int64_t tile = wi - h.plan.tile_pref[pos];
         tstart = c.off + tile * kTileSamples;
         const int64_t tl = c.len - tile * kTileSamples;
         tlen = (int)(tl < kTileSamples ? tl : kTileSamples);
+        // debug build: a tile that fails its index checks is empty
+        if (!hi::dbg_range_ok(bt, tstart, tlen, c.off / kL + ch + (tstart - c.off) / kL, (tlen + kL - 1) / kL))
+            tlen = 0;
     };
     for (;;) {
         if (w >= wend) {
@@ -744,14 +751,19 @@ __global__ void __launch_bounds__(256) hi_lag_kernel(HiArgs h, Batch bt) {
             wend = w + kRun < total ? w + kRun : total;
         }
         const int64_t pos = h.plan.tile_pos[w];
-        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int64_t ch = hi::plan_channel(h.plan, pos, bt);
         const Channel c = channel_of(bt, ch);
         const int64_t tile = w - h.plan.tile_pref[pos];
         const int64_t tstart = c.off + tile * kTileSamples;
         const int64_t tl = c.len - tile * kTileSamples;
-        const int tlen = (int)(tl < kTileSamples ? tl : kTileSamples);
-        const int nch = (tlen + kL - 1) / kL;
+        int tlen = (int)(tl < kTileSamples ? tl : kTileSamples);
+        int nch = (tlen + kL - 1) / kL;
         const int64_t slot0 = c.off / kL + ch + tile * kChunks;
+        // debug build: a tile that fails its index checks is empty (its partial is zero)
+        if (!hi::dbg_range_ok(bt, tstart, tlen, slot0, nch)) {
+            tlen = 0;
+            nch = 0;
+        }
         const int nbx = (c.N + 1 + 15) / 16, nby = (c.M + 15) / 16, nblk = nbx + nby;
         const int units = 64 * nblk;
         float acc[UPT][16];
@@ -861,14 +873,15 @@ __global__ void __launch_bounds__(256) hi_yfix_kernel(HiArgs h, Batch bt) {
         const int64_t pos = h.plan.span_pos[w];
         const int64_t sp = w - h.plan.span_pref[pos];
         if (sp == 0) continue;
-        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int64_t ch = hi::plan_channel(h.plan, pos, bt);
         const int hl = h.hlen[ch];
         if (hl <= 0) continue;
         const Channel c = channel_of(bt, ch);
         const int64_t s0 = sp * span_len;
         const int64_t slen = c.len - s0 < span_len ? c.len - s0 : span_len;
         const int64_t want = (int64_t)hl + c.M - 1;
-        const int64_t rlen = want < slen ? want : slen;
+        int64_t rlen = want < slen ? want : slen;
+        if (!hi::dbg_range_ok(bt, c.off + s0, rlen, 0, 0)) rlen = 0;   // debug build: skip
         __syncthreads();   // the previous span's P and h are no longer read
         if (t < MB) P[t] = t < c.M ? h.entry[(size_t)w * bt.Mstride + t] : make_float2(0.f, 0.f);
         const float2 *hc = h.htab + (size_t)ch * h.tcap;
@@ -927,14 +940,15 @@ __global__ void __launch_bounds__(256) hi_ufix_kernel(HiArgs h, Batch bt) {
         const int64_t pos = h.plan.span_pos[w];
         const int64_t s = w - h.plan.span_pref[pos];   // processing index (last in time first)
         if (s == 0) continue;
-        const int64_t ch = hi::plan_channel(h.plan, pos);
+        const int64_t ch = hi::plan_channel(h.plan, pos, bt);
         const int hl = h.hlen[ch];
         if (hl <= 0) continue;
         const Channel c = channel_of(bt, ch);
         const int64_t nsp = h.plan.span_pref[pos + 1] - h.plan.span_pref[pos];
         const int64_t end = (nsp - s) * span_len;       // a full span ends here
         const int64_t want = (int64_t)hl + 3 * MB;
-        const int64_t R = want < span_len ? want : span_len;
+        int64_t R = want < span_len ? want : span_len;
+        if (!hi::dbg_range_ok(bt, c.off + end - R, R, 0, 0)) R = 0;   // debug build: skip
         __syncthreads();   // the previous span's shared data is no longer read
         if (t < MB) P[t] = t < c.M ? h.entry[(size_t)w * bt.Mstride + t] : make_float2(0.f, 0.f);
         __syncthreads();
@@ -1028,7 +1042,7 @@ __global__ void __launch_bounds__(128) hi_reduce_kernel(HiArgs h, Batch bt) {
     const int lane = threadIdx.x & 31;
     const int64_t pos = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
     if (pos >= hi::plan_count(h.plan, bt)) return;
-    const int64_t ch = hi::plan_channel(h.plan, pos);
+    const int64_t ch = hi::plan_channel(h.plan, pos, bt);
     const Channel c = channel_of(bt, ch);
     const int64_t tb = h.plan.tile_pref[pos], nt = h.plan.tile_pref[pos + 1] - tb;
     // spans corrected by hi_ufix (processing index >= 1 of channels with a table)

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the tile's position (tiles of one channel are consecutive)
             if (w != w_prev + 1 || pos < 0 || w >= h.plan.tile_pref[pos + 1]) {
                 pos = h.plan.tile_pos[w];
-                ch = hi::plan_channel(h.plan, pos);
+                ch = hi::plan_channel(h.plan, pos, bt);
                 c = channel_of(bt, ch);
             }
             w_prev = w;
@@ -383,6 +383,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             d.flags = (ch != ch1 ? kNewB : 0) | (ch != ch2 ? kNewOT : 0);
             ch2 = ch1;
             ch1 = ch;
+            // debug build: a tile that fails its index checks becomes empty (no sample or
+            // state is read or written)
+            if (!hi::dbg_range_ok(bt, d.tstart, d.tlen, d.slot0, d.nch)) {
+                d.tlen = 0;
+                d.nch = 0;
+            }
             // one staging buffer: convert the previous tile before refilling it
             if (NRAW == 1 && k >= 1 && !finish(k - 1, dprev, true)) {
                 ok = false;

@@ -95,6 +95,7 @@ extern "C" dfilt_status dfilt_forward_noalloc(const float *x, const float *b, co
     bt.status = status;
     bt.wait_limit = wait_limit;
     bt.stall_drill = drill;
+    bt.dbg_limit = B * T;
     bt.list = nullptr;
     bt.list_range = nullptr;
     bt.fwd_stride = 0;

@@ -18,13 +18,15 @@ import threading
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdfilt.so")
+# DFILT_LIBRARY=debug loads the debug build (device-side index checks, build.py --debug)
+LIB_PATH = os.path.join(_HERE, "libdfilt_debug.so" if os.environ.get("DFILT_LIBRARY") == "debug"
+                        else "libdfilt.so")
 
 ALGOS = {"auto": 0, "sequential": 1, "chunked": 2}
 PRECISIONS = {"fp32": 0, "tf32": 1, "tf32x3": 3}
 STATUS = {0: "DFILT_OK", 1: "DFILT_ERR_INVALID_ARG", 2: "DFILT_ERR_UNSUPPORTED",
           3: "DFILT_ERR_CUDA", 4: "DFILT_ERR_TIMEOUT", 5: "DFILT_ERR_NUMERIC",
-          6: "DFILT_ERR_WORKSPACE"}
+          6: "DFILT_ERR_WORKSPACE", 7: "DFILT_ERR_BOUNDS"}
 EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_workspace_size",
            "dfilt_forward", "dfilt_backward", "dfilt_workspace_size_ragged",
            "dfilt_forward_ragged", "dfilt_backward_ragged", "dfilt_sync_status",
@@ -34,7 +36,8 @@ EXPORTS = ["dfilt_version", "dfilt_status_string", "dfilt_default_opts", "dfilt_
            "dfilt_ic_df1", "dfilt_ic_df1_backward", "dfilt_kernel_timing_read_classes",
            "dfilt_launch_count", "dfilt_tuning_set", "dfilt_tuning_get",
            "dfilt_diag_workspace_size", "dfilt_diag_forward", "dfilt_diag_backward",
-           "dfilt_tv_workspace_size", "dfilt_tv_forward", "dfilt_tv_backward"]
+           "dfilt_tv_workspace_size", "dfilt_tv_forward", "dfilt_tv_backward",
+           "dfilt_debug_build", "dfilt_debug_set_limit"]
 
 
 class DfiltError(RuntimeError):
@@ -97,6 +100,8 @@ def lib():
                                                 i64, i64, i32, i32, PO, P]
             L.dfilt_sync_status.argtypes = [P]
             L.dfilt_set_wait_limit.argtypes = [i64]
+            L.dfilt_debug_build.restype = i32
+            L.dfilt_debug_set_limit.argtypes = [i64]
             L.dfilt_set_numeric_check.argtypes = [i32]
             L.dfilt_forward_noalloc.argtypes = [P, P, P, P, P, i64, i64, i32, i32, PO, P]
             L.dfilt_kernel_timing.argtypes = [i32]
@@ -450,6 +455,17 @@ def dfilt_sync_status(stream=None) -> int:
 
 def dfilt_set_wait_limit(iters: int):
     _check(lib().dfilt_set_wait_limit(int(iters)), "dfilt_set_wait_limit")
+
+
+def dfilt_debug_build() -> bool:
+    """True when the loaded library is the debug build (device-side index checks)."""
+    return bool(lib().dfilt_debug_build())
+
+
+def dfilt_debug_set_limit(samples: int):
+    """Debug build only: the index checks treat every signal as at most `samples` long
+    (<= 0: no limit); later calls skip the work past it and report DFILT_ERR_BOUNDS."""
+    _check(lib().dfilt_debug_set_limit(int(samples)), "dfilt_debug_set_limit")
 
 
 def dfilt_set_numeric_check(enable: bool):

@@ -185,3 +185,25 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(dfilt, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         dfilt.lib()
+
+
+def test_debug_entry_points_in_release(L):
+    """The release library compiles the device-side index checks out: it says so, and
+    refuses the debug limit."""
+    assert L.dfilt_debug_build() == 0
+    assert L.dfilt_debug_set_limit(ctypes.c_int64(1000)) == 2   # DFILT_ERR_UNSUPPORTED
+    assert L.dfilt_status_string(7) == b"DFILT_ERR_BOUNDS"
+
+
+def test_debug_library_builds_and_exports():
+    """build.py --debug links libdfilt_debug.so (the checked units recompiled with
+    -DDFILT_DEBUG); it loads without a GPU, exports every declared symbol, reports
+    itself as the debug build and accepts the limit."""
+    path = pkg_build.build_debug()
+    D = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(D, s), s
+    D.dfilt_debug_set_limit.argtypes = [ctypes.c_int64]
+    assert D.dfilt_debug_build() == 1
+    assert D.dfilt_debug_set_limit(1000) == 0
+    assert D.dfilt_debug_set_limit(0) == 0
