@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(MB *TPR) hi_jump_kernel(HiArgs h, Batch bt, in
     //    (the free response of the impulse's state entering chunk c, double words) goes
     //    into the table until ||S_c||_1 <= 2^-40, from where on every |h[n]| <= 2^-40
     //    max|h| (h[64c + n] = sum_m S_c[m] h[n - m]).
-    // (state bucket 64 rescans: at M = 64 the corrections' double-word sums, about 2M + N
-    // terms per sample of a region, plus this table cost more than the rescans they save,
-    // measured on the order-64 workload; up to M = 32 they save about half the scan time)
-    const bool tab = !bwd && MB <= 32 && h.htab != nullptr && h.tcap > 0;
+    // (every state bucket: the corrections' double-word sums, about 2M + N terms per
+    // sample of a region, cost in proportion to the number of spans, the rescans they
+    // replace in proportion to the samples; with spans long enough for the impulse
+    // response to decay within half of one, they save the second pass over every span)
+    const bool tab = !bwd && h.htab != nullptr && h.tcap > 0;
     const int64_t tchunks = tab ? ((int64_t)h.tcap / kL < K ? (int64_t)h.tcap / kL : K) : 0;
     float2 *ht = tab ? h.htab + (size_t)ch * h.tcap : nullptr;
     int64_t hz = -1;   // first chunk whose entering state is below the bound
@@ -893,20 +894,30 @@ __global__ void __launch_bounds__(256) hi_yfix_kernel(HiArgs h, Batch bt) {
                 hs[i] = (j >= 0 && j < hl) ? hc[j] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-#pragma unroll 1
-            for (int q = 0; q < kBlk / 256; ++q) {
-                const int i = t + 256 * q;
-                if (b0 + i < rlen) {
-                    float hh = 0.f, ll = 0.f;
+            // the thread's four samples t + 256 q as four independent chains (each
+            // sample still sums its terms in the order m = 0, 1, ...)
+            constexpr int Q = kBlk / 256;
+            float hh[Q], ll[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                hh[q] = 0.f;
+                ll[q] = 0.f;
+            }
 #pragma unroll 4
-                    for (int m = 0; m < MB; ++m) {
-                        if (m < c.M) {
-                            const float2 hv = hs[i + MB - 1 - m];
-                            pipe::dw_acc(hh, ll, P[m], hv.x, hv.y);
-                        }
+            for (int m = 0; m < MB; ++m) {
+                if (m < c.M) {
+                    const float2 pm = P[m];
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const float2 hv = hs[t + 256 * q + MB - 1 - m];
+                        pipe::dw_acc(hh[q], ll[q], pm, hv.x, hv.y);
                     }
-                    yp[b0 + i] += hh + ll;
                 }
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int i = t + 256 * q;
+                if (b0 + i < rlen) yp[b0 + i] += hh[q] + ll[q];
             }
         }
     }
@@ -974,33 +985,61 @@ __global__ void __launch_bounds__(256) hi_ufix_kernel(HiArgs h, Batch bt) {
                 hs[q] = (j >= 0 && j < hl) ? hc[j] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            // v over this block into vs[cur][MB + q]
-            for (int q = t; q < kBlk; q += NT) {
-                float hh = 0.f, ll = 0.f;
-                if (b0 + q < R) {
+            // v over this block into vs[cur][MB + q]: the thread's four samples q = t + NT e
+            // as four independent chains (each sums in the order j = 0, 1, ...)
+            constexpr int Q = kBlk / NT;
+            {
+                float hh[Q], ll[Q];
+#pragma unroll
+                for (int e = 0; e < Q; ++e) {
+                    hh[e] = 0.f;
+                    ll[e] = 0.f;
+                }
 #pragma unroll 4
-                    for (int j = 0; j < MB; ++j) {
-                        if (j < c.M) {
-                            const float2 hv = hs[q + MB - 1 - j];
-                            pipe::dw_acc(hh, ll, W[j], hv.x, hv.y);
+                for (int j = 0; j < MB; ++j) {
+                    if (j < c.M) {
+                        const float2 wj = W[j];
+#pragma unroll
+                        for (int e = 0; e < Q; ++e) {
+                            const float2 hv = hs[t + NT * e + MB - 1 - j];
+                            pipe::dw_acc(hh[e], ll[e], wj, hv.x, hv.y);
                         }
                     }
                 }
-                const dw v = fast_two_sum(hh, ll);
-                vs[cur][MB + q] = make_float2(v.hi, v.lo);
+#pragma unroll
+                for (int e = 0; e < Q; ++e) {
+                    const int q = t + NT * e;
+                    const dw v = b0 + q < R ? fast_two_sum(hh[e], ll[e]) : dw{0.f, 0.f};
+                    vs[cur][MB + q] = make_float2(v.hi, v.lo);
+                }
             }
             __syncthreads();
-            // grad_x and the lag sums of this block's samples
-            for (int q = t; q < kBlk; q += NT) {
+            // grad_x of this block's samples (the thread's four as independent chains, each
+            // in the order k = 0, 1, ...), then the lag sums sample by sample
+            float gh[Q], gl[Q];
+#pragma unroll
+            for (int e = 0; e < Q; ++e) {
+                gh[e] = 0.f;
+                gl[e] = 0.f;
+            }
+#pragma unroll 4
+            for (int k = 0; k <= MB; ++k) {
+                if (k <= c.N) {
+                    const float2 bk = make_float2(Bk[k], 0.f);
+#pragma unroll
+                    for (int e = 0; e < Q; ++e) {
+                        const float2 vk = vs[cur][MB + t + NT * e - k];
+                        pipe::dw_acc(gh[e], gl[e], bk, vk.x, vk.y);
+                    }
+                }
+            }
+#pragma unroll 1
+            for (int e = 0; e < Q; ++e) {
+                const int q = t + NT * e;
                 const int64_t i = b0 + q;
                 if (i >= R) break;
                 const float2 *vq = &vs[cur][MB + q];   // vq[-k] = v[i - k]
-                float hh = 0.f, ll = 0.f;
-#pragma unroll 4
-                for (int k = 0; k <= MB; ++k) {
-                    if (k <= c.N) pipe::dw_acc(hh, ll, make_float2(Bk[k], 0.f), vq[-k].x, vq[-k].y);
-                }
-                if (h.out) gp[-i] += hh + ll;
+                if (h.out) gp[-i] += gh[e] + gl[e];
                 const float xv = xp[-i], yv = yp[-i];
 #pragma unroll
                 for (int k = 0; k <= MB; ++k) {
