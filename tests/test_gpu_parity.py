@@ -82,7 +82,7 @@ def check(name, mode, w, needs=(True, True, True, True), tol=None, gtol=None, no
 
 # The plain normwise bound on grad_b, grad_a, grad_zi where the workloads' conditioning
 # allows it (order 2, poles up to radius 0.95 / 0.99): the stated 1e-5 of the FP32
-# paths, in the survey's metric.
+# paths, as max_k |got - ref| / max_k |ref| per channel.
 NORM = {"seq": 1e-5, "chunk3": 1e-5, "chunk1": None, "chunk3d": 1e-5}
 
 
