@@ -196,30 +196,45 @@ def radius_bins(per_channel: dict, radius) -> dict:
     return out
 
 
-def profiled_traffic(kname, workload):
-    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kname`
-    from the committed ncu summary of this workload, scaled to one full launch; None
-    when there is no summary or the kernel source changed since it was captured."""
+def profiled_marker(tag, field, kname, workload):
+    """A figure recorded in a committed ncu summary: the `field` of the
+    `<!-- tag kernel=... workload=... field=... sources=... sha256=... -->` marker of
+    `kname` on `workload`; None when there is no summary or a source of the kernel
+    changed since the counters were taken (the recorded SHA-256 no longer matches)."""
     import glob
     import hashlib
     import re
     base = kname.split("<")[0]
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{base}_*.md"))):
         txt = open(path).read()
-        m = re.search(r"<!-- traffic kernel=(\S+) workload=(\S+) bytes_per_launch=([0-9.e+]+) "
-                      r"sources=(\S+) sha256=([0-9a-f]+) -->", txt)
-        if not m or m.group(1) != kname.replace(" ", "") or m.group(2) != workload:
-            continue
-        h = hashlib.sha256()
-        for rel in m.group(4).split(","):
-            src = os.path.join(ROOT, rel)
-            if not os.path.exists(src):
-                return None
-            h.update(open(src, "rb").read())
-        if h.hexdigest() != m.group(5):
-            return None   # stale: the kernel changed since the counters were taken
-        return float(m.group(3))
+        for m in re.finditer(r"<!-- " + tag + r" kernel=(\S+) workload=(\S+) " + field +
+                             r"=([0-9.e+-]+) sources=(\S+) sha256=([0-9a-f]+) -->", txt):
+            if m.group(1) != kname.replace(" ", "") or m.group(2) != workload:
+                continue
+            h = hashlib.sha256()
+            for rel in m.group(4).split(","):
+                src = os.path.join(ROOT, rel)
+                if not os.path.exists(src):
+                    return None
+                h.update(open(src, "rb").read())
+            if h.hexdigest() != m.group(5):
+                return None   # stale: the kernel changed since the counters were taken
+            return float(m.group(3))
     return None
+
+
+def profiled_traffic(kname, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kname`
+    from the committed ncu summary of this workload, scaled to one full launch; None
+    when there is no summary or the kernel source changed since it was captured."""
+    return profiled_marker("traffic", "bytes_per_launch", kname, workload)
+
+
+def profiled_tensor(kname, workload):
+    """Tensor-pipe activity of `kname` (sm__pipe_tensor_cycles_active, % of peak while
+    active, duration-weighted over the captured launches) from the committed ncu summary
+    of this workload; None when there is none or the sources changed."""
+    return profiled_marker("tensor", "active_pct", kname, workload)
 
 
 # ----------------------------------------------------------------------------
@@ -836,10 +851,23 @@ def main():
             "gpu_launches_note": "library kernels per step (dfilt_launch_count); the loss "
                                  "gradient is one torch elementwise op",
             "configs": configs, "jvp": jvp, "state_space": ssl, "parameter_varying": tvl,
+            "tensor_pipe": tensor_pipe(a.workload),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def tensor_pipe(workload):
+    """The tensor-core tile passes' tensor-pipe activity on this workload, from the
+    committed ncu summary (None when none matches the current sources)."""
+    pct = profiled_tensor("hi_tc_kernel", workload)
+    if pct is None:
+        return None
+    return {"kernel": "hi_tc_kernel (Y and U tile passes, every state bucket)",
+            "active_pct_of_peak": pct,
+            "source": "committed ncu summary: sm__pipe_tensor_cycles_active while active, "
+                      "duration-weighted over the captured launches"}
 
 
 def run_e2e(r, w, torch, stream, world, samples, barrier, maxrank):

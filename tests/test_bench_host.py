@@ -61,6 +61,27 @@ def test_profiled_traffic_reads_marker_and_detects_stale_sources(tmp_path, monke
     assert bench.profiled_traffic("my_kernel<2, 0>", "wl") is None
 
 
+def test_profiled_tensor_reads_its_own_marker(tmp_path, monkeypatch):
+    """A summary may hold several markers: the tensor-pipe lookup takes the `tensor`
+    marker of the kernel and workload, beside the traffic one, and goes stale with the
+    sources like it."""
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernel v1")
+    digest = hashlib.sha256(b"kernel v1").hexdigest()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "tc_kernel_wl.md").write_text(
+        f"# summary\n<!-- traffic kernel=tc_kernel workload=wl bytes_per_launch=2e+09 "
+        f"sources=k.cu sha256={digest} -->\n<!-- tensor kernel=tc_kernel workload=wl "
+        f"active_pct=6.86 sources=k.cu sha256={digest} -->\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("tc_kernel", "wl") == 2e9
+    assert bench.profiled_tensor("tc_kernel", "wl") == 6.86
+    assert bench.profiled_tensor("tc_kernel", "other") is None
+    src.write_bytes(b"kernel v2")
+    assert bench.profiled_tensor("tc_kernel", "wl") is None
+
+
 def test_tuner_choice_is_deterministic():
     """The tuner's pick depends only on the measurements: the fastest pair, ties broken
     toward the shorter span and then fewer chains, whatever the order of the candidates."""
